@@ -1,0 +1,635 @@
+/*
+ * ORACLE -- test infrastructure only.  A plain, slow, single-threaded FP64 restatement of
+ * the Kalman-filter track fit and combinatorial track building described in Cerati et al.,
+ * "Kalman filter tracking on parallel architectures" (arXiv:1702.06359).  Only the test
+ * suite, the smoke check and the benchmark's CPU-baseline leg load this file; the product
+ * path never does.  It shares no code, header or table with the CUDA library.
+ *
+ * Everything is written in the textbook form with full 6x6 / 2x6 / 2x2 matrices so that it
+ * can be checked against the equations by eye; no sparsity is exploited.
+ *
+ * State p = (x, y, z, q/pT, phi, theta): global Cartesian position plus polar momentum, the
+ * hybrid coordinates of Sec. 2.2.  Units cm, GeV, T, rad.
+ *
+ * Where the paper is silent, the readings below are used (each is listed with its reason in
+ * the design notes of the repository):
+ *   - propagation to a barrel cylinder is the exact helix/cylinder intersection (Sec. 2.2,
+ *     ideal barrel, uniform Bz), one step, smallest positive transverse path;
+ *   - the measurement is made on the plane tangent to the cylinder at the hit (Sec. 2.2):
+ *     u = rphi offset along the tangent, v = z offset;
+ *   - thin-layer multiple scattering with the Highland width, added after the update of a
+ *     layer, except on the outermost layer;
+ *   - building: window = chi2-cut bounding box of S, one hole branch per parent that finds
+ *     no compatible hit, branches ranked by (nHits desc, chi2 asc, parent rank asc, hit id
+ *     asc), best N kept (Sec. 2: "branching to explore multiple candidate tracks per seed");
+ *     a hit is compatible if it lies on the same half of the cylinder as the prediction and
+ *     its chi2 is below the cut.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "tkf_oracle.h"
+
+#define NPAR 6
+static const double ORC_KB = 0.00299792458; /* GeV / (T cm) */
+static const double ORC_PI = 3.14159265358979323846;
+
+/* ------------------------------------------------------------------ small matrix helpers */
+
+static void mat_mul(int n, int m, int k, const double *A, const double *B, double *C)
+{ /* C[n x k] = A[n x m] B[m x k], all row-major */
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < k; ++j) {
+            double s = 0.0;
+            for (int t = 0; t < m; ++t) s += A[i * m + t] * B[t * k + j];
+            C[i * k + j] = s;
+        }
+}
+
+static void mat_transpose(int n, int m, const double *A, double *At)
+{ /* At[m x n] = A[n x m]^T */
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < m; ++j) At[j * n + i] = A[i * m + j];
+}
+
+/* C = A P A^T for square 6x6 A, P */
+static void sandwich6(const double *A, const double *P, double *C)
+{
+    double AP[36], At[36];
+    mat_mul(6, 6, 6, A, P, AP);
+    mat_transpose(6, 6, A, At);
+    mat_mul(6, 6, 6, AP, At, C);
+    for (int i = 0; i < 6; ++i) /* the product is symmetric; remove rounding asymmetry */
+        for (int j = 0; j < i; ++j) {
+            const double m = 0.5 * (C[i * 6 + j] + C[j * 6 + i]);
+            C[i * 6 + j] = m; C[j * 6 + i] = m;
+        }
+}
+
+static double wrap_phi(double phi)
+{ /* into [-pi, pi) */
+    while (phi >= ORC_PI) phi -= 2.0 * ORC_PI;
+    while (phi < -ORC_PI) phi += 2.0 * ORC_PI;
+    return phi;
+}
+
+/* ------------------------------------------------------------------ propagation (Sec. 2.2) */
+
+/*
+ * Exact propagation of a helix in a uniform field Bz to the cylinder r = R.
+ * Helix with curvature kappa = -K_B Bz q/pT (signed d phi / d s_T):
+ *   x(s) = x0 + (sin(phi0 + kappa s) - sin phi0) / kappa
+ *   y(s) = y0 - (cos(phi0 + kappa s) - cos phi0) / kappa
+ *   z(s) = z0 + s cot(theta),  phi(s) = phi0 + kappa s.
+ * The crossing is found by intersecting the circle |x| = R with the track circle (centre c,
+ * radius 1/|kappa|) and taking the smallest positive turning angle in the direction of motion.
+ * The transport Jacobian J = dp_out/dp_in is the analytic derivative at fixed s plus
+ * (dp_out/ds)(ds/dp_in), with ds/dp_in = -(dr/dp_in)/(dr/ds) from the constraint r(s, p_in) = R.
+ */
+int orc_propagate(const orc_geom *g, const double pin[6], double R, double pout[6], double J[36])
+{
+    const double x0 = pin[0], y0 = pin[1], z0 = pin[2], w = pin[3], phi0 = pin[4], th = pin[5];
+    const double kappa = -ORC_KB * g->bz * w;
+    const double cot_th = cos(th) / sin(th);
+    double s;
+
+    if (fabs(kappa) < 1e-12) { /* straight line: |p0 + s u|^2 = R^2 */
+        const double ux = cos(phi0), uy = sin(phi0);
+        const double b = x0 * ux + y0 * uy;
+        const double disc = b * b - (x0 * x0 + y0 * y0 - R * R);
+        if (disc < 0.0) return ORC_ERR_NOREACH;
+        s = -b + sqrt(disc);
+        if (!(s > 0.0)) return ORC_ERR_NOREACH;
+    } else {
+        const double rho = 1.0 / fabs(kappa);
+        const double cx = x0 - sin(phi0) / kappa, cy = y0 + cos(phi0) / kappa;
+        const double d = sqrt(cx * cx + cy * cy);
+        if (d == 0.0) return ORC_ERR_NOREACH;
+        const double a = (R * R - rho * rho + d * d) / (2.0 * d);
+        const double h2 = R * R - a * a;
+        if (h2 < 0.0) return ORC_ERR_NOREACH;
+        const double h = sqrt(h2);
+        const double ex = cx / d, ey = cy / d;
+        double best = -1.0;
+        for (int sign = -1; sign <= 1; sign += 2) {
+            const double px = a * ex - sign * h * ey, py = a * ey + sign * h * ex;
+            const double v0x = x0 - cx, v0y = y0 - cy, v1x = px - cx, v1y = py - cy;
+            double ang = atan2(v0x * v1y - v0y * v1x, v0x * v1x + v0y * v1y); /* ccw, (-pi, pi] */
+            if (kappa < 0.0) ang = -ang;                                     /* direction of motion */
+            if (ang <= 0.0) ang += 2.0 * ORC_PI;                              /* into (0, 2 pi] */
+            const double st = ang * rho;
+            if (st > 0.0 && (best < 0.0 || st < best)) best = st;
+        }
+        if (best < 0.0) return ORC_ERR_NOREACH;
+        s = best;
+    }
+
+    double phi1, x1, y1;
+    if (fabs(kappa) < 1e-12) {
+        phi1 = phi0;
+        x1 = x0 + s * cos(phi0);
+        y1 = y0 + s * sin(phi0);
+    } else {
+        phi1 = phi0 + kappa * s;
+        x1 = x0 + (sin(phi1) - sin(phi0)) / kappa;
+        y1 = y0 - (cos(phi1) - cos(phi0)) / kappa;
+    }
+    const double z1 = z0 + s * cot_th;
+    pout[0] = x1; pout[1] = y1; pout[2] = z1; pout[3] = w; pout[4] = wrap_phi(phi1); pout[5] = th;
+
+    if (!J) return ORC_OK;
+
+    /* partial derivatives at fixed s: F[i][j] = d pout_i / d pin_j */
+    double F[36];
+    memset(F, 0, sizeof F);
+    for (int i = 0; i < 6; ++i) F[i * 6 + i] = 1.0;
+    const double dkdw = -ORC_KB * g->bz;
+    double dx_dk, dy_dk;
+    if (fabs(kappa) < 1e-12) {
+        dx_dk = -0.5 * s * s * sin(phi0);
+        dy_dk = 0.5 * s * s * cos(phi0);
+        F[0 * 6 + 4] = -s * sin(phi0);
+        F[1 * 6 + 4] = s * cos(phi0);
+    } else {
+        dx_dk = s * cos(phi1) / kappa - (sin(phi1) - sin(phi0)) / (kappa * kappa);
+        dy_dk = s * sin(phi1) / kappa + (cos(phi1) - cos(phi0)) / (kappa * kappa);
+        F[0 * 6 + 4] = (cos(phi1) - cos(phi0)) / kappa;
+        F[1 * 6 + 4] = (sin(phi1) - sin(phi0)) / kappa;
+    }
+    F[0 * 6 + 3] = dx_dk * dkdw;
+    F[1 * 6 + 3] = dy_dk * dkdw;
+    F[2 * 6 + 5] = -s / (sin(th) * sin(th));
+    F[4 * 6 + 3] = s * dkdw;
+
+    /* derivative along the path */
+    double dp_ds[6] = {cos(phi1), sin(phi1), cot_th, 0.0, kappa, 0.0};
+    /* constraint r^2 = x^2 + y^2 = R^2:  ds/dp_j = -(x dx/dp_j + y dy/dp_j) / (x dx/ds + y dy/ds) */
+    const double drds = x1 * dp_ds[0] + y1 * dp_ds[1];
+    if (drds == 0.0) return ORC_ERR_NOREACH;
+    double ds_dp[6];
+    for (int j = 0; j < 6; ++j) ds_dp[j] = -(x1 * F[0 * 6 + j] + y1 * F[1 * 6 + j]) / drds;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) J[i * 6 + j] = F[i * 6 + j] + dp_ds[i] * ds_dp[j];
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ multiple scattering */
+
+/*
+ * Thin-scatterer process noise at layer l (Highland width, unit charge, mass hypothesis m):
+ *   theta0 = 0.0136/(beta p) sqrt(t) (1 + 0.038 ln(t / beta^2)),  t = (x/X0) / |cos alpha|,
+ * alpha the angle between the direction and the cylinder normal.  Two independent kicks of
+ * width theta0 orthogonal to the direction change theta by d1 and phi by d2/sin(theta); with
+ * |p| fixed, q/pT changes by -(q/pT) cot(theta) d1.
+ */
+void orc_scatter(const orc_geom *g, int layer, const double p[6], double P[36])
+{
+    const double xt = g->x_over_x0[layer];
+    if (xt <= 0.0) return;
+    const double w = p[3], phi = p[4], th = p[5];
+    const double mom = 1.0 / (fabs(w) * sin(th));
+    const double beta = mom / sqrt(mom * mom + g->mass * g->mass);
+    const double r = sqrt(p[0] * p[0] + p[1] * p[1]);
+    const double d[3] = {sin(th) * cos(phi), sin(th) * sin(phi), cos(th)};
+    const double nrm[3] = {p[0] / r, p[1] / r, 0.0};
+    const double cos_a = fabs(d[0] * nrm[0] + d[1] * nrm[1] + d[2] * nrm[2]);
+    const double t = xt / cos_a;
+    const double th0 = 0.0136 / (beta * mom) * sqrt(t) * (1.0 + 0.038 * log(t / (beta * beta)));
+    const double v = th0 * th0;
+    const double cot = cos(th) / sin(th);
+    /* Jacobian of (w, phi, theta) w.r.t. the two kick angles (d1 along e_theta, d2 along e_phi) */
+    double G[6][2] = {{0, 0}, {0, 0}, {0, 0}, {-w * cot, 0}, {0, 1.0 / sin(th)}, {1.0, 0}};
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) P[i * 6 + j] += v * (G[i][0] * G[j][0] + G[i][1] * G[j][1]);
+}
+
+/* ------------------------------------------------------------------ Kalman update (Sec. 2.2) */
+
+/* Measurement model on the plane tangent to the cylinder at the hit: rows of H are the
+ * tangent direction (-sin phi_h, cos phi_h, 0) and the z axis. */
+static void meas_model(const double p[6], const orc_hit *h, double H[12], double r[2], double V[4])
+{
+    const double ph = atan2(h->y, h->x);
+    const double sh = sin(ph), ch = cos(ph);
+    memset(H, 0, 12 * sizeof(double));
+    H[0] = -sh; H[1] = ch; H[6 + 2] = 1.0;
+    r[0] = -sh * (h->x - p[0]) + ch * (h->y - p[1]);
+    r[1] = h->z - p[2];
+    V[0] = h->var_u; V[1] = 0.0; V[2] = 0.0; V[3] = h->var_v;
+}
+
+static int innovation(const double P[36], const double H[12], const double V[4], double S[4], double Si[4])
+{
+    double Ht[12], PHt[12];
+    mat_transpose(2, 6, H, Ht);
+    mat_mul(6, 6, 2, P, Ht, PHt);
+    mat_mul(2, 6, 2, H, PHt, S);
+    for (int i = 0; i < 4; ++i) S[i] += V[i];
+    const double det = S[0] * S[3] - S[1] * S[2];
+    if (!(det > 0.0)) return ORC_ERR_SINGULAR;
+    Si[0] = S[3] / det; Si[1] = -S[1] / det; Si[2] = -S[2] / det; Si[3] = S[0] / det;
+    return ORC_OK;
+}
+
+double orc_chi2(const double p[6], const double P[36], const orc_hit *h)
+{
+    double H[12], r[2], V[4], S[4], Si[4];
+    meas_model(p, h, H, r, V);
+    if (innovation(P, H, V, S, Si) != ORC_OK) return INFINITY;
+    return r[0] * (Si[0] * r[0] + Si[1] * r[1]) + r[1] * (Si[2] * r[0] + Si[3] * r[1]);
+}
+
+/*
+ * Kalman update with the Joseph-form covariance:
+ *   S = H P H^T + V,  K = P H^T S^-1,  p <- p + K r,
+ *   P <- (I - K H) P (I - K H)^T + K V K^T,  chi2 = r^T S^-1 r (predicted S).
+ */
+int orc_update(double p[6], double P[36], const orc_hit *h, double *chi2)
+{
+    double H[12], r[2], V[4], S[4], Si[4];
+    meas_model(p, h, H, r, V);
+    int st = innovation(P, H, V, S, Si);
+    if (st != ORC_OK) return st;
+    double Ht[12], PHt[12], K[12];
+    mat_transpose(2, 6, H, Ht);
+    mat_mul(6, 6, 2, P, Ht, PHt);
+    mat_mul(6, 2, 2, PHt, Si, K);
+    if (chi2) *chi2 = r[0] * (Si[0] * r[0] + Si[1] * r[1]) + r[1] * (Si[2] * r[0] + Si[3] * r[1]);
+    for (int i = 0; i < 6; ++i) p[i] += K[i * 2 + 0] * r[0] + K[i * 2 + 1] * r[1];
+    p[4] = wrap_phi(p[4]);
+
+    double KH[36], A[36], APAt[36], KV[12], Kt[12], KVKt[36];
+    mat_mul(6, 2, 6, K, H, KH);
+    for (int i = 0; i < 36; ++i) A[i] = -KH[i];
+    for (int i = 0; i < 6; ++i) A[i * 6 + i] += 1.0;
+    sandwich6(A, P, APAt);
+    mat_mul(6, 2, 2, K, V, KV);
+    mat_transpose(6, 2, K, Kt);
+    mat_mul(6, 2, 6, KV, Kt, KVKt);
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) P[i * 6 + j] = APAt[i * 6 + j] + KVKt[i * 6 + j];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < i; ++j) {
+            const double m = 0.5 * (P[i * 6 + j] + P[j * 6 + i]);
+            P[i * 6 + j] = m; P[j * 6 + i] = m;
+        }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ seed estimate */
+
+/*
+ * Initial state from three hits (the seeding stage of Sec. 2): the circle through the
+ * three (x, y) points gives the curvature and the charge sign, phi is the tangent at the
+ * first hit in the direction of motion, cot(theta) = (z3 - z1) / (transverse arc 1->3),
+ * and the position is the first hit.  Prior covariance is diagonal (g->prior_sigma).
+ */
+int orc_seed_estimate(const orc_geom *g, const orc_hit *h1, const orc_hit *h2, const orc_hit *h3,
+                      double p[6], double P[36])
+{
+    const double x1 = h1->x, y1 = h1->y, x2 = h2->x, y2 = h2->y, x3 = h3->x, y3 = h3->y;
+    const double D = 2.0 * (x1 * (y2 - y3) + x2 * (y3 - y1) + x3 * (y1 - y2));
+    double kappa, phi, s13;
+    if (D == 0.0) { /* collinear: straight line */
+        kappa = 0.0;
+        phi = atan2(y3 - y1, x3 - x1);
+        s13 = hypot(x3 - x1, y3 - y1);
+    } else {
+        const double n1 = x1 * x1 + y1 * y1, n2 = x2 * x2 + y2 * y2, n3 = x3 * x3 + y3 * y3;
+        const double cx = (n1 * (y2 - y3) + n2 * (y3 - y1) + n3 * (y1 - y2)) / D;
+        const double cy = (n1 * (x3 - x2) + n2 * (x1 - x3) + n3 * (x2 - x1)) / D;
+        const double rho = hypot(x1 - cx, y1 - cy);
+        const double turn = (x2 - x1) * (y3 - y2) - (y2 - y1) * (x3 - x2);
+        const int ccw = turn > 0.0;
+        kappa = (ccw ? 1.0 : -1.0) / rho;
+        const double r1x = x1 - cx, r1y = y1 - cy, r3x = x3 - cx, r3y = y3 - cy;
+        const double tx = ccw ? -r1y : r1y, ty = ccw ? r1x : -r1x;
+        phi = atan2(ty, tx);
+        double ang = atan2(r1x * r3y - r1y * r3x, r1x * r3x + r1y * r3y);
+        if (!ccw) ang = -ang;
+        if (ang <= 0.0) ang += 2.0 * ORC_PI;
+        s13 = ang * rho;
+    }
+    const double cot = (h3->z - h1->z) / s13;
+    p[0] = x1; p[1] = y1; p[2] = h1->z;
+    p[3] = -kappa / (ORC_KB * g->bz);
+    p[4] = wrap_phi(phi);
+    p[5] = atan2(1.0, cot);
+    memset(P, 0, 36 * sizeof(double));
+    for (int i = 0; i < 6; ++i) P[i * 6 + i] = g->prior_sigma[i] * g->prior_sigma[i];
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ fit (Sec. 2) */
+
+/*
+ * Kalman fit of one track over layers first..last with a known hit per layer (-1 = none):
+ * the state starts on layer `first` (no propagation there); each later layer is reached by
+ * exact propagation; the hit (if any) is added by the Kalman update; scattering noise of the
+ * layer follows unless it is the outermost layer of the detector.
+ */
+int orc_fit_track(const orc_geom *g, const double pin[6], const double Pin[36], const orc_hit *hits,
+                  const int *hit_of_layer, int first, int last, double pout[6], double Pout[36],
+                  double *chi2, int *nhits)
+{
+    double p[6], P[36], J[36], q[6], PJ[36];
+    memcpy(p, pin, sizeof p);
+    memcpy(P, Pin, sizeof P);
+    double c2 = 0.0;
+    int nh = 0;
+    for (int l = first; l <= last; ++l) {
+        if (l > first) {
+            int st = orc_propagate(g, p, g->radius[l], q, J);
+            if (st != ORC_OK) return st;
+            sandwich6(J, P, PJ);
+            memcpy(p, q, sizeof p);
+            memcpy(P, PJ, sizeof P);
+        }
+        const int hid = hit_of_layer[l];
+        if (hid >= 0) {
+            double dc2;
+            int st = orc_update(p, P, &hits[hid], &dc2);
+            if (st != ORC_OK) return st;
+            c2 += dc2;
+            nh += 1;
+        }
+        if (l < g->n_layers - 1) orc_scatter(g, l, p, P);
+    }
+    memcpy(pout, p, sizeof p);
+    memcpy(Pout, P, sizeof P);
+    if (chi2) *chi2 = c2;
+    if (nhits) *nhits = nh;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ hit index (binning) */
+
+int orc_eta_bin(const orc_geom *g, int layer, double z)
+{
+    const double eta = asinh(z / g->radius[layer]);
+    int b = (int)floor((eta - g->eta_min) / g->eta_bin_w);
+    if (b < 0) b = 0;
+    if (b >= g->n_eta_bins) b = g->n_eta_bins - 1;
+    return b;
+}
+
+int orc_phi_bin(const orc_geom *g, double phi)
+{
+    int b = (int)floor((phi + ORC_PI) / (2.0 * ORC_PI) * g->n_phi_bins);
+    if (b < 0) b = 0;
+    if (b >= g->n_phi_bins) b = g->n_phi_bins - 1;
+    return b;
+}
+
+static const orc_hit *g_sort_hits;
+static const int *g_sort_bin;
+static int cmp_hit_order(const void *a, const void *b)
+{
+    const int i = *(const int *)a, j = *(const int *)b;
+    const int li = g_sort_hits[i].layer, lj = g_sort_hits[j].layer;
+    if (li != lj) return li < lj ? -1 : 1;
+    if (g_sort_bin[i] != g_sort_bin[j]) return g_sort_bin[i] < g_sort_bin[j] ? -1 : 1;
+    return i < j ? -1 : (i > j);
+}
+
+/* Bins every hit of one event by (layer, eta bin, phi bin) and orders hit ids by
+ * (layer, eta bin, phi bin, id); bin_off[l * (nb + 1) + b] is the CSR offset of bin b of
+ * layer l into `order` (nb = n_eta_bins * n_phi_bins, bin = eta_bin * n_phi_bins + phi_bin). */
+int orc_hit_index(const orc_geom *g, int n, const orc_hit *hits, int *bin_of_hit, int *order, int *bin_off)
+{
+    const int nb = g->n_eta_bins * g->n_phi_bins;
+    for (int i = 0; i < n; ++i) {
+        const orc_hit *h = &hits[i];
+        if (h->layer < 0 || h->layer >= g->n_layers) return ORC_ERR_INVALID;
+        bin_of_hit[i] = orc_eta_bin(g, h->layer, h->z) * g->n_phi_bins + orc_phi_bin(g, atan2(h->y, h->x));
+        order[i] = i;
+    }
+    g_sort_hits = hits;
+    g_sort_bin = bin_of_hit;
+    qsort(order, (size_t)n, sizeof(int), cmp_hit_order);
+    for (int k = 0; k < g->n_layers * (nb + 1); ++k) bin_off[k] = 0;
+    for (int i = 0; i < n; ++i) bin_off[hits[i].layer * (nb + 1) + bin_of_hit[i] + 1] += 1;
+    int base = 0; /* layers follow one another in `order` */
+    for (int l = 0; l < g->n_layers; ++l) {
+        int *off = bin_off + l * (nb + 1);
+        off[0] = base;
+        for (int b = 0; b < nb; ++b) off[b + 1] += off[b];
+        base = off[nb];
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ building (Sec. 2, 3.2) */
+
+typedef struct {
+    double p[6], P[36], chi2;
+    int nhits, parent, hit; /* hit = event hit id added on this layer, -1 for a hole */
+    int hits[ORC_MAX_LAYERS];
+} orc_cand;
+
+static int cmp_branch(const void *a, const void *b)
+{
+    const orc_cand *x = (const orc_cand *)a, *y = (const orc_cand *)b;
+    if (x->nhits != y->nhits) return x->nhits > y->nhits ? -1 : 1;
+    if (x->chi2 != y->chi2) return x->chi2 < y->chi2 ? -1 : 1;
+    if (x->parent != y->parent) return x->parent < y->parent ? -1 : 1;
+    const unsigned hx = (unsigned)x->hit, hy = (unsigned)y->hit; /* a hole (-1) sorts last */
+    return hx < hy ? -1 : (hx > hy);
+}
+
+static void window_bins(const orc_geom *g, int layer, const double p[6], const double P[36],
+                        double var_u, double var_v, int *eb0, int *eb1, int *pb0, int *pb1)
+{
+    /* chi2-cut bounding box of the innovation covariance at phi_h = phi of the prediction */
+    const double R = g->radius[layer];
+    const double ph = atan2(p[1], p[0]);
+    orc_hit probe = {R * cos(ph), R * sin(ph), p[2], var_u, var_v, layer};
+    double H[12], r[2], V[4], S[4], Si[4];
+    meas_model(p, &probe, H, r, V);
+    innovation(P, H, V, S, Si);
+    const double U = sqrt(g->chi2_cut * S[0]) * (1.0 + g->window_margin);
+    const double W = sqrt(g->chi2_cut * S[3]) * (1.0 + g->window_margin);
+    const double dphi = asin(U / R < 1.0 ? U / R : 1.0);
+    *eb0 = orc_eta_bin(g, layer, p[2] - W);
+    *eb1 = orc_eta_bin(g, layer, p[2] + W);
+    const double f0 = (ph - dphi + ORC_PI) / (2.0 * ORC_PI) * g->n_phi_bins;
+    const double f1 = (ph + dphi + ORC_PI) / (2.0 * ORC_PI) * g->n_phi_bins;
+    *pb0 = (int)floor(f0);
+    *pb1 = (int)floor(f1);
+    if (*pb1 - *pb0 + 1 >= g->n_phi_bins) { *pb0 = 0; *pb1 = g->n_phi_bins - 1; }
+}
+
+static int near(double a, double b, double tol)
+{
+    const double m = fabs(a) > fabs(b) ? fabs(a) : fabs(b);
+    return fabs(a - b) <= tol * (m > 1.0 ? m : 1.0);
+}
+
+/*
+ * Combinatorial building of one seed through layers first..n_layers-1.
+ * For each layer and each candidate in rank order: propagate; collect every compatible hit
+ * of the window (or of the whole layer when brute_force) as a branch; a candidate with no
+ * compatible hit yields one hole branch.  All branches of the seed are ranked and the best
+ * n_cand kept (n_cand <= 0: keep all); hit branches get the Kalman update, then every kept
+ * branch gets the scattering noise of the layer (except on the outermost layer).
+ */
+static int build_seed(const orc_geom *g, const orc_event *ev, const double sp[6], const double sP[36],
+                      double schi2, int snhits, const int *shits, orc_seed_result *res, orc_stats *stats)
+{
+    int cap = 16, n = 1;
+    orc_cand *C = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)cap);
+    memcpy(C[0].p, sp, sizeof C[0].p);
+    memcpy(C[0].P, sP, sizeof C[0].P);
+    C[0].chi2 = schi2;
+    C[0].nhits = snhits;
+    C[0].parent = 0;
+    C[0].hit = -1;
+    for (int l = 0; l < ORC_MAX_LAYERS; ++l) C[0].hits[l] = l < g->n_layers ? shits[l] : -1;
+    res->fragile_layer = g->n_layers;
+    const double tol = g->tie_tol;
+
+    for (int l = g->first_build_layer; l < g->n_layers; ++l) {
+        int nb = 0, bcap = 16;
+        orc_cand *B = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)bcap);
+        const double R = g->radius[l];
+        for (int c = 0; c < n; ++c) {
+            double q[6], J[36], Q[36];
+            if (stats) stats->n_prop += 1;
+            if (orc_propagate(g, C[c].p, R, q, J) != ORC_OK) continue; /* dropped */
+            sandwich6(J, C[c].P, Q);
+            int found = 0;
+            int eb0, eb1, pb0, pb1;
+            window_bins(g, l, q, Q, ev->var_u_max[l], ev->var_v_max[l], &eb0, &eb1, &pb0, &pb1);
+            const int nbin = g->n_eta_bins * g->n_phi_bins;
+            const int *off = ev->bin_off + l * (nbin + 1);
+            int k_lo, k_hi, e_lo, e_hi;
+            if (g->brute_force) { e_lo = 0; e_hi = 0; k_lo = 0; k_hi = 0; }
+            else { e_lo = eb0; e_hi = eb1; k_lo = pb0; k_hi = pb1; }
+            for (int e = e_lo; e <= e_hi; ++e)
+                for (int k = k_lo; k <= k_hi; ++k) {
+                    int i0, i1;
+                    if (g->brute_force) { i0 = off[0]; i1 = off[nbin]; }
+                    else {
+                        const int pb = ((k % g->n_phi_bins) + g->n_phi_bins) % g->n_phi_bins;
+                        i0 = off[e * g->n_phi_bins + pb];
+                        i1 = off[e * g->n_phi_bins + pb + 1];
+                    }
+                    for (int t = i0; t < i1; ++t) {
+                        const int hid = ev->order[t];
+                        const orc_hit *h = &ev->hits[hid];
+                        if (stats) stats->n_hits_examined += 1;
+                        if (q[0] * h->x + q[1] * h->y <= 0.0) continue; /* far half of the cylinder */
+                        const double c2 = orc_chi2(q, Q, h);
+                        if (near(c2, g->chi2_cut, tol) && res->fragile_layer > l) res->fragile_layer = l;
+                        if (!(c2 < g->chi2_cut)) continue;
+                        if (nb == bcap) { bcap *= 2; B = (orc_cand *)realloc(B, sizeof(orc_cand) * (size_t)bcap); }
+                        orc_cand *b = &B[nb++];
+                        memcpy(b->p, q, sizeof q);
+                        memcpy(b->P, Q, sizeof Q);
+                        b->chi2 = C[c].chi2 + c2;
+                        b->nhits = C[c].nhits + 1;
+                        b->parent = c;
+                        b->hit = hid;
+                        memcpy(b->hits, C[c].hits, sizeof b->hits);
+                        b->hits[l] = hid;
+                        found = 1;
+                    }
+                }
+            if (!found) {
+                if (nb == bcap) { bcap *= 2; B = (orc_cand *)realloc(B, sizeof(orc_cand) * (size_t)bcap); }
+                orc_cand *b = &B[nb++];
+                memcpy(b->p, q, sizeof q);
+                memcpy(b->P, Q, sizeof Q);
+                b->chi2 = C[c].chi2;
+                b->nhits = C[c].nhits;
+                b->parent = c;
+                b->hit = -1;
+                memcpy(b->hits, C[c].hits, sizeof b->hits);
+                b->hits[l] = -1;
+            }
+        }
+        qsort(B, (size_t)nb, sizeof(orc_cand), cmp_branch);
+        const int keep = (g->n_cand > 0 && nb > g->n_cand) ? g->n_cand : nb;
+        const int look = keep < nb ? keep + 1 : keep;
+        for (int i = 0; i + 1 < look; ++i)
+            if (B[i].nhits == B[i + 1].nhits && near(B[i].chi2, B[i + 1].chi2, tol) && res->fragile_layer > l)
+                res->fragile_layer = l;
+        for (int i = 0; i < keep; ++i) {
+            if (B[i].hit >= 0) {
+                double dc2;
+                if (stats) stats->n_updates += 1;
+                orc_update(B[i].p, B[i].P, &ev->hits[B[i].hit], &dc2);
+            }
+            if (l < g->n_layers - 1) orc_scatter(g, l, B[i].p, B[i].P);
+        }
+        if (stats) stats->n_kept += keep;
+        free(C);
+        C = B;
+        n = keep;
+        cap = bcap;
+        if (n == 0) break;
+    }
+    (void)cap;
+    res->n_cand = n;
+    const int nout = n < res->cap ? n : res->cap;
+    for (int i = 0; i < nout; ++i) {
+        memcpy(res->par + 6 * i, C[i].p, 6 * sizeof(double));
+        memcpy(res->cov + 36 * i, C[i].P, 36 * sizeof(double));
+        res->chi2[i] = C[i].chi2;
+        res->nhits[i] = C[i].nhits;
+        for (int l = 0; l < g->n_layers; ++l) res->hits[i * g->n_layers + l] = C[i].hits[l];
+    }
+    free(C);
+    return ORC_OK;
+}
+
+int orc_build_seed(const orc_geom *g, const orc_event *ev, const double sp[6], const double sP[36],
+                   double schi2, int snhits, const int *shits, orc_seed_result *res, orc_stats *stats)
+{
+    if (g->n_layers > ORC_MAX_LAYERS || g->first_build_layer < 1) return ORC_ERR_INVALID;
+    return build_seed(g, ev, sp, sP, schi2, snhits, shits, res, stats);
+}
+
+/* ------------------------------------------------------------------ batch helpers */
+
+int orc_seed_batch(const orc_geom *g, const orc_hit *hits, int n, const int *seed_hits, double *par, double *cov)
+{
+    for (int i = 0; i < n; ++i) {
+        const int *s = seed_hits + 3 * i;
+        int st = orc_seed_estimate(g, &hits[s[0]], &hits[s[1]], &hits[s[2]], par + 6 * i, cov + 36 * i);
+        if (st != ORC_OK) return st;
+    }
+    return ORC_OK;
+}
+
+int orc_fit_batch(const orc_geom *g, const orc_hit *hits, int n, const double *par_in, const double *cov_in,
+                  const int *hit_ids, int first, int last, double *par_out, double *cov_out, double *chi2,
+                  int *nhits, int *status)
+{
+    for (int i = 0; i < n; ++i)
+        status[i] = orc_fit_track(g, par_in + 6 * i, cov_in + 36 * i, hits, hit_ids + g->n_layers * i, first,
+                                  last, par_out + 6 * i, cov_out + 36 * i, chi2 + i, nhits + i);
+    return ORC_OK;
+}
+
+int orc_build_batch(const orc_geom *g, const orc_event *ev, int n, const double *sp, const double *sP,
+                    const double *schi2, const int *snhits, const int *shits, int cap, int *n_cand,
+                    double *par, double *cov, double *chi2, int *nhits, int *hits, int *fragile,
+                    orc_stats *stats)
+{
+    for (int i = 0; i < n; ++i) {
+        orc_seed_result r;
+        r.cap = cap;
+        r.par = par + (size_t)i * cap * 6;
+        r.cov = cov + (size_t)i * cap * 36;
+        r.chi2 = chi2 + (size_t)i * cap;
+        r.nhits = nhits + (size_t)i * cap;
+        r.hits = hits + (size_t)i * cap * g->n_layers;
+        int st = orc_build_seed(g, ev, sp + 6 * i, sP + 36 * i, schi2[i], snhits[i], shits + g->n_layers * i, &r, stats);
+        if (st != ORC_OK) return st;
+        n_cand[i] = r.n_cand;
+        fragile[i] = r.fragile_layer;
+    }
+    return ORC_OK;
+}

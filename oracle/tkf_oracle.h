@@ -1,0 +1,83 @@
+/*
+ * ORACLE -- test infrastructure only (see tkf_oracle.c).  Plain FP64 C; no code shared with
+ * the CUDA library.
+ */
+#ifndef TKF_ORACLE_H
+#define TKF_ORACLE_H
+
+#define ORC_MAX_LAYERS 16
+
+enum { ORC_OK = 0, ORC_ERR_NOREACH = 1, ORC_ERR_SINGULAR = 2, ORC_ERR_INVALID = 3 };
+
+typedef struct {
+    int n_layers;
+    double radius[ORC_MAX_LAYERS];
+    double bz;
+    double x_over_x0[ORC_MAX_LAYERS];
+    double mass;
+    double prior_sigma[6];
+    double eta_min, eta_bin_w;
+    int n_eta_bins, n_phi_bins;
+    double chi2_cut;
+    double window_margin;
+    double tie_tol;        /* relative closeness that marks a ranking or cut decision fragile */
+    int n_cand;            /* candidates kept per seed; <= 0 keeps every branch */
+    int brute_force;       /* 1: examine every hit of the layer instead of the binned window */
+    int first_build_layer; /* 0-based layer where building starts (3 = fourth layer) */
+} orc_geom;
+
+typedef struct {
+    double x, y, z, var_u, var_v;
+    int layer;
+} orc_hit;
+
+typedef struct {
+    int n_hits;
+    const orc_hit *hits;   /* event-local ids 0..n_hits-1 */
+    const int *order;      /* hit ids sorted by (layer, bin, id) */
+    const int *bin_off;    /* [n_layers][n_bins + 1] CSR offsets into order */
+    double var_u_max[ORC_MAX_LAYERS], var_v_max[ORC_MAX_LAYERS];
+} orc_event;
+
+typedef struct {
+    int cap;        /* candidates the output arrays can hold */
+    int n_cand;     /* candidates at the end (may exceed cap when n_cand <= 0) */
+    int fragile_layer;
+    double *par;    /* [cap][6] */
+    double *cov;    /* [cap][36] */
+    double *chi2;   /* [cap] */
+    int *nhits;     /* [cap] */
+    int *hits;      /* [cap][n_layers] */
+} orc_seed_result;
+
+typedef struct {
+    long long n_prop, n_hits_examined, n_updates, n_kept;
+} orc_stats;
+
+int orc_propagate(const orc_geom *g, const double pin[6], double R, double pout[6], double J[36]);
+void orc_scatter(const orc_geom *g, int layer, const double p[6], double P[36]);
+double orc_chi2(const double p[6], const double P[36], const orc_hit *h);
+int orc_update(double p[6], double P[36], const orc_hit *h, double *chi2);
+int orc_seed_estimate(const orc_geom *g, const orc_hit *h1, const orc_hit *h2, const orc_hit *h3,
+                      double p[6], double P[36]);
+int orc_fit_track(const orc_geom *g, const double pin[6], const double Pin[36], const orc_hit *hits,
+                  const int *hit_of_layer, int first, int last, double pout[6], double Pout[36],
+                  double *chi2, int *nhits);
+int orc_eta_bin(const orc_geom *g, int layer, double z);
+int orc_phi_bin(const orc_geom *g, double phi);
+int orc_hit_index(const orc_geom *g, int n, const orc_hit *hits, int *bin_of_hit, int *order, int *bin_off);
+int orc_build_seed(const orc_geom *g, const orc_event *ev, const double sp[6], const double sP[36],
+                   double schi2, int snhits, const int *shits, orc_seed_result *res, orc_stats *stats);
+
+/* batch helpers (plain loops over the single-object functions above) */
+int orc_seed_batch(const orc_geom *g, const orc_hit *hits, int n, const int *seed_hits /*[n][3]*/,
+                   double *par /*[n][6]*/, double *cov /*[n][36]*/);
+int orc_fit_batch(const orc_geom *g, const orc_hit *hits, int n, const double *par_in, const double *cov_in,
+                  const int *hit_ids /*[n][n_layers]*/, int first, int last, double *par_out, double *cov_out,
+                  double *chi2, int *nhits, int *status);
+int orc_build_batch(const orc_geom *g, const orc_event *ev, int n, const double *sp, const double *sP,
+                    const double *schi2, const int *snhits, const int *shits /*[n][n_layers]*/, int cap,
+                    int *n_cand, double *par, double *cov, double *chi2, int *nhits, int *hits,
+                    int *fragile, orc_stats *stats);
+
+#endif

@@ -1,0 +1,269 @@
+"""Seeded synthetic barrel events: the toy test scenario of the paper's Sec. 2.2.
+
+A particle gun (flat pT, flat eta, flat phi, random charge, Gaussian vertex) is simulated
+through an ideal barrel of thin cylinders in a uniform solenoid field Bz.  At each cylinder
+the exact helix crossing is found, a hit is made by Gaussian smearing along the cylinder
+(r-phi and z), and the direction is then deflected by a thin-scatterer multiple-scattering
+kick (two Gaussian angles of Highland width, |p| conserved).  Uniform random noise hits are
+added per layer.  The paper's own toy had no material; the thin scatterers follow the
+build's workload definition and can be switched off.
+
+This is an input producer, not an implementation of the method: it finds helix/cylinder
+crossings by Newton iteration on the exact helix (the reconstruction side uses other
+algorithms), and it draws every random number from Philox4x32-10 keyed by
+(run seed, event) with counter (object, stream, block, kind), so results are identical on
+every machine and any event can be regenerated alone.
+
+Units: cm, GeV, T, rad.  Track state convention: (x, y, z, q/pT, phi, theta) with phi the
+azimuth and theta the polar angle of the momentum.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .philox import normals, uniforms
+
+K_B = 0.00299792458  # GeV / (T cm): curvature constant, 1/rho = K_B * Bz / pT
+
+
+@dataclass(frozen=True)
+class Detector:
+    """Ideal barrel: n thin cylinders at radius[l], uniform Bz, thickness x/X0 per layer."""
+
+    radii: tuple = tuple(4.0 * (l + 1) for l in range(10))
+    bz: float = 3.8
+    x_over_x0: tuple = tuple(0.03 for _ in range(10))
+    mass: float = 0.13957  # scattering mass hypothesis (charged pion)
+    sigma_rphi: float = 0.01
+    sigma_z: float = 0.1
+
+    @property
+    def n_layers(self) -> int:
+        return len(self.radii)
+
+
+@dataclass
+class EventSpec:
+    """What to generate.  `n_tracks` and `noise_frac` are scalars or per-event arrays."""
+
+    seed: int = 1
+    n_events: int = 1
+    n_tracks: object = 1000
+    pt_min: float = 0.5
+    pt_max: float = 10.0
+    eta_max: float = 1.0
+    noise_frac: object = 0.0
+    vertex_sigma: tuple = (0.01, 0.01, 1.0)
+    scatter: bool = True
+    smear: bool = True
+    shuffle_hits: bool = True
+    keep_f64: bool = False  # also keep the unrounded FP64 hit positions in extras["xyz64"]
+
+
+@dataclass
+class EventBatch:
+    """Hits and truth of several events, concatenated event by event.
+
+    Hits of event e occupy [hit_off[e], hit_off[e+1]); within an event they are ordered by
+    layer and, inside a layer, in a seeded random order.  Tracks of event e occupy
+    [trk_off[e], trk_off[e+1]).  `trk_hits[t, l]` is the global index of track t's hit on
+    layer l.  `truth[t, l]` is the exact state where track t crosses layer l, before that
+    layer's scattering kick; `truth_after[t, l]` is the same state right after the kick.
+    """
+
+    detector: Detector
+    spec: EventSpec
+    hit_off: np.ndarray
+    trk_off: np.ndarray
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    var_u: np.ndarray
+    var_v: np.ndarray
+    layer: np.ndarray
+    mc: np.ndarray
+    trk_event: np.ndarray
+    trk_hits: np.ndarray
+    truth: np.ndarray
+    truth_after: np.ndarray
+    vertex_state: np.ndarray
+    extras: dict = field(default_factory=dict)
+
+    @property
+    def n_events(self) -> int:
+        return len(self.hit_off) - 1
+
+    @property
+    def n_hits(self) -> int:
+        return len(self.x)
+
+    @property
+    def n_tracks(self) -> int:
+        return len(self.trk_event)
+
+
+# Philox stream ids (second counter word); documented so that both sides could regenerate.
+_KIN, _LAYER0, _NOISE0, _SHUF0, _EVT = 0, 1, 40, 80, 120
+
+
+def event_sizes(seed: int, n_events: int, median=3000.0, sigma_ln=0.8, lo=200, hi=20000,
+                noise_lo=0.2, noise_hi=0.5):
+    """Per-event track counts (lognormal, clipped) and noise fractions (uniform)."""
+    ev = np.arange(n_events, dtype=np.uint64)
+    key = (np.uint64(seed), np.uint64(0xFFFFFFFF))
+    g0, _ = normals(key, (ev, _EVT, 0, 2))
+    u0, _ = uniforms(key, (ev, _EVT, 1, 2))
+    n = np.clip(np.rint(median * np.exp(sigma_ln * g0)), lo, hi).astype(np.int64)
+    f = noise_lo + (noise_hi - noise_lo) * u0
+    return n, f
+
+
+def _helix_to_cylinder(x, y, z, w, phi, theta, radius, kb):
+    """Exact helix crossing of r = radius by Newton iteration on the transverse path s."""
+    kappa = -kb * w
+    cphi, sphi = np.cos(phi), np.sin(phi)
+    a = x * cphi + y * sphi
+    s = -a + np.sqrt(np.maximum(a * a + radius * radius - (x * x + y * y), 0.0))
+    for _ in range(60):
+        ang = phi + kappa * s
+        xs = x + (np.sin(ang) - sphi) / kappa
+        ys = y - (np.cos(ang) - cphi) / kappa
+        g = xs * xs + ys * ys - radius * radius
+        dg = 2.0 * (xs * np.cos(ang) + ys * np.sin(ang))
+        step = g / dg
+        s = s - step
+        if np.all(np.abs(step) < 1e-13 * (1.0 + np.abs(s))):
+            break
+    ang = phi + kappa * s
+    xs = x + (np.sin(ang) - sphi) / kappa
+    ys = y - (np.cos(ang) - cphi) / kappa
+    zs = z + s * np.cos(theta) / np.sin(theta)
+    if not np.all(np.abs(np.hypot(xs, ys) - radius) < 1e-9):
+        raise RuntimeError("helix/cylinder Newton iteration did not converge")
+    if not np.all(s > 0):
+        raise RuntimeError("a generated track does not move outward")
+    phi_new = np.arctan2(np.sin(ang), np.cos(ang))
+    return xs, ys, zs, phi_new
+
+
+def highland_theta0(p, mass, thickness):
+    """Highland width of the projected scattering angle for unit charge (PDG form)."""
+    beta = p / np.sqrt(p * p + mass * mass)
+    return 0.0136 / (beta * p) * np.sqrt(thickness) * (1.0 + 0.038 * np.log(thickness / (beta * beta)))
+
+
+def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
+    n_ev = spec.n_events
+    n_trk = np.broadcast_to(np.asarray(spec.n_tracks, dtype=np.int64), (n_ev,)).copy()
+    noise_frac = np.broadcast_to(np.asarray(spec.noise_frac, dtype=np.float64), (n_ev,)).copy()
+    L = det.n_layers
+    kb = K_B * det.bz
+
+    trk_off = np.zeros(n_ev + 1, dtype=np.int64)
+    trk_off[1:] = np.cumsum(n_trk)
+    T = int(trk_off[-1])
+    trk_event = np.repeat(np.arange(n_ev, dtype=np.int64), n_trk)
+    trk_local = np.arange(T, dtype=np.int64) - trk_off[trk_event]
+    key = (np.uint64(spec.seed), trk_event.astype(np.uint64))
+    tl = trk_local.astype(np.uint64)
+
+    # --- kinematics at the vertex
+    u_pt, u_eta = uniforms(key, (tl, _KIN, 0, 0))
+    u_phi, u_q = uniforms(key, (tl, _KIN, 1, 0))
+    gvx, gvy = normals(key, (tl, _KIN, 2, 0))
+    gvz, _ = normals(key, (tl, _KIN, 3, 0))
+    pt = spec.pt_min + (spec.pt_max - spec.pt_min) * u_pt
+    eta = -spec.eta_max + 2.0 * spec.eta_max * u_eta
+    theta = 2.0 * np.arctan(np.exp(-eta))
+    phi = -np.pi + 2.0 * np.pi * u_phi
+    q = np.where(u_q < 0.5, 1.0, -1.0)
+    x = spec.vertex_sigma[0] * gvx
+    y = spec.vertex_sigma[1] * gvy
+    z = spec.vertex_sigma[2] * gvz
+    w = q / pt
+    vertex_state = np.stack([x, y, z, w, phi, theta], axis=1)
+
+    truth = np.zeros((T, L, 6))
+    truth_after = np.zeros((T, L, 6))
+    sig_hit = np.zeros((T, L, 3))  # x, y, z of the signal hit
+    for l in range(L):
+        R = det.radii[l]
+        x, y, z, phi = _helix_to_cylinder(x, y, z, w, phi, theta, R, kb)
+        truth[:, l] = np.stack([x, y, z, w, phi, theta], axis=1)
+        g_rphi, g_z = normals(key, (tl, _LAYER0 + l, 0, 0))
+        phi_pos = np.arctan2(y, x)
+        if spec.smear:
+            phi_h = phi_pos + det.sigma_rphi * g_rphi / R
+            z_h = z + det.sigma_z * g_z
+        else:
+            phi_h, z_h = phi_pos, z.copy()
+        sig_hit[:, l] = np.stack([R * np.cos(phi_h), R * np.sin(phi_h), z_h], axis=1)
+        if spec.scatter and det.x_over_x0[l] > 0.0:
+            a1, a2 = normals(key, (tl, _LAYER0 + l, 1, 0))
+            p = 1.0 / (np.abs(w) * np.sin(theta))
+            d = np.stack([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)], axis=1)
+            radial = np.stack([np.cos(phi_pos), np.sin(phi_pos), np.zeros_like(phi_pos)], axis=1)
+            cos_inc = np.abs(np.sum(d * radial, axis=1))
+            th0 = highland_theta0(p, det.mass, det.x_over_x0[l] / cos_inc)
+            e_th = np.stack([np.cos(theta) * np.cos(phi), np.cos(theta) * np.sin(phi), -np.sin(theta)], axis=1)
+            e_ph = np.stack([-np.sin(phi), np.cos(phi), np.zeros_like(phi)], axis=1)
+            dn = d + (th0 * a1)[:, None] * e_th + (th0 * a2)[:, None] * e_ph
+            dn /= np.linalg.norm(dn, axis=1)[:, None]
+            theta = np.arccos(np.clip(dn[:, 2], -1.0, 1.0))
+            phi = np.arctan2(dn[:, 1], dn[:, 0])
+            w = q / (p * np.sin(theta))
+        truth_after[:, l] = np.stack([x, y, z, w, phi, theta], axis=1)
+
+    # --- assemble hits event by event: layer-major, signal then noise, then shuffled
+    xs, ys, zs, lays, mcs = [], [], [], [], []
+    hit_off = np.zeros(n_ev + 1, dtype=np.int64)
+    trk_hits = np.full((T, L), -1, dtype=np.int64)
+    for e in range(n_ev):
+        t0, t1 = int(trk_off[e]), int(trk_off[e + 1])
+        nt = t1 - t0
+        base = int(hit_off[e])
+        ekey = (np.uint64(spec.seed), np.uint64(e))
+        for l in range(L):
+            R = det.radii[l]
+            n_noise = int(np.rint(noise_frac[e] * nt))
+            nid = np.arange(n_noise, dtype=np.uint64)
+            u_a, u_b = uniforms(ekey, (nid, _NOISE0 + l, 0, 1))
+            zl = R * np.sinh(spec.eta_max) + 3.0 * spec.vertex_sigma[2]
+            nphi = -np.pi + 2.0 * np.pi * u_a
+            hx = np.concatenate([sig_hit[t0:t1, l, 0], R * np.cos(nphi)])
+            hy = np.concatenate([sig_hit[t0:t1, l, 1], R * np.sin(nphi)])
+            hz = np.concatenate([sig_hit[t0:t1, l, 2], -zl + 2.0 * zl * u_b])
+            mc = np.concatenate([np.arange(t0, t1, dtype=np.int64), np.full(n_noise, -1, dtype=np.int64)])
+            n_l = nt + n_noise
+            if spec.shuffle_hits:
+                h_idx = np.arange(n_l, dtype=np.uint64)
+                k0, _ = uniforms(ekey, (h_idx, _SHUF0 + l, 0, 3))
+                perm = np.argsort(k0, kind="stable")
+            else:
+                perm = np.arange(n_l)
+            hx, hy, hz, mc = hx[perm], hy[perm], hz[perm], mc[perm]
+            pos = base + np.arange(n_l, dtype=np.int64)
+            sig = mc >= 0
+            trk_hits[mc[sig], l] = pos[sig]
+            xs.append(hx); ys.append(hy); zs.append(hz); mcs.append(mc)
+            lays.append(np.full(n_l, l, dtype=np.int32))
+            base += n_l
+        hit_off[e + 1] = base
+
+    n_hits = int(hit_off[-1])
+    extras = {}
+    if spec.keep_f64:
+        extras["xyz64"] = np.stack([np.concatenate(xs), np.concatenate(ys), np.concatenate(zs)], axis=1)
+    cat = lambda parts, dt: np.concatenate(parts).astype(dt) if parts else np.zeros(0, dt)
+    batch = EventBatch(
+        detector=det, spec=spec, hit_off=hit_off, trk_off=trk_off,
+        x=cat(xs, np.float32), y=cat(ys, np.float32), z=cat(zs, np.float32),
+        var_u=np.full(n_hits, det.sigma_rphi ** 2, dtype=np.float32),
+        var_v=np.full(n_hits, det.sigma_z ** 2, dtype=np.float32),
+        layer=cat(lays, np.int32), mc=cat(mcs, np.int64),
+        trk_event=trk_event, trk_hits=trk_hits, truth=truth, truth_after=truth_after,
+        vertex_state=vertex_state, extras=extras,
+    )
+    return batch

@@ -1,0 +1,210 @@
+"""Pins of the oracle's hit index and combinatorial track building (Sec. 2, Sec. 3.2).
+
+Building is checked against: a scan of every hit of the layer instead of the binned window
+(the window must lose nothing), an exhaustive enumeration of every compatible hit path
+(N unlimited), the greedy best-chi2 path (N = 1), and noise-free events (every seed must
+recover exactly its own hits).  The hit index is checked by the properties that define it
+and by hand-worked bins.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from _helpers import oracle_seeds, rotate_into_jet, small_event
+from synth import Detector
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "hit_bins.txt")
+
+
+def _index(g, b):
+    hits = O.hits_of(b)
+    return hits, O.hit_index(g, hits)
+
+
+def test_hit_index_properties(det):
+    b = small_event(det, 31, 2000, 0.3)
+    g = O.make_geom(det)
+    hits, idx = _index(g, b)
+    n = len(hits)
+    assert sorted(idx.order.tolist()) == list(range(n))
+    nb = g.n_eta_bins * g.n_phi_bins
+    flat_start = 0
+    for l in range(det.n_layers):
+        off = idx.bin_off[l]
+        assert off[0] == flat_start and np.all(np.diff(off) >= 0)
+        assert off[-1] - off[0] == np.sum(hits["layer"] == l)
+        for bb in range(nb):
+            members = idx.order[off[bb]:off[bb + 1]]
+            assert np.all(hits["layer"][members] == l)
+            assert np.all(idx.bin_of_hit[members] == bb)
+            assert np.all(np.diff(members) > 0)  # ascending id inside a bin
+        flat_start = off[-1]
+    # each hit's bin is the one whose eta and phi intervals contain it (clamped at the ends)
+    R = np.asarray(det.radii)[hits["layer"]]
+    eta = np.arcsinh(hits["z"] / R)
+    phi = np.arctan2(hits["y"], hits["x"])
+    eb, pb = idx.bin_of_hit // g.n_phi_bins, idx.bin_of_hit % g.n_phi_bins
+    lo_e = g.eta_min + eb * g.eta_bin_w
+    assert np.all((eta >= lo_e - 1e-12) | (eb == 0)) and np.all((eta < lo_e + g.eta_bin_w + 1e-12) | (eb == g.n_eta_bins - 1))
+    w = 2 * math.pi / g.n_phi_bins
+    lo_p = -math.pi + pb * w
+    assert np.all(phi >= lo_p - 1e-12) and np.all(phi < lo_p + w + 1e-12)
+
+
+def test_hit_bins_hand_worked(det):
+    """Bins of a few hand-placed hits, worked out by hand (tests/golden/hit_bins.txt)."""
+    g = O.make_geom(det)
+    for line in open(GOLD):
+        if line.startswith("#") or not line.strip():
+            continue
+        layer, x, y, z, eb, pb = line.split()
+        assert O.lib().orc_eta_bin(g, int(layer), float(z)) == int(eb), line
+        assert O.lib().orc_phi_bin(g, math.atan2(float(y), float(x))) == int(pb), line
+
+
+def _build(g, b, hits, idx, n_cand=None, brute=False, cap=None):
+    st = O.Settings(n_cand=g.n_cand if n_cand is None else n_cand, brute_force=brute)
+    gg = O.make_geom(b.detector, st)
+    sp, sP, sc2, snh, sh = oracle_seeds(gg, hits, b.trk_hits)
+    return O.build(gg, idx, sp, sP, sc2, snh, sh, cap=cap)
+
+
+@pytest.mark.parametrize("n_tracks,noise", [(40, 0.25), (400, 0.5)])
+def test_binned_window_equals_all_hit_scan(det, n_tracks, noise):
+    b = small_event(det, 32 + n_tracks, n_tracks, noise)
+    g = O.make_geom(det)
+    hits, idx = _index(g, b)
+    r1 = _build(g, b, hits, idx)
+    r2 = _build(g, b, hits, idx, brute=True)
+    assert np.array_equal(r1.n_cand, r2.n_cand)
+    assert np.array_equal(r1.hits, r2.hits)
+    assert np.array_equal(r1.chi2, r2.chi2)
+    assert np.array_equal(r1.par, r2.par)
+    assert r1.stats["n_hits_examined"] < r2.stats["n_hits_examined"] / 5
+
+
+# ----------------------------------------------------------------- reference searches written here
+
+def _prop(g, p, P, R):
+    st, q, J = O.propagate(g, p, R)
+    return st, q, J @ P @ J.T
+
+
+def _compatible(g, layer, q, Q, hits, ids):
+    out = []
+    for h in ids:
+        hh = hits[h]
+        if q[0] * hh["x"] + q[1] * hh["y"] <= 0.0:
+            continue
+        c2 = O.chi2(q, Q, O.make_hit(hh["x"], hh["y"], hh["z"], hh["var_u"], hh["var_v"], layer))
+        if c2 < g.chi2_cut:
+            out.append((h, c2))
+    return out
+
+
+def _advance(g, layer, q, Q, hits, h):
+    if h >= 0:
+        hh = hits[h]
+        st, q, Q, _ = O.update(q, Q, O.make_hit(hh["x"], hh["y"], hh["z"], hh["var_u"], hh["var_v"], layer))
+    if layer < g.n_layers - 1:
+        Q = O.scatter(g, layer, q, Q)
+    return q, Q
+
+
+def _exhaustive(g, hits, p, P, c2, nh, path, layer, out):
+    """Every path in which each hit has chi2 below the cut; a hole only where nothing passes."""
+    if layer == g.n_layers:
+        out.append((tuple(path), nh, c2))
+        return
+    st, q, Q = _prop(g, p, P, g.radius[layer])
+    if st:
+        return
+    ids = np.nonzero(hits["layer"] == layer)[0]
+    comp = _compatible(g, layer, q, Q, hits, ids)
+    if not comp:
+        q2, Q2 = _advance(g, layer, q, Q, hits, -1)
+        _exhaustive(g, hits, q2, Q2, c2, nh, path + [-1], layer + 1, out)
+    for h, dc2 in comp:
+        q2, Q2 = _advance(g, layer, q, Q, hits, h)
+        _exhaustive(g, hits, q2, Q2, c2 + dc2, nh + 1, path + [int(h)], layer + 1, out)
+
+
+def test_unlimited_candidates_equal_exhaustive_enumeration(det):
+    # a narrow jet and a looser cut make seeds branch; the logic under test is the same
+    b = rotate_into_jet(small_event(det, 33, 6, 0.5), width=0.003)
+    g = O.make_geom(det, O.Settings(n_cand=0, chi2_cut=300.0))
+    hits, idx = _index(g, b)
+    sp, sP, sc2, snh, sh = oracle_seeds(g, hits, b.trk_hits)
+    res = O.build(g, idx, sp, sP, sc2, snh, sh, cap=4096)
+    n_branching = 0
+    for s in range(b.n_tracks):
+        ref = []
+        _exhaustive(g, hits, sp[s], sP[s], sc2[s], snh[s], list(sh[s, :3]), 3, ref)
+        got = [(tuple(res.hits[s, i, :].tolist()), int(res.nhits[s, i]), float(res.chi2[s, i]))
+               for i in range(res.n_cand[s])]
+        assert res.n_cand[s] == len(ref)
+        n_branching += len(ref) > 1
+        ref_sorted = sorted(ref, key=lambda r: (-r[1], r[2]))
+        assert [r[0] for r in sorted(got, key=lambda r: (-r[1], r[2]))] == [tuple(int(v) for v in r[0]) for r in ref_sorted]
+        for a, r in zip(sorted(got, key=lambda r: (-r[1], r[2])), ref_sorted):
+            assert a[2] == pytest.approx(r[2], rel=1e-9, abs=1e-9)
+    assert n_branching >= 2, n_branching  # the jet makes several seeds branch
+
+
+def _greedy(g, hits, p, P, c2, nh, path):
+    for layer in range(3, g.n_layers):
+        st, q, Q = _prop(g, p, P, g.radius[layer])
+        assert st == 0
+        comp = _compatible(g, layer, q, Q, hits, np.nonzero(hits["layer"] == layer)[0])
+        if comp:
+            h, dc2 = min(comp, key=lambda t: (t[1], t[0]))
+            c2, nh = c2 + dc2, nh + 1
+        else:
+            h = -1
+        p, P = _advance(g, layer, q, Q, hits, h)
+        path = path + [int(h)]
+    return path, nh, c2
+
+
+def test_single_candidate_is_greedy_best_chi2(det):
+    b = rotate_into_jet(small_event(det, 34, 12, 0.5), width=0.003)
+    g = O.make_geom(det, O.Settings(n_cand=1, chi2_cut=300.0))
+    hits, idx = _index(g, b)
+    sp, sP, sc2, snh, sh = oracle_seeds(g, hits, b.trk_hits)
+    res = O.build(g, idx, sp, sP, sc2, snh, sh)
+    for s in range(b.n_tracks):
+        path, nh, c2 = _greedy(g, hits, sp[s], sP[s], sc2[s], snh[s], list(sh[s, :3]))
+        assert res.n_cand[s] == 1
+        assert res.hits[s, 0].tolist() == path
+        assert res.nhits[s, 0] == nh
+        assert res.chi2[s, 0] == pytest.approx(c2, rel=1e-9)
+
+
+def test_noise_free_events_recover_truth_hits():
+    det = Detector(x_over_x0=(0.0,) * 10)
+    b = small_event(det, 35, 500, 0.0, scatter=False, smear=False, keep_f64=True)
+    g = O.make_geom(det)
+    hits = O.hits_of(b, exact=True)
+    idx = O.hit_index(g, hits)
+    sp, sP, sc2, snh, sh = oracle_seeds(g, hits, b.trk_hits)
+    res = O.build(g, idx, sp, sP, sc2, snh, sh)
+    assert np.array_equal(res.hits[:, 0, :], b.trk_hits)
+    assert np.all(res.nhits[:, 0] == det.n_layers)
+
+
+def test_building_efficiency_on_the_plain_workload(det):
+    """Fraction of seeds whose best candidate has >= 75% of its hits from the seed's own
+    simulated track, on one event of the plain building workload (5000 tracks, 20% noise)."""
+    b = small_event(det, 1, 5000, 0.2)
+    g = O.make_geom(det)
+    hits, idx = _index(g, b)
+    res = _build(g, b, hits, idx)
+    best = res.hits[:, 0, :]
+    own = (b.mc[np.maximum(best, 0)] == np.arange(b.n_tracks)[:, None]) & (best >= 0)
+    frac = own.sum(1) / np.maximum((best >= 0).sum(1), 1)
+    eff = np.mean(frac >= 0.75)
+    assert eff > 0.97, eff
+    assert np.mean(res.nhits[:, 0] == det.n_layers) > 0.9
