@@ -76,14 +76,29 @@ static double wrap_phi(double phi)
 
 /* ------------------------------------------------------------------ propagation (Sec. 2.2) */
 
+/* sin(x)/x and its derivative, written so that nothing cancels near x = 0 (the series are
+ * used where their first omitted term is below 1e-17). */
+static double sinc(double x) { return fabs(x) < 1e-4 ? 1.0 - x * x / 6.0 : sin(x) / x; }
+static double dsinc(double x)
+{
+    return fabs(x) < 1e-3 ? -x / 3.0 + x * x * x / 30.0 : (x * cos(x) - sin(x)) / (x * x);
+}
+
 /*
  * Exact propagation of a helix in a uniform field Bz to the cylinder r = R.
- * Helix with curvature kappa = -K_B Bz q/pT (signed d phi / d s_T):
- *   x(s) = x0 + (sin(phi0 + kappa s) - sin phi0) / kappa
- *   y(s) = y0 - (cos(phi0 + kappa s) - cos phi0) / kappa
- *   z(s) = z0 + s cot(theta),  phi(s) = phi0 + kappa s.
- * The crossing is found by intersecting the circle |x| = R with the track circle (centre c,
- * radius 1/|kappa|) and taking the smallest positive turning angle in the direction of motion.
+ * Helix with curvature kappa = -K_B Bz q/pT (signed d phi / d s_T), s_T the transverse path:
+ *   x(s) = x0 + (sin(phi0 + kappa s) - sin phi0) / kappa = x0 + s cos(phi0 + kappa s/2) sinc(kappa s/2)
+ *   y(s) = y0 - (cos(phi0 + kappa s) - cos phi0) / kappa = y0 + s sin(phi0 + kappa s/2) sinc(kappa s/2)
+ *   z(s) = z0 + s cot(theta),  phi(s) = phi0 + kappa s,
+ * the right-hand forms following from sin a - sin b = 2 cos((a+b)/2) sin((a-b)/2) and
+ * cos a - cos b = -2 sin((a+b)/2) sin((a-b)/2); they stay exact as kappa -> 0.
+ * The crossing is the intersection of the circle |x| = R with the track circle, centre
+ * c = p0 + n0/kappa (n0 = (-sin phi0, cos phi0)), radius rho = 1/|kappa|: with
+ * d = |c| the chord lies at distance a = (R^2 - rho^2 + d^2)/(2d) from the origin along c, and
+ * d^2 - rho^2 = r0^2 + 2 (p0 . n0)/kappa.  The turning angle from p0 to a crossing p (seen from
+ * c, counter-clockwise) is atan2(v0 x v1, v0 . v1) with v0 = -n0/kappa, v1 = (p - p0) - n0/kappa;
+ * multiplying both arguments by kappa^2 > 0 gives atan2(-kappa n0 x dp, 1 - kappa n0 . dp).
+ * The smallest positive turning angle in the direction of motion gives s = angle / |kappa|.
  * The transport Jacobian J = dp_out/dp_in is the analytic derivative at fixed s plus
  * (dp_out/ds)(ds/dp_in), with ds/dp_in = -(dr/dp_in)/(dr/ds) from the constraint r(s, p_in) = R.
  */
@@ -92,6 +107,7 @@ int orc_propagate(const orc_geom *g, const double pin[6], double R, double pout[
     const double x0 = pin[0], y0 = pin[1], z0 = pin[2], w = pin[3], phi0 = pin[4], th = pin[5];
     const double kappa = -ORC_KB * g->bz * w;
     const double cot_th = cos(th) / sin(th);
+    const double nx = -sin(phi0), ny = cos(phi0);
     double s;
 
     if (fabs(kappa) < 1e-12) { /* straight line: |p0 + s u|^2 = R^2 */
@@ -102,11 +118,11 @@ int orc_propagate(const orc_geom *g, const double pin[6], double R, double pout[
         s = -b + sqrt(disc);
         if (!(s > 0.0)) return ORC_ERR_NOREACH;
     } else {
-        const double rho = 1.0 / fabs(kappa);
-        const double cx = x0 - sin(phi0) / kappa, cy = y0 + cos(phi0) / kappa;
+        const double cx = x0 + nx / kappa, cy = y0 + ny / kappa;
         const double d = sqrt(cx * cx + cy * cy);
         if (d == 0.0) return ORC_ERR_NOREACH;
-        const double a = (R * R - rho * rho + d * d) / (2.0 * d);
+        const double r02 = x0 * x0 + y0 * y0, B = x0 * nx + y0 * ny;
+        const double a = (R * R + r02 + 2.0 * B / kappa) / (2.0 * d);
         const double h2 = R * R - a * a;
         if (h2 < 0.0) return ORC_ERR_NOREACH;
         const double h = sqrt(h2);
@@ -114,27 +130,22 @@ int orc_propagate(const orc_geom *g, const double pin[6], double R, double pout[
         double best = -1.0;
         for (int sign = -1; sign <= 1; sign += 2) {
             const double px = a * ex - sign * h * ey, py = a * ey + sign * h * ex;
-            const double v0x = x0 - cx, v0y = y0 - cy, v1x = px - cx, v1y = py - cy;
-            double ang = atan2(v0x * v1y - v0y * v1x, v0x * v1x + v0y * v1y); /* ccw, (-pi, pi] */
-            if (kappa < 0.0) ang = -ang;                                     /* direction of motion */
-            if (ang <= 0.0) ang += 2.0 * ORC_PI;                              /* into (0, 2 pi] */
-            const double st = ang * rho;
+            const double dx = px - x0, dy = py - y0;
+            double ang = atan2(-kappa * (nx * dy - ny * dx), 1.0 - kappa * (nx * dx + ny * dy)); /* ccw */
+            if (kappa < 0.0) ang = -ang;                                                        /* direction of motion */
+            if (ang <= 0.0) ang += 2.0 * ORC_PI;                                                 /* into (0, 2 pi] */
+            const double st = ang / fabs(kappa);
             if (st > 0.0 && (best < 0.0 || st < best)) best = st;
         }
         if (best < 0.0) return ORC_ERR_NOREACH;
         s = best;
     }
 
-    double phi1, x1, y1;
-    if (fabs(kappa) < 1e-12) {
-        phi1 = phi0;
-        x1 = x0 + s * cos(phi0);
-        y1 = y0 + s * sin(phi0);
-    } else {
-        phi1 = phi0 + kappa * s;
-        x1 = x0 + (sin(phi1) - sin(phi0)) / kappa;
-        y1 = y0 - (cos(phi1) - cos(phi0)) / kappa;
-    }
+    const double half = 0.5 * kappa * s, mid = phi0 + half;
+    const double sn = sinc(half);
+    const double x1 = x0 + s * cos(mid) * sn;
+    const double y1 = y0 + s * sin(mid) * sn;
+    const double phi1 = phi0 + kappa * s;
     const double z1 = z0 + s * cot_th;
     pout[0] = x1; pout[1] = y1; pout[2] = z1; pout[3] = w; pout[4] = wrap_phi(phi1); pout[5] = th;
 
@@ -145,18 +156,12 @@ int orc_propagate(const orc_geom *g, const double pin[6], double R, double pout[
     memset(F, 0, sizeof F);
     for (int i = 0; i < 6; ++i) F[i * 6 + i] = 1.0;
     const double dkdw = -ORC_KB * g->bz;
-    double dx_dk, dy_dk;
-    if (fabs(kappa) < 1e-12) {
-        dx_dk = -0.5 * s * s * sin(phi0);
-        dy_dk = 0.5 * s * s * cos(phi0);
-        F[0 * 6 + 4] = -s * sin(phi0);
-        F[1 * 6 + 4] = s * cos(phi0);
-    } else {
-        dx_dk = s * cos(phi1) / kappa - (sin(phi1) - sin(phi0)) / (kappa * kappa);
-        dy_dk = s * sin(phi1) / kappa + (cos(phi1) - cos(phi0)) / (kappa * kappa);
-        F[0 * 6 + 4] = (cos(phi1) - cos(phi0)) / kappa;
-        F[1 * 6 + 4] = (sin(phi1) - sin(phi0)) / kappa;
-    }
+    const double dsn = dsinc(half);
+    /* d/dkappa of s cos(mid) sinc(half) with d mid/d kappa = d half/d kappa = s/2 */
+    const double dx_dk = s * (-sin(mid) * 0.5 * s * sn + cos(mid) * dsn * 0.5 * s);
+    const double dy_dk = s * (cos(mid) * 0.5 * s * sn + sin(mid) * dsn * 0.5 * s);
+    F[0 * 6 + 4] = -(y1 - y0);
+    F[1 * 6 + 4] = x1 - x0;
     F[0 * 6 + 3] = dx_dk * dkdw;
     F[1 * 6 + 3] = dy_dk * dkdw;
     F[2 * 6 + 5] = -s / (sin(th) * sin(th));

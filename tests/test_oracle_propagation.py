@@ -114,13 +114,15 @@ def test_charge_conjugation_mirror(det):
         assert abs(_wrap(-o2[4] - o1[4])) < 1e-10
 
 
-@pytest.mark.parametrize("pt_hi", [10.0, 100.0])
+@pytest.mark.parametrize("pt_hi", [10.0, 100.0, 1e5, 1e9])
 def test_jacobian_matches_finite_differences(det, pt_hi):
+    """Includes nearly straight helices (pT up to 1e9 GeV), as three-hit seed estimates of
+    stiff tracks produce."""
     g = O.make_geom(det)
     rng = np.random.default_rng(5)
     for _ in range(60):
         p = _state(rng, r0=rng.uniform(3.0, 30.0))
-        p[3] = math.copysign(1.0 / rng.uniform(0.5, pt_hi), p[3])
+        p[3] = math.copysign(1.0 / (pt_hi if pt_hi > 100 else rng.uniform(0.5, pt_hi)) * rng.uniform(0.5, 1.0), p[3])
         # steps large against the ~1e-12 cm rounding of the closed form, small against curvature
         steps = np.array([1e-4, 1e-4, 1e-4, 1e-4 * max(abs(p[3]), 0.05), 1e-5, 1e-5])
         R = math.hypot(p[0], p[1]) + rng.uniform(1.0, 10.0)
@@ -153,6 +155,26 @@ def test_agrees_with_generator_simulation(det):
             d[4] = _wrap(d[4])
             worst = max(worst, np.max(np.abs(d)))
     assert worst < 1e-9
+
+
+def test_continuous_at_the_straight_line_limit(det):
+    """Curvature just above and just below the straight-line switch gives the same crossing
+    and Jacobian as an exactly straight track."""
+    g = O.make_geom(det)
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        p = _state(rng, r0=rng.uniform(3.0, 30.0))
+        R = math.hypot(p[0], p[1]) + rng.uniform(1.0, 10.0)
+        p0 = p.copy()
+        p0[3] = 0.0
+        _, o0, J0 = O.propagate(g, p0, R)
+        for w in (1e-11, 1e-9, 1e-7):
+            p1 = p.copy()
+            p1[3] = w
+            _, o1, J1 = O.propagate(g, p1, R)
+            # the curvature itself moves the crossing by about K_B Bz w s^2 / 2 < 0.006 w R^2
+            assert np.allclose(o1, o0, atol=1e-12 + 0.01 * w * R * R)
+            assert np.allclose(J1, J0, atol=1e-9 + 0.01 * w * R * R)
 
 
 def test_no_reach_is_reported(det):
