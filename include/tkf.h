@@ -1,0 +1,185 @@
+/*
+ * tkf -- Kalman-filter track building and fitting on one GB300 (sm_103a).
+ *
+ * C ABI of the library libtkf.so.  The method is the Kalman-filter (KF) tracking of
+ * Cerati et al., "Kalman filter tracking on parallel architectures" (arXiv:1702.06359):
+ * seeding, combinatorial track building and a final KF fit (Sec. 2), in the hybrid
+ * coordinates of Sec. 2.2 (global Cartesian position, polar momentum) on the ideal barrel of
+ * Sec. 2.2 (thin cylinders, uniform solenoid field Bz), with the KF update on the plane
+ * tangent to the cylinder at the hit (Sec. 2.2).
+ *
+ * Conventions for every call:
+ *  - Return value: TKF_OK (0) or a TKF_ERR_* code; no C++ exception crosses the ABI.  The
+ *    text of the last error of a context is given by tkf_last_error().
+ *  - Array arguments named "device" are CUDA device pointers owned by the caller (for
+ *    example PyTorch tensors); they must stay valid until the work queued on `stream` has
+ *    completed.  Host structs passed by pointer are read during the call only.
+ *  - Work is queued asynchronously on `stream` (NULL = the legacy default stream); a call
+ *    returning TKF_OK means the work was queued, not that it finished.  Errors found while
+ *    the kernels run are reported per track (see tkf_tracks.nhits) and by tkf_sync_status().
+ *  - Track state p = (x, y, z, q/pT, phi, theta) in cm, GeV^-1, rad; covariances are the 21
+ *    elements of the lower triangle in row order: (0,0) (1,0) (1,1) (2,0) (2,1) (2,2) ...
+ *  - Layers are numbered from 0 (innermost).  Hit ids are indices into the caller's hit
+ *    arrays (tkf_hits); -1 means "no hit on this layer" (a hole).
+ */
+#ifndef TKF_H
+#define TKF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TKF_MAX_LAYERS 16
+#define TKF_MAX_CAND 16
+
+typedef struct CUstream_st *tkf_stream; /* a cudaStream_t */
+
+enum tkf_status_code {
+    TKF_OK = 0,
+    TKF_ERR_INVALID = 1,  /* bad argument or configuration; nothing was queued */
+    TKF_ERR_CUDA = 2,     /* a CUDA runtime call failed (text in tkf_last_error) */
+    TKF_ERR_NOMEM = 3,    /* device allocation failed */
+    TKF_ERR_AGAIN = 4,    /* queue or device-memory budget full: retry later */
+    TKF_ERR_TIMEOUT = 5,  /* a bounded wait ran out */
+    TKF_ERR_NOTREADY = 6, /* result not available yet */
+    TKF_ERR_KERNEL = 7    /* a kernel reported an internal error word */
+};
+
+/* Arithmetic of the KF steps.  FP32: everything in float.  MIXED: float, except the
+ * innovation-covariance inverse and the Joseph-form covariance update, done in double and
+ * rounded back.  FP64: everything in double (track arrays hold double). */
+enum tkf_precision { TKF_FP32 = 0, TKF_MIXED = 1, TKF_FP64 = 2 };
+
+/* Per-track status written to tkf_tracks.nhits when a track fails (nhits < 0). */
+enum tkf_track_status { TKF_TRACK_NOREACH = -1, TKF_TRACK_SINGULAR = -2, TKF_TRACK_LOST = -3 };
+
+typedef struct {
+    int32_t n_layers;                 /* barrel cylinders, <= TKF_MAX_LAYERS */
+    double radius[TKF_MAX_LAYERS];    /* cm, increasing */
+    double x_over_x0[TKF_MAX_LAYERS]; /* thin-scatterer thickness of each layer (0 = none) */
+    double bz;                        /* T, uniform field along z */
+    double mass;                      /* GeV, mass hypothesis for the scattering width */
+    double prior_sigma[6];            /* seed prior (cm, cm, cm, GeV^-1, rad, rad) */
+    double eta_min, eta_bin_w;        /* hit index: eta bins of width eta_bin_w from eta_min */
+    int32_t n_eta_bins, n_phi_bins;   /* phi bins cover [-pi, pi) */
+    double chi2_cut;                  /* a hit is compatible when chi2 < chi2_cut (2 dof) */
+    double window_margin;             /* relative widening of the chi2 bounding box */
+    int32_t n_cand;                   /* candidates kept per seed while building, 1..16 */
+    int32_t first_build_layer;        /* seeds are states on layer first_build_layer - 1 */
+    int32_t precision;                /* enum tkf_precision */
+    int32_t seeds_per_block;          /* seeds per work tile of the build kernel; 0 = autotuned */
+} tkf_config;
+
+/* Hits of one or more events (device arrays of length n, caller-owned).  The hits of event e
+ * are [event_off[e], event_off[e+1]); at most 8388606 hits per event.  layer in
+ * [0, n_layers).  var_u / var_v: measurement variances along the cylinder's tangent (r-phi)
+ * and along z (cm^2). */
+typedef struct {
+    const float *x, *y, *z, *var_u, *var_v;
+    const int32_t *layer;
+    const int32_t *event_off; /* device, n_events + 1 entries */
+    int32_t n, n_events;
+} tkf_hits;
+
+/* Track structure-of-arrays, track-major planes of `stride` elements (caller-owned device
+ * memory).  Element type of par/cov/chi2 is float, or double when precision == TKF_FP64.
+ *   par     [6][stride]   cov [21][stride]   chi2 [stride]
+ *   nhits   [stride]  hits used (< 0: enum tkf_track_status)
+ *   hit_idx [n_layers][stride]  hit id per layer, -1 = none (may be NULL where unused)
+ *   event   [stride]  event index of each track (may be NULL: every track in event 0) */
+typedef struct {
+    void *par, *cov, *chi2;
+    int32_t *nhits, *hit_idx, *event;
+    int32_t n, stride;
+} tkf_tracks;
+
+typedef struct tkf_ctx tkf_ctx;
+typedef struct tkf_hit_index tkf_hit_index;
+
+/* Device view of a hit index (pointers owned by the index). */
+typedef struct {
+    const float *hit_xyzi;   /* [n][4] sorted hits: x, y, z, event-local hit id (bits of an int32) */
+    const float *hit_var;    /* [n][2] sorted hits: var_u, var_v */
+    const int32_t *pos_of_hit; /* [n] sorted position of hit id i */
+    const int32_t *bin_off;  /* [n_events * n_layers * n_bins + 1] CSR offsets into the sorted hits;
+                                bin (e, l, b) is [off[(e*L+l)*n_bins+b], off[(e*L+l)*n_bins+b+1]) */
+    const float *var_max;    /* [n_events][n_layers][2] largest var_u, var_v of the layer */
+    const int32_t *event_off; /* [n_events + 1] copy of the hits' event offsets */
+    int32_t n, n_events, n_layers, n_bins;
+} tkf_hit_index_view;
+
+/* ---------------------------------------------------------------- context */
+
+/* Fills `cfg` with the plain-building workload of the toy barrel: 10 cylinders at
+ * 4, 8, ..., 40 cm, Bz = 3.8 T, x/X0 = 0.03 per layer, pion mass, 40 x 0.1 eta bins from
+ * -2, 63 phi bins, chi2 < 30, 6 candidates, building from layer 3, FP32. */
+void tkf_default_config(tkf_config *cfg);
+
+/* Creates a context on the current CUDA device.  The context owns its scratch memory. */
+int tkf_create(const tkf_config *cfg, tkf_ctx **out);
+int tkf_destroy(tkf_ctx *ctx);
+const char *tkf_last_error(const tkf_ctx *ctx);
+const char *tkf_status_string(int status);
+/* Copies the context's configuration (with the autotuned seeds_per_block, if any). */
+int tkf_get_config(const tkf_ctx *ctx, tkf_config *out);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* Hit index (the hit-candidate data structure of Sec. 3.2.1): every hit is binned by
+ * (event, layer, eta bin, phi bin), eta = asinh(z / radius[layer]) clamped to the bin range;
+ * hits are reordered by (event, layer, eta bin, phi bin, hit id) into float4/float2 planes
+ * with CSR bin offsets.  *out: NULL to allocate a new index, or an index from an earlier call
+ * whose storage is reused (grown if too small).  Library-owned until tkf_hit_index_free.
+ * Errors: TKF_ERR_INVALID (bad sizes), TKF_ERR_NOMEM. */
+int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out, tkf_stream stream);
+int tkf_hit_index_free(tkf_hit_index *idx);
+int tkf_hit_index_get_view(const tkf_hit_index *idx, tkf_hit_index_view *view);
+
+/* Seed estimate (the seeding stage of Sec. 2): for each track, the state on layer 0 from its
+ * hits on layers 0, 1, 2: curvature and charge from the circle through the three (x, y)
+ * points, phi = tangent at the first hit, cot(theta) = dz / transverse arc, position = first
+ * hit; covariance = diag(prior_sigma^2); chi2 = 0, nhits = 0; hit_idx rows 0..2 copied,
+ * others -1 (when out->hit_idx is not NULL).
+ *   seed_hits: device int32 [3][stride_in] hit ids, stride_in = out->stride.
+ * Errors: TKF_ERR_INVALID. */
+int tkf_seed_state(tkf_ctx *ctx, const tkf_hits *hits, const int32_t *seed_hits, tkf_tracks *out,
+                   tkf_stream stream);
+
+/* Track fit (Sec. 2: the KF applied without branching over a known hit list): each track
+ * starts from `init` (a state on layer first_layer), gets the KF update with its hit on
+ * first_layer, then for each layer up to last_layer: exact helix propagation to the cylinder
+ * (with transport Jacobian), KF update with the hit (if any) in Joseph form, and the layer's
+ * scattering noise (Highland width) unless the layer is the outermost one.  chi2 and nhits of
+ * `init` are accumulated.  hit_idx: device int32 [n_layers][init->stride] (NULL: init->hit_idx).
+ * `out` may alias `init`.  Failed tracks get nhits < 0 (enum tkf_track_status).
+ * Errors: TKF_ERR_INVALID. */
+int tkf_fit(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx,
+            int32_t first_layer, int32_t last_layer, tkf_tracks *out, tkf_stream stream);
+
+/* Combinatorial track building (Sec. 2, Sec. 3.2): each seed (a state on layer
+ * first_build_layer - 1, with chi2, nhits and the hit ids of the seeding layers) is extended
+ * outward layer by layer: every candidate is propagated to the next cylinder, every hit of
+ * the eta-phi window around it with chi2 < chi2_cut (on the same half of the cylinder) makes
+ * a branch, a candidate without any makes one hole branch, the branches of the seed are
+ * ranked by (nHits desc, chi2 asc, parent rank asc, hit id asc) and the best n_cand are kept,
+ * updated by the KF and given the layer's scattering noise.  One persistent launch over all
+ * seeds of all events (tiles of seeds_per_block seeds pulled from an atomic counter).
+ *   out: best candidate per seed (out->stride >= seeds->n).
+ *   out_all: NULL, or every final candidate: candidate r of seed s at s * n_cand + r
+ *            (stride >= seeds->n * n_cand); n_cand_out (device int32 [seeds->n], may be NULL)
+ *            receives the number of candidates of each seed.
+ * Errors: TKF_ERR_INVALID; per seed nhits < 0 when every candidate was lost. */
+int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *seeds, tkf_tracks *out,
+                     tkf_tracks *out_all, int32_t *n_cand_out, tkf_stream stream);
+
+/* Waits for `stream` and reports errors raised by kernels of this context since the last
+ * call (TKF_ERR_KERNEL with text in tkf_last_error), or a CUDA error (TKF_ERR_CUDA). */
+int tkf_sync_status(tkf_ctx *ctx, tkf_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,306 @@
+// Combinatorial track building kernel (Sec. 2 and Sec. 3.2 of arXiv:1702.06359).
+//
+// Mapping: a seed owns a segment of N consecutive lanes of a warp (N = candidates kept per
+// seed); lane r of the segment holds the candidate of rank r, its state (6 parameters, 21
+// covariance elements, chi2, nHits) in registers for the whole trajectory.  Per layer:
+//   1. every live candidate is propagated to the cylinder (helix + Jacobian, kf_math.cuh);
+//   2. it scans the hits of its eta-phi window (CSR bins of the hit index), scores each by
+//      chi2 and keeps its own best-N branch keys in a register list; a candidate with no
+//      compatible hit contributes one hole key;
+//   3. the segment merges its lanes' lists: N rounds of a segmented warp-shuffle minimum give
+//      the seed's N best branches in rank order (the paper's "branching to explore multiple
+//      candidate tracks per seed" and the per-seed repacking of Sec. 3.2.1);
+//   4. the lane of rank r fetches its parent's predicted state with shuffles, applies the
+//      Kalman update (U = float or double) for a hit branch and the layer's scattering noise.
+// Hit history is kept per warp in shared memory (parent rank, hit id per layer and lane) and
+// the best candidate is backtracked at the end.  Work balance follows the paper's dynamic
+// work stealing (Sec. 2.3): blocks pull tiles of seeds_per_block seeds from an atomic counter
+// until the seeds of every event are done (one persistent launch over many events, Sec. 4).
+//
+// Branch key (64 bits, smaller = better): [63:59] 31 - nHits, [58:27] float bits of the total
+// chi2 (non-negative, so integer order = value order), [26:23] parent rank, [22:0]
+// event-local hit id (0x7FFFFF for a hole).  This is the total order
+// (nHits desc, chi2 asc, parent rank asc, hit id asc).
+#pragma once
+
+#include "internal.h"
+#include "kf_math.cuh"
+
+namespace tkf {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint64_t kEmpty = ~0ull;
+
+template <class R> __device__ __forceinline__ R pick(float f, double d);
+template <> __device__ __forceinline__ float pick<float>(float f, double) { return f; }
+template <> __device__ __forceinline__ double pick<double>(float, double d) { return d; }
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(double v) { return __double2float_rn(v); }
+
+__device__ __forceinline__ uint64_t make_key(int nhits, float chi2, int parent, int hit)
+{
+    const uint64_t c = __float_as_uint(chi2) & 0x7FFFFFFFu;
+    return ((uint64_t)(31 - nhits) << 59) | (c << 27) | ((uint64_t)parent << 23) | (uint64_t)hit;
+}
+
+template <int NMAX> __device__ __forceinline__ void list_insert(uint64_t (&list)[NMAX], uint64_t k)
+{
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+        const uint64_t lo = k < list[i] ? k : list[i];
+        const uint64_t hi = k < list[i] ? list[i] : k;
+        list[i] = lo;
+        k = hi;
+    }
+}
+
+template <int NMAX> __device__ __forceinline__ void list_pop(uint64_t (&list)[NMAX])
+{
+#pragma unroll
+    for (int i = 0; i + 1 < NMAX; ++i) list[i] = list[i + 1];
+    list[NMAX - 1] = kEmpty;
+}
+
+template <class R>
+__device__ __forceinline__ int eta_bin(R z, R inv_r, R eta_min, R inv_w, int n_eta)
+{
+    const int b = (int)flr((ash(z * inv_r) - eta_min) * inv_w);
+    return b < 0 ? 0 : (b >= n_eta ? n_eta - 1 : b);
+}
+
+// Scores every hit of the candidate's window and fills its branch list.
+template <int NMAX, class R>
+__device__ __forceinline__ void scan_window(const BuildArgs &a, int ev, int l, R Rl, const R p[6], const R P[21],
+                                            R chi2, int nh, int rank, uint64_t (&list)[NMAX])
+{
+    const int seg = ev * a.L + l;
+    const float2 vmax = a.var_max[seg];
+    const R xp = p[0], yp = p[1], zp = p[2];
+    const R rp = sq(xp * xp + yp * yp);
+    const R sf = yp / rp, cf = xp / rp;
+    // innovation covariance at phi_h = phi of the prediction, with the layer's largest V
+    const R Suu = sf * (sf * P[sym(0, 0)] - cf * P[sym(1, 0)]) + cf * (cf * P[sym(1, 1)] - sf * P[sym(1, 0)]) + R(vmax.x);
+    const R Svv = P[sym(2, 2)] + R(vmax.y);
+    const R cut = pick<R>(a.cut_f, a.cut);
+    const R mg = R(1) + pick<R>(a.margin_f, a.margin);
+    const R U = sq(cut * Suu) * mg, W = sq(cut * Svv) * mg;
+    const R phip = at2(yp, xp);
+    const R ur = U / Rl;
+    const R dphi = asn(ur < R(1) ? ur : R(1));
+    const R bscale = R(a.n_phi) / R(2.0 * kPi);
+    int k0 = (int)flr((phip - dphi + R(kPi)) * bscale);
+    int k1 = (int)flr((phip + dphi + R(kPi)) * bscale);
+    const int nphi = a.n_phi;
+    if (k1 - k0 + 1 >= nphi) {
+        k0 = 0;
+        k1 = nphi - 1;
+    }
+    const R inv_r = R(1) / Rl;
+    const R emin = pick<R>(a.eta_min_f, a.eta_min), iw = pick<R>(a.inv_eta_w_f, a.inv_eta_w);
+    const int e0 = eta_bin(zp - W, inv_r, emin, iw, a.n_eta);
+    const int e1 = eta_bin(zp + W, inv_r, emin, iw, a.n_eta);
+    int ra0, ra1, rb0, rb1;
+    if (k0 < 0) {
+        ra0 = k0 + nphi; ra1 = nphi - 1; rb0 = 0; rb1 = k1;
+    } else if (k1 >= nphi) {
+        ra0 = k0; ra1 = nphi - 1; rb0 = 0; rb1 = k1 - nphi;
+    } else {
+        ra0 = k0; ra1 = k1; rb0 = 0; rb1 = -1;
+    }
+    bool found = false;
+    const int row0 = seg * a.n_bins;
+    for (int e = e0; e <= e1; ++e) {
+        const int row = row0 + e * nphi;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            const int b0 = part ? rb0 : ra0, b1 = part ? rb1 : ra1;
+            if (b1 < b0) continue;
+            const int i0 = __ldg(&a.bin_off[row + b0]), i1 = __ldg(&a.bin_off[row + b1 + 1]);
+            for (int i = i0; i < i1; ++i) {
+                const float4 h = __ldg(&a.hxyzi[i]);
+                if (!(xp * R(h.x) + yp * R(h.y) > R(0))) continue;  // far half of the cylinder
+                const float2 hv = __ldg(&a.hvar[i]);
+                const R c2 = hit_chi2<R>(p, P, R(h.x), R(h.y), R(h.z), R(hv.x), R(hv.y));
+                if (c2 < cut) {
+                    list_insert(list, make_key(nh + 1, to_f32(chi2 + c2), rank, __float_as_int(h.w)));
+                    found = true;
+                }
+            }
+        }
+    }
+    if (!found) list_insert(list, make_key(nh, to_f32(chi2), rank, kHoleId));
+}
+
+template <class R> __device__ __forceinline__ void store_track(void *par, void *cov, void *c2, int stride, int i,
+                                                                  const R p[6], const R P[21], R chi2)
+{
+    R *pp = (R *)par, *pc = (R *)cov, *px = (R *)c2;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) pp[(size_t)k * stride + i] = p[k];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) pc[(size_t)k * stride + i] = P[k];
+    px[i] = chi2;
+}
+
+template <int NMAX, class R, class U>
+__global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a)
+{
+    constexpr int W = kBuildThreads / 32;
+    __shared__ int s_tile;
+    __shared__ int hist_hit[W][TKF_MAX_LAYERS][32];
+    __shared__ signed char hist_par[W][TKF_MAX_LAYERS][32];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = a.ncand;
+    const int spw = 32 / N;
+    const int grp = lane / N;
+    const int r = lane - grp * N;
+    const int gbase = grp * N;
+    const bool lane_ok = grp < spw;
+    const R kb = pick<R>(a.kb_f, a.kb), mass = pick<R>(a.mass_f, a.mass);
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1);
+        __syncthreads();
+        const long long t0 = (long long)s_tile * a.seeds_per_block;
+        if (t0 >= a.n_seeds) return;
+        const int t1 = (int)min((long long)a.n_seeds, t0 + a.seeds_per_block);
+        for (int sb = (int)t0 + warp * spw; sb < t1; sb += W * spw) {
+            const int seed = sb + grp;
+            bool has = lane_ok && seed < t1;
+            const int ev = (has && a.s_event) ? a.s_event[seed] : 0;
+            if (has && (ev < 0 || ev >= a.n_events)) {
+                atomicOr(a.err, kErrBadEvent);
+                a.o_nhits[seed] = TKF_TRACK_LOST;
+                has = false;
+            }
+            R p[6], P[21], chi2 = R(0);
+            int nh = 0;
+            bool alive = has && r == 0;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) p[k] = R(0);
+#pragma unroll
+            for (int k = 0; k < 21; ++k) P[k] = R(0);
+            if (alive) {
+                const R *sp = (const R *)a.s_par, *sc_ = (const R *)a.s_cov;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) p[k] = sp[(size_t)k * a.s_stride + seed];
+#pragma unroll
+                for (int k = 0; k < 21; ++k) P[k] = sc_[(size_t)k * a.s_stride + seed];
+                chi2 = ((const R *)a.s_chi2)[seed];
+                nh = a.s_nhits[seed];
+            }
+            int ns = 0;
+            for (int l = a.first; l < a.L; ++l) {
+                const R Rl = pick<R>(a.radius_f[l], a.radius[l]);
+                const bool ok = alive && propagate<R>(p, P, Rl, kb);
+                uint64_t list[NMAX];
+#pragma unroll
+                for (int i = 0; i < NMAX; ++i) list[i] = kEmpty;
+                if (ok) scan_window<NMAX, R>(a, ev, l, Rl, p, P, chi2, nh, r, list);
+
+                // merge the segment's lists: N rounds of a segmented minimum
+                uint64_t mine = kEmpty;
+                ns = 0;
+                for (int k = 0; k < N; ++k) {
+                    uint64_t m = list[0];
+                    for (int off = 1; off < N; off <<= 1) {
+                        const uint64_t o = __shfl_down_sync(kFull, m, off);
+                        if (r + off < N && o < m) m = o;
+                    }
+                    m = __shfl_sync(kFull, m, gbase);
+                    if (m != kEmpty) {
+                        if (list[0] == m) list_pop(list);
+                        if (r == k) mine = m;
+                        ns = k + 1;
+                    }
+                }
+
+                // survivors take their parent's predicted state
+                const int parent = mine != kEmpty ? (int)((mine >> 23) & 0xF) : r;
+                const int src = lane_ok ? gbase + parent : lane;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) p[k] = __shfl_sync(kFull, p[k], src);
+#pragma unroll
+                for (int k = 0; k < 21; ++k) P[k] = __shfl_sync(kFull, P[k], src);
+                const R pchi2 = __shfl_sync(kFull, chi2, src);
+                alive = mine != kEmpty;
+                if (alive) {
+                    nh = 31 - (int)(mine >> 59);
+                    const int hl = (int)(mine & (uint64_t)kHoleId);
+                    int gh = -1;
+                    chi2 = sizeof(R) == 8 ? pchi2 : R(__uint_as_float((unsigned)((mine >> 27) & 0xFFFFFFFFull)));
+                    if (hl != kHoleId) {
+                        gh = __ldg(&a.ev_off[ev]) + hl;
+                        const int pos = __ldg(&a.pos_of_hit[gh]);
+                        const float4 h = __ldg(&a.hxyzi[pos]);
+                        const float2 hv = __ldg(&a.hvar[pos]);
+                        U dc2 = U(0);
+                        kalman_update<U, R>(p, P, R(h.x), R(h.y), R(h.z), R(hv.x), R(hv.y), &dc2);
+                        if (sizeof(R) == 8) chi2 = pchi2 + R(dc2);
+                    }
+                    if (l < a.L - 1) scatter<R>(p, P, pick<R>(a.xx0_f[l], a.xx0[l]), mass);
+                    hist_hit[warp][l][lane] = gh;
+                    hist_par[warp][l][lane] = (signed char)parent;
+                }
+            }
+            __syncwarp();
+            if (has && r == 0) {
+                if (ns > 0) {
+                    store_track<R>(a.o_par, a.o_cov, a.o_chi2, a.o_stride, seed, p, P, chi2);
+                    a.o_nhits[seed] = nh;
+                } else {
+                    a.o_nhits[seed] = TKF_TRACK_LOST;
+                }
+                if (a.o_hit) {
+                    for (int l = 0; l < a.first; ++l)
+                        a.o_hit[(size_t)l * a.o_stride + seed] = a.s_hit ? a.s_hit[(size_t)l * a.s_stride + seed] : -1;
+                    int rank = 0;
+                    for (int l = a.L - 1; l >= a.first; --l) {
+                        const int slot = gbase + rank;
+                        a.o_hit[(size_t)l * a.o_stride + seed] = ns > 0 ? hist_hit[warp][l][slot] : -1;
+                        rank = hist_par[warp][l][slot];
+                    }
+                }
+            }
+            if (a.n_cand_out && has && r == 0) a.n_cand_out[seed] = ns;
+            if (a.a_par && has && r < ns) {
+                const int o = seed * N + r;
+                store_track<R>(a.a_par, a.a_cov, a.a_chi2, a.a_stride, o, p, P, chi2);
+                a.a_nhits[o] = nh;
+                if (a.a_hit) {
+                    for (int l = 0; l < a.first; ++l)
+                        a.a_hit[(size_t)l * a.a_stride + o] = a.s_hit ? a.s_hit[(size_t)l * a.s_stride + seed] : -1;
+                    int rank = r;
+                    for (int l = a.L - 1; l >= a.first; --l) {
+                        const int slot = gbase + rank;
+                        a.a_hit[(size_t)l * a.a_stride + o] = hist_hit[warp][l][slot];
+                        rank = hist_par[warp][l][slot];
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <class R, class U>
+cudaError_t launch_build_t(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy)
+{
+    const void *fn = nullptr;
+    switch (nmax) {
+    case 1: fn = (const void *)k_build<1, R, U>; break;
+    case 4: fn = (const void *)k_build<4, R, U>; break;
+    case 6: fn = (const void *)k_build<6, R, U>; break;
+    case 10: fn = (const void *)k_build<10, R, U>; break;
+    case 16: fn = (const void *)k_build<16, R, U>; break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (occupancy) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, fn, kBuildThreads, 0);
+    void *args[] = {(void *)&a};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kBuildThreads), args, 0, s);
+}
+
+}  // namespace tkf

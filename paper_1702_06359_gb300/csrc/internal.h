@@ -1,0 +1,87 @@
+// Host-side internals shared by the translation units of libtkf.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "tkf.h"
+
+namespace tkf {
+
+constexpr int kBuildThreads = 128;  // 4 warps per block
+constexpr int kHoleId = 0x7FFFFF;   // event-local hit id field value of a hole branch
+constexpr int kMaxHitsPerEvent = 0x7FFFFF - 1;
+
+// error bits raised by kernels (atomicOr into the context's error word)
+enum : int { kErrBadLayer = 1, kErrBadHitId = 2, kErrTooManyHits = 4, kErrBadEvent = 8 };
+
+struct BuildArgs {
+    int L, first, ncand, n_eta, n_phi, n_bins, seeds_per_block, n_seeds, n_events;
+    float radius_f[TKF_MAX_LAYERS], xx0_f[TKF_MAX_LAYERS];
+    double radius[TKF_MAX_LAYERS], xx0[TKF_MAX_LAYERS];
+    float kb_f, mass_f, eta_min_f, inv_eta_w_f, cut_f, margin_f;
+    double kb, mass, eta_min, inv_eta_w, cut, margin;
+    // hit index
+    const float4 *hxyzi;
+    const float2 *hvar;
+    const int *pos_of_hit;
+    const int *bin_off;
+    const float2 *var_max;
+    const int *ev_off;
+    // seeds
+    const void *s_par, *s_cov, *s_chi2;
+    const int *s_nhits, *s_hit, *s_event;
+    int s_stride;
+    // best candidate per seed
+    void *o_par, *o_cov, *o_chi2;
+    int *o_nhits, *o_hit;
+    int o_stride;
+    // every final candidate (optional)
+    void *a_par, *a_cov, *a_chi2;
+    int *a_nhits, *a_hit;
+    int a_stride;
+    int *n_cand_out;
+    int *tile_counter;
+    int *err;
+};
+
+// Launchers of the build kernel, one translation unit per precision.  `nmax` is the
+// compile-time candidate capacity (1, 4, 6, 10 or 16) >= a.ncand.  `occupancy` (if not
+// null) receives the resident blocks per SM of that instantiation instead of launching.
+cudaError_t launch_build_fp32(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
+cudaError_t launch_build_mixed(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
+cudaError_t launch_build_fp64(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
+
+inline int build_nmax(int n)
+{
+    return n <= 1 ? 1 : n <= 4 ? 4 : n <= 6 ? 6 : n <= 10 ? 10 : 16;
+}
+
+}  // namespace tkf
+
+struct tkf_ctx {
+    tkf_config cfg;
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+    int *d_tile = nullptr;  // work-tile counter of the persistent build kernel
+    int *d_err = nullptr;   // error bits raised by kernels
+};
+
+struct tkf_hit_index {
+    tkf_ctx *ctx = nullptr;
+    int n = 0, n_events = 0, n_layers = 0, n_bins = 0;
+    size_t cap_hits = 0, cap_bins = 0, cap_segs = 0;
+    float4 *hxyzi = nullptr;
+    float2 *hvar = nullptr;
+    int *pos_of_hit = nullptr;
+    int *keys = nullptr;
+    int *bin_off = nullptr;   // cap_bins + 1
+    int *counts = nullptr;    // cap_bins
+    int *seg_count = nullptr; // cap_segs
+    int *seg_base = nullptr;  // cap_segs
+    float2 *var_max = nullptr;
+    int *ev_off = nullptr;    // cap_segs + 1 (>= n_events + 1)
+};

@@ -1,0 +1,296 @@
+// Device-side Kalman-filter arithmetic for one track state (Sec. 2, 2.2 of arXiv:1702.06359):
+// helix propagation to a barrel cylinder with its transport Jacobian, thin-layer scattering
+// noise, chi2 of a hit and the Kalman update on the plane tangent to the cylinder.
+//
+// State p = (x, y, z, w = q/pT, phi, theta); covariance P as the 21-element packed lower
+// triangle, row order.  Everything is written out with the sparsity of the Jacobian and of H
+// (the paper's Matriplex generator idea of skipping known zeros and ones, Sec. 2.1, done by
+// hand), so no 6x6 product is ever formed densely.  Templated on the real type R (float or
+// double) so that one source serves the FP32, mixed and FP64 modes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tkf {
+
+constexpr double kCurv = 0.00299792458;  // GeV / (T cm)
+constexpr double kPi = 3.14159265358979323846;
+
+__host__ __device__ constexpr int sym(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
+
+// ------------------------------------------------------------------ math wrappers per type
+__host__ __device__ __forceinline__ void sc(float a, float *s, float *c) { sincosf(a, s, c); }
+__host__ __device__ __forceinline__ void sc(double a, double *s, double *c) { sincos(a, s, c); }
+__host__ __device__ __forceinline__ float sq(float a) { return sqrtf(a); }
+__host__ __device__ __forceinline__ double sq(double a) { return sqrt(a); }
+__host__ __device__ __forceinline__ float lg(float a) { return logf(a); }
+__host__ __device__ __forceinline__ double lg(double a) { return log(a); }
+__host__ __device__ __forceinline__ float at2(float y, float x) { return atan2f(y, x); }
+__host__ __device__ __forceinline__ double at2(double y, double x) { return atan2(y, x); }
+__host__ __device__ __forceinline__ float asn(float a) { return asinf(a); }
+__host__ __device__ __forceinline__ double asn(double a) { return asin(a); }
+__host__ __device__ __forceinline__ float ash(float a) { return asinhf(a); }
+__host__ __device__ __forceinline__ double ash(double a) { return asinh(a); }
+__host__ __device__ __forceinline__ float ab(float a) { return fabsf(a); }
+__host__ __device__ __forceinline__ double ab(double a) { return fabs(a); }
+__host__ __device__ __forceinline__ float flr(float a) { return floorf(a); }
+__host__ __device__ __forceinline__ double flr(double a) { return floor(a); }
+
+template <class R> struct Lim;
+template <> struct Lim<float> {
+    static constexpr float series = 0.25f;  // |kappa s| below which the helix functions use series
+    static constexpr int newton = 3;
+};
+template <> struct Lim<double> {
+    static constexpr double series = 0.05;
+    static constexpr int newton = 4;
+};
+
+template <class R> __host__ __device__ __forceinline__ R wrap_phi(R phi)
+{
+    const R tp = R(2.0 * kPi);
+    if (phi >= R(kPi)) phi -= tp;
+    if (phi < R(-kPi)) phi += tp;
+    return phi;
+}
+
+// S(a) = sin(a)/a, C(a) = (1 - cos a)/a and their derivatives dS/da, dC/da.  Near a = 0 the
+// Taylor series are used (they keep full relative precision where the direct forms cancel).
+template <class R> __host__ __device__ __forceinline__ void helix_fn(R a, R &S, R &C, R &Sd, R &Cd)
+{
+    if (ab(a) < Lim<R>::series) {
+        const R a2 = a * a;
+        S = R(1) + a2 * (R(-1.0 / 6) + a2 * (R(1.0 / 120) + a2 * (R(-1.0 / 5040) + a2 * R(1.0 / 362880))));
+        C = a * (R(0.5) + a2 * (R(-1.0 / 24) + a2 * (R(1.0 / 720) + a2 * (R(-1.0 / 40320) + a2 * R(1.0 / 3628800)))));
+        Sd = a * (R(-1.0 / 3) + a2 * (R(1.0 / 30) + a2 * (R(-1.0 / 840) + a2 * (R(1.0 / 45360) - a2 * R(1.0 / 3991680)))));
+        Cd = R(0.5) + a2 * (R(-1.0 / 8) + a2 * (R(1.0 / 144) + a2 * (R(-1.0 / 5760) + a2 * R(1.0 / 403200))));
+    } else {
+        R sn, cs;
+        sc(a, &sn, &cs);
+        const R ia = R(1) / a;
+        S = sn * ia;
+        C = (R(1) - cs) * ia;
+        Sd = (cs - S) * ia;
+        Cd = (sn - C) * ia;
+    }
+}
+
+// ------------------------------------------------------------------ propagation (Sec. 2.2)
+//
+// Exact propagation of the helix  x(s) = x0 + s (cos phi S(ks) - sin phi C(ks)),
+// y(s) = y0 + s (sin phi S(ks) + cos phi C(ks)), z(s) = z0 + s cot(theta), phi(s) = phi + k s
+// (k = -K Bz q/pT, s the transverse path) to the cylinder r = radius: s is found by Newton's
+// method on g(s) = x(s)^2 + y(s)^2 - radius^2 from the straight-line solution.  The transport
+// Jacobian is the derivative at fixed s plus (dp/ds)(ds/dp_in) with ds/dp_in from the
+// constraint r(s, p_in) = radius; P <- J P J^T uses its sparsity (rows of q/pT and theta are
+// unit rows, rows x, y, phi touch columns x, y, q/pT, phi only).
+// Returns false when the cylinder is not reached.
+template <class R> __host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R kb)
+{
+    const R x = p[0], y = p[1], z = p[2], w = p[3], phi = p[4], th = p[5];
+    R sp, cp;
+    sc(phi, &sp, &cp);
+    const R kappa = -kb * w;
+    const R A = x * cp + y * sp;
+    const R r0 = sq(x * x + y * y);
+    const R disc = A * A + (radius - r0) * (radius + r0);
+    if (!(disc >= R(0))) return false;
+    R s = -A + sq(disc);
+    R S, C, Sd, Cd;
+#pragma unroll
+    for (int it = 0; it < Lim<R>::newton; ++it) {
+        const R a = kappa * s;
+        helix_fn(a, S, C, Sd, Cd);
+        const R sa = a * S, ca = R(1) - a * C;
+        const R xs = x + s * (cp * S - sp * C);
+        const R ys = y + s * (sp * S + cp * C);
+        const R c1 = cp * ca - sp * sa, s1 = sp * ca + cp * sa;
+        const R g = xs * xs + ys * ys - radius * radius;
+        const R dg = R(2) * (xs * c1 + ys * s1);
+        s -= g / dg;
+    }
+    const R a = kappa * s;
+    helix_fn(a, S, C, Sd, Cd);
+    const R sa = a * S, ca = R(1) - a * C;
+    const R xs = x + s * (cp * S - sp * C);
+    const R ys = y + s * (sp * S + cp * C);
+    const R c1 = cp * ca - sp * sa, s1 = sp * ca + cp * sa;
+    const R D = xs * c1 + ys * s1;  // r dr/ds
+    if (!(s > R(0)) || !(ab(D) > R(1e-6) * radius) || !(ab(xs * xs + ys * ys - radius * radius) < R(1e-3) * radius))
+        return false;
+    R st, ct;
+    sc(th, &st, &ct);
+    const R cot = ct / st;
+
+    // derivatives at fixed s
+    const R s2kb = -kb * s * s;
+    const R dx_dw = s2kb * (cp * Sd - sp * Cd);
+    const R dy_dw = s2kb * (sp * Sd + cp * Cd);
+    const R dx_dphi = -(ys - y), dy_dphi = xs - x;
+    // ds/dp from r(s, p) = radius
+    const R iD = R(1) / D;
+    const R s_x = -xs * iD, s_y = -ys * iD;
+    const R s_w = -(xs * dx_dw + ys * dy_dw) * iD;
+    const R s_f = -(xs * dx_dphi + ys * dy_dphi) * iD;
+    // Jacobian rows (non-trivial entries only)
+    const R a0 = R(1) + c1 * s_x, a1 = c1 * s_y, a3 = dx_dw + c1 * s_w, a4 = dx_dphi + c1 * s_f;  // x
+    const R b0 = s1 * s_x, b1 = R(1) + s1 * s_y, b3 = dy_dw + s1 * s_w, b4 = dy_dphi + s1 * s_f;  // y
+    const R c0 = cot * s_x, cc1 = cot * s_y, c3 = cot * s_w, c4 = cot * s_f, c5 = -s / (st * st); // z (c2 = 1)
+    const R f0 = kappa * s_x, f1 = kappa * s_y, f3 = -kb * s + kappa * s_w, f4 = R(1) + kappa * s_f; // phi
+
+    // T = J P (rows x, y, z, phi; rows w, theta of T are rows 3, 5 of P)
+    R Tx[6], Ty[6], Tz[6], Tf[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const R p0 = P[sym(0, j)], p1 = P[sym(1, j)], p2 = P[sym(2, j)], p3 = P[sym(3, j)], p4 = P[sym(4, j)],
+                p5 = P[sym(5, j)];
+        Tx[j] = a0 * p0 + a1 * p1 + a3 * p3 + a4 * p4;
+        Ty[j] = b0 * p0 + b1 * p1 + b3 * p3 + b4 * p4;
+        Tz[j] = c0 * p0 + cc1 * p1 + p2 + c3 * p3 + c4 * p4 + c5 * p5;
+        Tf[j] = f0 * p0 + f1 * p1 + f3 * p3 + f4 * p4;
+    }
+    R Tw[6], Tt[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        Tw[j] = P[sym(3, j)];
+        Tt[j] = P[sym(5, j)];
+    }
+    // P' = T J^T, lower triangle
+#define TKF_DOT_X(T) (T[0] * a0 + T[1] * a1 + T[3] * a3 + T[4] * a4)
+#define TKF_DOT_Y(T) (T[0] * b0 + T[1] * b1 + T[3] * b3 + T[4] * b4)
+#define TKF_DOT_Z(T) (T[0] * c0 + T[1] * cc1 + T[2] + T[3] * c3 + T[4] * c4 + T[5] * c5)
+#define TKF_DOT_F(T) (T[0] * f0 + T[1] * f1 + T[3] * f3 + T[4] * f4)
+    R Q[21];
+    Q[sym(0, 0)] = TKF_DOT_X(Tx);
+    Q[sym(1, 0)] = TKF_DOT_X(Ty);
+    Q[sym(1, 1)] = TKF_DOT_Y(Ty);
+    Q[sym(2, 0)] = TKF_DOT_X(Tz);
+    Q[sym(2, 1)] = TKF_DOT_Y(Tz);
+    Q[sym(2, 2)] = TKF_DOT_Z(Tz);
+    Q[sym(3, 0)] = TKF_DOT_X(Tw);
+    Q[sym(3, 1)] = TKF_DOT_Y(Tw);
+    Q[sym(3, 2)] = TKF_DOT_Z(Tw);
+    Q[sym(3, 3)] = Tw[3];
+    Q[sym(4, 0)] = TKF_DOT_X(Tf);
+    Q[sym(4, 1)] = TKF_DOT_Y(Tf);
+    Q[sym(4, 2)] = TKF_DOT_Z(Tf);
+    Q[sym(4, 3)] = Tf[3];
+    Q[sym(4, 4)] = TKF_DOT_F(Tf);
+    Q[sym(5, 0)] = TKF_DOT_X(Tt);
+    Q[sym(5, 1)] = TKF_DOT_Y(Tt);
+    Q[sym(5, 2)] = TKF_DOT_Z(Tt);
+    Q[sym(5, 3)] = Tt[3];
+    Q[sym(5, 4)] = TKF_DOT_F(Tt);
+    Q[sym(5, 5)] = Tt[5];
+#undef TKF_DOT_X
+#undef TKF_DOT_Y
+#undef TKF_DOT_Z
+#undef TKF_DOT_F
+#pragma unroll
+    for (int k = 0; k < 21; ++k) P[k] = Q[k];
+    p[0] = xs;
+    p[1] = ys;
+    p[2] = z + s * cot;
+    p[4] = wrap_phi(phi + a);
+    return true;
+}
+
+// ------------------------------------------------------------------ scattering noise
+// Thin scatterer of thickness x/X0 crossed at angle alpha to the cylinder normal: Highland
+// width theta0 = 0.0136/(beta p) sqrt(t) (1 + 0.038 ln(t/beta^2)), t = (x/X0)/|cos alpha|;
+// two kicks orthogonal to the direction add theta0^2 to theta, theta0^2/sin^2(theta) to phi,
+// and (through pT = p sin(theta) at fixed p) the q/pT terms.
+template <class R> __host__ __device__ __forceinline__ void scatter(const R p[6], R P[21], R xx0, R mass)
+{
+    if (!(xx0 > R(0))) return;
+    R st, ct, sp, cp;
+    sc(p[5], &st, &ct);
+    sc(p[4], &sp, &cp);
+    const R w = p[3];
+    const R mom = R(1) / (ab(w) * st);
+    const R beta2 = mom * mom / (mom * mom + mass * mass);
+    const R beta = sq(beta2);
+    const R r = sq(p[0] * p[0] + p[1] * p[1]);
+    const R cosa = ab(st * (p[0] * cp + p[1] * sp) / r);
+    const R t = xx0 / cosa;
+    const R th0 = R(0.0136) / (beta * mom) * sq(t) * (R(1) + R(0.038) * lg(t / beta2));
+    const R v = th0 * th0;
+    const R cot = ct / st;
+    P[sym(3, 3)] += w * w * cot * cot * v;
+    P[sym(5, 3)] += -w * cot * v;
+    P[sym(4, 4)] += v / (st * st);
+    P[sym(5, 5)] += v;
+}
+
+// ------------------------------------------------------------------ measurement model
+// Measurement on the plane tangent to the cylinder at the hit (Sec. 2.2): u along the tangent
+// (-sin phi_h, cos phi_h, 0), v along z.  H = [[-s, c, 0, 0, 0, 0], [0, 0, 1, 0, 0, 0]].
+
+// chi2 = r^T S^-1 r with S = H P H^T + V; returns +inf when S is not positive definite.
+template <class R>
+__host__ __device__ __forceinline__ R hit_chi2(const R p[6], const R P[21], R xh, R yh, R zh, R vu, R vv)
+{
+    const R ir = R(1) / sq(xh * xh + yh * yh);
+    const R sh = yh * ir, ch = xh * ir;
+    const R u = ch * (yh - p[1]) - sh * (xh - p[0]);
+    const R v = zh - p[2];
+    const R Suu = sh * (sh * P[sym(0, 0)] - ch * P[sym(1, 0)]) + ch * (ch * P[sym(1, 1)] - sh * P[sym(1, 0)]) + vu;
+    const R Suv = ch * P[sym(2, 1)] - sh * P[sym(2, 0)];
+    const R Svv = P[sym(2, 2)] + vv;
+    const R det = Suu * Svv - Suv * Suv;
+    if (!(det > R(0))) return R(INFINITY);
+    return (u * (Svv * u - R(2) * Suv * v) + Suu * v * v) / det;
+}
+
+// Kalman update with the Joseph-form covariance, computed in the real type U:
+//   B = H P (2x6), S = B H^T + V, K = B^T S^-1, p += K r,
+//   P' = (I - K H) P (I - K H)^T + K V K^T = P - K B - (B^T - K S) K^T   (element-wise below).
+// Returns false when S is not positive definite; writes the hit's chi2 to *chi2.
+template <class U, class R>
+__host__ __device__ __forceinline__ bool kalman_update(R pR[6], R PR[21], R xh_, R yh_, R zh_, R vu_, R vv_, U *chi2)
+{
+    U p[6], P[21];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) p[i] = U(pR[i]);
+#pragma unroll
+    for (int k = 0; k < 21; ++k) P[k] = U(PR[k]);
+    const U xh = U(xh_), yh = U(yh_), zh = U(zh_);
+    const U ir = U(1) / sq(xh * xh + yh * yh);
+    const U sh = yh * ir, ch = xh * ir;
+    const U u = ch * (yh - p[1]) - sh * (xh - p[0]);
+    const U v = zh - p[2];
+    U B0[6], B1[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        B0[j] = ch * P[sym(1, j)] - sh * P[sym(0, j)];
+        B1[j] = P[sym(2, j)];
+    }
+    const U Suu = ch * B0[1] - sh * B0[0] + U(vu_);
+    const U Suv = B0[2];
+    const U Svv = B1[2] + U(vv_);
+    const U det = Suu * Svv - Suv * Suv;
+    if (!(det > U(0))) return false;
+    const U id = U(1) / det;
+    const U i00 = Svv * id, i01 = -Suv * id, i11 = Suu * id;
+    *chi2 = u * (i00 * u + i01 * v) + v * (i01 * u + i11 * v);
+    U K0[6], K1[6], D0[6], D1[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        K0[i] = B0[i] * i00 + B1[i] * i01;
+        K1[i] = B0[i] * i01 + B1[i] * i11;
+        D0[i] = B0[i] - (K0[i] * Suu + K1[i] * Suv);
+        D1[i] = B1[i] - (K0[i] * Suv + K1[i] * Svv);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) pR[i] = R(p[i] + K0[i] * u + K1[i] * v);
+    pR[4] = wrap_phi(pR[4]);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j)
+            PR[sym(i, j)] = R(P[sym(i, j)] - (K0[i] * B0[j] + K1[i] * B1[j]) - (D0[i] * K0[j] + D1[i] * K1[j]));
+    return true;
+}
+
+}  // namespace tkf

@@ -1,0 +1,731 @@
+// libtkf.so: context, hit index, seed estimate and track fit kernels, and the C ABI entry
+// points declared in include/tkf.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+#include "kf_math.cuh"
+
+using namespace tkf;
+
+namespace {
+
+// ------------------------------------------------------------------ error helpers
+
+int set_err(tkf_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_err(tkf_ctx *ctx, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return set_err(ctx, e == cudaErrorMemoryAllocation ? TKF_ERR_NOMEM : TKF_ERR_CUDA, m);
+}
+
+#define TKF_CUDA(ctx, call)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_err(ctx, e_, #call); \
+    } while (0)
+
+size_t elem_size(const tkf_ctx *ctx) { return ctx->cfg.precision == TKF_FP64 ? sizeof(double) : sizeof(float); }
+
+// ------------------------------------------------------------------ hit index kernels
+
+__device__ __forceinline__ int find_event(const int *off, int n_events, int i)
+{  // largest e with off[e] <= i
+    int lo = 0, hi = n_events;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&off[mid]) <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+struct IndexGeom {
+    int L, n_eta, n_phi, n_bins, n_events;
+    float radius[TKF_MAX_LAYERS];
+    float eta_min, inv_eta_w;
+};
+
+__device__ __forceinline__ int hit_bin(const IndexGeom &g, int l, float x, float y, float z)
+{
+    int eb = (int)floorf((asinhf(z / g.radius[l]) - g.eta_min) * g.inv_eta_w);
+    eb = eb < 0 ? 0 : (eb >= g.n_eta ? g.n_eta - 1 : eb);
+    int pb = (int)floorf((atan2f(y, x) + (float)kPi) * (float)(g.n_phi / (2.0 * kPi)));
+    pb = pb < 0 ? 0 : (pb >= g.n_phi ? g.n_phi - 1 : pb);
+    return eb * g.n_phi + pb;
+}
+
+// key = ((event * L + layer) * n_bins + bin); counts per key and per (event, layer)
+__global__ void k_hit_count(const IndexGeom g, const tkf_hits h, int *keys, int *counts, int *seg_count, int *var_max,
+                            int *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= h.n) return;
+    const int e = find_event(h.event_off, g.n_events, i);
+    const int l = h.layer[i];
+    if (l < 0 || l >= g.L) {
+        keys[i] = -1;
+        atomicOr(err, kErrBadLayer);
+        return;
+    }
+    const int seg = e * g.L + l;
+    const int key = seg * g.n_bins + hit_bin(g, l, h.x[i], h.y[i], h.z[i]);
+    keys[i] = key;
+    atomicAdd(&counts[key], 1);
+    atomicAdd(&seg_count[seg], 1);
+    atomicMax(&var_max[2 * seg + 0], __float_as_int(fmaxf(h.var_u[i], 0.f)));
+    atomicMax(&var_max[2 * seg + 1], __float_as_int(fmaxf(h.var_v[i], 0.f)));
+}
+
+// exclusive scan of the (event, layer) hit counts, one block
+__global__ void k_seg_scan(const int *seg_count, int *seg_base, int n)
+{
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < n ? seg_count[i] : 0;
+        int x = v;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane == 31) warp_sums[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += t;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const int incl = x + (w > 0 ? warp_sums[w - 1] : 0) + carry;
+        if (i < n) seg_base[i] = incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = incl;
+        __syncthreads();
+    }
+}
+
+// CSR offsets of the bins of one (event, layer) segment per block
+__global__ void k_bin_scan(const int *counts, const int *seg_base, int *bin_off, int n_bins, int n_segs)
+{
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    const int seg = blockIdx.x;
+    if (threadIdx.x == 0) carry = seg_base[seg];
+    __syncthreads();
+    const int *c = counts + (size_t)seg * n_bins;
+    int *o = bin_off + (size_t)seg * n_bins;
+    for (int base = 0; base < n_bins; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < n_bins ? c[i] : 0;
+        int x = v;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += t;
+        }
+        if (lane == 31) warp_sums[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, s, d);
+                if (lane >= d) s += t;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const int incl = x + (w > 0 ? warp_sums[w - 1] : 0) + carry;
+        if (i < n_bins) o[i] = incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = incl;
+        __syncthreads();
+    }
+    if (seg == n_segs - 1 && threadIdx.x == 0) bin_off[(size_t)n_segs * n_bins] = carry;
+}
+
+// place each hit into its bin (order inside a bin fixed afterwards)
+__global__ void k_hit_scatter(const IndexGeom g, const tkf_hits h, const int *keys, int *counts, const int *bin_off,
+                              float4 *hxyzi, float2 *hvar)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= h.n) return;
+    const int key = keys[i];
+    if (key < 0) return;
+    const int slot = atomicSub(&counts[key], 1) - 1;
+    const int pos = bin_off[key] + slot;
+    const int e = key / (g.L * g.n_bins);
+    const int local = i - h.event_off[e];
+    hxyzi[pos] = make_float4(h.x[i], h.y[i], h.z[i], __int_as_float(local));
+    hvar[pos] = make_float2(h.var_u[i], h.var_v[i]);
+}
+
+// sort each bin by event-local hit id (bins hold a handful of hits) and fill pos_of_hit
+__global__ void k_bin_sort(const IndexGeom g, const int *bin_off, const int *ev_off, int n_bins_total, float4 *hxyzi,
+                           float2 *hvar, int *pos_of_hit)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_bins_total) return;
+    const int i0 = bin_off[b], i1 = bin_off[b + 1];
+    if (i1 <= i0) return;
+    for (int i = i0 + 1; i < i1; ++i) {
+        const float4 k4 = hxyzi[i];
+        const float2 k2 = hvar[i];
+        const int key = __float_as_int(k4.w);
+        int j = i - 1;
+        while (j >= i0 && __float_as_int(hxyzi[j].w) > key) {
+            hxyzi[j + 1] = hxyzi[j];
+            hvar[j + 1] = hvar[j];
+            --j;
+        }
+        hxyzi[j + 1] = k4;
+        hvar[j + 1] = k2;
+    }
+    const int e = b / (g.L * g.n_bins);
+    const int base = ev_off[e];
+    for (int i = i0; i < i1; ++i) pos_of_hit[base + __float_as_int(hxyzi[i].w)] = i;
+}
+
+// ------------------------------------------------------------------ seed estimate and fit
+
+struct FitGeom {
+    int L;
+    double radius[TKF_MAX_LAYERS], xx0[TKF_MAX_LAYERS];
+    float radius_f[TKF_MAX_LAYERS], xx0_f[TKF_MAX_LAYERS];
+    double kb, mass, prior[6];
+    float kb_f, mass_f;
+};
+
+template <class R> __device__ __forceinline__ R gpick(float f, double d);
+template <> __device__ __forceinline__ float gpick<float>(float f, double) { return f; }
+template <> __device__ __forceinline__ double gpick<double>(float, double d) { return d; }
+
+// asin(x)/x, accurate near 0
+template <class R> __device__ __forceinline__ R asin_over(R x)
+{
+    if (ab(x) < R(1e-2)) {
+        const R x2 = x * x;
+        return R(1) + x2 * (R(1.0 / 6) + x2 * R(3.0 / 40));
+    }
+    return asn(x) / x;
+}
+
+// Initial state from three hits: signed curvature 2 (P2-P1)x(P3-P2) / (|P2-P1||P3-P2||P3-P1|)
+// (positive for a counter-clockwise turn), tangent at P1 = chord direction P1->P2 turned back by
+// half the subtended angle, transverse arc P1->P3 = chord * asin(k c/2)/(k c/2).
+template <class R>
+__global__ void k_seed(const FitGeom g, const tkf_hits h, const int *seed_hits, tkf_tracks out, int *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= out.n) return;
+    const int h1 = seed_hits[i], h2 = seed_hits[out.stride + i], h3 = seed_hits[2 * out.stride + i];
+    if (h1 < 0 || h2 < 0 || h3 < 0 || h1 >= h.n || h2 >= h.n || h3 >= h.n) {
+        atomicOr(err, kErrBadHitId);
+        out.nhits[i] = TKF_TRACK_SINGULAR;
+        return;
+    }
+    const R x1 = h.x[h1], y1 = h.y[h1], z1 = h.z[h1];
+    const R x2 = h.x[h2], y2 = h.y[h2];
+    const R x3 = h.x[h3], y3 = h.y[h3], z3 = h.z[h3];
+    const R ax = x2 - x1, ay = y2 - y1, bx = x3 - x2, by = y3 - y2, cx = x3 - x1, cy = y3 - y1;
+    const R d12 = sq(ax * ax + ay * ay), d23 = sq(bx * bx + by * by), d13 = sq(cx * cx + cy * cy);
+    const R kappa = R(2) * (ax * by - ay * bx) / (d12 * d23 * d13);
+    R h12 = kappa * d12 * R(0.5), h13 = kappa * d13 * R(0.5);
+    h12 = h12 > R(1) ? R(1) : (h12 < R(-1) ? R(-1) : h12);
+    h13 = h13 > R(1) ? R(1) : (h13 < R(-1) ? R(-1) : h13);
+    const R phi = at2(ay, ax) - asn(h12);
+    const R s13 = d13 * asin_over(h13);
+    const R cot = (z3 - z1) / s13;
+    const R kb = gpick<R>(g.kb_f, g.kb);
+    R *par = (R *)out.par, *cov = (R *)out.cov;
+    const size_t st = out.stride;
+    par[0 * st + i] = x1;
+    par[1 * st + i] = y1;
+    par[2 * st + i] = z1;
+    par[3 * st + i] = -kappa / kb;
+    par[4 * st + i] = wrap_phi(phi);
+    par[5 * st + i] = at2(R(1), cot);
+    for (int k = 0; k < 21; ++k) cov[k * st + i] = R(0);
+    for (int k = 0; k < 6; ++k) cov[sym(k, k) * st + i] = R(g.prior[k] * g.prior[k]);
+    ((R *)out.chi2)[i] = R(0);
+    out.nhits[i] = 0;
+    if (out.hit_idx) {
+        for (int l = 0; l < g.L; ++l) out.hit_idx[l * st + i] = l < 3 ? seed_hits[l * st + i] : -1;
+    }
+}
+
+template <class R, class U>
+__global__ void k_fit(const FitGeom g, const tkf_hits h, const tkf_tracks in, const int *hit_idx, int first, int last,
+                      tkf_tracks out, int *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= in.n) return;
+    const size_t si = in.stride, so = out.stride;
+    R p[6], P[21];
+    const R *ip = (const R *)in.par, *ic = (const R *)in.cov;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[k] = ip[k * si + i];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) P[k] = ic[k * si + i];
+    R chi2 = ((const R *)in.chi2)[i];
+    int nh = in.nhits[i];
+    int status = nh < 0 ? nh : 0;
+    const R kb = gpick<R>(g.kb_f, g.kb), mass = gpick<R>(g.mass_f, g.mass);
+    for (int l = first; l <= last && status == 0; ++l) {
+        if (l > first && !propagate<R>(p, P, gpick<R>(g.radius_f[l], g.radius[l]), kb)) {
+            status = TKF_TRACK_NOREACH;
+            break;
+        }
+        const int hid = hit_idx[l * si + i];
+        if (hid >= h.n) {
+            atomicOr(err, kErrBadHitId);
+            status = TKF_TRACK_SINGULAR;
+            break;
+        }
+        if (hid >= 0) {
+            U dc2;
+            if (!kalman_update<U, R>(p, P, R(h.x[hid]), R(h.y[hid]), R(h.z[hid]), R(h.var_u[hid]), R(h.var_v[hid]),
+                                     &dc2)) {
+                status = TKF_TRACK_SINGULAR;
+                break;
+            }
+            chi2 += R(dc2);
+            nh += 1;
+        }
+        if (l < g.L - 1) scatter<R>(p, P, gpick<R>(g.xx0_f[l], g.xx0[l]), mass);
+    }
+    R *op = (R *)out.par, *oc = (R *)out.cov;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) op[k * so + i] = p[k];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) oc[k * so + i] = P[k];
+    ((R *)out.chi2)[i] = chi2;
+    out.nhits[i] = status ? status : nh;
+    if (out.hit_idx && out.hit_idx != hit_idx)
+        for (int l = 0; l < g.L; ++l) out.hit_idx[l * so + i] = hit_idx[l * si + i];
+}
+
+FitGeom fit_geom(const tkf_ctx *ctx)
+{
+    FitGeom g{};
+    const tkf_config &c = ctx->cfg;
+    g.L = c.n_layers;
+    for (int l = 0; l < c.n_layers; ++l) {
+        g.radius[l] = c.radius[l];
+        g.xx0[l] = c.x_over_x0[l];
+        g.radius_f[l] = (float)c.radius[l];
+        g.xx0_f[l] = (float)c.x_over_x0[l];
+    }
+    g.kb = kCurv * c.bz;
+    g.kb_f = (float)g.kb;
+    g.mass = c.mass;
+    g.mass_f = (float)c.mass;
+    for (int k = 0; k < 6; ++k) g.prior[k] = c.prior_sigma[k];
+    return g;
+}
+
+int check_tracks(tkf_ctx *ctx, const tkf_tracks *t, bool need_hits, const char *name)
+{
+    if (!t) return set_err(ctx, TKF_ERR_INVALID, std::string(name) + " is null");
+    if (t->n < 0 || t->stride < t->n) return set_err(ctx, TKF_ERR_INVALID, std::string(name) + ": need 0 <= n <= stride");
+    if (t->n > 0 && (!t->par || !t->cov || !t->chi2 || !t->nhits))
+        return set_err(ctx, TKF_ERR_INVALID, std::string(name) + ": par, cov, chi2 and nhits are required");
+    if (need_hits && t->n > 0 && !t->hit_idx) return set_err(ctx, TKF_ERR_INVALID, std::string(name) + ": hit_idx is required");
+    return TKF_OK;
+}
+
+int check_hits(tkf_ctx *ctx, const tkf_hits *h)
+{
+    if (!h) return set_err(ctx, TKF_ERR_INVALID, "hits is null");
+    if (h->n < 0 || h->n_events < 1) return set_err(ctx, TKF_ERR_INVALID, "hits: need n >= 0 and n_events >= 1");
+    if (!h->event_off) return set_err(ctx, TKF_ERR_INVALID, "hits: event_off is required");
+    if (h->n > 0 && (!h->x || !h->y || !h->z || !h->var_u || !h->var_v || !h->layer))
+        return set_err(ctx, TKF_ERR_INVALID, "hits: x, y, z, var_u, var_v and layer are required");
+    return TKF_OK;
+}
+
+template <class T> int grow(tkf_ctx *ctx, T **p, size_t n)
+{
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_err(ctx, e, "cudaMalloc (hit index)");
+    }
+    return TKF_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+void tkf_default_config(tkf_config *cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->n_layers = 10;
+    for (int l = 0; l < 10; ++l) {
+        cfg->radius[l] = 4.0 * (l + 1);
+        cfg->x_over_x0[l] = 0.03;
+    }
+    cfg->bz = 3.8;
+    cfg->mass = 0.13957;
+    const double prior[6] = {0.1, 0.1, 1.0, 0.5, 0.05, 0.05};
+    for (int k = 0; k < 6; ++k) cfg->prior_sigma[k] = prior[k];
+    cfg->eta_min = -2.0;
+    cfg->eta_bin_w = 0.1;
+    cfg->n_eta_bins = 40;
+    cfg->n_phi_bins = 63;
+    cfg->chi2_cut = 30.0;
+    cfg->window_margin = 1e-3;
+    cfg->n_cand = 6;
+    cfg->first_build_layer = 3;
+    cfg->precision = TKF_FP32;
+    cfg->seeds_per_block = 0;
+}
+
+const char *tkf_status_string(int status)
+{
+    switch (status) {
+    case TKF_OK: return "ok";
+    case TKF_ERR_INVALID: return "invalid argument";
+    case TKF_ERR_CUDA: return "CUDA error";
+    case TKF_ERR_NOMEM: return "out of device memory";
+    case TKF_ERR_AGAIN: return "busy, try again";
+    case TKF_ERR_TIMEOUT: return "timed out";
+    case TKF_ERR_NOTREADY: return "not ready";
+    case TKF_ERR_KERNEL: return "kernel reported an error";
+    default: return "unknown status";
+    }
+}
+
+int tkf_create(const tkf_config *cfg, tkf_ctx **out)
+{
+    if (!cfg || !out) return TKF_ERR_INVALID;
+    *out = nullptr;
+    const tkf_config &c = *cfg;
+    if (c.n_layers < 4 || c.n_layers > TKF_MAX_LAYERS || c.n_cand < 1 || c.n_cand > TKF_MAX_CAND ||
+        c.first_build_layer < 3 || c.first_build_layer > c.n_layers || c.n_eta_bins < 1 || c.n_phi_bins < 1 ||
+        c.n_eta_bins * c.n_phi_bins > 1 << 20 || !(c.eta_bin_w > 0) || !(c.chi2_cut > 0) || !(c.bz != 0) ||
+        c.precision < TKF_FP32 || c.precision > TKF_FP64 || c.seeds_per_block < 0 || c.window_margin < 0)
+        return TKF_ERR_INVALID;
+    for (int l = 0; l < c.n_layers; ++l)
+        if (!(c.radius[l] > 0) || (l > 0 && !(c.radius[l] > c.radius[l - 1])) || c.x_over_x0[l] < 0) return TKF_ERR_INVALID;
+    tkf_ctx *ctx = new (std::nothrow) tkf_ctx();
+    if (!ctx) return TKF_ERR_NOMEM;
+    ctx->cfg = c;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_tile, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        if (ctx->d_tile) cudaFree(ctx->d_tile);
+        if (ctx->d_err) cudaFree(ctx->d_err);
+        delete ctx;
+        return e == cudaErrorMemoryAllocation ? TKF_ERR_NOMEM : TKF_ERR_CUDA;
+    }
+    *out = ctx;
+    return TKF_OK;
+}
+
+int tkf_destroy(tkf_ctx *ctx)
+{
+    if (!ctx) return TKF_ERR_INVALID;
+    cudaFree(ctx->d_tile);
+    cudaFree(ctx->d_err);
+    delete ctx;
+    return TKF_OK;
+}
+
+const char *tkf_last_error(const tkf_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int tkf_get_config(const tkf_ctx *ctx, tkf_config *out)
+{
+    if (!ctx || !out) return TKF_ERR_INVALID;
+    *out = ctx->cfg;
+    return TKF_OK;
+}
+
+int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out, tkf_stream stream)
+{
+    if (!ctx || !out) return TKF_ERR_INVALID;
+    int st = check_hits(ctx, hits);
+    if (st) return st;
+    const tkf_config &c = ctx->cfg;
+    const int L = c.n_layers, NB = c.n_eta_bins * c.n_phi_bins;
+    const size_t n_segs = (size_t)hits->n_events * L;
+    const size_t n_bins = n_segs * NB;
+    if (n_bins >= (size_t)1 << 31 || n_segs > (1 << 22))
+        return set_err(ctx, TKF_ERR_INVALID, "hit index: too many events for the bin table");
+    tkf_hit_index *idx = *out;
+    const bool fresh = idx == nullptr;
+    if (fresh) {
+        idx = new (std::nothrow) tkf_hit_index();
+        if (!idx) return set_err(ctx, TKF_ERR_NOMEM, "hit index: host allocation failed");
+        idx->ctx = ctx;
+    }
+    const size_t nh = (size_t)hits->n;
+    if (nh > idx->cap_hits || fresh) {
+        const size_t cap = std::max<size_t>(nh, 1);
+        if ((st = grow(ctx, &idx->hxyzi, cap)) || (st = grow(ctx, &idx->hvar, cap)) ||
+            (st = grow(ctx, &idx->pos_of_hit, cap)) || (st = grow(ctx, &idx->keys, cap)))
+            goto fail;
+        idx->cap_hits = cap;
+    }
+    if (n_bins > idx->cap_bins || fresh) {
+        if ((st = grow(ctx, &idx->bin_off, n_bins + 1)) || (st = grow(ctx, &idx->counts, n_bins))) goto fail;
+        idx->cap_bins = n_bins;
+    }
+    if (n_segs > idx->cap_segs || (size_t)hits->n_events + 1 > idx->cap_segs + 1 || fresh) {
+        if ((st = grow(ctx, &idx->seg_count, n_segs)) || (st = grow(ctx, &idx->seg_base, n_segs)) ||
+            (st = grow(ctx, &idx->var_max, n_segs)) || (st = grow(ctx, &idx->ev_off, n_segs + 1)))
+            goto fail;
+        idx->cap_segs = n_segs;
+    }
+    {
+        idx->n = hits->n;
+        idx->n_events = hits->n_events;
+        idx->n_layers = L;
+        idx->n_bins = NB;
+        cudaStream_t s = (cudaStream_t)stream;
+        IndexGeom g{};
+        g.L = L;
+        g.n_eta = c.n_eta_bins;
+        g.n_phi = c.n_phi_bins;
+        g.n_bins = NB;
+        g.n_events = hits->n_events;
+        for (int l = 0; l < L; ++l) g.radius[l] = (float)c.radius[l];
+        g.eta_min = (float)c.eta_min;
+        g.inv_eta_w = (float)(1.0 / c.eta_bin_w);
+        TKF_CUDA(ctx, cudaMemsetAsync(idx->counts, 0, n_bins * sizeof(int), s));
+        TKF_CUDA(ctx, cudaMemsetAsync(idx->seg_count, 0, n_segs * sizeof(int), s));
+        TKF_CUDA(ctx, cudaMemsetAsync(idx->var_max, 0, n_segs * sizeof(float2), s));
+        TKF_CUDA(ctx, cudaMemcpyAsync(idx->ev_off, hits->event_off, (hits->n_events + 1) * sizeof(int),
+                                      cudaMemcpyDeviceToDevice, s));
+        if (hits->n > 0) {
+            const int nb = (hits->n + 255) / 256;
+            k_hit_count<<<nb, 256, 0, s>>>(g, *hits, idx->keys, idx->counts, idx->seg_count, (int *)idx->var_max,
+                                           ctx->d_err);
+        }
+        k_seg_scan<<<1, 1024, 0, s>>>(idx->seg_count, idx->seg_base, (int)n_segs);
+        k_bin_scan<<<(unsigned)n_segs, 256, 0, s>>>(idx->counts, idx->seg_base, idx->bin_off, NB, (int)n_segs);
+        if (hits->n > 0) {
+            const int nb = (hits->n + 255) / 256;
+            k_hit_scatter<<<nb, 256, 0, s>>>(g, *hits, idx->keys, idx->counts, idx->bin_off, idx->hxyzi, idx->hvar);
+        }
+        k_bin_sort<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(g, idx->bin_off, idx->ev_off, (int)n_bins,
+                                                                     idx->hxyzi, idx->hvar, idx->pos_of_hit);
+        TKF_CUDA(ctx, cudaGetLastError());
+    }
+    *out = idx;
+    return TKF_OK;
+fail:
+    if (fresh) {
+        tkf_hit_index_free(idx);
+    }
+    return st;
+}
+
+int tkf_hit_index_free(tkf_hit_index *idx)
+{
+    if (!idx) return TKF_ERR_INVALID;
+    cudaFree(idx->hxyzi);
+    cudaFree(idx->hvar);
+    cudaFree(idx->pos_of_hit);
+    cudaFree(idx->keys);
+    cudaFree(idx->bin_off);
+    cudaFree(idx->counts);
+    cudaFree(idx->seg_count);
+    cudaFree(idx->seg_base);
+    cudaFree(idx->var_max);
+    cudaFree(idx->ev_off);
+    delete idx;
+    return TKF_OK;
+}
+
+int tkf_hit_index_get_view(const tkf_hit_index *idx, tkf_hit_index_view *v)
+{
+    if (!idx || !v) return TKF_ERR_INVALID;
+    v->hit_xyzi = (const float *)idx->hxyzi;
+    v->hit_var = (const float *)idx->hvar;
+    v->pos_of_hit = idx->pos_of_hit;
+    v->bin_off = idx->bin_off;
+    v->var_max = (const float *)idx->var_max;
+    v->event_off = idx->ev_off;
+    v->n = idx->n;
+    v->n_events = idx->n_events;
+    v->n_layers = idx->n_layers;
+    v->n_bins = idx->n_bins;
+    return TKF_OK;
+}
+
+int tkf_seed_state(tkf_ctx *ctx, const tkf_hits *hits, const int32_t *seed_hits, tkf_tracks *out, tkf_stream stream)
+{
+    if (!ctx) return TKF_ERR_INVALID;
+    int st = check_hits(ctx, hits);
+    if (st || (st = check_tracks(ctx, out, false, "out"))) return st;
+    if (out->n > 0 && !seed_hits) return set_err(ctx, TKF_ERR_INVALID, "seed_hits is null");
+    if (out->n == 0) return TKF_OK;
+    const FitGeom g = fit_geom(ctx);
+    const int nb = (out->n + 127) / 128;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (ctx->cfg.precision == TKF_FP64)
+        k_seed<double><<<nb, 128, 0, s>>>(g, *hits, seed_hits, *out, ctx->d_err);
+    else
+        k_seed<float><<<nb, 128, 0, s>>>(g, *hits, seed_hits, *out, ctx->d_err);
+    TKF_CUDA(ctx, cudaGetLastError());
+    return TKF_OK;
+}
+
+int tkf_fit(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx, int32_t first_layer,
+            int32_t last_layer, tkf_tracks *out, tkf_stream stream)
+{
+    if (!ctx) return TKF_ERR_INVALID;
+    int st = check_hits(ctx, hits);
+    if (st || (st = check_tracks(ctx, init, hit_idx == nullptr, "init")) || (st = check_tracks(ctx, out, false, "out")))
+        return st;
+    if (out->n != init->n) return set_err(ctx, TKF_ERR_INVALID, "out->n must equal init->n");
+    if (first_layer < 0 || last_layer < first_layer || last_layer >= ctx->cfg.n_layers)
+        return set_err(ctx, TKF_ERR_INVALID, "need 0 <= first_layer <= last_layer < n_layers");
+    if (init->n == 0) return TKF_OK;
+    const int32_t *hidx = hit_idx ? hit_idx : init->hit_idx;
+    const FitGeom g = fit_geom(ctx);
+    const int nb = (init->n + 127) / 128;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (ctx->cfg.precision) {
+    case TKF_FP32: k_fit<float, float><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, *out, ctx->d_err); break;
+    case TKF_MIXED: k_fit<float, double><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, *out, ctx->d_err); break;
+    default: k_fit<double, double><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, *out, ctx->d_err); break;
+    }
+    TKF_CUDA(ctx, cudaGetLastError());
+    return TKF_OK;
+}
+
+int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *seeds, tkf_tracks *out,
+                     tkf_tracks *out_all, int32_t *n_cand_out, tkf_stream stream)
+{
+    if (!ctx) return TKF_ERR_INVALID;
+    if (!idx) return set_err(ctx, TKF_ERR_INVALID, "hit index is null");
+    const tkf_config &c = ctx->cfg;
+    int st = check_tracks(ctx, seeds, false, "seeds");
+    if (st || (st = check_tracks(ctx, out, false, "out"))) return st;
+    if (out->stride < seeds->n) return set_err(ctx, TKF_ERR_INVALID, "out->stride < seeds->n");
+    if (out_all && ((st = check_tracks(ctx, out_all, false, "out_all")) ||
+                    (size_t)out_all->stride < (size_t)seeds->n * c.n_cand))
+        return st ? st : set_err(ctx, TKF_ERR_INVALID, "out_all->stride < seeds->n * n_cand");
+    if (idx->n_layers != c.n_layers || idx->n_bins != c.n_eta_bins * c.n_phi_bins)
+        return set_err(ctx, TKF_ERR_INVALID, "hit index built with another geometry");
+    if (seeds->n == 0) return TKF_OK;
+    BuildArgs a{};
+    a.L = c.n_layers;
+    a.first = c.first_build_layer;
+    a.ncand = c.n_cand;
+    a.n_eta = c.n_eta_bins;
+    a.n_phi = c.n_phi_bins;
+    a.n_bins = c.n_eta_bins * c.n_phi_bins;
+    a.seeds_per_block = c.seeds_per_block > 0 ? c.seeds_per_block : 64;
+    a.n_seeds = seeds->n;
+    a.n_events = idx->n_events;
+    for (int l = 0; l < c.n_layers; ++l) {
+        a.radius[l] = c.radius[l];
+        a.xx0[l] = c.x_over_x0[l];
+        a.radius_f[l] = (float)c.radius[l];
+        a.xx0_f[l] = (float)c.x_over_x0[l];
+    }
+    a.kb = kCurv * c.bz;
+    a.mass = c.mass;
+    a.eta_min = c.eta_min;
+    a.inv_eta_w = 1.0 / c.eta_bin_w;
+    a.cut = c.chi2_cut;
+    a.margin = c.window_margin;
+    a.kb_f = (float)a.kb;
+    a.mass_f = (float)a.mass;
+    a.eta_min_f = (float)a.eta_min;
+    a.inv_eta_w_f = (float)a.inv_eta_w;
+    a.cut_f = (float)a.cut;
+    a.margin_f = (float)a.margin;
+    a.hxyzi = idx->hxyzi;
+    a.hvar = idx->hvar;
+    a.pos_of_hit = idx->pos_of_hit;
+    a.bin_off = idx->bin_off;
+    a.var_max = idx->var_max;
+    a.ev_off = idx->ev_off;
+    a.s_par = seeds->par;
+    a.s_cov = seeds->cov;
+    a.s_chi2 = seeds->chi2;
+    a.s_nhits = seeds->nhits;
+    a.s_hit = seeds->hit_idx;
+    a.s_event = seeds->event;
+    a.s_stride = seeds->stride;
+    a.o_par = out->par;
+    a.o_cov = out->cov;
+    a.o_chi2 = out->chi2;
+    a.o_nhits = out->nhits;
+    a.o_hit = out->hit_idx;
+    a.o_stride = out->stride;
+    if (out_all) {
+        a.a_par = out_all->par;
+        a.a_cov = out_all->cov;
+        a.a_chi2 = out_all->chi2;
+        a.a_nhits = out_all->nhits;
+        a.a_hit = out_all->hit_idx;
+        a.a_stride = out_all->stride;
+    }
+    a.n_cand_out = n_cand_out;
+    a.tile_counter = ctx->d_tile;
+    a.err = ctx->d_err;
+    const int nmax = build_nmax(c.n_cand);
+    auto launch = c.precision == TKF_FP32 ? launch_build_fp32 : c.precision == TKF_MIXED ? launch_build_mixed : launch_build_fp64;
+    int occ = 0;
+    TKF_CUDA(ctx, launch(a, nmax, 0, nullptr, &occ));
+    const long long tiles = ((long long)seeds->n + a.seeds_per_block - 1) / a.seeds_per_block;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)std::max(occ, 1) * ctx->sm_count));
+    cudaStream_t s = (cudaStream_t)stream;
+    TKF_CUDA(ctx, cudaMemsetAsync(ctx->d_tile, 0, sizeof(int), s));
+    TKF_CUDA(ctx, launch(a, nmax, grid, s, nullptr));
+    TKF_CUDA(ctx, cudaGetLastError());
+    return TKF_OK;
+}
+
+int tkf_sync_status(tkf_ctx *ctx, tkf_stream stream)
+{
+    if (!ctx) return TKF_ERR_INVALID;
+    TKF_CUDA(ctx, cudaStreamSynchronize((cudaStream_t)stream));
+    int e = 0;
+    TKF_CUDA(ctx, cudaMemcpy(&e, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        TKF_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "kernel error bits 0x%x (1: hit layer out of range, 2: hit id out of range, 8: seed event out of range)", e);
+        return set_err(ctx, TKF_ERR_KERNEL, buf);
+    }
+    return TKF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,279 @@
+"""Python binding of libtkf.so (include/tkf.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module only turns torch
+tensors into the C structs of the ABI and checks status codes.  It raises if the library
+has not been built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from dataclasses import dataclass
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libtkf.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "tkf.h")
+
+MAX_LAYERS = 16
+MAX_CAND = 16
+FP32, MIXED, FP64 = 0, 1, 2
+OK, ERR_INVALID, ERR_CUDA, ERR_NOMEM, ERR_AGAIN, ERR_TIMEOUT, ERR_NOTREADY, ERR_KERNEL = range(8)
+TRACK_NOREACH, TRACK_SINGULAR, TRACK_LOST = -1, -2, -3
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("n_layers", C.c_int32),
+        ("radius", C.c_double * MAX_LAYERS),
+        ("x_over_x0", C.c_double * MAX_LAYERS),
+        ("bz", C.c_double),
+        ("mass", C.c_double),
+        ("prior_sigma", C.c_double * 6),
+        ("eta_min", C.c_double),
+        ("eta_bin_w", C.c_double),
+        ("n_eta_bins", C.c_int32),
+        ("n_phi_bins", C.c_int32),
+        ("chi2_cut", C.c_double),
+        ("window_margin", C.c_double),
+        ("n_cand", C.c_int32),
+        ("first_build_layer", C.c_int32),
+        ("precision", C.c_int32),
+        ("seeds_per_block", C.c_int32),
+    ]
+
+
+class Hits(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("var_u", C.c_void_p),
+                ("var_v", C.c_void_p), ("layer", C.c_void_p), ("event_off", C.c_void_p),
+                ("n", C.c_int32), ("n_events", C.c_int32)]
+
+
+class Tracks(C.Structure):
+    _fields_ = [("par", C.c_void_p), ("cov", C.c_void_p), ("chi2", C.c_void_p), ("nhits", C.c_void_p),
+                ("hit_idx", C.c_void_p), ("event", C.c_void_p), ("n", C.c_int32), ("stride", C.c_int32)]
+
+
+class HitIndexView(C.Structure):
+    _fields_ = [("hit_xyzi", C.c_void_p), ("hit_var", C.c_void_p), ("pos_of_hit", C.c_void_p),
+                ("bin_off", C.c_void_p), ("var_max", C.c_void_p), ("event_off", C.c_void_p),
+                ("n", C.c_int32), ("n_events", C.c_int32), ("n_layers", C.c_int32), ("n_bins", C.c_int32)]
+
+
+_lib = None
+
+
+def declared_functions() -> list[str]:
+    """Names of every function declared in include/tkf.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(tkf_\w+)\s*\(", text, flags=re.M)))
+
+
+def lib():
+    """Loads libtkf.so (built by paper_1702_06359_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtkf.so is not built (%s); run `python -c 'import __graft_entry__ as g; "
+                               "g.build()'` -- there is no CPU fallback" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        vp, i32 = C.c_void_p, C.c_int32
+        L.tkf_default_config.argtypes = [C.POINTER(Config)]
+        L.tkf_default_config.restype = None
+        L.tkf_create.argtypes = [C.POINTER(Config), C.POINTER(vp)]
+        L.tkf_destroy.argtypes = [vp]
+        L.tkf_last_error.argtypes = [vp]
+        L.tkf_last_error.restype = C.c_char_p
+        L.tkf_status_string.argtypes = [C.c_int]
+        L.tkf_status_string.restype = C.c_char_p
+        L.tkf_get_config.argtypes = [vp, C.POINTER(Config)]
+        L.tkf_build_hit_index.argtypes = [vp, C.POINTER(Hits), C.POINTER(vp), vp]
+        L.tkf_hit_index_free.argtypes = [vp]
+        L.tkf_hit_index_get_view.argtypes = [vp, C.POINTER(HitIndexView)]
+        L.tkf_seed_state.argtypes = [vp, C.POINTER(Hits), vp, C.POINTER(Tracks), vp]
+        L.tkf_fit.argtypes = [vp, C.POINTER(Hits), C.POINTER(Tracks), vp, i32, i32, C.POINTER(Tracks), vp]
+        L.tkf_build_tracks.argtypes = [vp, vp, C.POINTER(Tracks), C.POINTER(Tracks), C.POINTER(Tracks), vp, vp]
+        L.tkf_sync_status.argtypes = [vp, vp]
+        for name in declared_functions():
+            getattr(L, name).restype = getattr(L, name).restype if name in (
+                "tkf_last_error", "tkf_status_string", "tkf_default_config") else C.c_int
+        _lib = L
+    return _lib
+
+
+class TkfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (lib().tkf_status_string(code).decode(), code, msg))
+        self.code = code
+
+
+def default_config(**kw) -> Config:
+    cfg = Config()
+    lib().tkf_default_config(C.byref(cfg))
+    for k, v in kw.items():
+        if k in ("radius", "x_over_x0", "prior_sigma"):
+            arr = getattr(cfg, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class DeviceHits:
+    """Hits of a batch of events as torch CUDA tensors (float32 x, y, z, var_u, var_v; int32
+    layer; int32 event_off with n_events + 1 entries)."""
+
+    x: object
+    y: object
+    z: object
+    var_u: object
+    var_v: object
+    layer: object
+    event_off: object
+
+    def struct(self) -> Hits:
+        h = Hits()
+        h.x, h.y, h.z = self.x.data_ptr(), self.y.data_ptr(), self.z.data_ptr()
+        h.var_u, h.var_v = self.var_u.data_ptr(), self.var_v.data_ptr()
+        h.layer, h.event_off = self.layer.data_ptr(), self.event_off.data_ptr()
+        h.n = self.x.numel()
+        h.n_events = self.event_off.numel() - 1
+        return h
+
+
+@dataclass
+class DeviceTracks:
+    """Track SoA planes as torch tensors: par [6, stride], cov [21, stride], chi2 [stride],
+    nhits [stride] int32, hit_idx [n_layers, stride] int32, event [stride] int32."""
+
+    par: object
+    cov: object
+    chi2: object
+    nhits: object
+    hit_idx: object = None
+    event: object = None
+    n: int = -1
+
+    @staticmethod
+    def empty(n, n_layers, precision=FP32, device="cuda", stride=None):
+        import torch
+        stride = n if stride is None else stride
+        dt = torch.float64 if precision == FP64 else torch.float32
+        return DeviceTracks(
+            par=torch.zeros((6, stride), dtype=dt, device=device),
+            cov=torch.zeros((21, stride), dtype=dt, device=device),
+            chi2=torch.zeros(stride, dtype=dt, device=device),
+            nhits=torch.zeros(stride, dtype=torch.int32, device=device),
+            hit_idx=torch.full((n_layers, stride), -1, dtype=torch.int32, device=device),
+            event=torch.zeros(stride, dtype=torch.int32, device=device),
+            n=n,
+        )
+
+    @property
+    def stride(self):
+        return self.par.shape[1]
+
+    def struct(self) -> Tracks:
+        t = Tracks()
+        t.par, t.cov, t.chi2 = self.par.data_ptr(), self.cov.data_ptr(), self.chi2.data_ptr()
+        t.nhits = self.nhits.data_ptr()
+        t.hit_idx = self.hit_idx.data_ptr() if self.hit_idx is not None else None
+        t.event = self.event.data_ptr() if self.event is not None else None
+        t.stride = self.stride
+        t.n = self.stride if self.n < 0 else self.n
+        return t
+
+
+class HitIndex:
+    def __init__(self, ctx, handle):
+        self.ctx, self.handle = ctx, handle
+
+    def view(self) -> HitIndexView:
+        v = HitIndexView()
+        self.ctx._check(lib().tkf_hit_index_get_view(self.handle, C.byref(v)))
+        return v
+
+    def free(self):
+        if self.handle:
+            lib().tkf_hit_index_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """A tkf_ctx on the current CUDA device."""
+
+    def __init__(self, cfg: Config | None = None, **kw):
+        self.cfg = cfg if cfg is not None else default_config(**kw)
+        h = C.c_void_p()
+        code = lib().tkf_create(C.byref(self.cfg), C.byref(h))
+        if code != OK:
+            raise TkfError(code, "tkf_create")
+        self.handle = h
+
+    def _check(self, code):
+        if code != OK:
+            raise TkfError(code, lib().tkf_last_error(self.handle).decode())
+
+    def config(self) -> Config:
+        c = Config()
+        self._check(lib().tkf_get_config(self.handle, C.byref(c)))
+        return c
+
+    def build_hit_index(self, hits: DeviceHits, reuse: HitIndex | None = None, stream=None) -> HitIndex:
+        hs = hits.struct()
+        h = C.c_void_p(reuse.handle if reuse is not None else None)
+        self._check(lib().tkf_build_hit_index(self.handle, C.byref(hs), C.byref(h), _stream(stream)))
+        if reuse is not None:
+            reuse.handle = h.value
+            return reuse
+        return HitIndex(self, h.value)
+
+    def seed_state(self, hits: DeviceHits, seed_hits, out: DeviceTracks, stream=None):
+        hs, ts = hits.struct(), out.struct()
+        self._check(lib().tkf_seed_state(self.handle, C.byref(hs), _ptr(seed_hits), C.byref(ts), _stream(stream)))
+
+    def fit(self, hits: DeviceHits, init: DeviceTracks, first, last, out: DeviceTracks, hit_idx=None, stream=None):
+        hs, ti, to = hits.struct(), init.struct(), out.struct()
+        self._check(lib().tkf_fit(self.handle, C.byref(hs), C.byref(ti), _ptr(hit_idx), int(first), int(last),
+                                  C.byref(to), _stream(stream)))
+
+    def build_tracks(self, index: HitIndex, seeds: DeviceTracks, out: DeviceTracks, out_all: DeviceTracks = None,
+                     n_cand_out=None, stream=None):
+        ss, so = seeds.struct(), out.struct()
+        sa = C.byref(out_all.struct()) if out_all is not None else None
+        self._check(lib().tkf_build_tracks(self.handle, index.handle, C.byref(ss), C.byref(so), sa, _ptr(n_cand_out),
+                                           _stream(stream)))
+
+    def sync_status(self, stream=None):
+        self._check(lib().tkf_sync_status(self.handle, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tkf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

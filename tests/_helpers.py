@@ -43,3 +43,30 @@ def rotate_into_jet(batch, width=0.05, seed=0):
 
 def small_event(det, seed, n_tracks, noise_frac, **kw):
     return generate(EventSpec(seed=seed, n_events=1, n_tracks=n_tracks, noise_frac=noise_frac, **kw), det)
+
+
+def select_events(batch, events):
+    """A new batch made of the listed events of `batch` (repeats allowed), re-indexed."""
+    import copy
+    hs, ts = [], []
+    hit_off, trk_off = [0], [0]
+    for e in events:
+        h0, h1 = batch.hit_off[e], batch.hit_off[e + 1]
+        t0, t1 = batch.trk_off[e], batch.trk_off[e + 1]
+        hs.append((h0, h1, hit_off[-1]))
+        ts.append((t0, t1, trk_off[-1], hit_off[-1] - h0))
+        hit_off.append(hit_off[-1] + h1 - h0)
+        trk_off.append(trk_off[-1] + t1 - t0)
+    out = copy.copy(batch)
+    cat = lambda a: np.concatenate([a[h0:h1] for h0, h1, _ in hs])
+    for k in ("x", "y", "z", "var_u", "var_v", "layer"):
+        setattr(out, k, cat(getattr(batch, k)))
+    out.mc = np.concatenate([np.where(batch.mc[h0:h1] >= 0, batch.mc[h0:h1] - batch.trk_off[e] + trk_off[i], -1)
+                             for i, ((h0, h1, _), e) in enumerate(zip(hs, events))])
+    out.trk_hits = np.concatenate([np.where(batch.trk_hits[t0:t1] >= 0, batch.trk_hits[t0:t1] + shift, -1)
+                                   for t0, t1, _, shift in ts])
+    out.truth = np.concatenate([batch.truth[t0:t1] for t0, t1, _, _ in ts])
+    out.trk_event = np.repeat(np.arange(len(events)), [t1 - t0 for t0, t1, _, _ in ts])
+    out.hit_off = np.asarray(hit_off, dtype=np.int64)
+    out.trk_off = np.asarray(trk_off, dtype=np.int64)
+    return out
