@@ -60,6 +60,7 @@ class EventSpec:
     smear: bool = True
     shuffle_hits: bool = True
     keep_f64: bool = False  # also keep the unrounded FP64 hit positions in extras["xyz64"]
+    first_event: int = 0    # events first_event .. first_event + n_events - 1 of the run
 
 
 @dataclass
@@ -126,16 +127,15 @@ def _helix_to_cylinder(x, y, z, w, phi, theta, radius, kb):
     cphi, sphi = np.cos(phi), np.sin(phi)
     a = x * cphi + y * sphi
     s = -a + np.sqrt(np.maximum(a * a + radius * radius - (x * x + y * y), 0.0))
-    for _ in range(60):
+    # a fixed number of iterations (quadratic convergence from the straight-line start needs
+    # about four) keeps every track's result independent of which tracks share the array
+    for _ in range(8):
         ang = phi + kappa * s
         xs = x + (np.sin(ang) - sphi) / kappa
         ys = y - (np.cos(ang) - cphi) / kappa
         g = xs * xs + ys * ys - radius * radius
         dg = 2.0 * (xs * np.cos(ang) + ys * np.sin(ang))
-        step = g / dg
-        s = s - step
-        if np.all(np.abs(step) < 1e-13 * (1.0 + np.abs(s))):
-            break
+        s = s - g / dg
     ang = phi + kappa * s
     xs = x + (np.sin(ang) - sphi) / kappa
     ys = y - (np.cos(ang) - cphi) / kappa
@@ -166,7 +166,7 @@ def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
     T = int(trk_off[-1])
     trk_event = np.repeat(np.arange(n_ev, dtype=np.int64), n_trk)
     trk_local = np.arange(T, dtype=np.int64) - trk_off[trk_event]
-    key = (np.uint64(spec.seed), trk_event.astype(np.uint64))
+    key = (np.uint64(spec.seed), (trk_event + spec.first_event).astype(np.uint64))
     tl = trk_local.astype(np.uint64)
 
     # --- kinematics at the vertex
@@ -224,7 +224,7 @@ def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
         t0, t1 = int(trk_off[e]), int(trk_off[e + 1])
         nt = t1 - t0
         base = int(hit_off[e])
-        ekey = (np.uint64(spec.seed), np.uint64(e))
+        ekey = (np.uint64(spec.seed), np.uint64(e + spec.first_event))
         for l in range(L):
             R = det.radii[l]
             n_noise = int(np.rint(noise_frac[e] * nt))
@@ -267,3 +267,25 @@ def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
         vertex_state=vertex_state, extras=extras,
     )
     return batch
+
+
+def concat(batches):
+    """One batch holding the events of several batches in order (hit and track ids re-based)."""
+    b0 = batches[0]
+    hit_base = np.cumsum([0] + [b.n_hits for b in batches])
+    trk_base = np.cumsum([0] + [b.n_tracks for b in batches])
+    ev_base = np.cumsum([0] + [b.n_events for b in batches])
+    cat = lambda k: np.concatenate([getattr(b, k) for b in batches])
+    extras = {}
+    if all("xyz64" in b.extras for b in batches):
+        extras["xyz64"] = np.concatenate([b.extras["xyz64"] for b in batches])
+    return EventBatch(
+        detector=b0.detector, spec=b0.spec,
+        hit_off=np.concatenate([[0]] + [b.hit_off[1:] + hb for b, hb in zip(batches, hit_base)]),
+        trk_off=np.concatenate([[0]] + [b.trk_off[1:] + tb for b, tb in zip(batches, trk_base)]),
+        x=cat("x"), y=cat("y"), z=cat("z"), var_u=cat("var_u"), var_v=cat("var_v"), layer=cat("layer"),
+        mc=np.concatenate([np.where(b.mc >= 0, b.mc + tb, -1) for b, tb in zip(batches, trk_base)]),
+        trk_event=np.concatenate([b.trk_event + eb for b, eb in zip(batches, ev_base)]),
+        trk_hits=np.concatenate([np.where(b.trk_hits >= 0, b.trk_hits + hb, -1) for b, hb in zip(batches, hit_base)]),
+        truth=cat("truth"), truth_after=cat("truth_after"), vertex_state=cat("vertex_state"), extras=extras,
+    )

@@ -50,3 +50,15 @@ def test_event_sizes_recipe():
     assert np.all((f >= 0.2) & (f <= 0.5))
     inner = n[(n > 200) & (n < 20000)]
     assert abs(np.std(np.log(inner)) - 0.8) < 0.05
+
+
+def test_events_generated_in_chunks_equal_one_batch(det):
+    from synth import concat
+    n = [30, 0, 45, 12, 60]
+    whole = generate(EventSpec(seed=8, n_events=5, n_tracks=n, noise_frac=0.3), det)
+    parts = [generate(EventSpec(seed=8, n_events=2, n_tracks=n[0:2], noise_frac=0.3), det),
+             generate(EventSpec(seed=8, n_events=3, n_tracks=n[2:5], noise_frac=0.3, first_event=2), det)]
+    c = concat(parts)
+    for k in ("hit_off", "trk_off", "x", "y", "z", "layer", "mc", "trk_event", "trk_hits"):
+        assert np.array_equal(getattr(c, k), getattr(whole, k)), k
+    assert np.array_equal(c.truth, whole.truth)
