@@ -45,7 +45,8 @@ enum tkf_status_code {
     TKF_ERR_AGAIN = 4,    /* queue or device-memory budget full: retry later */
     TKF_ERR_TIMEOUT = 5,  /* a bounded wait ran out */
     TKF_ERR_NOTREADY = 6, /* result not available yet */
-    TKF_ERR_KERNEL = 7    /* a kernel reported an internal error word */
+    TKF_ERR_KERNEL = 7,   /* a kernel reported an internal error word */
+    TKF_ERR_TOO_LARGE = 8 /* input exceeds the fixed capacity of tkf_build_hit_index_noalloc */
 };
 
 /* Arithmetic of the KF steps.  FP32: everything in float.  MIXED: float, except the
@@ -178,6 +179,46 @@ int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *s
 /* Waits for `stream` and reports errors raised by kernels of this context since the last
  * call (TKF_ERR_KERNEL with text in tkf_last_error), or a CUDA error (TKF_ERR_CUDA). */
 int tkf_sync_status(tkf_ctx *ctx, tkf_stream stream);
+
+/* ---------------------------------------------------------------- allocation-free variant */
+
+/* Caller-owned output arrays of tkf_build_hit_index_noalloc (device memory), laid out as in
+ * tkf_hit_index_view: hit_xyzi [n][4], hit_var [n][2], pos_of_hit [n],
+ * bin_off [n_events * n_layers * n_bins + 1], var_max [n_events * n_layers][2],
+ * event_off [n_events + 1], with n_bins = n_eta_bins * n_phi_bins. */
+typedef struct {
+    float *hit_xyzi, *hit_var;
+    int32_t *pos_of_hit, *bin_off;
+    float *var_max;
+    int32_t *event_off;
+} tkf_hit_index_out;
+
+/* Capacity of the fixed scratch of tkf_build_hit_index_noalloc. */
+#define TKF_NOALLOC_MAX_HITS (1 << 20)      /* hits per call */
+#define TKF_NOALLOC_MAX_BINS (1 << 18)      /* n_events * n_layers * n_eta_bins * n_phi_bins */
+#define TKF_NOALLOC_MAX_SEGMENTS 1024       /* n_events * n_layers */
+
+/* The same hit index as tkf_build_hit_index, written into caller-owned arrays, for callers
+ * that cannot allocate device memory: code running where cudaMalloc is not allowed or not
+ * wanted (inside another framework's memory pool, in a process whose device memory is fully
+ * reserved up front, or where an allocation could block or fail in the middle of a time-
+ * critical trigger path).  The paper has no counterpart; this is an interface addition.
+ *
+ * It allocates nothing: no cudaMalloc, cudaFree or allocating library call, and it needs no
+ * tkf_ctx.  Its temporary work space is one fixed array in the library's own device memory
+ * (TKF_NOALLOC_MAX_HITS + TKF_NOALLOC_MAX_BINS + 2 * TKF_NOALLOC_MAX_SEGMENTS int32, about
+ * 5 MB), which every GPU that loads libtkf.so keeps until the process exits.  Inputs larger
+ * than that capacity are rejected with TKF_ERR_TOO_LARGE before any work is queued.
+ *
+ * The first call on a device looks up the device address of that array (with that device
+ * current); make that first call before capturing a stream into a CUDA graph.  All calls
+ * share the one array and the call clears what must start at zero, so calls may follow each
+ * other freely on one stream, but calls whose work overlaps on the GPU (other streams, other
+ * host threads) race on it and must be serialised by the caller.  Kernel-side errors (a hit
+ * layer out of range) are not reported; validate inputs beforehand.
+ * Errors: TKF_ERR_INVALID (bad configuration or arguments), TKF_ERR_TOO_LARGE, TKF_ERR_CUDA. */
+int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits *hits, const tkf_hit_index_out *out,
+                                tkf_stream stream);
 
 #ifdef __cplusplus
 }

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -420,6 +421,7 @@ const char *tkf_status_string(int status)
     case TKF_ERR_TIMEOUT: return "timed out";
     case TKF_ERR_NOTREADY: return "not ready";
     case TKF_ERR_KERNEL: return "kernel reported an error";
+    case TKF_ERR_TOO_LARGE: return "input exceeds the fixed capacity of the allocation-free entry point";
     default: return "unknown status";
     }
 }
@@ -728,4 +730,92 @@ int tkf_sync_status(tkf_ctx *ctx, tkf_stream stream)
     return TKF_OK;
 }
 
+// ---------------------------------------------------------------- allocation-free hit index
+//
+// Scratch of tkf_build_hit_index_noalloc: per-hit bin keys, per-bin counters, per-segment
+// totals and bases, and one error word, in a fixed array of the library's device memory.
+
 }  // extern "C"
+
+namespace {
+
+constexpr size_t kNoallocWords =
+    (size_t)TKF_NOALLOC_MAX_HITS + TKF_NOALLOC_MAX_BINS + 2 * (size_t)TKF_NOALLOC_MAX_SEGMENTS + 64;
+static __device__ __align__(256) int g_noalloc_scratch[kNoallocWords];
+
+// Device address of g_noalloc_scratch per device, looked up once with that device current.
+std::mutex g_noalloc_mutex;
+int *g_noalloc_addr[64] = {};
+
+int noalloc_scratch(int **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TKF_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        int *p = nullptr;
+        if (cudaGetSymbolAddress((void **)&p, g_noalloc_scratch) != cudaSuccess || !p) return TKF_ERR_CUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return TKF_OK;
+}
+
+}  // namespace
+
+extern "C" int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits *hits, const tkf_hit_index_out *out,
+                                           tkf_stream stream)
+{
+    if (!cfg || !hits || !out) return TKF_ERR_INVALID;
+    const tkf_config &c = *cfg;
+    if (c.n_layers < 1 || c.n_layers > TKF_MAX_LAYERS || c.n_eta_bins < 1 || c.n_phi_bins < 1 ||
+        !(c.eta_bin_w > 0))
+        return TKF_ERR_INVALID;
+    for (int l = 0; l < c.n_layers; ++l)
+        if (!(c.radius[l] > 0)) return TKF_ERR_INVALID;
+    if (hits->n < 0 || hits->n_events < 1 || !hits->event_off) return TKF_ERR_INVALID;
+    if (hits->n > 0 && (!hits->x || !hits->y || !hits->z || !hits->var_u || !hits->var_v || !hits->layer))
+        return TKF_ERR_INVALID;
+    if (!out->hit_xyzi || !out->hit_var || !out->pos_of_hit || !out->bin_off || !out->var_max || !out->event_off)
+        return TKF_ERR_INVALID;
+    const int L = c.n_layers, NB = c.n_eta_bins * c.n_phi_bins;
+    const size_t n_segs = (size_t)hits->n_events * L;
+    const size_t n_bins = n_segs * NB;
+    if ((size_t)hits->n > TKF_NOALLOC_MAX_HITS || n_bins > TKF_NOALLOC_MAX_BINS || n_segs > TKF_NOALLOC_MAX_SEGMENTS)
+        return TKF_ERR_TOO_LARGE;
+    int *scratch = nullptr;
+    int st = noalloc_scratch(&scratch);
+    if (st) return st;
+    int *keys = scratch;
+    int *counts = keys + TKF_NOALLOC_MAX_HITS;
+    int *seg_count = counts + TKF_NOALLOC_MAX_BINS;
+    int *seg_base = seg_count + TKF_NOALLOC_MAX_SEGMENTS;
+    int *err = seg_base + TKF_NOALLOC_MAX_SEGMENTS;
+    IndexGeom g{};
+    g.L = L;
+    g.n_eta = c.n_eta_bins;
+    g.n_phi = c.n_phi_bins;
+    g.n_bins = NB;
+    g.n_events = hits->n_events;
+    for (int l = 0; l < L; ++l) g.radius[l] = (float)c.radius[l];
+    g.eta_min = (float)c.eta_min;
+    g.inv_eta_w = (float)(1.0 / c.eta_bin_w);
+    cudaStream_t s = (cudaStream_t)stream;
+    float4 *hxyzi = (float4 *)out->hit_xyzi;
+    float2 *hvar = (float2 *)out->hit_var;
+    if (cudaMemsetAsync(counts, 0, n_bins * sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(seg_count, 0, n_segs * sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(out->var_max, 0, n_segs * 2 * sizeof(float), s) != cudaSuccess ||
+        cudaMemcpyAsync(out->event_off, hits->event_off, (hits->n_events + 1) * sizeof(int), cudaMemcpyDeviceToDevice,
+                        s) != cudaSuccess)
+        return TKF_ERR_CUDA;
+    if (hits->n > 0)
+        k_hit_count<<<(hits->n + 255) / 256, 256, 0, s>>>(g, *hits, keys, counts, seg_count, (int *)out->var_max, err);
+    k_seg_scan<<<1, 1024, 0, s>>>(seg_count, seg_base, (int)n_segs);
+    k_bin_scan<<<(unsigned)n_segs, 256, 0, s>>>(counts, seg_base, out->bin_off, NB, (int)n_segs);
+    if (hits->n > 0)
+        k_hit_scatter<<<(hits->n + 255) / 256, 256, 0, s>>>(g, *hits, keys, counts, out->bin_off, hxyzi, hvar);
+    k_bin_sort<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(g, out->bin_off, out->event_off, (int)n_bins, hxyzi,
+                                                                 hvar, out->pos_of_hit);
+    return cudaGetLastError() == cudaSuccess ? TKF_OK : TKF_ERR_CUDA;
+}

@@ -18,7 +18,8 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "tkf.h")
 MAX_LAYERS = 16
 MAX_CAND = 16
 FP32, MIXED, FP64 = 0, 1, 2
-OK, ERR_INVALID, ERR_CUDA, ERR_NOMEM, ERR_AGAIN, ERR_TIMEOUT, ERR_NOTREADY, ERR_KERNEL = range(8)
+OK, ERR_INVALID, ERR_CUDA, ERR_NOMEM, ERR_AGAIN, ERR_TIMEOUT, ERR_NOTREADY, ERR_KERNEL, ERR_TOO_LARGE = range(9)
+NOALLOC_MAX_HITS, NOALLOC_MAX_BINS, NOALLOC_MAX_SEGMENTS = 1 << 20, 1 << 18, 1024
 TRACK_NOREACH, TRACK_SINGULAR, TRACK_LOST = -1, -2, -3
 
 
@@ -52,6 +53,11 @@ class Hits(C.Structure):
 class Tracks(C.Structure):
     _fields_ = [("par", C.c_void_p), ("cov", C.c_void_p), ("chi2", C.c_void_p), ("nhits", C.c_void_p),
                 ("hit_idx", C.c_void_p), ("event", C.c_void_p), ("n", C.c_int32), ("stride", C.c_int32)]
+
+
+class HitIndexOut(C.Structure):
+    _fields_ = [("hit_xyzi", C.c_void_p), ("hit_var", C.c_void_p), ("pos_of_hit", C.c_void_p),
+                ("bin_off", C.c_void_p), ("var_max", C.c_void_p), ("event_off", C.c_void_p)]
 
 
 class HitIndexView(C.Structure):
@@ -95,6 +101,7 @@ def lib():
         L.tkf_fit.argtypes = [vp, C.POINTER(Hits), C.POINTER(Tracks), vp, i32, i32, C.POINTER(Tracks), vp]
         L.tkf_build_tracks.argtypes = [vp, vp, C.POINTER(Tracks), C.POINTER(Tracks), C.POINTER(Tracks), vp, vp]
         L.tkf_sync_status.argtypes = [vp, vp]
+        L.tkf_build_hit_index_noalloc.argtypes = [C.POINTER(Config), C.POINTER(Hits), C.POINTER(HitIndexOut), vp]
         for name in declared_functions():
             getattr(L, name).restype = getattr(L, name).restype if name in (
                 "tkf_last_error", "tkf_status_string", "tkf_default_config") else C.c_int
@@ -277,3 +284,14 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def build_hit_index_noalloc(cfg: Config, hits: DeviceHits, out: dict, stream=None):
+    """tkf_build_hit_index_noalloc into caller-owned tensors `out` (keys hit_xyzi [n, 4] f32,
+    hit_var [n, 2] f32, pos_of_hit [n] i32, bin_off [E*L*bins + 1] i32, var_max [E*L, 2] f32,
+    event_off [E + 1] i32); returns the status code."""
+    o = HitIndexOut()
+    for k in ("hit_xyzi", "hit_var", "pos_of_hit", "bin_off", "var_max", "event_off"):
+        setattr(o, k, out[k].data_ptr())
+    hs = hits.struct()
+    return lib().tkf_build_hit_index_noalloc(C.byref(cfg), C.byref(hs), C.byref(o), _stream(stream))
