@@ -49,6 +49,9 @@ FLOP_PER_SEED = (PER_SEED["n_prop"] * (FLOP_PROPAGATE + FLOP_WINDOW) + PER_SEED[
                  + PER_SEED["n_updates"] * FLOP_UPDATE + PER_SEED["n_kept"] * 6.0 / 7.0 * FLOP_SCATTER)
 # FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
+# libtkf.so kernels per step: hit index (count, segment totals, segment scan, bin scan,
+# scatter, bin sort), seed estimate, seed fit, build, final fit
+KERNELS_PER_STEP = 10
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 
 
@@ -214,7 +217,7 @@ def run_reference(a):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["tkf", "reference"], default="tkf")
     ap.add_argument("--events", type=int, default=640)
@@ -243,7 +246,6 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_1702_06359_gb300 import tkf
-    from paper_1702_06359_gb300.pipeline import Pipeline
 
     # weak scaling: every rank builds its own 640-event batch (seed offset by rank)
     b = workload(a.seed + 1000 * rank, a.events, pool)
@@ -258,34 +260,57 @@ def main():
     }
     d = {k: v.to(dev, non_blocking=False) for k, v in host.items()}
     hits = tkf.DeviceHits(d["x"], d["y"], d["z"], d["var_u"], d["var_v"], d["layer"], d["event_off"])
-    cfg = tkf.default_config(seeds_per_block=64)
-    ctx = tkf.Context(cfg)
-    pipe = Pipeline(ctx, n_tr, device=dev)
+    ctx = tkf.Context(tkf.default_config())
+    L = ctx.cfg.n_layers
+    pipe = tkf.DevicePipeline(ctx, n_hits, b.n_events, n_tr, use_graph=True)
     stream = torch.cuda.current_stream()
 
-    def step(ev_pair=None):
-        return pipe.run(hits, d["seed_hits"], d["seed_event"], stream=stream, build_events=ev_pair)
+    def step():
+        pipe.run(hits, d["seed_hits"], d["seed_event"], n_tr, stream=stream)
 
+    # work-tile autotuner of the building kernel (seeds pulled per warp), then warm-up
+    step()
+    seeds_t, built_t, fitted_t = pipe.outputs()
+    spw = 32 // ctx.cfg.n_cand
+    tiles = [spw, 2 * spw, 4 * spw, 32, 64, 128]
+
+    class _T:
+        def __init__(self, t):
+            self.t = t
+
+        def struct(self):
+            return self.t
+    scratch_out = tkf.DeviceTracks.empty(n_tr, L, device=dev)
+    best_tile, tile_ms = ctx.autotune_build(pipe.index(), _T(seeds_t), scratch_out, tiles, repeats=2, stream=stream)
+    del scratch_out
+    # the clock sampler starts before the warm-up: nvidia-smi's start-up must not fall in the
+    # timed region
+    clocks = ClockSampler(local).__enter__()
+    time.sleep(0.5)
     for _ in range(a.warmup):
         step()
     ctx.sync_status(stream)
 
-    # ---------------- device-resident throughput
+    # ---------------- device-resident throughput (one graph replay per step)
     ev_start = torch.cuda.Event(enable_timing=True)
     ev_stop = torch.cuda.Event(enable_timing=True)
-    build_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    build_ms = []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
-        ev_start.record(stream)
-        for k in range(a.steps):
-            step(build_evs[k])
-        ev_stop.record(stream)
-        torch.cuda.synchronize()
+    n_before = len(clocks.lines)
+    ev_start.record(stream)
+    for k in range(a.steps):
+        step()
+        build_ms.append(pipe.build_ms())  # waits for the build kernel of this step only
+    ev_stop.record(stream)
+    torch.cuda.synchronize()
+    time.sleep(0.25)
+    clocks.__exit__(None, None, None)
+    clocks.lines = clocks.lines[n_before:] or clocks.lines[-2:]
     ctx.sync_status(stream)
     ms = ev_start.elapsed_time(ev_stop) / a.steps
-    build_ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in build_evs)
+    build_ms = statistics.mean(build_ms)
     t = torch.tensor([ms], device=dev)
     if dist:
         dist.barrier()
@@ -295,9 +320,11 @@ def main():
     value = total_tracks / (ms_max / 1e3)
 
     # ---------------- end to end through host buffers
-    out_bytes = lambda: [pipe.final.par, pipe.final.chi2, pipe.final.nhits, pipe.built.hit_idx]
+    _, built_t, fitted_t = pipe.outputs()
+    fv = tkf.tracks_tensors(fitted_t, L)
+    outs = [fv["par"][:, :n_tr], fv["chi2"][:n_tr], fv["nhits"][:n_tr], fv["hit_idx"][:, :n_tr]]
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    res_host = [torch.empty_like(t_, device="cpu").pin_memory() for t_ in out_bytes()]
+    res_host = [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs]
     d2h = sum(r.numel() * r.element_size() for r in res_host)
     e2e_start = torch.cuda.Event(enable_timing=True)
     e2e_stop = torch.cuda.Event(enable_timing=True)
@@ -307,20 +334,20 @@ def main():
         for k, v in host.items():
             d[k].copy_(v, non_blocking=True)
         step()
-        for r, t_ in zip(res_host, out_bytes()):
-            r.copy_(t_, non_blocking=True)
+        for r, o in zip(res_host, outs):
+            r.copy_(o, non_blocking=True)
     e2e_stop.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e2e_start.elapsed_time(e2e_stop) / a.steps
 
-    # ---------------- plain form: one event at a time (per-event latency)
+    # ---------------- plain form: one event per pass (direct launches), per-event latency
     plain = None
     if a.plain_events > 0:
         n_pe = min(a.plain_events, b.n_events)
         views = []
-        hit_off = b.hit_off
-        trk_off = b.trk_off
+        hit_off, trk_off = b.hit_off, b.trk_off
         stride = int(np.max(np.diff(trk_off[:n_pe + 1])))
+        max_h = int(np.max(np.diff(hit_off[:n_pe + 1])))
         for e in range(n_pe):
             h0, h1, t0_, t1_ = int(hit_off[e]), int(hit_off[e + 1]), int(trk_off[e]), int(trk_off[e + 1])
             off = torch.tensor([0, h1 - h0], dtype=torch.int32, device=dev)
@@ -329,10 +356,10 @@ def main():
             views.append((tkf.DeviceHits(d["x"][h0:h1], d["y"][h0:h1], d["z"][h0:h1], d["var_u"][h0:h1],
                                          d["var_v"][h0:h1], d["layer"][h0:h1], off), sh,
                           torch.zeros(stride, dtype=torch.int32, device=dev), t1_ - t0_))
-        pctx = tkf.Context(tkf.default_config(seeds_per_block=64))
-        ppipe = Pipeline(pctx, stride, device=dev)
+        pctx = tkf.Context(tkf.default_config())
+        ppipe = tkf.DevicePipeline(pctx, max_h, 1, stride, use_graph=False)
         for hv, sh, se, nt in views[:3]:
-            ppipe.run(hv, sh, se, stream=stream, n_tracks=nt)
+            ppipe.run(hv, sh, se, nt, stream=stream)
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in views]
         p_start = torch.cuda.Event(enable_timing=True)
@@ -340,7 +367,7 @@ def main():
         p_start.record(stream)
         for (hv, sh, se, nt), (e0, e1) in zip(views, evs):
             e0.record(stream)
-            ppipe.run(hv, sh, se, stream=stream, n_tracks=nt)
+            ppipe.run(hv, sh, se, nt, stream=stream)
             e1.record(stream)
         p_stop.record(stream)
         torch.cuda.synchronize()
@@ -349,7 +376,8 @@ def main():
         pe_tracks = int(trk_off[n_pe])
         plain = {"value": pe_tracks / (p_start.elapsed_time(p_stop) / 1e3), "unit": UNIT, "events": n_pe,
                  "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
-                 "form": "one event per launch sequence, same kernels, same stream"}
+                 "form": "one event per pipeline pass, direct launches, same kernels and stream"}
+        ppipe.close()
 
     # ---------------- CPU baseline
     cpu = None
@@ -368,10 +396,12 @@ def main():
         "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batched building: %d events, lognormal tracks (median 3000, sigma_ln 0.8, "
-                               "200..20000), noise 20-50%%, N=6, fp32, one persistent build launch per step"
+                               "200..20000), noise 20-50%%, N=6, fp32, one persistent build launch per step, "
+                               "whole step replayed from a CUDA graph"
                                % b.n_events,
                    "events": b.n_events, "tracks": n_tr, "hits": n_hits, "n_cand": 6, "precision": "fp32",
-                   "seeds_per_block": 64, "l2": "inputs larger than L2 (%.0f MB of hit planes)" % (n_hits * 24 / 1e6),
+                   "seeds_per_warp_tile": best_tile, "cuda_graph": True,
+                   "l2": "inputs larger than L2 (%.0f MB of hit planes)" % (n_hits * 24 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"kernel": "k_build<6,float,float>", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
@@ -381,7 +411,8 @@ def main():
         "e2e": {"value": total_tracks / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "plain": plain,
-        "gpu_launches": Pipeline.KERNELS_PER_RUN * a.steps,
+        "autotune": {"tiles": tiles, "build_ms": [round(x, 4) for x in tile_ms], "best": best_tile},
+        "gpu_launches": KERNELS_PER_STEP * a.steps,
         "clocks": clocks.summary(),
     }
     if rank == 0:

@@ -71,7 +71,8 @@ typedef struct {
     int32_t n_cand;                   /* candidates kept per seed while building, 1..16 */
     int32_t first_build_layer;        /* seeds are states on layer first_build_layer - 1 */
     int32_t precision;                /* enum tkf_precision */
-    int32_t seeds_per_block;          /* seeds per work tile of the build kernel; 0 = autotuned */
+    int32_t seeds_per_block;          /* seeds per work tile of the build kernel (one warp takes a
+                                         tile at a time); 0 = default */
 } tkf_config;
 
 /* Hits of one or more events (device arrays of length n, caller-owned).  The hits of event e
@@ -104,6 +105,9 @@ typedef struct tkf_hit_index tkf_hit_index;
 typedef struct {
     const float *hit_xyzi;   /* [n][4] sorted hits: x, y, z, event-local hit id (bits of an int32) */
     const float *hit_var;    /* [n][2] sorted hits: var_u, var_v */
+    const uint32_t *bin_sub; /* [n_events * n_layers * n_bins][4]: bytes 0..14 = start of phi
+                                sixteenths 1..15 of each bin relative to its first hit (all bytes
+                                0xFF: the bin holds more than 255 hits) */
     const int32_t *pos_of_hit; /* [n] sorted position of hit id i */
     const int32_t *bin_off;  /* [n_events * n_layers * n_bins + 1] CSR offsets into the sorted hits;
                                 bin (e, l, b) is [off[(e*L+l)*n_bins+b], off[(e*L+l)*n_bins+b+1]) */
@@ -131,8 +135,10 @@ int tkf_get_config(const tkf_ctx *ctx, tkf_config *out);
 
 /* Hit index (the hit-candidate data structure of Sec. 3.2.1): every hit is binned by
  * (event, layer, eta bin, phi bin), eta = asinh(z / radius[layer]) clamped to the bin range;
- * hits are reordered by (event, layer, eta bin, phi bin, hit id) into float4/float2 planes
- * with CSR bin offsets.  *out: NULL to allocate a new index, or an index from an earlier call
+ * hits are reordered by (event, layer, eta bin, phi bin) into float4/float2 planes with CSR
+ * bin offsets; inside a bin they are ordered by (phi sixteenth of the bin, hit id), and the
+ * start of each sixteenth is recorded, so that a search window reads only the sixteenths it
+ * overlaps.  *out: NULL to allocate a new index, or an index from an earlier call
  * whose storage is reused (grown if too small).  Library-owned until tkf_hit_index_free.
  * Errors: TKF_ERR_INVALID (bad sizes), TKF_ERR_NOMEM. */
 int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out, tkf_stream stream);
@@ -172,7 +178,8 @@ int tkf_fit(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const in
  *   out_all: NULL, or every final candidate: candidate r of seed s at s * n_cand + r
  *            (stride >= seeds->n * n_cand); n_cand_out (device int32 [seeds->n], may be NULL)
  *            receives the number of candidates of each seed.
- * Errors: TKF_ERR_INVALID; per seed nhits < 0 when every candidate was lost. */
+ * Errors: TKF_ERR_INVALID; per seed nhits = TKF_TRACK_LOST (state, covariance, chi2 zero) when
+ * every candidate was lost or the seed's event is out of range. */
 int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *seeds, tkf_tracks *out,
                      tkf_tracks *out_all, int32_t *n_cand_out, tkf_stream stream);
 
@@ -180,14 +187,66 @@ int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *s
  * call (TKF_ERR_KERNEL with text in tkf_last_error), or a CUDA error (TKF_ERR_CUDA). */
 int tkf_sync_status(tkf_ctx *ctx, tkf_stream stream);
 
+/* ---------------------------------------------------------------- batched pipeline */
+
+typedef struct tkf_pipeline tkf_pipeline;
+
+/* A reusable pipeline for batches of up to max_hits hits, max_events events and max_tracks
+ * seeds: the whole chain of Sec. 2 -- hit index, seed estimate, KF fit of the seeding layers,
+ * combinatorial building, final KF fit of the built hit lists -- over every event of a batch
+ * at once (the multi-event packing of Sec. 4, with the building kernel's dynamic work tiles
+ * standing for the TBB work stealing of Sec. 2.3).  All buffers (hit index, four track sets)
+ * are allocated here, so a run allocates nothing.  With use_graph != 0 the first run with a
+ * given input signature (hit pointers and sizes, seed pointers, n_tracks) is captured into a
+ * CUDA graph on the pipeline's own stream and replayed by every later run with the same
+ * signature (one cudaGraphLaunch); another signature re-captures.
+ * Errors: TKF_ERR_INVALID, TKF_ERR_NOMEM, TKF_ERR_CUDA. */
+int tkf_pipeline_create(tkf_ctx *ctx, int32_t max_hits, int32_t max_events, int32_t max_tracks, int32_t use_graph,
+                        tkf_pipeline **out);
+int tkf_pipeline_destroy(tkf_pipeline *p);
+
+/* One pass over a batch, queued on `stream`.  seed_hits: device int32 [3][max_tracks] hit ids
+ * of each seed on layers 0..2; seed_event: device int32 [n_tracks] event of each seed.  The
+ * results stay in pipeline-owned track sets (tkf_pipeline_outputs), valid until the next run.
+ * Errors: TKF_ERR_INVALID (batch larger than the creation sizes), TKF_ERR_CUDA. */
+int tkf_pipeline_run(tkf_pipeline *p, const tkf_hits *hits, const int32_t *seed_hits, const int32_t *seed_event,
+                     int32_t n_tracks, tkf_stream stream);
+
+/* Views of the pipeline's track sets of the last run (stride = max_tracks; any may be NULL):
+ * `seeds` = states after the seeding layers (with their event ids), `built` = best candidate
+ * per seed after building, `fitted` = its final fit (hit_idx = the built hit list). */
+int tkf_pipeline_outputs(const tkf_pipeline *p, tkf_tracks *seeds, tkf_tracks *built, tkf_tracks *fitted);
+
+/* Number of graph captures so far (replays do not count); -1 for a null pipeline. */
+int tkf_pipeline_captures(const tkf_pipeline *p);
+
+/* The pipeline's hit index (valid after a run; owned by the pipeline). */
+const tkf_hit_index *tkf_pipeline_index(const tkf_pipeline *p);
+
+/* Milliseconds between CUDA events recorded just before and after the building kernel of the
+ * last run (event-record nodes inside the graph); waits for the second event only.
+ * Errors: TKF_ERR_INVALID (no run yet), TKF_ERR_CUDA. */
+int tkf_pipeline_build_ms(tkf_pipeline *p, float *ms);
+
+/* Work-tile autotuner of the building kernel (the paper tunes its TBB task size against tail
+ * effects, Sec. 2.3): times `repeats` launches of tkf_build_tracks for each tile size in
+ * tiles[0..n_tiles) (seeds pulled per warp), writes the mean milliseconds to ms_out (may be
+ * NULL), keeps the fastest in the context's seeds_per_block and returns it in *best.
+ * Synchronises `stream`.  Errors: TKF_ERR_INVALID, TKF_ERR_CUDA. */
+int tkf_autotune_build(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *seeds, tkf_tracks *out,
+                       const int32_t *tiles, int32_t n_tiles, int32_t repeats, float *ms_out, int32_t *best,
+                       tkf_stream stream);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 
 /* Caller-owned output arrays of tkf_build_hit_index_noalloc (device memory), laid out as in
- * tkf_hit_index_view: hit_xyzi [n][4], hit_var [n][2], pos_of_hit [n],
+ * tkf_hit_index_view: hit_xyzi [n][4], hit_var [n][2], bin_sub [n_events * n_layers * n_bins][4],
+ * pos_of_hit [n],
  * bin_off [n_events * n_layers * n_bins + 1], var_max [n_events * n_layers][2],
  * event_off [n_events + 1], with n_bins = n_eta_bins * n_phi_bins. */
 typedef struct {
     float *hit_xyzi, *hit_var;
+    uint32_t *bin_sub;
     int32_t *pos_of_hit, *bin_off;
     float *var_max;
     int32_t *event_off;

@@ -14,7 +14,7 @@
 //      Kalman update (U = float or double) for a hit branch and the layer's scattering noise.
 // Hit history is kept per warp in shared memory (parent rank, hit id per layer and lane) and
 // the best candidate is backtracked at the end.  Work balance follows the paper's dynamic
-// work stealing (Sec. 2.3): blocks pull tiles of seeds_per_block seeds from an atomic counter
+// work stealing (Sec. 2.3): warps pull tiles of seeds_per_block seeds from an atomic counter
 // until the seeds of every event are done (one persistent launch over many events, Sec. 4).
 //
 // Branch key (64 bits, smaller = better): [63:59] 31 - nHits, [58:27] float bits of the total
@@ -44,6 +44,7 @@ __device__ __forceinline__ uint64_t make_key(int nhits, float chi2, int parent, 
     return ((uint64_t)(31 - nhits) << 59) | (c << 27) | ((uint64_t)parent << 23) | (uint64_t)hit;
 }
 
+// A lane's branch list: the NMAX smallest keys in ascending order.
 template <int NMAX> __device__ __forceinline__ void list_insert(uint64_t (&list)[NMAX], uint64_t k)
 {
 #pragma unroll
@@ -62,11 +63,44 @@ template <int NMAX> __device__ __forceinline__ void list_pop(uint64_t (&list)[NM
     list[NMAX - 1] = kEmpty;
 }
 
-template <class R>
-__device__ __forceinline__ int eta_bin(R z, R inv_r, R eta_min, R inv_w, int n_eta)
+// Hit ranges of phi sub-bins inside a bin, from the packed bytes of bin_sub (byte t - 1 holds
+// the start of sub-bin t relative to the bin's first hit; the top byte is unused, so a top
+// word of 0xFFFFFFFF only occurs for a bin of more than 255 hits, whose sub-bins are unknown).
+__device__ __forceinline__ int sub_byte(const uint4 w, int t)  // start of sub-bin t, 1 <= t < kSubBins
 {
-    const int b = (int)flr((ash(z * inv_r) - eta_min) * inv_w);
+    const unsigned word = t <= 4 ? w.x : (t <= 8 ? w.y : (t <= 12 ? w.z : w.w));
+    return (int)((word >> (8 * ((t - 1) & 3))) & 0xFFu);
+}
+// first hit of sub-bin s (s = 0: the bin's first hit)
+__device__ __forceinline__ int sub_first(const uint4 w, int s)
+{
+    return (s <= 0 || w.w == 0xFFFFFFFFu) ? 0 : sub_byte(w, s);
+}
+// one past the last hit of sub-bin s (s = kSubBins - 1: the bin's hit count)
+__device__ __forceinline__ int sub_end(const uint4 w, int s, int count)
+{
+    return (s >= kSubBins - 1 || w.w == 0xFFFFFFFFu) ? count : sub_byte(w, s + 1);
+}
+
+template <class R>
+__device__ __forceinline__ int eta_bin_window(R z, R inv_r, R eta_min, R inv_w, int n_eta, R slack)
+{
+    const R x = z * inv_r;
+    const R ax = ab(x);
+    const R e = copysign(fast_log(ax + sq(ax * ax + R(1))), x);
+    const int b = (int)flr((e - eta_min) * inv_w + slack);
     return b < 0 ? 0 : (b >= n_eta ? n_eta - 1 : b);
+}
+
+// asin(x) for 0 <= x <= 1; below 0.5 the series x (1 + x^2/6 + 3x^4/40 + 5x^6/112) (relative
+// error < 1.3e-4, an underestimate covered by the window's relative margin on U)
+template <class R> __device__ __forceinline__ R asin_window(R x)
+{
+    if (x < R(0.5)) {
+        const R x2 = x * x;
+        return x * (R(1) + x2 * (R(1.0 / 6) + x2 * (R(3.0 / 40) + x2 * R(5.0 / 112))));
+    }
+    return asn(x < R(1) ? x : R(1));
 }
 
 // Scores every hit of the candidate's window and fills its branch list.
@@ -86,27 +120,35 @@ __device__ __forceinline__ void scan_window(const BuildArgs &a, int ev, int l, R
     const R mg = R(1) + pick<R>(a.margin_f, a.margin);
     const R U = sq(cut * Suu) * mg, W = sq(cut * Svv) * mg;
     const R phip = at2(yp, xp);
-    const R ur = U / Rl;
-    const R dphi = asn(ur < R(1) ? ur : R(1));
+    // compatible hits satisfy |u| = r_p |sin(phi_h - phi_p)| <= U on the near half-cylinder,
+    // so |phi_h - phi_p| <= asin(U / R); a 2e-5 rad slack covers float rounding of both angles
+    const R dphi = asin_window(U / Rl) + R(2e-5);
     const R bscale = R(a.n_phi) / R(2.0 * kPi);
-    int k0 = (int)flr((phip - dphi + R(kPi)) * bscale);
-    int k1 = (int)flr((phip + dphi + R(kPi)) * bscale);
+    const R xlo = (phip - dphi + R(kPi)) * bscale, xhi = (phip + dphi + R(kPi)) * bscale;  // phi-bin units
+    const int k0 = (int)flr(xlo), k1 = (int)flr(xhi);
+    int s0 = (int)flr((xlo - R(k0)) * R(kSubBins)), s1 = (int)flr((xhi - R(k1)) * R(kSubBins));
+    s0 = s0 < 0 ? 0 : (s0 >= kSubBins ? kSubBins - 1 : s0);
+    s1 = s1 < 0 ? 0 : (s1 >= kSubBins ? kSubBins - 1 : s1);
     const int nphi = a.n_phi;
-    if (k1 - k0 + 1 >= nphi) {
-        k0 = 0;
-        k1 = nphi - 1;
-    }
     const R inv_r = R(1) / Rl;
     const R emin = pick<R>(a.eta_min_f, a.eta_min), iw = pick<R>(a.inv_eta_w_f, a.inv_eta_w);
-    const int e0 = eta_bin(zp - W, inv_r, emin, iw, a.n_eta);
-    const int e1 = eta_bin(zp + W, inv_r, emin, iw, a.n_eta);
-    int ra0, ra1, rb0, rb1;
-    if (k0 < 0) {
-        ra0 = k0 + nphi; ra1 = nphi - 1; rb0 = 0; rb1 = k1;
+    const int e0 = eta_bin_window(zp - W, inv_r, emin, iw, a.n_eta, R(-1e-4));
+    const int e1 = eta_bin_window(zp + W, inv_r, emin, iw, a.n_eta, R(1e-4));
+    // up to two parts (first bin, first sub-bin) .. (last bin, last sub-bin): the window may
+    // wrap around phi = +-pi
+    int pb0[2], ps0[2], pb1[2], ps1[2];
+    if (k1 - k0 + 1 >= nphi) {
+        pb0[0] = 0; ps0[0] = 0; pb1[0] = nphi - 1; ps1[0] = kSubBins - 1;
+        pb0[1] = 0; ps0[1] = 0; pb1[1] = -1; ps1[1] = 0;
+    } else if (k0 < 0) {
+        pb0[0] = k0 + nphi; ps0[0] = s0; pb1[0] = nphi - 1; ps1[0] = kSubBins - 1;
+        pb0[1] = 0; ps0[1] = 0; pb1[1] = k1; ps1[1] = s1;
     } else if (k1 >= nphi) {
-        ra0 = k0; ra1 = nphi - 1; rb0 = 0; rb1 = k1 - nphi;
+        pb0[0] = k0; ps0[0] = s0; pb1[0] = nphi - 1; ps1[0] = kSubBins - 1;
+        pb0[1] = 0; ps0[1] = 0; pb1[1] = k1 - nphi; ps1[1] = s1;
     } else {
-        ra0 = k0; ra1 = k1; rb0 = 0; rb1 = -1;
+        pb0[0] = k0; ps0[0] = s0; pb1[0] = k1; ps1[0] = s1;
+        pb0[1] = 0; ps0[1] = 0; pb1[1] = -1; ps1[1] = 0;
     }
     bool found = false;
     const int row0 = seg * a.n_bins;
@@ -114,14 +156,27 @@ __device__ __forceinline__ void scan_window(const BuildArgs &a, int ev, int l, R
         const int row = row0 + e * nphi;
 #pragma unroll
         for (int part = 0; part < 2; ++part) {
-            const int b0 = part ? rb0 : ra0, b1 = part ? rb1 : ra1;
-            if (b1 < b0) continue;
-            const int i0 = __ldg(&a.bin_off[row + b0]), i1 = __ldg(&a.bin_off[row + b1 + 1]);
+            if (pb1[part] < pb0[part]) continue;
+            // first hit of the first sub-bin and end of the last sub-bin (independent loads)
+            const int ba = row + pb0[part], bb = row + pb1[part];
+            const int oa = __ldg(&a.bin_off[ba]);
+            const int ob = __ldg(&a.bin_off[bb]), ob1 = __ldg(&a.bin_off[bb + 1]);
+            const uint4 wa = __ldg(&a.bin_sub[ba]), wb = __ldg(&a.bin_sub[bb]);
+            const int i0 = oa + sub_first(wa, ps0[part]);
+            const int i1 = ob + sub_end(wb, ps1[part], ob1 - ob);
             for (int i = i0; i < i1; ++i) {
                 const float4 h = __ldg(&a.hxyzi[i]);
-                if (!(xp * R(h.x) + yp * R(h.y) > R(0))) continue;  // far half of the cylinder
+                const R hx = R(h.x), hy = R(h.y);
+                if (!(xp * hx + yp * hy > R(0))) continue;  // far half of the cylinder
+                // residual on the hit's tangent plane; |u| <= U and |v| <= W bound every hit
+                // with chi2 < cut (U, W are the extents of the cut ellipse of the largest S)
+                const R ir = fast_rsqrt(hx * hx + hy * hy);
+                const R sh = hy * ir, ch = hx * ir;
+                const R u = ch * (hy - yp) - sh * (hx - xp);
+                const R v = R(h.z) - zp;
+                if (ab(u) > U || ab(v) > W) continue;
                 const float2 hv = __ldg(&a.hvar[i]);
-                const R c2 = hit_chi2<R>(p, P, R(h.x), R(h.y), R(h.z), R(hv.x), R(hv.y));
+                const R c2 = chi2_uv<R>(P, u, v, sh, ch, R(hv.x), R(hv.y));
                 if (c2 < cut) {
                     list_insert(list, make_key(nh + 1, to_f32(chi2 + c2), rank, __float_as_int(h.w)));
                     found = true;
@@ -143,11 +198,21 @@ template <class R> __device__ __forceinline__ void store_track(void *par, void *
     px[i] = chi2;
 }
 
+// Resident blocks per SM requested from the register allocator: the all-float kernels with up
+// to 6 candidates are held to 72 registers per thread (7 blocks of 128 threads), which costs a
+// few spilled words; the wider lists and the double-precision updates keep their natural
+// register count.
+#ifndef TKF_BUILD_MINBLOCKS_F32
+#define TKF_BUILD_MINBLOCKS_F32 7
+#endif
+template <int NMAX, class R, class U> struct BuildMinBlocks {
+    static constexpr int value = (sizeof(R) == 4 && sizeof(U) == 4 && NMAX <= 6) ? TKF_BUILD_MINBLOCKS_F32 : 1;
+};
+
 template <int NMAX, class R, class U>
-__global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a)
+__global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U>::value)) k_build(const BuildArgs a)
 {
     constexpr int W = kBuildThreads / 32;
-    __shared__ int s_tile;
     __shared__ int hist_hit[W][TKF_MAX_LAYERS][32];
     __shared__ signed char hist_par[W][TKF_MAX_LAYERS][32];
 
@@ -160,20 +225,26 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a)
     const bool lane_ok = grp < spw;
     const R kb = pick<R>(a.kb_f, a.kb), mass = pick<R>(a.mass_f, a.mass);
 
+    // each warp pulls tiles of seeds_per_block seeds from the counter (no block barrier: a warp
+    // that finishes early takes the next tile at once)
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1);
-        __syncthreads();
-        const long long t0 = (long long)s_tile * a.seeds_per_block;
+        int tile = 0;
+        if (lane == 0) tile = atomicAdd(a.tile_counter, 1);
+        tile = __shfl_sync(kFull, tile, 0);
+        const long long t0 = (long long)tile * a.seeds_per_block;
         if (t0 >= a.n_seeds) return;
         const int t1 = (int)min((long long)a.n_seeds, t0 + a.seeds_per_block);
-        for (int sb = (int)t0 + warp * spw; sb < t1; sb += W * spw) {
+        for (int sb = (int)t0; sb < t1; sb += spw) {
             const int seed = sb + grp;
             bool has = lane_ok && seed < t1;
             const int ev = (has && a.s_event) ? a.s_event[seed] : 0;
             if (has && (ev < 0 || ev >= a.n_events)) {
                 atomicOr(a.err, kErrBadEvent);
-                a.o_nhits[seed] = TKF_TRACK_LOST;
+                if (r == 0) {
+                    const R zp[6] = {}, zc[21] = {};
+                    store_track<R>(a.o_par, a.o_cov, a.o_chi2, a.o_stride, seed, zp, zc, R(0));
+                    a.o_nhits[seed] = TKF_TRACK_LOST;
+                }
                 has = false;
             }
             R p[6], P[21], chi2 = R(0);
@@ -205,6 +276,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a)
                 uint64_t mine = kEmpty;
                 ns = 0;
                 for (int k = 0; k < N; ++k) {
+                    if (!__any_sync(kFull, list[0] != kEmpty)) break;  // no segment has branches left
                     uint64_t m = list[0];
                     for (int off = 1; off < N; off <<= 1) {
                         const uint64_t o = __shfl_down_sync(kFull, m, off);
@@ -251,7 +323,9 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(const BuildArgs a)
                 if (ns > 0) {
                     store_track<R>(a.o_par, a.o_cov, a.o_chi2, a.o_stride, seed, p, P, chi2);
                     a.o_nhits[seed] = nh;
-                } else {
+                } else {  // every candidate lost: defined zero state
+                    const R zp[6] = {}, zc[21] = {};
+                    store_track<R>(a.o_par, a.o_cov, a.o_chi2, a.o_stride, seed, zp, zc, R(0));
                     a.o_nhits[seed] = TKF_TRACK_LOST;
                 }
                 if (a.o_hit) {

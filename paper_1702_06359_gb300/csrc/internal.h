@@ -13,6 +13,7 @@ namespace tkf {
 constexpr int kBuildThreads = 128;  // 4 warps per block
 constexpr int kHoleId = 0x7FFFFF;   // event-local hit id field value of a hole branch
 constexpr int kMaxHitsPerEvent = 0x7FFFFF - 1;
+constexpr int kSubBins = 16;        // phi sub-bins per phi bin recorded by the hit index
 
 // error bits raised by kernels (atomicOr into the context's error word)
 enum : int { kErrBadLayer = 1, kErrBadHitId = 2, kErrTooManyHits = 4, kErrBadEvent = 8 };
@@ -26,6 +27,7 @@ struct BuildArgs {
     // hit index
     const float4 *hxyzi;
     const float2 *hvar;
+    const uint4 *bin_sub;
     const int *pos_of_hit;
     const int *bin_off;
     const float2 *var_max;
@@ -54,6 +56,10 @@ cudaError_t launch_build_fp32(const BuildArgs &a, int nmax, int grid, cudaStream
 cudaError_t launch_build_mixed(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
 cudaError_t launch_build_fp64(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
 
+// Allocates (or grows) `*idx` so that batches of up to max_hits hits and max_events events
+// need no further allocation (used before capturing the pipeline into a CUDA graph).
+int hit_index_reserve(tkf_ctx *ctx, tkf_hit_index **idx, size_t max_hits, size_t max_events);
+
 inline int build_nmax(int n)
 {
     return n <= 1 ? 1 : n <= 4 ? 4 : n <= 6 ? 6 : n <= 10 ? 10 : 16;
@@ -76,6 +82,7 @@ struct tkf_hit_index {
     size_t cap_hits = 0, cap_bins = 0, cap_segs = 0;
     float4 *hxyzi = nullptr;
     float2 *hvar = nullptr;
+    uint4 *bin_sub = nullptr;  // cap_bins
     int *pos_of_hit = nullptr;
     int *keys = nullptr;
     int *bin_off = nullptr;   // cap_bins + 1

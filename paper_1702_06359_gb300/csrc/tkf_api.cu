@@ -57,35 +57,73 @@ struct IndexGeom {
     float eta_min, inv_eta_w;
 };
 
+// continuous phi-bin coordinate (phi + pi) * n_phi / (2 pi); its floor is the phi bin
+__device__ __forceinline__ float phi_coord(const IndexGeom &g, float x, float y)
+{
+    return (atan2f(y, x) + (float)kPi) * (float)(g.n_phi / (2.0 * kPi));
+}
+
 __device__ __forceinline__ int hit_bin(const IndexGeom &g, int l, float x, float y, float z)
 {
     int eb = (int)floorf((asinhf(z / g.radius[l]) - g.eta_min) * g.inv_eta_w);
     eb = eb < 0 ? 0 : (eb >= g.n_eta ? g.n_eta - 1 : eb);
-    int pb = (int)floorf((atan2f(y, x) + (float)kPi) * (float)(g.n_phi / (2.0 * kPi)));
+    int pb = (int)floorf(phi_coord(g, x, y));
     pb = pb < 0 ? 0 : (pb >= g.n_phi ? g.n_phi - 1 : pb);
     return eb * g.n_phi + pb;
 }
 
-// key = ((event * L + layer) * n_bins + bin); counts per key and per (event, layer)
+// phi sub-bin (0..kSubBins-1) of a hit inside its phi bin pb, from the same phi coordinate
+__device__ __forceinline__ int hit_sub(const IndexGeom &g, float x, float y, int pb)
+{
+    const int s = (int)floorf((phi_coord(g, x, y) - (float)pb) * (float)kSubBins);
+    return s < 0 ? 0 : (s >= kSubBins ? kSubBins - 1 : s);
+}
+
+// key = ((event * L + layer) * n_bins + bin); counts per key.  The largest variances of each
+// (event, layer) are reduced within the warp first (hits of one segment usually arrive
+// together), so only one atomic per warp and segment reaches L2.
 __global__ void k_hit_count(const IndexGeom g, const tkf_hits h, int *keys, int *counts, int *seg_count, int *var_max,
                             int *err)
 {
+    // every lane of the warp reaches the warp-wide reductions below (blockDim is a multiple of 32)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= h.n) return;
-    const int e = find_event(h.event_off, g.n_events, i);
-    const int l = h.layer[i];
-    if (l < 0 || l >= g.L) {
+    (void)seg_count;
+    const bool in = i < h.n;
+    const int l = in ? h.layer[i] : 0;
+    const bool ok = in && l >= 0 && l < g.L;
+    const int seg = ok ? find_event(h.event_off, g.n_events, i) * g.L + l : -1;
+    if (ok) {
+        const int key = seg * g.n_bins + hit_bin(g, l, h.x[i], h.y[i], h.z[i]);
+        keys[i] = key;
+        atomicAdd(&counts[key], 1);
+    } else if (in) {
         keys[i] = -1;
         atomicOr(err, kErrBadLayer);
-        return;
     }
-    const int seg = e * g.L + l;
-    const int key = seg * g.n_bins + hit_bin(g, l, h.x[i], h.y[i], h.z[i]);
-    keys[i] = key;
-    atomicAdd(&counts[key], 1);
-    atomicAdd(&seg_count[seg], 1);
-    atomicMax(&var_max[2 * seg + 0], __float_as_int(fmaxf(h.var_u[i], 0.f)));
-    atomicMax(&var_max[2 * seg + 1], __float_as_int(fmaxf(h.var_v[i], 0.f)));
+    const unsigned same = __match_any_sync(0xffffffffu, seg);
+    const int vu = __reduce_max_sync(same, ok ? __float_as_int(fmaxf(h.var_u[i], 0.f)) : 0);
+    const int vv = __reduce_max_sync(same, ok ? __float_as_int(fmaxf(h.var_v[i], 0.f)) : 0);
+    if (ok && (int)(threadIdx.x & 31) == __ffs(same) - 1) {
+        atomicMax(&var_max[2 * seg + 0], vu);
+        atomicMax(&var_max[2 * seg + 1], vv);
+    }
+}
+
+// hits per (event, layer): sum of the segment's bin counts, one block per segment
+__global__ void k_seg_total(const int *counts, int *seg_count, int n_bins)
+{
+    __shared__ int part[32];
+    const int *c = counts + (size_t)blockIdx.x * n_bins;
+    int s = 0;
+    for (int b = threadIdx.x; b < n_bins; b += blockDim.x) s += c[b];
+    s = __reduce_add_sync(0xffffffffu, s);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int t = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0;
+        t = __reduce_add_sync(0xffffffffu, t);
+        if (threadIdx.x == 0) seg_count[blockIdx.x] = t;
+    }
 }
 
 // exclusive scan of the (event, layer) hit counts, one block
@@ -182,14 +220,26 @@ __global__ void k_hit_scatter(const IndexGeom g, const tkf_hits h, const int *ke
     hvar[pos] = make_float2(h.var_u[i], h.var_v[i]);
 }
 
-// sort each bin by event-local hit id (bins hold a handful of hits) and fill pos_of_hit
+// Orders each bin by (phi sub-bin, event-local hit id) -- bins hold a handful of hits -- and
+// records where sub-bins 1..15 start (bytes of bin_sub; all 0xFF when the bin holds more than
+// 255 hits: scan it whole), so that a window reads only the sub-bins it overlaps; fills
+// pos_of_hit.  The sort key (sub-bin << 23 | id) lives in the w word while sorting.
 __global__ void k_bin_sort(const IndexGeom g, const int *bin_off, const int *ev_off, int n_bins_total, float4 *hxyzi,
-                           float2 *hvar, int *pos_of_hit)
+                           float2 *hvar, uint4 *bin_sub, int *pos_of_hit)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_bins_total) return;
     const int i0 = bin_off[b], i1 = bin_off[b + 1];
-    if (i1 <= i0) return;
+    if (i1 <= i0) {
+        bin_sub[b] = make_uint4(0u, 0u, 0u, 0u);
+        return;
+    }
+    const int pb = (b % g.n_bins) % g.n_phi;
+    for (int i = i0; i < i1; ++i) {
+        float4 q = hxyzi[i];
+        q.w = __int_as_float((hit_sub(g, q.x, q.y, pb) << 23) | __float_as_int(q.w));
+        hxyzi[i] = q;
+    }
     for (int i = i0 + 1; i < i1; ++i) {
         const float4 k4 = hxyzi[i];
         const float2 k2 = hvar[i];
@@ -205,7 +255,23 @@ __global__ void k_bin_sort(const IndexGeom g, const int *bin_off, const int *ev_
     }
     const int e = b / (g.L * g.n_bins);
     const int base = ev_off[e];
-    for (int i = i0; i < i1; ++i) pos_of_hit[base + __float_as_int(hxyzi[i].w)] = i;
+    int start[kSubBins + 1] = {};
+    for (int i = i0; i < i1; ++i) {
+        float4 q = hxyzi[i];
+        const int key = __float_as_int(q.w);
+        const int sb = key >> 23, id = key & 0x7FFFFF;
+        for (int t = sb + 1; t <= kSubBins; ++t) start[t] += 1;
+        q.w = __int_as_float(id);
+        hxyzi[i] = q;
+        pos_of_hit[base + id] = i;
+    }
+    unsigned packed[4] = {0u, 0u, 0u, 0u};
+    if (i1 - i0 > 255) {
+        packed[0] = packed[1] = packed[2] = packed[3] = 0xFFFFFFFFu;
+    } else {
+        for (int t = 1; t < kSubBins; ++t) packed[(t - 1) >> 2] |= (unsigned)start[t] << (8 * ((t - 1) & 3));
+    }
+    bin_sub[b] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
 }
 
 // ------------------------------------------------------------------ seed estimate and fit
@@ -381,6 +447,46 @@ template <class T> int grow(tkf_ctx *ctx, T **p, size_t n)
 
 }  // namespace
 
+namespace tkf {
+
+int hit_index_reserve(tkf_ctx *ctx, tkf_hit_index **out, size_t max_hits, size_t max_events)
+{
+    const tkf_config &c = ctx->cfg;
+    const size_t n_segs = max_events * (size_t)c.n_layers;
+    const size_t n_bins = n_segs * (size_t)c.n_eta_bins * c.n_phi_bins;
+    if (n_bins >= (size_t)1 << 31) return set_err(ctx, TKF_ERR_INVALID, "hit index: too many events for the bin table");
+    tkf_hit_index *idx = *out;
+    if (!idx) {
+        idx = new (std::nothrow) tkf_hit_index();
+        if (!idx) return set_err(ctx, TKF_ERR_NOMEM, "hit index: host allocation failed");
+        idx->ctx = ctx;
+        *out = idx;
+    }
+    int st = TKF_OK;
+    if (max_hits > idx->cap_hits || !idx->hxyzi) {
+        const size_t cap = std::max<size_t>(max_hits, 1);
+        if ((st = grow(ctx, &idx->hxyzi, cap)) || (st = grow(ctx, &idx->hvar, cap)) ||
+            (st = grow(ctx, &idx->pos_of_hit, cap)) || (st = grow(ctx, &idx->keys, cap)))
+            return st;
+        idx->cap_hits = cap;
+    }
+    if (n_bins > idx->cap_bins || !idx->bin_off) {
+        if ((st = grow(ctx, &idx->bin_off, n_bins + 1)) || (st = grow(ctx, &idx->counts, n_bins)) ||
+            (st = grow(ctx, &idx->bin_sub, n_bins)))
+            return st;
+        idx->cap_bins = n_bins;
+    }
+    if (n_segs > idx->cap_segs || !idx->seg_count) {
+        if ((st = grow(ctx, &idx->seg_count, n_segs)) || (st = grow(ctx, &idx->seg_base, n_segs)) ||
+            (st = grow(ctx, &idx->var_max, n_segs)) || (st = grow(ctx, &idx->ev_off, n_segs + 1)))
+            return st;
+        idx->cap_segs = n_segs;
+    }
+    return TKF_OK;
+}
+
+}  // namespace tkf
+
 // ====================================================================== C ABI
 
 extern "C" {
@@ -501,7 +607,9 @@ int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out,
         idx->cap_hits = cap;
     }
     if (n_bins > idx->cap_bins || fresh) {
-        if ((st = grow(ctx, &idx->bin_off, n_bins + 1)) || (st = grow(ctx, &idx->counts, n_bins))) goto fail;
+        if ((st = grow(ctx, &idx->bin_off, n_bins + 1)) || (st = grow(ctx, &idx->counts, n_bins)) ||
+            (st = grow(ctx, &idx->bin_sub, n_bins)))
+            goto fail;
         idx->cap_bins = n_bins;
     }
     if (n_segs > idx->cap_segs || (size_t)hits->n_events + 1 > idx->cap_segs + 1 || fresh) {
@@ -526,7 +634,6 @@ int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out,
         g.eta_min = (float)c.eta_min;
         g.inv_eta_w = (float)(1.0 / c.eta_bin_w);
         TKF_CUDA(ctx, cudaMemsetAsync(idx->counts, 0, n_bins * sizeof(int), s));
-        TKF_CUDA(ctx, cudaMemsetAsync(idx->seg_count, 0, n_segs * sizeof(int), s));
         TKF_CUDA(ctx, cudaMemsetAsync(idx->var_max, 0, n_segs * sizeof(float2), s));
         TKF_CUDA(ctx, cudaMemcpyAsync(idx->ev_off, hits->event_off, (hits->n_events + 1) * sizeof(int),
                                       cudaMemcpyDeviceToDevice, s));
@@ -535,6 +642,7 @@ int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out,
             k_hit_count<<<nb, 256, 0, s>>>(g, *hits, idx->keys, idx->counts, idx->seg_count, (int *)idx->var_max,
                                            ctx->d_err);
         }
+        k_seg_total<<<(unsigned)n_segs, 256, 0, s>>>(idx->counts, idx->seg_count, NB);
         k_seg_scan<<<1, 1024, 0, s>>>(idx->seg_count, idx->seg_base, (int)n_segs);
         k_bin_scan<<<(unsigned)n_segs, 256, 0, s>>>(idx->counts, idx->seg_base, idx->bin_off, NB, (int)n_segs);
         if (hits->n > 0) {
@@ -542,7 +650,7 @@ int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out,
             k_hit_scatter<<<nb, 256, 0, s>>>(g, *hits, idx->keys, idx->counts, idx->bin_off, idx->hxyzi, idx->hvar);
         }
         k_bin_sort<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(g, idx->bin_off, idx->ev_off, (int)n_bins,
-                                                                     idx->hxyzi, idx->hvar, idx->pos_of_hit);
+                                                                     idx->hxyzi, idx->hvar, idx->bin_sub, idx->pos_of_hit);
         TKF_CUDA(ctx, cudaGetLastError());
     }
     *out = idx;
@@ -560,6 +668,7 @@ int tkf_hit_index_free(tkf_hit_index *idx)
     cudaFree(idx->hxyzi);
     cudaFree(idx->hvar);
     cudaFree(idx->pos_of_hit);
+    cudaFree(idx->bin_sub);
     cudaFree(idx->keys);
     cudaFree(idx->bin_off);
     cudaFree(idx->counts);
@@ -576,6 +685,7 @@ int tkf_hit_index_get_view(const tkf_hit_index *idx, tkf_hit_index_view *v)
     if (!idx || !v) return TKF_ERR_INVALID;
     v->hit_xyzi = (const float *)idx->hxyzi;
     v->hit_var = (const float *)idx->hvar;
+    v->bin_sub = (const uint32_t *)idx->bin_sub;
     v->pos_of_hit = idx->pos_of_hit;
     v->bin_off = idx->bin_off;
     v->var_max = (const float *)idx->var_max;
@@ -651,7 +761,9 @@ int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *s
     a.n_eta = c.n_eta_bins;
     a.n_phi = c.n_phi_bins;
     a.n_bins = c.n_eta_bins * c.n_phi_bins;
-    a.seeds_per_block = c.seeds_per_block > 0 ? c.seeds_per_block : 64;
+    // default work tile: two groups of seeds per warp (small tiles keep every warp busy when
+    // a launch holds a single event)
+    a.seeds_per_block = c.seeds_per_block > 0 ? c.seeds_per_block : 2 * (32 / c.n_cand);
     a.n_seeds = seeds->n;
     a.n_events = idx->n_events;
     for (int l = 0; l < c.n_layers; ++l) {
@@ -674,6 +786,7 @@ int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *s
     a.margin_f = (float)a.margin;
     a.hxyzi = idx->hxyzi;
     a.hvar = idx->hvar;
+    a.bin_sub = idx->bin_sub;
     a.pos_of_hit = idx->pos_of_hit;
     a.bin_off = idx->bin_off;
     a.var_max = idx->var_max;
@@ -776,7 +889,8 @@ extern "C" int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits
     if (hits->n < 0 || hits->n_events < 1 || !hits->event_off) return TKF_ERR_INVALID;
     if (hits->n > 0 && (!hits->x || !hits->y || !hits->z || !hits->var_u || !hits->var_v || !hits->layer))
         return TKF_ERR_INVALID;
-    if (!out->hit_xyzi || !out->hit_var || !out->pos_of_hit || !out->bin_off || !out->var_max || !out->event_off)
+    if (!out->hit_xyzi || !out->hit_var || !out->bin_sub || !out->pos_of_hit || !out->bin_off || !out->var_max ||
+        !out->event_off)
         return TKF_ERR_INVALID;
     const int L = c.n_layers, NB = c.n_eta_bins * c.n_phi_bins;
     const size_t n_segs = (size_t)hits->n_events * L;
@@ -804,18 +918,18 @@ extern "C" int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits
     float4 *hxyzi = (float4 *)out->hit_xyzi;
     float2 *hvar = (float2 *)out->hit_var;
     if (cudaMemsetAsync(counts, 0, n_bins * sizeof(int), s) != cudaSuccess ||
-        cudaMemsetAsync(seg_count, 0, n_segs * sizeof(int), s) != cudaSuccess ||
         cudaMemsetAsync(out->var_max, 0, n_segs * 2 * sizeof(float), s) != cudaSuccess ||
         cudaMemcpyAsync(out->event_off, hits->event_off, (hits->n_events + 1) * sizeof(int), cudaMemcpyDeviceToDevice,
                         s) != cudaSuccess)
         return TKF_ERR_CUDA;
     if (hits->n > 0)
         k_hit_count<<<(hits->n + 255) / 256, 256, 0, s>>>(g, *hits, keys, counts, seg_count, (int *)out->var_max, err);
+    k_seg_total<<<(unsigned)n_segs, 256, 0, s>>>(counts, seg_count, NB);
     k_seg_scan<<<1, 1024, 0, s>>>(seg_count, seg_base, (int)n_segs);
     k_bin_scan<<<(unsigned)n_segs, 256, 0, s>>>(counts, seg_base, out->bin_off, NB, (int)n_segs);
     if (hits->n > 0)
         k_hit_scatter<<<(hits->n + 255) / 256, 256, 0, s>>>(g, *hits, keys, counts, out->bin_off, hxyzi, hvar);
     k_bin_sort<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(g, out->bin_off, out->event_off, (int)n_bins, hxyzi,
-                                                                 hvar, out->pos_of_hit);
+                                                                 hvar, (uint4 *)out->bin_sub, out->pos_of_hit);
     return cudaGetLastError() == cudaSuccess ? TKF_OK : TKF_ERR_CUDA;
 }

@@ -56,12 +56,12 @@ class Tracks(C.Structure):
 
 
 class HitIndexOut(C.Structure):
-    _fields_ = [("hit_xyzi", C.c_void_p), ("hit_var", C.c_void_p), ("pos_of_hit", C.c_void_p),
+    _fields_ = [("hit_xyzi", C.c_void_p), ("hit_var", C.c_void_p), ("bin_sub", C.c_void_p), ("pos_of_hit", C.c_void_p),
                 ("bin_off", C.c_void_p), ("var_max", C.c_void_p), ("event_off", C.c_void_p)]
 
 
 class HitIndexView(C.Structure):
-    _fields_ = [("hit_xyzi", C.c_void_p), ("hit_var", C.c_void_p), ("pos_of_hit", C.c_void_p),
+    _fields_ = [("hit_xyzi", C.c_void_p), ("hit_var", C.c_void_p), ("bin_sub", C.c_void_p), ("pos_of_hit", C.c_void_p),
                 ("bin_off", C.c_void_p), ("var_max", C.c_void_p), ("event_off", C.c_void_p),
                 ("n", C.c_int32), ("n_events", C.c_int32), ("n_layers", C.c_int32), ("n_bins", C.c_int32)]
 
@@ -101,10 +101,19 @@ def lib():
         L.tkf_fit.argtypes = [vp, C.POINTER(Hits), C.POINTER(Tracks), vp, i32, i32, C.POINTER(Tracks), vp]
         L.tkf_build_tracks.argtypes = [vp, vp, C.POINTER(Tracks), C.POINTER(Tracks), C.POINTER(Tracks), vp, vp]
         L.tkf_sync_status.argtypes = [vp, vp]
+        L.tkf_pipeline_create.argtypes = [vp, i32, i32, i32, i32, C.POINTER(vp)]
+        L.tkf_pipeline_destroy.argtypes = [vp]
+        L.tkf_pipeline_run.argtypes = [vp, C.POINTER(Hits), vp, vp, i32, vp]
+        L.tkf_pipeline_outputs.argtypes = [vp, C.POINTER(Tracks), C.POINTER(Tracks), C.POINTER(Tracks)]
+        L.tkf_pipeline_captures.argtypes = [vp]
+        L.tkf_pipeline_index.argtypes = [vp]
+        L.tkf_pipeline_build_ms.argtypes = [vp, C.POINTER(C.c_float)]
+        L.tkf_autotune_build.argtypes = [vp, vp, C.POINTER(Tracks), C.POINTER(Tracks), vp, i32, i32, vp, vp, vp]
         L.tkf_build_hit_index_noalloc.argtypes = [C.POINTER(Config), C.POINTER(Hits), C.POINTER(HitIndexOut), vp]
         for name in declared_functions():
-            getattr(L, name).restype = getattr(L, name).restype if name in (
-                "tkf_last_error", "tkf_status_string", "tkf_default_config") else C.c_int
+            if name not in ("tkf_last_error", "tkf_status_string", "tkf_default_config", "tkf_pipeline_index"):
+                getattr(L, name).restype = C.c_int
+        L.tkf_pipeline_index.restype = vp
         _lib = L
     return _lib
 
@@ -271,6 +280,17 @@ class Context:
         self._check(lib().tkf_build_tracks(self.handle, index.handle, C.byref(ss), C.byref(so), sa, _ptr(n_cand_out),
                                            _stream(stream)))
 
+    def autotune_build(self, index: HitIndex, seeds: DeviceTracks, out: DeviceTracks, tiles, repeats=3, stream=None):
+        """Times the building kernel for each work-tile size; keeps and returns the fastest and
+        the per-size milliseconds."""
+        arr = (C.c_int32 * len(tiles))(*tiles)
+        ms = (C.c_float * len(tiles))()
+        best = C.c_int32()
+        ss, so = seeds.struct(), out.struct()
+        self._check(lib().tkf_autotune_build(self.handle, index.handle, C.byref(ss), C.byref(so), arr, len(tiles),
+                                             int(repeats), ms, C.byref(best), _stream(stream)))
+        return best.value, list(ms)
+
     def sync_status(self, stream=None):
         self._check(lib().tkf_sync_status(self.handle, _stream(stream)))
 
@@ -288,10 +308,76 @@ class Context:
 
 def build_hit_index_noalloc(cfg: Config, hits: DeviceHits, out: dict, stream=None):
     """tkf_build_hit_index_noalloc into caller-owned tensors `out` (keys hit_xyzi [n, 4] f32,
-    hit_var [n, 2] f32, pos_of_hit [n] i32, bin_off [E*L*bins + 1] i32, var_max [E*L, 2] f32,
+    hit_var [n, 2] f32, bin_sub [E*L*bins, 4] i32, pos_of_hit [n] i32, bin_off [E*L*bins + 1] i32, var_max [E*L, 2] f32,
     event_off [E + 1] i32); returns the status code."""
     o = HitIndexOut()
-    for k in ("hit_xyzi", "hit_var", "pos_of_hit", "bin_off", "var_max", "event_off"):
+    for k in ("hit_xyzi", "hit_var", "bin_sub", "pos_of_hit", "bin_off", "var_max", "event_off"):
         setattr(o, k, out[k].data_ptr())
     hs = hits.struct()
     return lib().tkf_build_hit_index_noalloc(C.byref(cfg), C.byref(hs), C.byref(o), _stream(stream))
+
+
+class DevicePipeline:
+    """tkf_pipeline: buffers for batches up to the given sizes; run() issues the whole hot path
+    (replayed from a CUDA graph when use_graph)."""
+
+    def __init__(self, ctx: Context, max_hits, max_events, max_tracks, use_graph=True):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx._check(lib().tkf_pipeline_create(ctx.handle, int(max_hits), int(max_events), int(max_tracks),
+                                             int(bool(use_graph)), C.byref(h)))
+        self.handle = h
+        self.max_tracks = int(max_tracks)
+
+    def run(self, hits: DeviceHits, seed_hits, seed_event, n_tracks, stream=None):
+        hs = hits.struct()
+        self.ctx._check(lib().tkf_pipeline_run(self.handle, C.byref(hs), _ptr(seed_hits), _ptr(seed_event),
+                                               int(n_tracks), _stream(stream)))
+
+    def outputs(self):
+        """(seeds, built, fitted) as tkf_tracks structs (device pointers owned by the pipeline)."""
+        sd, b, f = Tracks(), Tracks(), Tracks()
+        self.ctx._check(lib().tkf_pipeline_outputs(self.handle, C.byref(sd), C.byref(b), C.byref(f)))
+        return sd, b, f
+
+    def captures(self):
+        return lib().tkf_pipeline_captures(self.handle)
+
+    def build_ms(self):
+        """Duration of the building kernel in the last run (CUDA events inside the graph)."""
+        ms = C.c_float()
+        self.ctx._check(lib().tkf_pipeline_build_ms(self.handle, C.byref(ms)))
+        return ms.value
+
+    def index(self) -> "HitIndex":
+        """The pipeline's hit index (not owned: do not free)."""
+        h = HitIndex(self.ctx, lib().tkf_pipeline_index(self.handle))
+        h.free = lambda: None
+        return h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tkf_pipeline_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tracks_tensors(t: Tracks, n_layers, precision=FP32):
+    """torch views (no copy) of a tkf_tracks struct's planes: par [6, stride], cov [21, stride],
+    chi2, nhits, hit_idx [n_layers, stride]."""
+    import torch
+    dt = torch.float64 if precision == FP64 else torch.float32
+    code = {torch.float32: "<f4", torch.float64: "<f8", torch.int32: "<i4"}
+
+    def wrap(ptr, shape, dtype):
+        class _W:
+            __cuda_array_interface__ = {"shape": shape, "typestr": code[dtype], "data": (ptr, False), "version": 3}
+        return torch.as_tensor(_W(), device="cuda")
+    s = t.stride
+    return dict(par=wrap(t.par, (6, s), dt), cov=wrap(t.cov, (21, s), dt), chi2=wrap(t.chi2, (s,), dt),
+                nhits=wrap(t.nhits, (s,), torch.int32), hit_idx=wrap(t.hit_idx, (n_layers, s), torch.int32))

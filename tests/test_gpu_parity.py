@@ -36,6 +36,9 @@ def _ctx(prec=tkf.FP32, **kw):
 # ------------------------------------------------------------------ hit index
 
 def test_hit_index_matches_oracle_bins(det):
+    """Same bin contents as the oracle's index (bit for bit, up to hits within rounding of a
+    bin edge); inside a bin the GPU orders hits by (phi sixteenth of the bin, id) instead of by
+    id, and records where each sixteenth starts."""
     b = generate(EventSpec(seed=41, n_events=3, n_tracks=[1500, 0, 2500], noise_frac=0.3), det)
     ctx = _ctx()
     idx = ctx.build_hit_index(device_hits(b))
@@ -44,10 +47,16 @@ def test_hit_index_matches_oracle_bins(det):
     v = idx.view()
     n, L, NB = b.n_hits, det.n_layers, v.n_bins
     xyzi = _copy_dev(v.hit_xyzi, n * 4, torch.float32).view(n, 4).cpu().numpy()
-    off = _copy_dev(v.bin_off, b.n_events * L * NB + 1, torch.int32).cpu().numpy()
+    nbt = b.n_events * L * NB
+    sub = _copy_dev(v.bin_sub, nbt * 4, torch.int32).view(nbt, 4).cpu().numpy().view(np.uint32)
+    off = _copy_dev(v.bin_off, nbt + 1, torch.int32).cpu().numpy()
     pos = _copy_dev(v.pos_of_hit, n, torch.int32).cpu().numpy()
     assert off[0] == 0 and off[-1] == n and np.all(np.diff(off) >= 0)
     ids = xyzi[:, 3].view(np.int32)
+    starts = np.zeros((nbt, 17), dtype=np.int64)  # start of each of the 16 phi sixteenths, and the count
+    for t in range(1, 16):
+        starts[:, t] = (sub[:, (t - 1) // 4] >> (8 * ((t - 1) % 4))) & 0xFF
+    starts[:, 16] = np.diff(off)
     g = O.make_geom(det)
     n_edge = 0
     for e in range(b.n_events):
@@ -58,17 +67,30 @@ def test_hit_index_matches_oracle_bins(det):
             for bb in range(NB):
                 k = (e * L + l) * NB + bb
                 got = ids[off[k]:off[k + 1]]
-                assert np.all(np.diff(got) > 0)  # ascending event-local id inside a bin
+                cnt = len(got)
                 assert np.all(pos[h0 + got] == np.arange(off[k], off[k + 1]))
+                if cnt:
+                    # sixteenths: recorded starts are monotone and every hit lies in its own
+                    assert np.all(np.diff(starts[k]) >= 0) and starts[k, 16] == cnt
+                    coord = (np.arctan2(b.y[h0 + got].astype(np.float64), b.x[h0 + got]) + np.pi) * 63 / (2 * np.pi)
+                    frac = np.clip((coord - bb % 63) * 16, 0, 15.999999)
+                    sb = np.floor(frac).astype(int)
+                    for j in range(cnt):
+                        lo, hi = starts[k, sb[j]], starts[k, sb[j] + 1]
+                        if not (lo <= j < hi):
+                            assert abs(frac[j] - round(frac[j])) < 1e-4, (k, j, frac[j])
+                    for t in range(16):
+                        seg_ids = got[starts[k, t]:starts[k, t + 1]]
+                        assert np.all(np.diff(seg_ids) > 0)
                 ref = oi.order[oi.bin_off[l, bb]:oi.bin_off[l, bb + 1]]
-                if not np.array_equal(got, ref):
+                if not np.array_equal(np.sort(got), ref):
                     # only hits within rounding of a bin edge may land in the neighbouring bin
                     for hid in np.setxor1d(got, ref):
                         h = hits[hid]
                         eta = (np.arcsinh(h["z"] / det.radii[l]) + 2.0) / 0.1
-                        phi = (np.arctan2(h["y"], h["x"]) + np.pi) / (2 * np.pi) * 63
-                        edge = min(abs(eta - round(eta)), abs(phi - round(phi)))
-                        assert edge < 1e-4, (e, l, bb, hid, eta, phi)
+                        ph = (np.arctan2(h["y"], h["x"]) + np.pi) / (2 * np.pi) * 63
+                        edge = min(abs(eta - round(eta)), abs(ph - round(ph)))
+                        assert edge < 1e-4, (e, l, bb, hid, eta, ph)
                         n_edge += 1
     assert n_edge <= 4
 

@@ -1,0 +1,113 @@
+"""The batched pipeline (tkf_pipeline_*) and the work-tile autotuner: a CUDA-graph replay of
+the whole step gives exactly the results of the direct call sequence, replays reuse one
+capture, and building results do not depend on how seeds are split into work tiles."""
+import numpy as np
+import pytest
+
+from _gpu import device_hits
+from synth import Detector, EventSpec, event_sizes, generate
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1702_06359_gb300 import tkf  # noqa: E402
+
+
+def _batch(seed, n_events=8):
+    sizes, noise = event_sizes(seed, n_events, median=600, lo=50, hi=3000)
+    return generate(EventSpec(seed=seed, n_events=n_events, n_tracks=sizes, noise_frac=noise), Detector())
+
+
+def _direct(ctx, b, dh, sh, se):
+    L = ctx.cfg.n_layers
+    n = b.n_tracks
+    init = tkf.DeviceTracks.empty(n, L)
+    seeds = tkf.DeviceTracks.empty(n, L)
+    built = tkf.DeviceTracks.empty(n, L)
+    final = tkf.DeviceTracks.empty(n, L)
+    seeds.event = se
+    idx = ctx.build_hit_index(dh)
+    ctx.seed_state(dh, sh, init)
+    ctx.fit(dh, init, 0, 2, seeds)
+    seeds.event = se
+    ctx.build_tracks(idx, seeds, built)
+    ctx.fit(dh, init, 0, L - 1, final, hit_idx=built.hit_idx)
+    ctx.sync_status()
+    return built, final
+
+
+def _pipe_out(pipe, L, n):
+    _, built, fitted = pipe.outputs()
+    bt = tkf.tracks_tensors(built, L)
+    ft = tkf.tracks_tensors(fitted, L)
+    return ({k: v[..., :n].clone() for k, v in bt.items()}, {k: v[..., :n].clone() for k, v in ft.items()})
+
+
+def test_graph_replay_equals_direct_calls():
+    b = _batch(61)
+    b2 = _batch(62)
+    # same sizes for the in-place update below
+    n = min(b.n_tracks, b2.n_tracks)
+    ctx = tkf.Context(tkf.default_config())
+    L = ctx.cfg.n_layers
+    dh = device_hits(b)
+    sh = torch.as_tensor(np.ascontiguousarray(b.trk_hits[:, :3].T), dtype=torch.int32, device="cuda")
+    se = torch.as_tensor(b.trk_event, dtype=torch.int32, device="cuda")
+    pipe = tkf.DevicePipeline(ctx, max(b.n_hits, b2.n_hits), b.n_events, b.n_tracks, use_graph=True)
+    for _ in range(3):
+        pipe.run(dh, sh, se, b.n_tracks)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert pipe.captures() == 1
+    gb, gf = _pipe_out(pipe, L, b.n_tracks)
+    db, df = _direct(ctx, b, dh, sh, se)
+    assert torch.equal(gb["hit_idx"], db.hit_idx)
+    assert torch.equal(gb["par"], db.par) and torch.equal(gb["chi2"], db.chi2) and torch.equal(gb["nhits"], db.nhits)
+    assert torch.equal(gf["par"], df.par) and torch.equal(gf["cov"], df.cov) and torch.equal(gf["chi2"], df.chi2)
+    assert pipe.build_ms() > 0
+    # new data in the same buffers: the replay (no new capture) follows the data
+    b2x = device_hits(b2)
+    m = min(b.n_hits, b2.n_hits)
+    for k in ("x", "y", "z", "var_u", "var_v", "layer"):
+        getattr(dh, k)[:m].copy_(getattr(b2x, k)[:m])
+    pipe.run(dh, sh, se, b.n_tracks)
+    torch.cuda.synchronize()
+    assert pipe.captures() == 1
+    gb2, _ = _pipe_out(pipe, L, b.n_tracks)
+    db2, _ = _direct(ctx, b, dh, sh, se)
+    assert torch.equal(gb2["hit_idx"], db2.hit_idx) and torch.equal(gb2["par"], db2.par)
+    assert not torch.equal(gb2["par"], gb["par"])
+    del n
+
+
+def test_results_do_not_depend_on_the_work_tile():
+    b = _batch(63, n_events=12)
+    ctx = tkf.Context(tkf.default_config())
+    L = ctx.cfg.n_layers
+    dh = device_hits(b)
+    sh = torch.as_tensor(np.ascontiguousarray(b.trk_hits[:, :3].T), dtype=torch.int32, device="cuda")
+    se = torch.as_tensor(b.trk_event, dtype=torch.int32, device="cuda")
+    pipe = tkf.DevicePipeline(ctx, b.n_hits, b.n_events, b.n_tracks, use_graph=True)
+    pipe.run(dh, sh, se, b.n_tracks)
+    ref_b, ref_f = _pipe_out(pipe, L, b.n_tracks)
+    seeds, _, _ = pipe.outputs()
+
+    class _T:
+        def struct(self):
+            return seeds
+    out = tkf.DeviceTracks.empty(b.n_tracks, L)
+    tiles = [1, 5, 10, 37, 128]
+    best, ms = ctx.autotune_build(pipe.index(), _T(), out, tiles, repeats=2)
+    assert best in tiles and len(ms) == len(tiles) and all(x > 0 for x in ms)
+    assert ctx.config().seeds_per_block == best
+    for tile in tiles:
+        c2 = tkf.Context(tkf.default_config(seeds_per_block=tile))
+        p2 = tkf.DevicePipeline(c2, b.n_hits, b.n_events, b.n_tracks, use_graph=True)
+        p2.run(dh, sh, se, b.n_tracks)
+        gb, gf = _pipe_out(p2, L, b.n_tracks)
+        assert torch.equal(gb["hit_idx"], ref_b["hit_idx"]) and torch.equal(gb["par"], ref_b["par"]), tile
+        assert torch.equal(gf["par"], ref_f["par"]), tile
+        p2.close()

@@ -20,7 +20,7 @@ def test_noalloc_rejects_inputs_beyond_its_capacity():
     cfg = tkf.default_config()
     fake = 256  # never dereferenced: the size check comes before any device work
     h = tkf.Hits(fake, fake, fake, fake, fake, fake, fake, tkf.NOALLOC_MAX_HITS + 1, 1)
-    o = tkf.HitIndexOut(fake, fake, fake, fake, fake, fake)
+    o = tkf.HitIndexOut(fake, fake, fake, fake, fake, fake, fake)
     L = tkf.lib()
     assert L.tkf_build_hit_index_noalloc(C.byref(cfg), C.byref(h), C.byref(o), None) == tkf.ERR_TOO_LARGE
     # 11 events x 10 layers x 2520 bins = 277 200 bins > 262 144
@@ -55,6 +55,7 @@ def test_noalloc_index_equals_allocating_index_on_consecutive_calls():
         dh = device_hits(b)
         n, E = b.n_hits, b.n_events
         out = {"hit_xyzi": torch.full((n, 4), -7.0, device="cuda"), "hit_var": torch.full((n, 2), -7.0, device="cuda"),
+               "bin_sub": torch.full((E * L * NB, 4), -7, dtype=torch.int32, device="cuda"),
                "pos_of_hit": torch.full((n,), -7, dtype=torch.int32, device="cuda"),
                "bin_off": torch.full((E * L * NB + 1,), -7, dtype=torch.int32, device="cuda"),
                "var_max": torch.full((E * L, 2), -7.0, device="cuda"),
@@ -71,6 +72,7 @@ def test_noalloc_index_equals_allocating_index_on_consecutive_calls():
         v = ref.view()
         assert torch.equal(out["hit_xyzi"].view(-1), raw(v.hit_xyzi, n * 4, torch.float32))
         assert torch.equal(out["hit_var"].view(-1), raw(v.hit_var, n * 2, torch.float32))
+        assert torch.equal(out["bin_sub"].view(-1), raw(v.bin_sub, E * L * NB * 4, torch.int32))
         assert torch.equal(out["pos_of_hit"], raw(v.pos_of_hit, n, torch.int32))
         assert torch.equal(out["bin_off"], raw(v.bin_off, E * L * NB + 1, torch.int32))
         assert torch.equal(out["var_max"].view(-1), raw(v.var_max, E * L * 2, torch.float32))
