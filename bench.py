@@ -50,8 +50,9 @@ FLOP_PER_SEED = (PER_SEED["n_prop"] * (FLOP_PROPAGATE + FLOP_WINDOW) + PER_SEED[
 # FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # libtkf.so kernels per step: hit index (count, segment totals, segment scan, bin scan,
-# scatter, bin sort), seed estimate, seed fit, build, final fit
-KERNELS_PER_STEP = 10
+# scatter, bin sort), seed estimate, seed fit, seed ordering (key, segment totals, segment
+# scan, bin scan, place), build, final fit
+KERNELS_PER_STEP = 15
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 
 
@@ -226,6 +227,8 @@ def main():
     ap.add_argument("--cpu-tracks", type=int, default=200000, help="oracle CPU-baseline sample (tracks)")
     ap.add_argument("--ref-tracks", type=int, default=60000, help="reference-arm sample per step (tracks)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--seed-order", type=int, default=1,
+                    help="batched form: 1 = build seeds grouped by detector region (the per-event form keeps input order)")
     a = ap.parse_args()
     if a.impl == "reference":
         run_reference(a)
@@ -260,7 +263,7 @@ def main():
     }
     d = {k: v.to(dev, non_blocking=False) for k, v in host.items()}
     hits = tkf.DeviceHits(d["x"], d["y"], d["z"], d["var_u"], d["var_v"], d["layer"], d["event_off"])
-    ctx = tkf.Context(tkf.default_config())
+    ctx = tkf.Context(tkf.default_config(seed_order=a.seed_order))
     L = ctx.cfg.n_layers
     pipe = tkf.DevicePipeline(ctx, n_hits, b.n_events, n_tr, use_graph=True)
     stream = torch.cuda.current_stream()

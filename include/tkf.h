@@ -73,6 +73,9 @@ typedef struct {
     int32_t precision;                /* enum tkf_precision */
     int32_t seeds_per_block;          /* seeds per work tile of the build kernel (one warp takes a
                                          tile at a time); 0 = default */
+    int32_t seed_order;               /* 1: build seeds grouped by (event, eta bin, phi bin) so that a
+                                         warp's seeds share hit-index cache lines (results do not
+                                         depend on it); 0: in input order */
 } tkf_config;
 
 /* Hits of one or more events (device arrays of length n, caller-owned).  The hits of event e
@@ -120,7 +123,7 @@ typedef struct {
 
 /* Fills `cfg` with the plain-building workload of the toy barrel: 10 cylinders at
  * 4, 8, ..., 40 cm, Bz = 3.8 T, x/X0 = 0.03 per layer, pion mass, 40 x 0.1 eta bins from
- * -2, 63 phi bins, chi2 < 30, 6 candidates, building from layer 3, FP32. */
+ * -2, 63 phi bins, chi2 < 30, 6 candidates, building from layer 3, FP32, seeds in input order. */
 void tkf_default_config(tkf_config *cfg);
 
 /* Creates a context on the current CUDA device.  The context owns its scratch memory. */

@@ -235,8 +235,9 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U>::va
         if (t0 >= a.n_seeds) return;
         const int t1 = (int)min((long long)a.n_seeds, t0 + a.seeds_per_block);
         for (int sb = (int)t0; sb < t1; sb += spw) {
-            const int seed = sb + grp;
-            bool has = lane_ok && seed < t1;
+            const int slot = sb + grp;
+            bool has = lane_ok && slot < t1;
+            const int seed = has ? (a.s_perm ? __ldg(&a.s_perm[slot]) : slot) : 0;
             const int ev = (has && a.s_event) ? a.s_event[seed] : 0;
             if (has && (ev < 0 || ev >= a.n_events)) {
                 atomicOr(a.err, kErrBadEvent);

@@ -35,6 +35,7 @@ struct BuildArgs {
     // seeds
     const void *s_par, *s_cov, *s_chi2;
     const int *s_nhits, *s_hit, *s_event;
+    const int *s_perm;  // processing order of the seeds (null: input order)
     int s_stride;
     // best candidate per seed
     void *o_par, *o_cov, *o_chi2;
@@ -60,6 +61,10 @@ cudaError_t launch_build_fp64(const BuildArgs &a, int nmax, int grid, cudaStream
 // need no further allocation (used before capturing the pipeline into a CUDA graph).
 int hit_index_reserve(tkf_ctx *ctx, tkf_hit_index **idx, size_t max_hits, size_t max_events);
 
+// Scratch of the seed ordering in tkf_build_tracks, sized for max_seeds seeds of max_events
+// events (grown on demand outside graph capture; reserved by the pipeline).
+int seed_order_reserve(tkf_ctx *ctx, size_t max_seeds, size_t max_events);
+
 inline int build_nmax(int n)
 {
     return n <= 1 ? 1 : n <= 4 ? 4 : n <= 6 ? 6 : n <= 10 ? 10 : 16;
@@ -74,6 +79,10 @@ struct tkf_ctx {
     std::string err;
     int *d_tile = nullptr;  // work-tile counter of the persistent build kernel
     int *d_err = nullptr;   // error bits raised by kernels
+    // seed ordering scratch: key and permutation per seed, counts and offsets per (event, bin)
+    int *ord_key = nullptr, *ord_perm = nullptr, *ord_counts = nullptr, *ord_off = nullptr;
+    int *ord_seg_count = nullptr, *ord_seg_base = nullptr;
+    size_t ord_cap_seeds = 0, ord_cap_bins = 0, ord_cap_events = 0;
 };
 
 struct tkf_hit_index {

@@ -274,6 +274,31 @@ __global__ void k_bin_sort(const IndexGeom g, const int *bin_off, const int *ev_
     bin_sub[b] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
 }
 
+// ------------------------------------------------------------------ seed ordering for locality
+
+// key of each seed = (event, eta bin, phi bin) of its position on layer `layer`
+template <class R>
+__global__ void k_seed_key(const IndexGeom g, int layer, const R *par, int stride, const int *event, int n,
+                           int *keys, int *counts)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int ev = event ? event[i] : 0;
+    ev = ev < 0 ? 0 : (ev >= g.n_events ? g.n_events - 1 : ev);  // bad ids are reported by the build
+    const float x = (float)par[i], y = (float)par[stride + i], z = (float)par[2 * stride + i];
+    const int key = ev * g.n_bins + hit_bin(g, layer, x, y, z);
+    keys[i] = key;
+    atomicAdd(&counts[key], 1);
+}
+
+__global__ void k_seed_place(const int *keys, int *counts, const int *off, int n, int *perm)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int key = keys[i];
+    perm[off[key] + atomicSub(&counts[key], 1) - 1] = i;
+}
+
 // ------------------------------------------------------------------ seed estimate and fit
 
 struct FitGeom {
@@ -485,6 +510,28 @@ int hit_index_reserve(tkf_ctx *ctx, tkf_hit_index **out, size_t max_hits, size_t
     return TKF_OK;
 }
 
+int seed_order_reserve(tkf_ctx *ctx, size_t max_seeds, size_t max_events)
+{
+    const size_t nb = max_events * (size_t)ctx->cfg.n_eta_bins * ctx->cfg.n_phi_bins;
+    int st = TKF_OK;
+    if (max_seeds > ctx->ord_cap_seeds || !ctx->ord_key) {
+        if ((st = grow(ctx, &ctx->ord_key, max_seeds)) || (st = grow(ctx, &ctx->ord_perm, max_seeds))) return st;
+        ctx->ord_cap_seeds = max_seeds;
+    }
+    if (nb > ctx->ord_cap_bins || !ctx->ord_counts) {
+        if ((st = grow(ctx, &ctx->ord_counts, nb)) || (st = grow(ctx, &ctx->ord_off, nb + 1))) return st;
+        if (cudaMemset(ctx->ord_counts, 0, nb * sizeof(int)) != cudaSuccess)
+            return set_err(ctx, TKF_ERR_CUDA, "cudaMemset (seed order)");
+        ctx->ord_cap_bins = nb;
+    }
+    if (max_events > ctx->ord_cap_events || !ctx->ord_seg_count) {
+        if ((st = grow(ctx, &ctx->ord_seg_count, max_events)) || (st = grow(ctx, &ctx->ord_seg_base, max_events)))
+            return st;
+        ctx->ord_cap_events = max_events;
+    }
+    return TKF_OK;
+}
+
 }  // namespace tkf
 
 // ====================================================================== C ABI
@@ -514,6 +561,7 @@ void tkf_default_config(tkf_config *cfg)
     cfg->first_build_layer = 3;
     cfg->precision = TKF_FP32;
     cfg->seeds_per_block = 0;
+    cfg->seed_order = 0;
 }
 
 const char *tkf_status_string(int status)
@@ -567,6 +615,8 @@ int tkf_destroy(tkf_ctx *ctx)
     if (!ctx) return TKF_ERR_INVALID;
     cudaFree(ctx->d_tile);
     cudaFree(ctx->d_err);
+    for (int *p : {ctx->ord_key, ctx->ord_perm, ctx->ord_counts, ctx->ord_off, ctx->ord_seg_count, ctx->ord_seg_base})
+        cudaFree(p);
     delete ctx;
     return TKF_OK;
 }
@@ -815,13 +865,39 @@ int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *s
     a.n_cand_out = n_cand_out;
     a.tile_counter = ctx->d_tile;
     a.err = ctx->d_err;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c.seed_order) {
+        // counting sort of the seeds by (event, eta bin, phi bin) on the last seeding layer
+        if ((st = tkf::seed_order_reserve(ctx, (size_t)seeds->n, (size_t)idx->n_events))) return st;
+        IndexGeom g{};
+        g.L = c.n_layers;
+        g.n_eta = c.n_eta_bins;
+        g.n_phi = c.n_phi_bins;
+        g.n_bins = c.n_eta_bins * c.n_phi_bins;
+        g.n_events = idx->n_events;
+        for (int l = 0; l < c.n_layers; ++l) g.radius[l] = (float)c.radius[l];
+        g.eta_min = (float)c.eta_min;
+        g.inv_eta_w = (float)(1.0 / c.eta_bin_w);
+        const int nb = (seeds->n + 255) / 256, layer = c.first_build_layer - 1;
+        if (c.precision == TKF_FP64)
+            k_seed_key<double><<<nb, 256, 0, s>>>(g, layer, (const double *)seeds->par, seeds->stride, seeds->event,
+                                                  seeds->n, ctx->ord_key, ctx->ord_counts);
+        else
+            k_seed_key<float><<<nb, 256, 0, s>>>(g, layer, (const float *)seeds->par, seeds->stride, seeds->event,
+                                                 seeds->n, ctx->ord_key, ctx->ord_counts);
+        k_seg_total<<<(unsigned)idx->n_events, 256, 0, s>>>(ctx->ord_counts, ctx->ord_seg_count, g.n_bins);
+        k_seg_scan<<<1, 1024, 0, s>>>(ctx->ord_seg_count, ctx->ord_seg_base, idx->n_events);
+        k_bin_scan<<<(unsigned)idx->n_events, 256, 0, s>>>(ctx->ord_counts, ctx->ord_seg_base, ctx->ord_off, g.n_bins,
+                                                           idx->n_events);
+        k_seed_place<<<nb, 256, 0, s>>>(ctx->ord_key, ctx->ord_counts, ctx->ord_off, seeds->n, ctx->ord_perm);
+        a.s_perm = ctx->ord_perm;  // counts are back to zero after k_seed_place
+    }
     const int nmax = build_nmax(c.n_cand);
     auto launch = c.precision == TKF_FP32 ? launch_build_fp32 : c.precision == TKF_MIXED ? launch_build_mixed : launch_build_fp64;
     int occ = 0;
     TKF_CUDA(ctx, launch(a, nmax, 0, nullptr, &occ));
     const long long tiles = ((long long)seeds->n + a.seeds_per_block - 1) / a.seeds_per_block;
     const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)std::max(occ, 1) * ctx->sm_count));
-    cudaStream_t s = (cudaStream_t)stream;
     TKF_CUDA(ctx, cudaMemsetAsync(ctx->d_tile, 0, sizeof(int), s));
     TKF_CUDA(ctx, launch(a, nmax, grid, s, nullptr));
     TKF_CUDA(ctx, cudaGetLastError());

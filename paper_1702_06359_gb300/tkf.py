@@ -41,6 +41,7 @@ class Config(C.Structure):
         ("first_build_layer", C.c_int32),
         ("precision", C.c_int32),
         ("seeds_per_block", C.c_int32),
+        ("seed_order", C.c_int32),
     ]
 
 
