@@ -240,6 +240,87 @@ int tkf_autotune_build(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks 
                        const int32_t *tiles, int32_t n_tiles, int32_t repeats, float *ms_out, int32_t *best,
                        tkf_stream stream);
 
+/* ---------------------------------------------------------------- serving loop */
+
+/* A trigger-like request loop over the pipeline (the paper's GPU port found host set-up
+ * copies dominating, Sec. 5; here events stream in while earlier ones run).  Events are
+ * submitted one at a time and wait in a host queue bounded by queue_bytes; a worker thread
+ * packs every queued event that fits into the next free slot and launches it while other
+ * slots still run (continuous batching).  Each slot owns a context, a pipeline and device
+ * buffers for max_batch_events / max_batch_hits / max_batch_tracks, allocated at creation, so
+ * the device memory in use is fixed by those limits (events are admitted into a batch only if
+ * they fit its buffers).  Results land in pinned host buffers drawn from a pool bounded by
+ * result_bytes; while unreleased results hold all of it, no new batch starts (the queue then
+ * fills and submissions get TKF_ERR_AGAIN), so callers release results promptly.  Results of
+ * an event do not depend on the batch it ran in. */
+typedef struct tkf_server tkf_server;
+
+typedef struct {
+    int32_t n_slots;          /* batches in flight at once */
+    int32_t max_batch_events; /* events per batch */
+    int32_t max_batch_hits;   /* hits per batch (also the largest event accepted) */
+    int32_t max_batch_tracks; /* seeds per batch (also the largest event accepted) */
+    size_t queue_bytes;       /* host bytes of submitted, not yet launched events */
+    size_t result_bytes;      /* pinned host bytes for results; at least one full batch,
+                                 max_batch_tracks * (29 + n_layers) * 4 */
+} tkf_server_options;
+
+/* One event in host memory: hit planes of length n_hits and seed_hits [3][n_seeds], the
+ * event-local hit ids of each seed on layers 0, 1, 2.  borrow = 0: tkf_submit_event copies the
+ * arrays (the caller may free them on return).  borrow = 1: the server reads them in place --
+ * the hit planes straight into device memory, fastest from pinned memory -- so the caller
+ * keeps them alive and unchanged until tkf_poll reports the event done (for an event released
+ * before that, until tkf_server_destroy returns). */
+typedef struct {
+    const float *x, *y, *z, *var_u, *var_v;
+    const int32_t *layer;
+    int32_t n_hits;
+    const int32_t *seed_hits;
+    int32_t n_seeds;
+    int32_t borrow;
+} tkf_event;
+
+/* Result of one event (pinned host memory owned by the server, valid until tkf_release): the
+ * final fit of the best built candidate of every seed -- par [6][stride], cov [21][stride],
+ * chi2, nhits, first n_tracks columns -- and its hit ids [n_layers][stride] (event-local,
+ * -1 = hole); timestamps (steady clock, ns) of submission, batch launch and completion. */
+typedef struct {
+    int32_t status, n_tracks, stride;
+    const float *par, *cov, *chi2;
+    const int32_t *nhits, *hit_idx;
+    int64_t t_submit_ns, t_start_ns, t_done_ns;
+} tkf_result;
+
+typedef struct {
+    int64_t submitted, rejected, events_done, tracks_done, batches, max_batch_events;
+} tkf_server_stats;
+
+/* Defaults: 3 slots, 64 events, 4 Mi hits and 256 Ki seeds per batch, 1 GiB host queue,
+ * 1 GiB of pinned result memory. */
+void tkf_server_default_options(tkf_server_options *opt);
+
+/* Creates the server on the current device (precision FP32 or MIXED) and starts its worker.
+ * Errors: TKF_ERR_INVALID (bad options, result_bytes below one batch), TKF_ERR_NOMEM,
+ * TKF_ERR_CUDA. */
+int tkf_server_create(const tkf_config *cfg, const tkf_server_options *opt, tkf_server **out);
+/* Stops the worker after the batches in flight finish, and frees everything. */
+int tkf_server_destroy(tkf_server *server);
+
+/* Non-blocking submission.  Errors: TKF_ERR_AGAIN (host queue full: retry later),
+ * TKF_ERR_INVALID (malformed event, or larger than a batch), a worker's earlier error. */
+int tkf_submit_event(tkf_server *server, const tkf_event *event, uint64_t *ticket);
+
+/* Result of `ticket`: waits up to timeout_us microseconds (0: do not wait).
+ * Errors: TKF_ERR_NOTREADY (timeout_us = 0 and not done), TKF_ERR_TIMEOUT, TKF_ERR_INVALID
+ * (unknown or released ticket). */
+int tkf_poll(tkf_server *server, uint64_t ticket, tkf_result *result, int64_t timeout_us);
+
+/* Frees the result of `ticket` (its pointers become invalid; its share of the result memory
+ * returns to the pool once every event of its batch is released). */
+int tkf_release(tkf_server *server, uint64_t ticket);
+
+int tkf_server_get_stats(tkf_server *server, tkf_server_stats *out);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 
 /* Caller-owned output arrays of tkf_build_hit_index_noalloc (device memory), laid out as in

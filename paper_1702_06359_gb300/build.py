@@ -15,7 +15,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtkf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tkf_api.cu", "tkf_build_fp32.cu", "tkf_build_mixed.cu", "tkf_build_fp64.cu", "tkf_pipeline.cu"]
+SOURCES = ["tkf_api.cu", "tkf_build_fp32.cu", "tkf_build_mixed.cu", "tkf_build_fp64.cu", "tkf_pipeline.cu",
+           "tkf_server.cu"]
 
 
 def nvcc() -> str:

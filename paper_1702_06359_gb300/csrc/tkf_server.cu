@@ -1,0 +1,580 @@
+// tkf_server: a trigger-like serving loop over the tracking pipeline.  Events arrive one at a
+// time (tkf_submit_event), wait in a bounded host queue, and a worker thread packs every
+// queued event that fits into the next free slot -- a slot owns a context, a pipeline and
+// device buffers sized at creation, so device memory is bounded up front -- and launches it
+// on the slot's stream while other slots are still running (continuous batching: arrivals
+// join the next batch as soon as a slot frees up).  Completion is observed with CUDA events;
+// each event's tracks are copied out with its submit/start/done timestamps (tkf_poll).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+int64_t now_ns()
+{
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+struct Pending {
+    uint64_t ticket;
+    std::vector<float> x, y, z, vu, vv;  // owned copies (borrow = 0)
+    std::vector<int> layer, seeds;       // seeds: [3][n_seeds] event-local hit ids
+    const float *bx = nullptr, *by = nullptr, *bz = nullptr, *bvu = nullptr, *bvv = nullptr;
+    const int *blayer = nullptr, *bseeds = nullptr;  // the caller's arrays (borrow = 1)
+    bool borrowed = false;
+    int n_hits, n_seeds;
+    int64_t t_submit;
+    size_t bytes;
+    const float *px() const { return borrowed ? bx : x.data(); }
+    const float *py() const { return borrowed ? by : y.data(); }
+    const float *pz() const { return borrowed ? bz : z.data(); }
+    const float *pvu() const { return borrowed ? bvu : vu.data(); }
+    const float *pvv() const { return borrowed ? bvv : vv.data(); }
+    const int *player() const { return borrowed ? blayer : layer.data(); }
+    const int *pseeds() const { return borrowed ? bseeds : seeds.data(); }
+};
+
+// Pinned host memory receiving one batch's results (planes of `cap` tracks), shared by that
+// batch's events until the last of them is released, then reused by a later batch.
+struct OutBuf {
+    float *par = nullptr, *cov = nullptr, *chi2 = nullptr;
+    int *nhits = nullptr, *hit = nullptr;
+    int cap = 0;
+    size_t bytes = 0;
+    int refs = 0;
+};
+
+struct Done {
+    OutBuf *buf = nullptr;  // results at column trk0 of the batch's planes (stride buf->cap)
+    int trk0 = 0;
+    int64_t t_submit = 0, t_start = 0, t_done = 0;
+    int status = TKF_OK;
+    int n = 0;
+    bool done = false;
+};
+
+template <class T> struct Pinned {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaError_t alloc(size_t count)
+    {
+        n = count;
+        return cudaMallocHost((void **)&p, std::max<size_t>(count, 1) * sizeof(T));
+    }
+    void free()
+    {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+    }
+};
+
+struct EvInfo {
+    uint64_t ticket;
+    int hit0, n_hits, trk0, n_tracks;
+    int64_t t_submit;
+};
+
+struct Slot {
+    tkf_ctx *ctx = nullptr;
+    tkf_pipeline *pipe = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    // host staging (pinned) and device inputs
+    Pinned<float> hx, hy, hz, hvu, hvv;
+    Pinned<int> hlayer, hoff, hseeds, hsev;
+    float *dx = nullptr, *dy = nullptr, *dz = nullptr, *dvu = nullptr, *dvv = nullptr;
+    int *dlayer = nullptr, *doff = nullptr, *dseeds = nullptr, *dsev = nullptr;
+    OutBuf *out = nullptr;  // result buffer of the running batch
+    bool busy = false;
+    int64_t t_start = 0;
+    int n_tracks = 0;
+    std::vector<EvInfo> evs;
+};
+
+}  // namespace
+
+struct tkf_server {
+    tkf_config cfg{};
+    tkf_server_options opt{};
+    int device = 0;
+    std::vector<Slot> slots;
+    std::deque<Pending> queue;
+    size_t queued_bytes = 0;
+    std::unordered_map<uint64_t, Done> results;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    tkf_server_stats stats{};
+    int worker_error = TKF_OK;
+    std::vector<OutBuf *> free_bufs;  // result buffers no event holds
+    size_t result_bytes = 0;          // pinned bytes of all result buffers, free or held
+};
+
+namespace {
+
+void free_slot(Slot &s)
+{
+    if (s.pipe) tkf_pipeline_destroy(s.pipe);
+    if (s.ctx) tkf_destroy(s.ctx);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.done) cudaEventDestroy(s.done);
+    for (void *p : {(void *)s.dx, (void *)s.dy, (void *)s.dz, (void *)s.dvu, (void *)s.dvv, (void *)s.dlayer,
+                    (void *)s.doff, (void *)s.dseeds, (void *)s.dsev})
+        cudaFree(p);
+    s.hx.free(); s.hy.free(); s.hz.free(); s.hvu.free(); s.hvv.free();
+    s.hlayer.free(); s.hoff.free(); s.hseeds.free(); s.hsev.free();
+}
+
+size_t outbuf_bytes(const tkf_server *sv, int cap) { return (size_t)cap * (29 + sv->cfg.n_layers) * 4; }
+
+void free_outbuf(tkf_server *sv, OutBuf *b)
+{
+    for (void *p : {(void *)b->par, (void *)b->cov, (void *)b->chi2, (void *)b->nhits, (void *)b->hit})
+        if (p) cudaFreeHost(p);
+    sv->result_bytes -= b->bytes;
+    delete b;
+}
+
+// A result buffer for a batch of `trk` tracks (called with the lock held): a free one of the
+// batch's size class (the next power of two from 1024, at most max_batch_tracks), else a new
+// one within the pinned-memory budget opt.result_bytes, freeing idle buffers of other sizes
+// first.  nullptr when the budget is held by unreleased results (the batch waits).
+OutBuf *get_outbuf(tkf_server *sv, int trk)
+{
+    int cap = 1024;
+    while (cap < trk) cap *= 2;
+    cap = std::min(cap, std::max(sv->opt.max_batch_tracks, trk));
+    for (size_t k = 0; k < sv->free_bufs.size(); ++k)
+        if (sv->free_bufs[k]->cap == cap) {
+            OutBuf *b = sv->free_bufs[k];
+            sv->free_bufs.erase(sv->free_bufs.begin() + k);
+            return b;
+        }
+    const size_t bytes = outbuf_bytes(sv, cap);
+    while (sv->result_bytes + bytes > sv->opt.result_bytes && !sv->free_bufs.empty()) {
+        free_outbuf(sv, sv->free_bufs.back());
+        sv->free_bufs.pop_back();
+    }
+    if (sv->result_bytes + bytes > sv->opt.result_bytes) return nullptr;
+    OutBuf *b = new (std::nothrow) OutBuf();
+    if (!b) return nullptr;
+    b->cap = cap;
+    b->bytes = bytes;
+    sv->result_bytes += bytes;
+    const size_t T = cap, L = sv->cfg.n_layers;
+    if (cudaMallocHost((void **)&b->par, 6 * T * 4) || cudaMallocHost((void **)&b->cov, 21 * T * 4) ||
+        cudaMallocHost((void **)&b->chi2, T * 4) || cudaMallocHost((void **)&b->nhits, T * 4) ||
+        cudaMallocHost((void **)&b->hit, L * T * 4)) {
+        free_outbuf(sv, b);
+        return nullptr;
+    }
+    return b;
+}
+
+void unref(tkf_server *sv, OutBuf *b)
+{
+    if (b && --b->refs == 0) sv->free_bufs.push_back(b);
+}
+
+int init_slot(tkf_server *sv, Slot &s)
+{
+    const tkf_server_options &o = sv->opt;
+    const size_t H = o.max_batch_hits, T = o.max_batch_tracks, E = o.max_batch_events;
+    int st = tkf_create(&sv->cfg, &s.ctx);
+    if (st) return st;
+    if ((st = tkf_pipeline_create(s.ctx, (int)H, (int)E, (int)T, 0, &s.pipe))) return st;
+    cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+    if (!e) e = s.hx.alloc(H); if (!e) e = s.hy.alloc(H); if (!e) e = s.hz.alloc(H);
+    if (!e) e = s.hvu.alloc(H); if (!e) e = s.hvv.alloc(H); if (!e) e = s.hlayer.alloc(H);
+    if (!e) e = s.hoff.alloc(E + 1); if (!e) e = s.hseeds.alloc(3 * T); if (!e) e = s.hsev.alloc(T);
+    const size_t h1 = std::max<size_t>(H, 1), t1 = std::max<size_t>(T, 1);
+    if (!e) e = cudaMalloc((void **)&s.dx, h1 * 4); if (!e) e = cudaMalloc((void **)&s.dy, h1 * 4);
+    if (!e) e = cudaMalloc((void **)&s.dz, h1 * 4); if (!e) e = cudaMalloc((void **)&s.dvu, h1 * 4);
+    if (!e) e = cudaMalloc((void **)&s.dvv, h1 * 4); if (!e) e = cudaMalloc((void **)&s.dlayer, h1 * 4);
+    if (!e) e = cudaMalloc((void **)&s.doff, (E + 1) * 4); if (!e) e = cudaMalloc((void **)&s.dseeds, 3 * t1 * 4);
+    if (!e) e = cudaMalloc((void **)&s.dsev, t1 * 4);
+    if (e) return e == cudaErrorMemoryAllocation ? TKF_ERR_NOMEM : TKF_ERR_CUDA;
+    return TKF_OK;
+}
+
+// Packs `evs` into slot `s` and queues copies, the pipeline and the result copies on its stream.
+// Borrowed hit planes are copied straight from the caller's memory to the device; owned ones
+// and every seed list (rebased to batch hit ids) go through the slot's pinned staging.
+int launch_batch(tkf_server *sv, Slot &s, std::vector<Pending> &evs)
+{
+    const int L = sv->cfg.n_layers;
+    const size_t T = sv->opt.max_batch_tracks;
+    cudaStream_t st = s.stream;
+    cudaError_t e = cudaSuccess;
+    auto h2d = [&](void *d, const void *h, size_t bytes) {
+        if (!e && bytes) e = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st);
+    };
+    int hit = 0, trk = 0, staged0 = -1;
+    s.evs.clear();
+    auto flush_staged = [&](int upto) {  // owned events staged in [staged0, upto)
+        if (staged0 < 0 || upto <= staged0) return;
+        const size_t n = (size_t)(upto - staged0) * 4;
+        h2d(s.dx + staged0, s.hx.p + staged0, n); h2d(s.dy + staged0, s.hy.p + staged0, n);
+        h2d(s.dz + staged0, s.hz.p + staged0, n); h2d(s.dvu + staged0, s.hvu.p + staged0, n);
+        h2d(s.dvv + staged0, s.hvv.p + staged0, n); h2d(s.dlayer + staged0, s.hlayer.p + staged0, n);
+        staged0 = -1;
+    };
+    for (size_t k = 0; k < evs.size(); ++k) {
+        Pending &p = evs[k];
+        const size_t nb = (size_t)p.n_hits * 4;
+        s.hoff.p[k] = hit;
+        if (p.borrowed) {
+            flush_staged(hit);
+            h2d(s.dx + hit, p.bx, nb); h2d(s.dy + hit, p.by, nb); h2d(s.dz + hit, p.bz, nb);
+            h2d(s.dvu + hit, p.bvu, nb); h2d(s.dvv + hit, p.bvv, nb); h2d(s.dlayer + hit, p.blayer, nb);
+        } else {
+            if (staged0 < 0) staged0 = hit;
+            std::memcpy(s.hx.p + hit, p.px(), nb);
+            std::memcpy(s.hy.p + hit, p.py(), nb);
+            std::memcpy(s.hz.p + hit, p.pz(), nb);
+            std::memcpy(s.hvu.p + hit, p.pvu(), nb);
+            std::memcpy(s.hvv.p + hit, p.pvv(), nb);
+            std::memcpy(s.hlayer.p + hit, p.player(), nb);
+        }
+        const int *sd = p.pseeds();
+        for (int j = 0; j < 3; ++j)
+            for (int t = 0; t < p.n_seeds; ++t) s.hseeds.p[j * T + trk + t] = sd[(size_t)j * p.n_seeds + t] + hit;
+        for (int t = 0; t < p.n_seeds; ++t) s.hsev.p[trk + t] = (int)k;
+        s.evs.push_back({p.ticket, hit, p.n_hits, trk, p.n_seeds, p.t_submit});
+        hit += p.n_hits;
+        trk += p.n_seeds;
+    }
+    flush_staged(hit);
+    const int E = (int)evs.size();
+    s.hoff.p[E] = hit;
+    s.n_tracks = trk;
+    h2d(s.doff, s.hoff.p, (E + 1) * 4);
+    if (!e && trk) e = cudaMemcpy2DAsync(s.dseeds, T * 4, s.hseeds.p, T * 4, trk * 4, 3, cudaMemcpyHostToDevice, st);
+    h2d(s.dsev, s.hsev.p, trk * 4);
+    if (e) return TKF_ERR_CUDA;
+    tkf_hits h{};
+    h.x = s.dx; h.y = s.dy; h.z = s.dz; h.var_u = s.dvu; h.var_v = s.dvv; h.layer = s.dlayer;
+    h.event_off = s.doff;
+    h.n = hit;
+    h.n_events = E;
+    int rc = tkf_pipeline_run(s.pipe, &h, s.dseeds, s.dsev, trk, (tkf_stream)st);
+    if (rc) return rc;
+    tkf_tracks built, fitted;
+    tkf_pipeline_outputs(s.pipe, nullptr, &built, &fitted);
+    const size_t es = sizeof(float), dp = (size_t)fitted.stride * es;
+    OutBuf *o = s.out;
+    const size_t hp = (size_t)o->cap * es;  // host pitch
+    if (trk) {
+        e = cudaMemcpy2DAsync(o->par, hp, fitted.par, dp, trk * es, 6, cudaMemcpyDeviceToHost, st);
+        if (!e) e = cudaMemcpy2DAsync(o->cov, hp, fitted.cov, dp, trk * es, 21, cudaMemcpyDeviceToHost, st);
+        if (!e) e = cudaMemcpyAsync(o->chi2, fitted.chi2, trk * es, cudaMemcpyDeviceToHost, st);
+        if (!e) e = cudaMemcpyAsync(o->nhits, fitted.nhits, trk * 4, cudaMemcpyDeviceToHost, st);
+        if (!e) e = cudaMemcpy2DAsync(o->hit, hp, built.hit_idx, (size_t)built.stride * 4, trk * 4, L,
+                                      cudaMemcpyDeviceToHost, st);
+    }
+    if (!e) e = cudaEventRecord(s.done, st);
+    if (e) return TKF_ERR_CUDA;
+    s.t_start = now_ns();
+    return TKF_OK;
+}
+
+// Hands each finished event its columns of the batch's result buffer, with hit ids made
+// event-local (called with the lock held).
+void harvest(tkf_server *sv, Slot &s)
+{
+    const int L = sv->cfg.n_layers;
+    const int64_t t_done = now_ns();
+    OutBuf *o = s.out;
+    const size_t T = o->cap;
+    o->refs = 1;  // held by this function until the end
+    for (const EvInfo &ev : s.evs) {
+        auto it = sv->results.find(ev.ticket);
+        if (it == sv->results.end()) continue;  // released before completion
+        Done &d = it->second;
+        for (int l = 0; l < L; ++l) {
+            int *row = o->hit + l * T + ev.trk0;
+            for (int t = 0; t < ev.n_tracks; ++t) row[t] = row[t] >= 0 ? row[t] - ev.hit0 : -1;
+        }
+        d.buf = o;
+        o->refs += 1;
+        d.trk0 = ev.trk0;
+        d.n = ev.n_tracks;
+        d.t_submit = ev.t_submit;
+        d.t_start = s.t_start;
+        d.t_done = t_done;
+        d.status = TKF_OK;
+        d.done = true;
+        sv->stats.events_done += 1;
+        sv->stats.tracks_done += ev.n_tracks;
+    }
+    unref(sv, o);
+    s.out = nullptr;
+    sv->stats.batches += 1;
+    sv->stats.max_batch_events = std::max<int64_t>(sv->stats.max_batch_events, (int64_t)s.evs.size());
+    s.busy = false;
+    s.evs.clear();
+}
+
+void worker_loop(tkf_server *sv)
+{
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    while (true) {
+        // completed batches
+        for (Slot &s : sv->slots)
+            if (s.busy && cudaEventQuery(s.done) == cudaSuccess) harvest(sv, s);
+        sv->cv_done.notify_all();
+        if (sv->stop) break;
+        // new batches on free slots: every queued event that fits
+        bool launched = false;
+        for (Slot &s : sv->slots) {
+            if (s.busy || sv->queue.empty()) continue;
+            std::vector<Pending> batch;
+            size_t hits = 0, trks = 0;
+            while (!sv->queue.empty() && (int)batch.size() < sv->opt.max_batch_events) {
+                Pending &p = sv->queue.front();
+                if (hits + p.n_hits > (size_t)sv->opt.max_batch_hits || trks + p.n_seeds > (size_t)sv->opt.max_batch_tracks)
+                    break;
+                hits += p.n_hits;
+                trks += p.n_seeds;
+                sv->queued_bytes -= p.bytes;
+                batch.push_back(std::move(p));
+                sv->queue.pop_front();
+            }
+            if (batch.empty()) continue;
+            s.out = get_outbuf(sv, (int)trks);
+            if (!s.out) {  // result memory held by unreleased results: put the batch back, wait
+                for (auto it = batch.rbegin(); it != batch.rend(); ++it) {
+                    sv->queued_bytes += it->bytes;
+                    sv->queue.push_front(std::move(*it));
+                }
+                break;
+            }
+            s.busy = true;  // owned by this thread from here; submitters only touch the queue
+            lk.unlock();
+            const int rc = launch_batch(sv, s, batch);
+            lk.lock();
+            if (rc) {
+                s.busy = false;
+                sv->free_bufs.push_back(s.out);
+                s.out = nullptr;
+                sv->worker_error = rc;
+                for (Pending &p : batch) {
+                    auto it = sv->results.find(p.ticket);
+                    if (it != sv->results.end()) {
+                        it->second.done = true;
+                        it->second.status = rc;
+                    }
+                }
+            }
+            launched = true;
+        }
+        bool any_busy = false;
+        for (Slot &s : sv->slots) any_busy |= s.busy;
+        if (!launched && !any_busy && !sv->queue.empty()) {
+            // the queue waits for result memory: sleep until a release (or stop)
+            sv->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        } else if (!launched) {
+            // wait for a submission, or poll the running batches every 20 microseconds
+            if (any_busy)
+                sv->cv_work.wait_for(lk, std::chrono::microseconds(20));
+            else
+                sv->cv_work.wait_for(lk, std::chrono::milliseconds(5),
+                                     [sv] { return sv->stop || !sv->queue.empty(); });
+        }
+    }
+    // drain: wait for running batches so that their buffers can be freed
+    for (Slot &s : sv->slots)
+        if (s.busy) {
+            lk.unlock();
+            cudaEventSynchronize(s.done);
+            lk.lock();
+            harvest(sv, s);
+        }
+    sv->cv_done.notify_all();
+}
+
+}  // namespace
+
+extern "C" {
+
+void tkf_server_default_options(tkf_server_options *o)
+{
+    if (!o) return;
+    o->n_slots = 3;
+    o->max_batch_events = 64;
+    o->max_batch_hits = 1 << 22;
+    o->max_batch_tracks = 1 << 18;
+    o->queue_bytes = (size_t)1 << 30;
+    o->result_bytes = (size_t)1 << 30;
+}
+
+int tkf_server_create(const tkf_config *cfg, const tkf_server_options *opt, tkf_server **out)
+{
+    if (!cfg || !opt || !out) return TKF_ERR_INVALID;
+    *out = nullptr;
+    if (opt->n_slots < 1 || opt->max_batch_events < 1 || opt->max_batch_hits < 1 || opt->max_batch_tracks < 1 ||
+        cfg->precision == TKF_FP64 || cfg->n_layers < 1 ||
+        opt->result_bytes < (size_t)opt->max_batch_tracks * (29 + cfg->n_layers) * 4)
+        return TKF_ERR_INVALID;
+    tkf_server *sv = new (std::nothrow) tkf_server();
+    if (!sv) return TKF_ERR_NOMEM;
+    sv->cfg = *cfg;
+    sv->opt = *opt;
+    if (cudaGetDevice(&sv->device) != cudaSuccess) {
+        delete sv;
+        return TKF_ERR_CUDA;
+    }
+    sv->slots.resize(opt->n_slots);
+    for (Slot &s : sv->slots) {
+        const int st = init_slot(sv, s);
+        if (st) {
+            for (Slot &t : sv->slots) free_slot(t);
+            delete sv;
+            return st;
+        }
+    }
+    sv->worker = std::thread(worker_loop, sv);
+    *out = sv;
+    return TKF_OK;
+}
+
+int tkf_server_destroy(tkf_server *sv)
+{
+    if (!sv) return TKF_ERR_INVALID;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    for (Slot &s : sv->slots) free_slot(s);
+    std::vector<OutBuf *> held;
+    for (auto &kv : sv->results)
+        if (kv.second.buf && std::find(held.begin(), held.end(), kv.second.buf) == held.end())
+            held.push_back(kv.second.buf);
+    for (OutBuf *b : held) free_outbuf(sv, b);
+    for (OutBuf *b : sv->free_bufs) free_outbuf(sv, b);
+    delete sv;
+    return TKF_OK;
+}
+
+int tkf_submit_event(tkf_server *sv, const tkf_event *ev, uint64_t *ticket)
+{
+    const int64_t t_submit = now_ns();
+    if (!sv || !ev || !ticket || ev->n_hits < 0 || ev->n_seeds < 0) return TKF_ERR_INVALID;
+    if (ev->n_hits > 0 && (!ev->x || !ev->y || !ev->z || !ev->var_u || !ev->var_v || !ev->layer)) return TKF_ERR_INVALID;
+    if (ev->n_seeds > 0 && !ev->seed_hits) return TKF_ERR_INVALID;
+    if (ev->n_hits > sv->opt.max_batch_hits || ev->n_seeds > sv->opt.max_batch_tracks) return TKF_ERR_INVALID;
+    for (int t = 0; t < 3 * ev->n_seeds; ++t)
+        if (ev->seed_hits[t] < 0 || ev->seed_hits[t] >= ev->n_hits) return TKF_ERR_INVALID;
+    const size_t bytes = ev->borrow ? 64 : (size_t)ev->n_hits * 24 + (size_t)ev->n_seeds * 12;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->worker_error) return sv->worker_error;
+        if (sv->queued_bytes + bytes > sv->opt.queue_bytes) {
+            sv->stats.rejected += 1;
+            return TKF_ERR_AGAIN;
+        }
+        sv->queued_bytes += bytes;  // reserve before copying outside the lock
+    }
+    Pending p;
+    p.n_hits = ev->n_hits;
+    p.n_seeds = ev->n_seeds;
+    if (ev->borrow) {
+        p.borrowed = true;
+        p.bx = ev->x; p.by = ev->y; p.bz = ev->z; p.bvu = ev->var_u; p.bvv = ev->var_v;
+        p.blayer = ev->layer;
+        p.bseeds = ev->seed_hits;
+    } else {
+        p.x.assign(ev->x, ev->x + ev->n_hits);
+        p.y.assign(ev->y, ev->y + ev->n_hits);
+        p.z.assign(ev->z, ev->z + ev->n_hits);
+        p.vu.assign(ev->var_u, ev->var_u + ev->n_hits);
+        p.vv.assign(ev->var_v, ev->var_v + ev->n_hits);
+        p.layer.assign(ev->layer, ev->layer + ev->n_hits);
+        p.seeds.assign(ev->seed_hits, ev->seed_hits + 3 * ev->n_seeds);
+    }
+    p.bytes = bytes;
+    p.t_submit = t_submit;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        p.ticket = sv->next_ticket++;
+        *ticket = p.ticket;
+        sv->results.emplace(p.ticket, Done());
+        sv->queue.push_back(std::move(p));
+        sv->stats.submitted += 1;
+    }
+    sv->cv_work.notify_one();
+    return TKF_OK;
+}
+
+int tkf_poll(tkf_server *sv, uint64_t ticket, tkf_result *r, int64_t timeout_us)
+{
+    if (!sv || !r) return TKF_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->results.find(ticket);
+    if (it == sv->results.end()) return TKF_ERR_INVALID;
+    if (!it->second.done) {
+        if (timeout_us == 0) return TKF_ERR_NOTREADY;
+        const bool ok = sv->cv_done.wait_for(lk, std::chrono::microseconds(std::max<int64_t>(timeout_us, 1)), [&] {
+            auto jt = sv->results.find(ticket);
+            return jt == sv->results.end() || jt->second.done;
+        });
+        it = sv->results.find(ticket);
+        if (it == sv->results.end()) return TKF_ERR_INVALID;
+        if (!ok || !it->second.done) return TKF_ERR_TIMEOUT;
+    }
+    const Done &d = it->second;
+    r->status = d.status;
+    r->n_tracks = d.n;
+    const OutBuf *o = d.buf;
+    r->stride = o ? o->cap : 0;
+    r->par = o ? o->par + d.trk0 : nullptr;
+    r->cov = o ? o->cov + d.trk0 : nullptr;
+    r->chi2 = o ? o->chi2 + d.trk0 : nullptr;
+    r->nhits = o ? o->nhits + d.trk0 : nullptr;
+    r->hit_idx = o ? o->hit + d.trk0 : nullptr;
+    r->t_submit_ns = d.t_submit;
+    r->t_start_ns = d.t_start;
+    r->t_done_ns = d.t_done;
+    return TKF_OK;
+}
+
+int tkf_release(tkf_server *sv, uint64_t ticket)
+{
+    if (!sv) return TKF_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->results.find(ticket);
+    if (it == sv->results.end()) return TKF_ERR_INVALID;
+    unref(sv, it->second.buf);
+    sv->results.erase(it);
+    sv->cv_work.notify_one();  // a batch may be waiting for result memory
+    return TKF_OK;
+}
+
+int tkf_server_get_stats(tkf_server *sv, tkf_server_stats *out)
+{
+    if (!sv || !out) return TKF_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    *out = sv->stats;
+    return TKF_OK;
+}
+
+}  // extern "C"

@@ -67,6 +67,28 @@ class HitIndexView(C.Structure):
                 ("n", C.c_int32), ("n_events", C.c_int32), ("n_layers", C.c_int32), ("n_bins", C.c_int32)]
 
 
+class ServerOptions(C.Structure):
+    _fields_ = [("n_slots", C.c_int32), ("max_batch_events", C.c_int32), ("max_batch_hits", C.c_int32),
+                ("max_batch_tracks", C.c_int32), ("queue_bytes", C.c_size_t), ("result_bytes", C.c_size_t)]
+
+
+class Event(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("var_u", C.c_void_p),
+                ("var_v", C.c_void_p), ("layer", C.c_void_p), ("n_hits", C.c_int32), ("seed_hits", C.c_void_p),
+                ("n_seeds", C.c_int32), ("borrow", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_tracks", C.c_int32), ("stride", C.c_int32), ("par", C.c_void_p), ("cov", C.c_void_p),
+                ("chi2", C.c_void_p), ("nhits", C.c_void_p), ("hit_idx", C.c_void_p), ("t_submit_ns", C.c_int64),
+                ("t_start_ns", C.c_int64), ("t_done_ns", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("submitted", "rejected", "events_done", "tracks_done", "batches",
+                                         "max_batch_events")]
+
+
 _lib = None
 
 
@@ -110,11 +132,20 @@ def lib():
         L.tkf_pipeline_index.argtypes = [vp]
         L.tkf_pipeline_build_ms.argtypes = [vp, C.POINTER(C.c_float)]
         L.tkf_autotune_build.argtypes = [vp, vp, C.POINTER(Tracks), C.POINTER(Tracks), vp, i32, i32, vp, vp, vp]
+        L.tkf_server_default_options.argtypes = [C.POINTER(ServerOptions)]
+        L.tkf_server_create.argtypes = [C.POINTER(Config), C.POINTER(ServerOptions), C.POINTER(vp)]
+        L.tkf_server_destroy.argtypes = [vp]
+        L.tkf_submit_event.argtypes = [vp, C.POINTER(Event), C.POINTER(C.c_uint64)]
+        L.tkf_poll.argtypes = [vp, C.c_uint64, C.POINTER(Result), C.c_int64]
+        L.tkf_release.argtypes = [vp, C.c_uint64]
+        L.tkf_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
         L.tkf_build_hit_index_noalloc.argtypes = [C.POINTER(Config), C.POINTER(Hits), C.POINTER(HitIndexOut), vp]
         for name in declared_functions():
-            if name not in ("tkf_last_error", "tkf_status_string", "tkf_default_config", "tkf_pipeline_index"):
+            if name not in ("tkf_last_error", "tkf_status_string", "tkf_default_config", "tkf_pipeline_index",
+                            "tkf_server_default_options"):
                 getattr(L, name).restype = C.c_int
         L.tkf_pipeline_index.restype = vp
+        L.tkf_server_default_options.restype = None
         _lib = L
     return _lib
 
@@ -382,3 +413,105 @@ def tracks_tensors(t: Tracks, n_layers, precision=FP32):
     s = t.stride
     return dict(par=wrap(t.par, (6, s), dt), cov=wrap(t.cov, (21, s), dt), chi2=wrap(t.chi2, (s,), dt),
                 nhits=wrap(t.nhits, (s,), torch.int32), hit_idx=wrap(t.hit_idx, (n_layers, s), torch.int32))
+
+
+def server_options(**kw) -> ServerOptions:
+    o = ServerOptions()
+    lib().tkf_server_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class HostEvent:
+    """One event's host arrays, kept alive while its tkf_event struct is used: float32 x, y, z,
+    var_u, var_v; int32 layer; int32 seed_hits [3, n_seeds] (event-local).  borrow=True lends
+    them to the server (held in pinned memory here) instead of having them copied."""
+
+    def __init__(self, x, y, z, var_u, var_v, layer, seed_hits, borrow=False):
+        import numpy as np
+        c = lambda a, dt: np.ascontiguousarray(a, dtype=dt)
+        self.arrays = [c(x, np.float32), c(y, np.float32), c(z, np.float32), c(var_u, np.float32),
+                       c(var_v, np.float32), c(layer, np.int32), c(seed_hits, np.int32)]
+        ptrs = [a.ctypes.data for a in self.arrays]
+        if borrow:
+            import torch
+            self.pinned = [torch.from_numpy(a).pin_memory() for a in self.arrays]
+            ptrs = [t.data_ptr() for t in self.pinned]
+        a = self.arrays
+        self.struct = Event(ptrs[0], ptrs[1], ptrs[2], ptrs[3], ptrs[4], ptrs[5], len(a[0]), ptrs[6], a[6].shape[1],
+                            int(bool(borrow)))
+
+
+class Server:
+    """tkf_server: submit(event) -> ticket; poll(ticket) -> dict of numpy copies; release."""
+
+    def __init__(self, cfg: Config = None, **opts):
+        self.cfg = cfg if cfg is not None else default_config()
+        self.opt = server_options(**opts)
+        h = C.c_void_p()
+        code = lib().tkf_server_create(C.byref(self.cfg), C.byref(self.opt), C.byref(h))
+        if code != OK:
+            raise TkfError(code, "tkf_server_create")
+        self.handle = h
+
+    def submit(self, ev):
+        """Submits a HostEvent or a raw Event struct; returns (status, ticket), status ERR_AGAIN
+        when the queue is full."""
+        t = C.c_uint64()
+        code = lib().tkf_submit_event(self.handle, C.byref(ev.struct if isinstance(ev, HostEvent) else ev),
+                                      C.byref(t))
+        return code, t.value
+
+    try_submit = submit
+
+    def submit_struct(self, ev, retry_us=20):
+        """Submits, waiting while the queue is full; returns the ticket, raises on errors."""
+        import time
+        while True:
+            code, t = self.submit(ev)
+            if code == OK:
+                return t
+            if code != ERR_AGAIN:
+                raise TkfError(code, "tkf_submit_event")
+            time.sleep(retry_us * 1e-6)
+
+    def poll(self, ticket, timeout_us=0, copy=True):
+        """(status, result): result holds numpy copies (copy=True) or the raw Result struct."""
+        import numpy as np
+        r = Result()
+        code = lib().tkf_poll(self.handle, int(ticket), C.byref(r), int(timeout_us))
+        if code != OK or not copy:
+            return code, r
+        n, L, st = r.n_tracks, self.cfg.n_layers, r.stride
+
+        def arr(ptr, rows, ct):
+            if not n:
+                return np.zeros((rows, 0) if rows else (0,), dtype=np.float32 if ct is C.c_float else np.int32)
+            full = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ct)), shape=((rows - 1) * st + n,) if rows else (n,))
+            if not rows:
+                return full.copy()
+            return np.stack([full[k * st:k * st + n] for k in range(rows)])
+        return code, dict(status=r.status, n_tracks=n, par=arr(r.par, 6, C.c_float),
+                          cov=arr(r.cov, 21, C.c_float), chi2=arr(r.chi2, 0, C.c_float),
+                          nhits=arr(r.nhits, 0, C.c_int32), hit_idx=arr(r.hit_idx, L, C.c_int32),
+                          t_submit_ns=r.t_submit_ns, t_start_ns=r.t_start_ns, t_done_ns=r.t_done_ns)
+
+    def release(self, ticket):
+        return lib().tkf_release(self.handle, int(ticket))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        lib().tkf_server_get_stats(self.handle, C.byref(st))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tkf_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -74,3 +74,17 @@ def test_product_path_never_uses_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"\boracle\b|tkf_oracle|orc_", text), os.path.join(dirpath, f)
+
+
+def test_server_options_are_checked_before_any_device_work(lib):
+    c = tkf.default_config()
+    h = C.c_void_p()
+    o = tkf.server_options(result_bytes=1000)  # below one full batch of results
+    assert lib.tkf_server_create(C.byref(c), C.byref(o), C.byref(h)) == tkf.ERR_INVALID
+    o = tkf.server_options(n_slots=0)
+    assert lib.tkf_server_create(C.byref(c), C.byref(o), C.byref(h)) == tkf.ERR_INVALID
+    o = tkf.server_options()
+    assert o.result_bytes >= o.max_batch_tracks * (29 + c.n_layers) * 4
+    c64 = tkf.default_config(precision=tkf.FP64)
+    assert lib.tkf_server_create(C.byref(c64), C.byref(o), C.byref(h)) == tkf.ERR_INVALID
+    assert not h.value
