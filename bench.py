@@ -54,6 +54,10 @@ SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # scatter, bin sort), seed estimate, seed fit, seed ordering (key, segment totals, segment
 # scan, bin scan, place), build, final fit
 KERNELS_PER_STEP = 15
+# DRAM bytes (read + write) per seed of the FP32 building kernel, from one ncu capture of the
+# kernel as built now (160-event case: 404.5 MB for 701 095 seeds; summary in profiles/);
+# None whenever the kernel changes until it is captured again
+BUILD_DRAM_BYTES_PER_SEED = 577.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 
 
@@ -233,9 +237,9 @@ class LentEvents:
                            blk.ctypes.data, t1 - t0, 1)
             self.events.append(ev)
         self.n_tracks = b.n_tracks
-        # bytes the server moves per pass: hit planes, seed ids + seed events + event offsets
-        # in; final parameters, covariance, chi2, nhits and hit ids out
-        self.h2d = b.n_hits * 24 + b.n_tracks * 16 + (b.n_events + 1) * 4
+        # bytes the server moves per pass: hit planes, seed ids and two offsets per event in;
+        # final parameters, covariance, chi2, nhits and hit ids out
+        self.h2d = b.n_hits * 24 + b.n_tracks * 12 + b.n_events * 8
         self.d2h = b.n_tracks * (6 + 21 + 1 + 1 + n_layers) * 4
 
 
@@ -551,9 +555,11 @@ def main():
         opts = dict(n_slots=3, max_batch_events=64, max_batch_hits=max(1 << 22, hmax), max_batch_tracks=1 << 18)
         mcfg = tkf.default_config(precision=tkf.MIXED)
         serve = {"batched": served_stream(tkf, lent, rates, a.serve_seconds, 20000, a.seed, cfg=mcfg, **opts),
+                 "batched_fp32": served_stream(tkf, lent, rates, a.serve_seconds, 20000, a.seed, **opts),
                  "plain": served_stream(tkf, lent, rates, a.serve_seconds, 4000, a.seed, n_slots=1,
                                         max_batch_events=1, max_batch_hits=max(hmax, 1), max_batch_tracks=1 << 16),
-                 "batched_form": "MIXED precision, continuous batching over 3 slots, up to 64 events per batch",
+                 "batched_form": "MIXED precision, continuous batching over 3 slots, up to 64 events per batch "
+                                 "(batched_fp32: the same in FP32)",
                  "plain_form": "FP32, one event per batch, one slot",
                  "arrivals": "Poisson (seeded exponential gaps), events cycled from the batch's first 200, "
                              "hit planes lent from pinned host memory",
@@ -585,7 +591,9 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"kernel": "k_build<6,float,float>", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": None, "launch_ms": build_ms, "flop_per_seed": FLOP_PER_SEED,
+                     "traffic": None if BUILD_DRAM_BYTES_PER_SEED is None else BUILD_DRAM_BYTES_PER_SEED * n_tr,
+                     "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled by seeds from the 160-event case)",
+                     "launch_ms": build_ms, "flop_per_seed": FLOP_PER_SEED,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
         "cpu_baseline": cpu,
         "e2e": e2e,

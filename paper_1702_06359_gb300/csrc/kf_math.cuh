@@ -286,34 +286,46 @@ __host__ __device__ __forceinline__ R hit_chi2(const R p[6], const R P[21], R xh
 
 // chi2 = r^T S^-1 r from the residual (u, v) already formed with the hit's tangent
 // (-sh, ch); returns +inf when S is not positive definite.
+// The same from the six position terms of P it needs (P00, P10, P11, P20, P21, P22).
 template <class R>
-__host__ __device__ __forceinline__ R chi2_uv(const R P[21], R u, R v, R sh, R ch, R vu, R vv)
+__host__ __device__ __forceinline__ R chi2_uv6(R p00, R p10, R p11, R p20, R p21, R p22, R u, R v, R sh, R ch, R vu,
+                                               R vv)
 {
-    const R Suu = sh * (sh * P[sym(0, 0)] - ch * P[sym(1, 0)]) + ch * (ch * P[sym(1, 1)] - sh * P[sym(1, 0)]) + vu;
-    const R Suv = ch * P[sym(2, 1)] - sh * P[sym(2, 0)];
-    const R Svv = P[sym(2, 2)] + vv;
+    const R Suu = sh * (sh * p00 - ch * p10) + ch * (ch * p11 - sh * p10) + vu;
+    const R Suv = ch * p21 - sh * p20;
+    const R Svv = p22 + vv;
     const R det = Suu * Svv - Suv * Suv;
     if (!(det > R(0))) return R(INFINITY);
     return fast_div(u * (Svv * u - R(2) * Suv * v) + Suu * v * v, det);
 }
 
-// Kalman update with the Joseph-form covariance, computed in the real type U:
+template <class R>
+__host__ __device__ __forceinline__ R chi2_uv(const R P[21], R u, R v, R sh, R ch, R vu, R vv)
+{
+    return chi2_uv6<R>(P[sym(0, 0)], P[sym(1, 0)], P[sym(1, 1)], P[sym(2, 0)], P[sym(2, 1)], P[sym(2, 2)], u, v, sh,
+                       ch, vu, vv);
+}
+
+// Kalman update with the Joseph-form covariance:
 //   B = H P (2x6), S = B H^T + V, K = B^T S^-1, p += K r,
 //   P' = (I - K H) P (I - K H)^T + K V K^T = P - K B - (B^T - K S) K^T   (element-wise below).
-// Returns false when S is not positive definite; writes the hit's chi2 to *chi2.
+// The measurement geometry (the hit's tangent direction and the residual r on its plane) is
+// formed in the state's type R; S, its inverse, the gain, the state update and the Joseph form
+// are computed in U (double in the mixed mode).  Returns false when S is not positive definite;
+// writes the hit's chi2 to *chi2.
 template <class U, class R>
 __host__ __device__ __forceinline__ bool kalman_update(R pR[6], R PR[21], R xh_, R yh_, R zh_, R vu_, R vv_, U *chi2)
 {
+    const R irR = R(1) / sq(xh_ * xh_ + yh_ * yh_);
+    const R shR = yh_ * irR, chR = xh_ * irR;
+    const U u = U(chR * (yh_ - pR[1]) - shR * (xh_ - pR[0]));
+    const U v = U(zh_ - pR[2]);
+    const U sh = U(shR), ch = U(chR);
     U p[6], P[21];
 #pragma unroll
     for (int i = 0; i < 6; ++i) p[i] = U(pR[i]);
 #pragma unroll
     for (int k = 0; k < 21; ++k) P[k] = U(PR[k]);
-    const U xh = U(xh_), yh = U(yh_), zh = U(zh_);
-    const U ir = U(1) / sq(xh * xh + yh * yh);
-    const U sh = yh * ir, ch = xh * ir;
-    const U u = ch * (yh - p[1]) - sh * (xh - p[0]);
-    const U v = zh - p[2];
     U B0[6], B1[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {

@@ -55,12 +55,13 @@ struct IndexGeom {
     int L, n_eta, n_phi, n_bins, n_events;
     float radius[TKF_MAX_LAYERS];
     float eta_min, inv_eta_w;
+    float phi_scale;  // n_phi / (2 pi), rounded once on the host
 };
 
 // continuous phi-bin coordinate (phi + pi) * n_phi / (2 pi); its floor is the phi bin
 __device__ __forceinline__ float phi_coord(const IndexGeom &g, float x, float y)
 {
-    return (atan2f(y, x) + (float)kPi) * (float)(g.n_phi / (2.0 * kPi));
+    return (atan2f(y, x) + (float)kPi) * g.phi_scale;
 }
 
 __device__ __forceinline__ int hit_bin(const IndexGeom &g, int l, float x, float y, float z)
@@ -220,20 +221,44 @@ __global__ void k_hit_scatter(const IndexGeom g, const tkf_hits h, const int *ke
     hvar[pos] = make_float2(h.var_u[i], h.var_v[i]);
 }
 
-// Orders each bin by (phi sub-bin, event-local hit id) -- bins hold a handful of hits -- and
-// records where sub-bins 1..15 start (bytes of bin_sub; all 0xFF when the bin holds more than
-// 255 hits: scan it whole), so that a window reads only the sub-bins it overlaps; fills
-// pos_of_hit.  The sort key (sub-bin << 23 | id) lives in the w word while sorting.
-__global__ void k_bin_sort(const IndexGeom g, const int *bin_off, const int *ev_off, int n_bins_total, float4 *hxyzi,
-                           float2 *hvar, uint4 *bin_sub, int *pos_of_hit)
+// Where sub-bins 1..15 of a bin start, packed one byte each (bytes 0..14 of bin_sub; byte 15
+// zero), from the sort keys (sub-bin << 23 | id) of its hits key[a0..a1); all 0xFF when the
+// bin holds more than 255 hits (a window then scans it whole).  The 16 per-sub-bin counts are
+// kept as bytes of four words and prefix-summed bytewise by one multiplication per word.
+template <class KeyAt>
+__device__ __forceinline__ uint4 sub_starts(KeyAt key_at, int a0, int a1)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_bins_total) return;
-    const int i0 = bin_off[b], i1 = bin_off[b + 1];
-    if (i1 <= i0) {
-        bin_sub[b] = make_uint4(0u, 0u, 0u, 0u);
-        return;
+    const int n = a1 - a0;
+    if (n <= 0) return make_uint4(0u, 0u, 0u, 0u);
+    if (n > 255) return make_uint4(~0u, ~0u, ~0u, ~0u);
+    unsigned h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+    for (int t = a0; t < a1; ++t) {
+        const int sb = (key_at(t) >> 23) & (kSubBins - 1);
+        const unsigned inc = 1u << (8 * (sb & 3));
+        const int wd = sb >> 2;
+        h0 += wd == 0 ? inc : 0u;
+        h1 += wd == 1 ? inc : 0u;
+        h2 += wd == 2 ? inc : 0u;
+        h3 += wd == 3 ? inc : 0u;
     }
+    // byte k of p = hits in sub-bins 0..k = start of sub-bin k + 1 (no byte exceeds n <= 255)
+    const unsigned p0 = h0 * 0x01010101u;
+    const unsigned p1 = (h1 + (p0 >> 24)) * 0x01010101u;
+    const unsigned p2 = (h2 + (p1 >> 24)) * 0x01010101u;
+    const unsigned p3 = ((h3 + (p2 >> 24)) * 0x01010101u) & 0x00FFFFFFu;
+    return make_uint4(p0, p1, p2, p3);
+}
+
+constexpr int kSortItems = 4;                    // hits per lane held in registers
+constexpr int kSortHits = 32 * kSortItems;       // hits a warp orders at once
+constexpr int kSortBinsPerWarp = 64;             // consecutive bins per warp
+constexpr int kSortWarps = 8;                    // warps per block
+
+// A bin too large for one warp pass (more than kSortHits hits), ordered in place by one lane
+// with an insertion sort in global memory; rare (hundreds of hits in one eta-phi bin).
+__device__ void sort_bin_serial(const IndexGeom &g, int b, int i0, int i1, const int *ev_off, float4 *hxyzi,
+                                float2 *hvar, uint4 *bin_sub, int *pos_of_hit)
+{
     const int pb = (b % g.n_bins) % g.n_phi;
     for (int i = i0; i < i1; ++i) {
         float4 q = hxyzi[i];
@@ -253,25 +278,98 @@ __global__ void k_bin_sort(const IndexGeom g, const int *bin_off, const int *ev_
         hxyzi[j + 1] = k4;
         hvar[j + 1] = k2;
     }
-    const int e = b / (g.L * g.n_bins);
-    const int base = ev_off[e];
-    int start[kSubBins + 1] = {};
+    bin_sub[b] = sub_starts([&](int t) { return __float_as_int(hxyzi[t].w); }, i0, i1);
+    const int base = ev_off[b / (g.L * g.n_bins)];
     for (int i = i0; i < i1; ++i) {
         float4 q = hxyzi[i];
-        const int key = __float_as_int(q.w);
-        const int sb = key >> 23, id = key & 0x7FFFFF;
-        for (int t = sb + 1; t <= kSubBins; ++t) start[t] += 1;
+        const int id = __float_as_int(q.w) & 0x7FFFFF;
         q.w = __int_as_float(id);
         hxyzi[i] = q;
         pos_of_hit[base + id] = i;
     }
-    unsigned packed[4] = {0u, 0u, 0u, 0u};
-    if (i1 - i0 > 255) {
-        packed[0] = packed[1] = packed[2] = packed[3] = 0xFFFFFFFFu;
-    } else {
-        for (int t = 1; t < kSubBins; ++t) packed[(t - 1) >> 2] |= (unsigned)start[t] << (8 * ((t - 1) & 3));
+}
+
+// Orders each bin by (phi sub-bin, event-local hit id) -- the order a window scan relies on to
+// read only the sub-bins it overlaps -- records the sub-bin starts (bin_sub) and fills
+// pos_of_hit.  Each warp walks kSortBinsPerWarp consecutive bins, taking as many whole bins
+// per pass as hold at most kSortHits hits: the pass loads their hits into registers
+// (coalesced), puts the sort keys in shared memory, ranks every hit among the keys of its bin
+// and writes it back to its ordered slot.  All loads of a pass precede its stores (the warp
+// synchronises in between), so ordering in place is safe.
+__global__ void __launch_bounds__(32 * kSortWarps)
+k_bin_sort(const IndexGeom g, const int *bin_off, const int *ev_off, int n_bins_total, float4 *hxyzi, float2 *hvar,
+           uint4 *bin_sub, int *pos_of_hit)
+{
+    __shared__ int s_key[kSortWarps][kSortHits];
+    __shared__ unsigned char s_bin[kSortWarps][kSortHits];
+    __shared__ int s_off[kSortWarps][33];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long first = ((long long)blockIdx.x * kSortWarps + w) * kSortBinsPerWarp;
+    if (first >= n_bins_total) return;  // warp-uniform
+    int b = (int)first;
+    const int b_end = (int)min(first + kSortBinsPerWarp, (long long)n_bins_total);
+    int *key = s_key[w];
+    unsigned char *lbin = s_bin[w];
+    int *off = s_off[w];
+    while (b < b_end) {  // warp-uniform loop
+        const int nb = min(32, b_end - b);
+        const int s_l = bin_off[b + min(lane, nb)];
+        const int e_l = bin_off[b + min(lane + 1, nb)];
+        const int o0 = __shfl_sync(full, s_l, 0);
+        const bool fits = lane < nb && e_l - o0 <= kSortHits;
+        const int m = __popc(__ballot_sync(full, fits));  // bins taken in this pass (a prefix)
+        if (m == 0) {
+            if (lane == 0) sort_bin_serial(g, b, s_l, e_l, ev_off, hxyzi, hvar, bin_sub, pos_of_hit);
+            __syncwarp();
+            b += 1;
+            continue;
+        }
+        const int n = __shfl_sync(full, e_l, m - 1) - o0;
+        if (lane < m) {
+            off[lane] = s_l - o0;
+            for (int k = s_l - o0; k < e_l - o0; ++k) lbin[k] = (unsigned char)lane;
+        }
+        if (lane == 0) off[m] = n;
+        __syncwarp();
+        float4 q[kSortItems];
+        float2 v[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const int k = lane + 32 * j;
+            if (k < n) {
+                q[j] = hxyzi[o0 + k];
+                v[j] = hvar[o0 + k];
+                const int pb = ((b + lbin[k]) % g.n_bins) % g.n_phi;
+                key[k] = (hit_sub(g, q[j].x, q[j].y, pb) << 23) | __float_as_int(q[j].w);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const int k = lane + 32 * j;
+            if (k < n) {
+                const int lb = lbin[k];
+                const int a0 = off[lb], a1 = off[lb + 1];
+                const int mine = key[k];
+                int r = 0;
+                for (int t = a0; t < a1; ++t) r += key[t] < mine;
+                const int d = o0 + a0 + r;
+                hxyzi[d] = q[j];  // w holds the event-local id
+                hvar[d] = v[j];
+                pos_of_hit[ev_off[(b + lb) / (g.L * g.n_bins)] + (mine & 0x7FFFFF)] = d;
+            }
+        }
+        if (lane < m) bin_sub[b + lane] = sub_starts([&](int t) { return key[t]; }, off[lane], off[lane + 1]);
+        __syncwarp();  // shared memory is reused by the next pass
+        b += m;
     }
-    bin_sub[b] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+}
+
+unsigned sort_blocks(size_t n_bins)
+{
+    const size_t per_block = (size_t)kSortWarps * kSortBinsPerWarp;
+    return (unsigned)std::max<size_t>(1, (n_bins + per_block - 1) / per_block);
 }
 
 // ------------------------------------------------------------------ seed ordering for locality
@@ -683,6 +781,7 @@ int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out,
         for (int l = 0; l < L; ++l) g.radius[l] = (float)c.radius[l];
         g.eta_min = (float)c.eta_min;
         g.inv_eta_w = (float)(1.0 / c.eta_bin_w);
+        g.phi_scale = (float)(c.n_phi_bins / (2.0 * kPi));
         TKF_CUDA(ctx, cudaMemsetAsync(idx->counts, 0, n_bins * sizeof(int), s));
         TKF_CUDA(ctx, cudaMemsetAsync(idx->var_max, 0, n_segs * sizeof(float2), s));
         TKF_CUDA(ctx, cudaMemcpyAsync(idx->ev_off, hits->event_off, (hits->n_events + 1) * sizeof(int),
@@ -699,8 +798,8 @@ int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out,
             const int nb = (hits->n + 255) / 256;
             k_hit_scatter<<<nb, 256, 0, s>>>(g, *hits, idx->keys, idx->counts, idx->bin_off, idx->hxyzi, idx->hvar);
         }
-        k_bin_sort<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(g, idx->bin_off, idx->ev_off, (int)n_bins,
-                                                                     idx->hxyzi, idx->hvar, idx->bin_sub, idx->pos_of_hit);
+        k_bin_sort<<<sort_blocks(n_bins), 32 * kSortWarps, 0, s>>>(g, idx->bin_off, idx->ev_off, (int)n_bins,
+                                                                   idx->hxyzi, idx->hvar, idx->bin_sub, idx->pos_of_hit);
         TKF_CUDA(ctx, cudaGetLastError());
     }
     *out = idx;
@@ -878,6 +977,7 @@ int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *s
         for (int l = 0; l < c.n_layers; ++l) g.radius[l] = (float)c.radius[l];
         g.eta_min = (float)c.eta_min;
         g.inv_eta_w = (float)(1.0 / c.eta_bin_w);
+        g.phi_scale = (float)(c.n_phi_bins / (2.0 * kPi));
         const int nb = (seeds->n + 255) / 256, layer = c.first_build_layer - 1;
         if (c.precision == TKF_FP64)
             k_seed_key<double><<<nb, 256, 0, s>>>(g, layer, (const double *)seeds->par, seeds->stride, seeds->event,
@@ -990,6 +1090,7 @@ extern "C" int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits
     for (int l = 0; l < L; ++l) g.radius[l] = (float)c.radius[l];
     g.eta_min = (float)c.eta_min;
     g.inv_eta_w = (float)(1.0 / c.eta_bin_w);
+    g.phi_scale = (float)(c.n_phi_bins / (2.0 * kPi));
     cudaStream_t s = (cudaStream_t)stream;
     float4 *hxyzi = (float4 *)out->hit_xyzi;
     float2 *hvar = (float2 *)out->hit_var;
@@ -1005,7 +1106,7 @@ extern "C" int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits
     k_bin_scan<<<(unsigned)n_segs, 256, 0, s>>>(counts, seg_base, out->bin_off, NB, (int)n_segs);
     if (hits->n > 0)
         k_hit_scatter<<<(hits->n + 255) / 256, 256, 0, s>>>(g, *hits, keys, counts, out->bin_off, hxyzi, hvar);
-    k_bin_sort<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(g, out->bin_off, out->event_off, (int)n_bins, hxyzi,
-                                                                 hvar, (uint4 *)out->bin_sub, out->pos_of_hit);
+    k_bin_sort<<<sort_blocks(n_bins), 32 * kSortWarps, 0, s>>>(g, out->bin_off, out->event_off, (int)n_bins, hxyzi,
+                                                               hvar, (uint4 *)out->bin_sub, out->pos_of_hit);
     return cudaGetLastError() == cudaSuccess ? TKF_OK : TKF_ERR_CUDA;
 }

@@ -92,11 +92,16 @@ struct Slot {
     tkf_pipeline *pipe = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    // host staging (pinned) and device inputs
+    // host staging (pinned) for copied events, and the per-batch event offsets
     Pinned<float> hx, hy, hz, hvu, hvv;
-    Pinned<int> hlayer, hoff, hseeds, hsev;
+    Pinned<int> hlayer, hraw, hoff, htoff;
+    // device inputs: hit planes, the events' seed blocks as submitted ([3][n] event-local ids
+    // per event, back to back), hit and seed offsets of the events; seed ids of the batch
+    // ([3][T], batch hit ids) and seed events made from them on the device; event-local hit
+    // ids of the built tracks ([L][T])
     float *dx = nullptr, *dy = nullptr, *dz = nullptr, *dvu = nullptr, *dvv = nullptr;
-    int *dlayer = nullptr, *doff = nullptr, *dseeds = nullptr, *dsev = nullptr;
+    int *dlayer = nullptr, *draw = nullptr, *doff = nullptr, *dtoff = nullptr, *dseeds = nullptr, *dsev = nullptr;
+    int *dlocal = nullptr;
     OutBuf *out = nullptr;  // result buffer of the running batch
     bool busy = false;
     int64_t t_start = 0;
@@ -134,10 +139,10 @@ void free_slot(Slot &s)
     if (s.stream) cudaStreamDestroy(s.stream);
     if (s.done) cudaEventDestroy(s.done);
     for (void *p : {(void *)s.dx, (void *)s.dy, (void *)s.dz, (void *)s.dvu, (void *)s.dvv, (void *)s.dlayer,
-                    (void *)s.doff, (void *)s.dseeds, (void *)s.dsev})
+                    (void *)s.draw, (void *)s.doff, (void *)s.dtoff, (void *)s.dseeds, (void *)s.dsev, (void *)s.dlocal})
         cudaFree(p);
     s.hx.free(); s.hy.free(); s.hz.free(); s.hvu.free(); s.hvv.free();
-    s.hlayer.free(); s.hoff.free(); s.hseeds.free(); s.hsev.free();
+    s.hlayer.free(); s.hraw.free(); s.hoff.free(); s.htoff.free();
 }
 
 size_t outbuf_bytes(const tkf_server *sv, int cap) { return (size_t)cap * (29 + sv->cfg.n_layers) * 4; }
@@ -202,71 +207,129 @@ int init_slot(tkf_server *sv, Slot &s)
     if (!e) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     if (!e) e = s.hx.alloc(H); if (!e) e = s.hy.alloc(H); if (!e) e = s.hz.alloc(H);
     if (!e) e = s.hvu.alloc(H); if (!e) e = s.hvv.alloc(H); if (!e) e = s.hlayer.alloc(H);
-    if (!e) e = s.hoff.alloc(E + 1); if (!e) e = s.hseeds.alloc(3 * T); if (!e) e = s.hsev.alloc(T);
-    const size_t h1 = std::max<size_t>(H, 1), t1 = std::max<size_t>(T, 1);
+    if (!e) e = s.hraw.alloc(3 * T); if (!e) e = s.hoff.alloc(E + 1); if (!e) e = s.htoff.alloc(E + 1);
+    const size_t h1 = std::max<size_t>(H, 1), t1 = std::max<size_t>(T, 1), L = sv->cfg.n_layers;
     if (!e) e = cudaMalloc((void **)&s.dx, h1 * 4); if (!e) e = cudaMalloc((void **)&s.dy, h1 * 4);
     if (!e) e = cudaMalloc((void **)&s.dz, h1 * 4); if (!e) e = cudaMalloc((void **)&s.dvu, h1 * 4);
     if (!e) e = cudaMalloc((void **)&s.dvv, h1 * 4); if (!e) e = cudaMalloc((void **)&s.dlayer, h1 * 4);
-    if (!e) e = cudaMalloc((void **)&s.doff, (E + 1) * 4); if (!e) e = cudaMalloc((void **)&s.dseeds, 3 * t1 * 4);
-    if (!e) e = cudaMalloc((void **)&s.dsev, t1 * 4);
+    if (!e) e = cudaMalloc((void **)&s.draw, 3 * t1 * 4); if (!e) e = cudaMalloc((void **)&s.doff, (E + 1) * 4);
+    if (!e) e = cudaMalloc((void **)&s.dtoff, (E + 1) * 4); if (!e) e = cudaMalloc((void **)&s.dseeds, 3 * t1 * 4);
+    if (!e) e = cudaMalloc((void **)&s.dsev, t1 * 4); if (!e) e = cudaMalloc((void **)&s.dlocal, L * t1 * 4);
     if (e) return e == cudaErrorMemoryAllocation ? TKF_ERR_NOMEM : TKF_ERR_CUDA;
     return TKF_OK;
 }
 
-// Packs `evs` into slot `s` and queues copies, the pipeline and the result copies on its stream.
-// Borrowed hit planes are copied straight from the caller's memory to the device; owned ones
-// and every seed list (rebased to batch hit ids) go through the slot's pinned staging.
+// Seed ids of the batch from the events' seed blocks: seed t of event e (its tl-th) reads
+// raw[3 * toff[e] + j * n_e + tl] and adds the event's first hit; its event is e.
+__global__ void k_prep_seeds(const int *raw, const int *toff, const int *hoff, int n_events, int n_tracks, int stride,
+                             int *seeds, int *sev)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tracks) return;
+    int lo = 0, hi = n_events;  // largest e with toff[e] <= t
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (toff[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int t0 = toff[lo], n_e = toff[lo + 1] - t0, h0 = hoff[lo];
+    const int *r = raw + 3 * (size_t)t0 + (t - t0);
+    seeds[t] = r[0] + h0;
+    seeds[stride + t] = r[n_e] + h0;
+    seeds[2 * (size_t)stride + t] = r[2 * n_e] + h0;
+    sev[t] = lo;
+}
+
+// Event-local hit ids of the built tracks ([L][stride] in, [L][out_stride] out; -1 = hole).
+__global__ void k_local_hits(const int *hit_idx, int stride, const int *sev, const int *hoff, int n_tracks, int L,
+                             int out_stride, int *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tracks) return;
+    const int h0 = hoff[sev[t]];
+    for (int l = 0; l < L; ++l) {
+        const int h = hit_idx[(size_t)l * stride + t];
+        out[(size_t)l * out_stride + t] = h >= 0 ? h - h0 : -1;
+    }
+}
+
+// Host-to-device copies of a batch, merged while consecutive pieces are adjacent on both sides
+// (events lent from one host buffer, or staged back to back, move in one copy per array).
+struct CopyRun {
+    const char *src = nullptr;
+    char *dst = nullptr;
+    size_t bytes = 0;
+    cudaError_t add(const void *s, void *d, size_t n, cudaStream_t st)
+    {
+        if (!n) return cudaSuccess;
+        if (bytes && (const char *)s == src + bytes && (char *)d == dst + bytes) {
+            bytes += n;
+            return cudaSuccess;
+        }
+        const cudaError_t e = flush(st);
+        src = (const char *)s;
+        dst = (char *)d;
+        bytes = n;
+        return e;
+    }
+    cudaError_t flush(cudaStream_t st)
+    {
+        cudaError_t e = cudaSuccess;
+        if (bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+        bytes = 0;
+        return e;
+    }
+};
+
+// Packs `evs` into slot `s` and queues, on its stream: the input copies (lent arrays straight
+// from the caller's memory, copied events from the slot's pinned staging), the seed and
+// event-id preparation, the pipeline, the event-local hit ids and the result copies.
 int launch_batch(tkf_server *sv, Slot &s, std::vector<Pending> &evs)
 {
     const int L = sv->cfg.n_layers;
     const size_t T = sv->opt.max_batch_tracks;
     cudaStream_t st = s.stream;
     cudaError_t e = cudaSuccess;
-    auto h2d = [&](void *d, const void *h, size_t bytes) {
-        if (!e && bytes) e = cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, st);
-    };
-    int hit = 0, trk = 0, staged0 = -1;
+    CopyRun run[7];
+    int hit = 0, trk = 0;
     s.evs.clear();
-    auto flush_staged = [&](int upto) {  // owned events staged in [staged0, upto)
-        if (staged0 < 0 || upto <= staged0) return;
-        const size_t n = (size_t)(upto - staged0) * 4;
-        h2d(s.dx + staged0, s.hx.p + staged0, n); h2d(s.dy + staged0, s.hy.p + staged0, n);
-        h2d(s.dz + staged0, s.hz.p + staged0, n); h2d(s.dvu + staged0, s.hvu.p + staged0, n);
-        h2d(s.dvv + staged0, s.hvv.p + staged0, n); h2d(s.dlayer + staged0, s.hlayer.p + staged0, n);
-        staged0 = -1;
-    };
     for (size_t k = 0; k < evs.size(); ++k) {
         Pending &p = evs[k];
-        const size_t nb = (size_t)p.n_hits * 4;
+        const size_t nb = (size_t)p.n_hits * 4, sb = (size_t)p.n_seeds * 12;
         s.hoff.p[k] = hit;
+        s.htoff.p[k] = trk;
+        const void *src[7];
         if (p.borrowed) {
-            flush_staged(hit);
-            h2d(s.dx + hit, p.bx, nb); h2d(s.dy + hit, p.by, nb); h2d(s.dz + hit, p.bz, nb);
-            h2d(s.dvu + hit, p.bvu, nb); h2d(s.dvv + hit, p.bvv, nb); h2d(s.dlayer + hit, p.blayer, nb);
+            src[0] = p.bx; src[1] = p.by; src[2] = p.bz; src[3] = p.bvu; src[4] = p.bvv; src[5] = p.blayer;
+            src[6] = p.bseeds;
         } else {
-            if (staged0 < 0) staged0 = hit;
             std::memcpy(s.hx.p + hit, p.px(), nb);
             std::memcpy(s.hy.p + hit, p.py(), nb);
             std::memcpy(s.hz.p + hit, p.pz(), nb);
             std::memcpy(s.hvu.p + hit, p.pvu(), nb);
             std::memcpy(s.hvv.p + hit, p.pvv(), nb);
             std::memcpy(s.hlayer.p + hit, p.player(), nb);
+            std::memcpy(s.hraw.p + 3 * (size_t)trk, p.pseeds(), sb);
+            src[0] = s.hx.p + hit; src[1] = s.hy.p + hit; src[2] = s.hz.p + hit; src[3] = s.hvu.p + hit;
+            src[4] = s.hvv.p + hit; src[5] = s.hlayer.p + hit; src[6] = s.hraw.p + 3 * (size_t)trk;
         }
-        const int *sd = p.pseeds();
-        for (int j = 0; j < 3; ++j)
-            for (int t = 0; t < p.n_seeds; ++t) s.hseeds.p[j * T + trk + t] = sd[(size_t)j * p.n_seeds + t] + hit;
-        for (int t = 0; t < p.n_seeds; ++t) s.hsev.p[trk + t] = (int)k;
+        void *dst[7] = {s.dx + hit, s.dy + hit, s.dz + hit, s.dvu + hit, s.dvv + hit, s.dlayer + hit,
+                        s.draw + 3 * (size_t)trk};
+        for (int j = 0; j < 7 && !e; ++j) e = run[j].add(src[j], dst[j], j < 6 ? nb : sb, st);
         s.evs.push_back({p.ticket, hit, p.n_hits, trk, p.n_seeds, p.t_submit});
         hit += p.n_hits;
         trk += p.n_seeds;
     }
-    flush_staged(hit);
+    for (int j = 0; j < 7 && !e; ++j) e = run[j].flush(st);
     const int E = (int)evs.size();
     s.hoff.p[E] = hit;
+    s.htoff.p[E] = trk;
     s.n_tracks = trk;
-    h2d(s.doff, s.hoff.p, (E + 1) * 4);
-    if (!e && trk) e = cudaMemcpy2DAsync(s.dseeds, T * 4, s.hseeds.p, T * 4, trk * 4, 3, cudaMemcpyHostToDevice, st);
-    h2d(s.dsev, s.hsev.p, trk * 4);
+    if (!e) e = cudaMemcpyAsync(s.doff, s.hoff.p, (E + 1) * 4, cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaMemcpyAsync(s.dtoff, s.htoff.p, (E + 1) * 4, cudaMemcpyHostToDevice, st);
+    if (!e && trk) {
+        k_prep_seeds<<<(trk + 255) / 256, 256, 0, st>>>(s.draw, s.dtoff, s.doff, E, trk, (int)T, s.dseeds, s.dsev);
+        e = cudaGetLastError();
+    }
     if (e) return TKF_ERR_CUDA;
     tkf_hits h{};
     h.x = s.dx; h.y = s.dy; h.z = s.dz; h.var_u = s.dvu; h.var_v = s.dvv; h.layer = s.dlayer;
@@ -281,12 +344,14 @@ int launch_batch(tkf_server *sv, Slot &s, std::vector<Pending> &evs)
     OutBuf *o = s.out;
     const size_t hp = (size_t)o->cap * es;  // host pitch
     if (trk) {
-        e = cudaMemcpy2DAsync(o->par, hp, fitted.par, dp, trk * es, 6, cudaMemcpyDeviceToHost, st);
+        k_local_hits<<<(trk + 255) / 256, 256, 0, st>>>(built.hit_idx, built.stride, s.dsev, s.doff, trk, L, (int)T,
+                                                        s.dlocal);
+        e = cudaGetLastError();
+        if (!e) e = cudaMemcpy2DAsync(o->par, hp, fitted.par, dp, trk * es, 6, cudaMemcpyDeviceToHost, st);
         if (!e) e = cudaMemcpy2DAsync(o->cov, hp, fitted.cov, dp, trk * es, 21, cudaMemcpyDeviceToHost, st);
         if (!e) e = cudaMemcpyAsync(o->chi2, fitted.chi2, trk * es, cudaMemcpyDeviceToHost, st);
         if (!e) e = cudaMemcpyAsync(o->nhits, fitted.nhits, trk * 4, cudaMemcpyDeviceToHost, st);
-        if (!e) e = cudaMemcpy2DAsync(o->hit, hp, built.hit_idx, (size_t)built.stride * 4, trk * 4, L,
-                                      cudaMemcpyDeviceToHost, st);
+        if (!e) e = cudaMemcpy2DAsync(o->hit, hp, s.dlocal, T * 4, trk * 4, L, cudaMemcpyDeviceToHost, st);
     }
     if (!e) e = cudaEventRecord(s.done, st);
     if (e) return TKF_ERR_CUDA;
@@ -294,23 +359,17 @@ int launch_batch(tkf_server *sv, Slot &s, std::vector<Pending> &evs)
     return TKF_OK;
 }
 
-// Hands each finished event its columns of the batch's result buffer, with hit ids made
-// event-local (called with the lock held).
+// Hands each finished event its columns of the batch's result buffer (called with the lock
+// held).
 void harvest(tkf_server *sv, Slot &s)
 {
-    const int L = sv->cfg.n_layers;
     const int64_t t_done = now_ns();
     OutBuf *o = s.out;
-    const size_t T = o->cap;
     o->refs = 1;  // held by this function until the end
     for (const EvInfo &ev : s.evs) {
         auto it = sv->results.find(ev.ticket);
         if (it == sv->results.end()) continue;  // released before completion
         Done &d = it->second;
-        for (int l = 0; l < L; ++l) {
-            int *row = o->hit + l * T + ev.trk0;
-            for (int t = 0; t < ev.n_tracks; ++t) row[t] = row[t] >= 0 ? row[t] - ev.hit0 : -1;
-        }
         d.buf = o;
         o->refs += 1;
         d.trk0 = ev.trk0;
@@ -482,8 +541,12 @@ int tkf_submit_event(tkf_server *sv, const tkf_event *ev, uint64_t *ticket)
     if (ev->n_hits > 0 && (!ev->x || !ev->y || !ev->z || !ev->var_u || !ev->var_v || !ev->layer)) return TKF_ERR_INVALID;
     if (ev->n_seeds > 0 && !ev->seed_hits) return TKF_ERR_INVALID;
     if (ev->n_hits > sv->opt.max_batch_hits || ev->n_seeds > sv->opt.max_batch_tracks) return TKF_ERR_INVALID;
-    for (int t = 0; t < 3 * ev->n_seeds; ++t)
-        if (ev->seed_hits[t] < 0 || ev->seed_hits[t] >= ev->n_hits) return TKF_ERR_INVALID;
+    int lo = 0, hi = 0;
+    for (int t = 0; t < 3 * ev->n_seeds; ++t) {
+        lo = std::min(lo, ev->seed_hits[t]);
+        hi = std::max(hi, ev->seed_hits[t]);
+    }
+    if (lo < 0 || (ev->n_seeds > 0 && hi >= ev->n_hits)) return TKF_ERR_INVALID;
     const size_t bytes = ev->borrow ? 64 : (size_t)ev->n_hits * 24 + (size_t)ev->n_seeds * 12;
     {
         std::lock_guard<std::mutex> lk(sv->mu);

@@ -1,0 +1,142 @@
+"""Precision sweep: the plain building workload's events (5000 tracks, 20% noise hits, N = 6)
+with pT up to 100 GeV, which stresses the conditioning of the covariance (stiff tracks have
+tiny q/pT variances next to centimetre-scale position terms).  The whole hot path -- hit
+index, seed estimate, seed fit, building, final fit, as the batched pipeline runs it -- in
+FP32, MIXED (FP64 innovation inverse and Joseph-form update, Sec. 3.2) and FP64, each
+against the FP64 oracle's whole path on the same events.
+
+Gates: every seed whose final hit list equals the oracle's has its final-fit parameters and
+chi2 within the parity tolerance (1e-8 in FP64); a differing hit list is allowed only from a
+layer where the oracle's own decision was fragile (two ranked totals within 1e-3, or a chi2
+within 1e-3 of the cut), and for at most 5% of seeds.  Reported per quantity and mode
+(printed, and written as JSON to $TKF_REPORT_DIR when set): relative error of each
+parameter, of each covariance diagonal element and of chi2, and the hit agreement."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from _gpu import PAR_FLOOR, chi2_violations, param_violations, unpack_cov
+from synth import Detector, EventSpec, generate
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1702_06359_gb300 import tkf  # noqa: E402
+
+N_EVENTS, N_TRACKS = 20, 5000
+NAMES = ["x", "y", "z", "q/pT", "phi", "theta"]
+
+
+@pytest.fixture(scope="module")
+def sweep_events():
+    det = Detector()
+    b = generate(EventSpec(seed=1, n_events=N_EVENTS, n_tracks=N_TRACKS, noise_frac=0.2, pt_max=100.0), det)
+    g = O.make_geom(det)
+    L = det.n_layers
+    refs = []
+    for e in range(b.n_events):
+        h0, h1 = b.hit_off[e], b.hit_off[e + 1]
+        t0, t1 = b.trk_off[e], b.trk_off[e + 1]
+        hits = O.hits_of(b, slice(h0, h1))
+        local = b.trk_hits[t0:t1] - h0
+        p0, c0 = O.seed_estimate(g, hits, local[:, :3])
+        ids = np.full((len(local), L), -1, dtype=np.int32)
+        ids[:, :3] = local[:, :3]
+        sp, sP, sc2, snh, _ = O.fit(g, hits, p0, c0, ids, 0, 2)
+        res = O.build(g, O.hit_index(g, hits), sp, sP, sc2, snh, ids)
+        fpar, fcov, fchi2, fnh, fst = O.fit(g, hits, p0, c0, res.hits[:, 0, :], 0, L - 1)
+        refs.append(dict(hits=res.hits[:, 0, :], n_cand=res.n_cand, fragile=res.fragile, par=fpar, cov=fcov,
+                         chi2=fchi2, nhits=fnh))
+    return det, b, refs
+
+
+def _gpu_path(b, det, prec):
+    from _gpu import device_hits
+    ctx = tkf.Context(tkf.default_config(precision=prec))
+    L = det.n_layers
+    n = b.n_tracks
+    dh = device_hits(b)
+    sh = torch.as_tensor(np.ascontiguousarray(b.trk_hits[:, :3].T), dtype=torch.int32, device="cuda")
+    se = torch.as_tensor(b.trk_event, dtype=torch.int32, device="cuda")
+    pipe = tkf.DevicePipeline(ctx, b.n_hits, b.n_events, n, use_graph=False)
+    pipe.run(dh, sh, se, n)
+    ctx.sync_status()
+    _, built, fitted = pipe.outputs()
+    bt = tkf.tracks_tensors(built, L, prec)
+    ft = tkf.tracks_tensors(fitted, L, prec)
+    out = dict(hits=bt["hit_idx"][:, :n].T.cpu().numpy(), built_nhits=bt["nhits"][:n].cpu().numpy(),
+               par=ft["par"][:, :n].double().T.cpu().numpy(), cov=unpack_cov(ft["cov"][:, :n].double().cpu().numpy()),
+               chi2=ft["chi2"][:n].double().cpu().numpy(), nhits=ft["nhits"][:n].cpu().numpy())
+    pipe.close()
+    ctx.close()
+    return out
+
+
+def _stats(x):
+    x = np.asarray(x)
+    if not len(x):
+        return {"max": 0.0, "p99": 0.0, "median": 0.0}
+    return {"max": float(np.max(x)), "p99": float(np.percentile(x, 99)), "median": float(np.median(x))}
+
+
+@pytest.mark.parametrize("prec", [tkf.FP32, tkf.MIXED, tkf.FP64], ids=["fp32", "mixed", "fp64"])
+def test_precision_sweep_whole_path(sweep_events, prec):
+    det, b, refs = sweep_events
+    got = _gpu_path(b, det, prec)
+    name = {tkf.FP32: "fp32", tkf.MIXED: "mixed", tkf.FP64: "fp64"}[prec]
+    n_same = n_div = n_lost = 0
+    par_err, cov_err, chi2_err = [], [], []
+    for e, ref in enumerate(refs):
+        t0, t1 = b.trk_off[e], b.trk_off[e + 1]
+        h0 = b.hit_off[e]
+        gh = got["hits"][t0:t1]
+        gh = np.where(gh >= 0, gh - h0, -1)
+        lost = ref["n_cand"] == 0
+        n_lost += int(lost.sum())
+        assert np.all(got["built_nhits"][t0:t1][lost] == tkf.TRACK_LOST)
+        same = np.all(gh == ref["hits"], axis=1) & ~lost
+        for s in np.nonzero(~same & ~lost)[0]:
+            d = int(np.argmax(gh[s] != ref["hits"][s]))
+            assert d >= ref["fragile"][s], ("hit list differs before any fragile decision", name, e, s, d)
+            n_div += 1
+        m = np.nonzero(same)[0]
+        n_same += len(m)
+        gp, rp = got["par"][t0 + m], ref["par"][m]
+        bad, worst = param_violations(gp, rp)
+        assert not bad.any(), (name, worst)
+        bad, worst = chi2_violations(got["chi2"][t0 + m], ref["chi2"][m])
+        assert not bad.any(), (name, worst)
+        assert np.array_equal(got["nhits"][t0 + m], ref["nhits"][m])
+        if prec == tkf.FP64:
+            assert param_violations(gp, rp, rel=1e-8)[1] <= 1.0
+        d = gp - rp
+        d[:, 4] = (d[:, 4] + np.pi) % (2 * np.pi) - np.pi
+        par_err.append(np.abs(d) / np.maximum(np.abs(rp), PAR_FLOOR[None, :]))
+        gd = np.diagonal(got["cov"][t0 + m], axis1=1, axis2=2)
+        rd = np.diagonal(ref["cov"][m], axis1=1, axis2=2)
+        cov_err.append(np.abs(gd - rd) / np.abs(rd))
+        chi2_err.append(np.abs(got["chi2"][t0 + m] - ref["chi2"][m]) / np.maximum(ref["chi2"][m], 1.0))
+    n_all = b.n_tracks
+    assert n_div <= 0.05 * n_all, (name, n_div, n_all)
+    par_err, cov_err, chi2_err = np.concatenate(par_err), np.concatenate(cov_err), np.concatenate(chi2_err)
+    report = {
+        "precision": name, "events": b.n_events, "tracks": n_all, "pt_gev": [0.5, 100.0],
+        "hit_list_identical": n_same / n_all, "hit_list_differs_after_fragile": n_div / n_all,
+        "lost_seeds": n_lost,
+        "param_rel_err": {NAMES[i]: _stats(par_err[:, i]) for i in range(6)},
+        "param_rel_err_note": "|d| / max(|ref|, floor), floors (1, 1, 1 cm, 0.1 1/GeV, 1, 1 rad)",
+        "cov_diag_rel_err": {NAMES[i]: _stats(cov_err[:, i]) for i in range(6)},
+        "chi2_rel_err": _stats(chi2_err),
+    }
+    print(json.dumps(report))
+    out_dir = os.environ.get("TKF_REPORT_DIR")
+    if out_dir:
+        os.makedirs(out_dir, exist_ok=True)
+        with open(os.path.join(out_dir, "precision_sweep_%s.json" % name), "w") as f:
+            json.dump(report, f, indent=1)
