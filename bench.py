@@ -55,9 +55,9 @@ SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # scan, bin scan, place), build, final fit
 KERNELS_PER_STEP = 15
 # DRAM bytes (read + write) per seed of the FP32 building kernel, from one ncu capture of the
-# kernel as built now (160-event case: 404.5 MB for 701 095 seeds; summary in profiles/);
+# kernel as built now (160-event case: 407.4 MB for 701 095 seeds; summary in profiles/);
 # None whenever the kernel changes until it is captured again
-BUILD_DRAM_BYTES_PER_SEED = 577.0
+BUILD_DRAM_BYTES_PER_SEED = 581.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 
 
@@ -332,6 +332,7 @@ def main():
     ap.add_argument("--serve", type=int, default=1, help="1: also measure the served stream")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--mixed", type=int, default=1, help="1: also time the batched step in MIXED precision")
+    ap.add_argument("--tile", type=int, default=0, help="seeds per warp work tile (0: autotuned)")
     ap.add_argument("--e2e-batch", type=int, default=128, help="events per server batch in the e2e measurement")
     ap.add_argument("--seed-order", type=int, default=1,
                     help="batched form: 1 = build seeds grouped by detector region (the per-event form keeps input order)")
@@ -369,7 +370,7 @@ def main():
     }
     d = {k: v.to(dev, non_blocking=False) for k, v in host.items()}
     hits = tkf.DeviceHits(d["x"], d["y"], d["z"], d["var_u"], d["var_v"], d["layer"], d["event_off"])
-    ctx = tkf.Context(tkf.default_config(seed_order=a.seed_order))
+    ctx = tkf.Context(tkf.default_config(seed_order=a.seed_order, seeds_per_block=max(a.tile, 0)))
     L = ctx.cfg.n_layers
     pipe = tkf.DevicePipeline(ctx, n_hits, b.n_events, n_tr, use_graph=True)
     stream = torch.cuda.current_stream()
@@ -390,11 +391,15 @@ def main():
         def struct(self):
             return self.t
     scratch_out = tkf.DeviceTracks.empty(n_tr, L, device=dev)
-    best_tile, tile_ms = ctx.autotune_build(pipe.index(), _T(seeds_t), scratch_out, tiles, repeats=2, stream=stream)
+    n_grid = {}
+    if a.tile > 0:  # fixed work tile (no search), e.g. for profiling a given configuration
+        best_tile, tile_ms, tiles = a.tile, [], [a.tile]
+    else:
+        best_tile, tile_ms = ctx.autotune_build(pipe.index(), _T(seeds_t), scratch_out, tiles, repeats=2,
+                                                stream=stream)
     # the same search at N = 4 and 10 candidates per seed (reported; the accuracy claim and the
     # headline stay at N = 6)
-    n_grid = {}
-    for n_cand in (4, 10):
+    for n_cand in ((4, 10) if a.tile <= 0 else ()):
         cn = tkf.Context(tkf.default_config(seed_order=a.seed_order, n_cand=n_cand))
         spw_n = 32 // n_cand
         tl = sorted({spw_n, 2 * spw_n, 4 * spw_n, 32, 64, 128})
