@@ -134,6 +134,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ----------------------------------------------------------------------------- replicas
+def job_rate(units, ms, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: the units of every rank summed, over the
+    slowest rank's time (ms).  Returns (units, ms_max, units per second)."""
+    import torch
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    units, ms = float(u.item()), float(m.item())
+    return units, ms, units / (ms / 1e3)
+
+
 # ----------------------------------------------------------------------------- CPU baseline (oracle)
 def _oracle_events(chunk):
     """Runs the oracle's whole path (index, seed, seed fit, build, final fit) on a few events,
@@ -436,13 +450,9 @@ def main():
     ctx.sync_status(stream)
     ms = ev_start.elapsed_time(ev_stop) / a.steps
     build_ms = statistics.mean(build_ms)
-    t = torch.tensor([ms], device=dev)
     if dist:
         dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    total_tracks = n_tr * world
-    value = total_tracks / (ms_max / 1e3)
+    total_tracks, ms_max, value = job_rate(n_tr, ms, dist, dev)
 
     # ---------------- end to end through host buffers
     _, built_t, fitted_t = pipe.outputs()
@@ -465,7 +475,7 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = e2e_start.elapsed_time(e2e_stop) / a.steps
 
-    e2e_pipe = {"value": total_tracks / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e_pipe = {"value": job_rate(n_tr, e2e_ms, dist, dev)[2], "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                 "form": "graph-replayed pipeline with torch copies of pinned host planes on the same stream"}
 
@@ -481,7 +491,8 @@ def main():
         assert nt == n_tr
         e2e_s.append(dt)
     sv.close()
-    e2e = {"value": total_tracks / statistics.mean(e2e_s), "unit": UNIT, "h2d_bytes_per_step": lent.h2d,
+    e2e = {"value": job_rate(n_tr, 1e3 * statistics.mean(e2e_s), dist, dev)[2], "unit": UNIT,
+           "h2d_bytes_per_step": lent.h2d,
            "d2h_bytes_per_step": lent.d2h, "ms_per_step": 1e3 * statistics.mean(e2e_s),
            "form": "tkf_submit_event of all %d events (hit planes lent from pinned host memory) then tkf_poll of "
                    "each; %d slots, batches of up to %d events; host wall clock" % (b.n_events, 3, a.e2e_batch)}
