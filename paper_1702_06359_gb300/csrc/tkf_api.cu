@@ -272,8 +272,8 @@ constexpr int kSortWarps = 8;                    // warps per block
 
 // A bin too large for one warp pass (more than kSortHits hits), ordered in place by one lane
 // with an insertion sort in global memory; rare (hundreds of hits in one eta-phi bin).
-__device__ void sort_bin_serial(const IndexGeom &g, int b, int i0, int i1, const int *ev_off, float4 *hxyzi,
-                                float2 *hvar, uint4 *bin_sub, int *pos_of_hit)
+__device__ void sort_bin_serial(const IndexGeom &g, int b, int i0, int i1, int base, float4 *hxyzi, float2 *hvar,
+                                uint4 *bin_sub, int *pos_of_hit)
 {
     const int pb = (b % g.n_bins) % g.n_phi;
     for (int i = i0; i < i1; ++i) {
@@ -295,7 +295,6 @@ __device__ void sort_bin_serial(const IndexGeom &g, int b, int i0, int i1, const
         hvar[j + 1] = k2;
     }
     bin_sub[b] = sub_starts([&](int t) { return __float_as_int(hxyzi[t].w); }, i0, i1);
-    const int base = ev_off[b / (g.L * g.n_bins)];
     for (int i = i0; i < i1; ++i) {
         float4 q = hxyzi[i];
         const int id = __float_as_int(q.w) & 0x7FFFFF;
@@ -305,38 +304,30 @@ __device__ void sort_bin_serial(const IndexGeom &g, int b, int i0, int i1, const
     }
 }
 
-// Orders each bin by (phi sub-bin, event-local hit id) -- the order a window scan relies on to
-// read only the sub-bins it overlaps -- records the sub-bin starts (bin_sub) and fills
-// pos_of_hit.  Each warp walks kSortBinsPerWarp consecutive bins, taking as many whole bins
-// per pass as hold at most kSortHits hits: the pass loads their hits into registers
-// (coalesced), puts the sort keys in shared memory, ranks every hit among the keys of its bin
-// and writes it back to its ordered slot.  All loads of a pass precede its stores (the warp
-// synchronises in between), so ordering in place is safe.
-__global__ void __launch_bounds__(32 * kSortWarps)
-k_bin_sort(const IndexGeom g, const int *bin_off, const int *ev_off, int n_bins_total, float4 *hxyzi, float2 *hvar,
-           uint4 *bin_sub, int *pos_of_hit)
+// Orders bins [b, b_end) by (phi sub-bin, event-local hit id) -- the order a window scan
+// relies on to read only the sub-bins it overlaps -- records their sub-bin starts (bin_sub)
+// and fills pos_of_hit; one warp.  off(k) is the first hit of bin k (off(b_end): one past the
+// last), base(k) the first hit of bin k's event, gbin(k) its index in bin_sub.  Each pass takes
+// as many whole bins as hold at most kSortHits hits: it loads their hits into registers
+// (coalesced), puts the sort keys in shared memory (key, lbin, off: this warp's arrays), ranks
+// every hit among the keys of its bin and writes it back to its ordered slot.  All loads of a
+// pass precede its stores (the warp synchronises in between), so ordering in place is safe.
+template <class OffAt, class BaseAt, class GbinAt>
+__device__ __forceinline__ void sort_bins_warp(const IndexGeom &g, int b, int b_end, OffAt off_at, BaseAt base_at,
+                                               GbinAt gbin_at, int *key, unsigned char *lbin, int *off, float4 *hxyzi,
+                                               float2 *hvar, uint4 *bin_sub, int *pos_of_hit)
 {
-    __shared__ int s_key[kSortWarps][kSortHits];
-    __shared__ unsigned char s_bin[kSortWarps][kSortHits];
-    __shared__ int s_off[kSortWarps][33];
     const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long first = ((long long)blockIdx.x * kSortWarps + w) * kSortBinsPerWarp;
-    if (first >= n_bins_total) return;  // warp-uniform
-    int b = (int)first;
-    const int b_end = (int)min(first + kSortBinsPerWarp, (long long)n_bins_total);
-    int *key = s_key[w];
-    unsigned char *lbin = s_bin[w];
-    int *off = s_off[w];
+    const int lane = threadIdx.x & 31;
     while (b < b_end) {  // warp-uniform loop
         const int nb = min(32, b_end - b);
-        const int s_l = bin_off[b + min(lane, nb)];
-        const int e_l = bin_off[b + min(lane + 1, nb)];
+        const int s_l = off_at(b + min(lane, nb));
+        const int e_l = off_at(b + min(lane + 1, nb));
         const int o0 = __shfl_sync(full, s_l, 0);
         const bool fits = lane < nb && e_l - o0 <= kSortHits;
         const int m = __popc(__ballot_sync(full, fits));  // bins taken in this pass (a prefix)
         if (m == 0) {
-            if (lane == 0) sort_bin_serial(g, b, s_l, e_l, ev_off, hxyzi, hvar, bin_sub, pos_of_hit);
+            if (lane == 0) sort_bin_serial(g, gbin_at(b), s_l, e_l, base_at(b), hxyzi, hvar, bin_sub, pos_of_hit);
             __syncwarp();
             b += 1;
             continue;
@@ -356,7 +347,7 @@ k_bin_sort(const IndexGeom g, const int *bin_off, const int *ev_off, int n_bins_
             if (k < n) {
                 q[j] = hxyzi[o0 + k];
                 v[j] = hvar[o0 + k];
-                const int pb = ((b + lbin[k]) % g.n_bins) % g.n_phi;
+                const int pb = (gbin_at(b + lbin[k]) % g.n_bins) % g.n_phi;
                 key[k] = (hit_sub(g, q[j].x, q[j].y, pb) << 23) | __float_as_int(q[j].w);
             }
         }
@@ -373,13 +364,194 @@ k_bin_sort(const IndexGeom g, const int *bin_off, const int *ev_off, int n_bins_
                 const int d = o0 + a0 + r;
                 hxyzi[d] = q[j];  // w holds the event-local id
                 hvar[d] = v[j];
-                pos_of_hit[ev_off[(b + lb) / (g.L * g.n_bins)] + (mine & 0x7FFFFF)] = d;
+                pos_of_hit[base_at(b + lb) + (mine & 0x7FFFFF)] = d;
             }
         }
-        if (lane < m) bin_sub[b + lane] = sub_starts([&](int t) { return key[t]; }, off[lane], off[lane + 1]);
+        if (lane < m) bin_sub[gbin_at(b + lane)] = sub_starts([&](int t) { return key[t]; }, off[lane], off[lane + 1]);
         __syncwarp();  // shared memory is reused by the next pass
         b += m;
     }
+}
+
+// Bin order of the whole index in one launch (used when an event's bins do not fit the
+// shared memory of the per-event kernel below): each warp takes kSortBinsPerWarp bins.
+__global__ void __launch_bounds__(32 * kSortWarps)
+k_bin_sort(const IndexGeom g, const int *bin_off, const int *ev_off, int n_bins_total, float4 *hxyzi, float2 *hvar,
+           uint4 *bin_sub, int *pos_of_hit)
+{
+    __shared__ int s_key[kSortWarps][kSortHits];
+    __shared__ unsigned char s_bin[kSortWarps][kSortHits];
+    __shared__ int s_off[kSortWarps][33];
+    const int w = threadIdx.x >> 5;
+    const long long first = ((long long)blockIdx.x * kSortWarps + w) * kSortBinsPerWarp;
+    if (first >= n_bins_total) return;  // warp-uniform
+    const int b_end = (int)min(first + kSortBinsPerWarp, (long long)n_bins_total);
+    const int per_event = g.L * g.n_bins;
+    sort_bins_warp(
+        g, (int)first, b_end, [&](int k) { return bin_off[k]; }, [&](int k) { return ev_off[k / per_event]; },
+        [](int k) { return k; }, s_key[w], s_bin[w], s_off[w], hxyzi, hvar, bin_sub, pos_of_hit);
+}
+
+// Order in which the per-event blocks below take the events: largest first (so that the
+// big events of a lognormal mix start early instead of trailing the launch); the rank of
+// event e counts the events larger than it, or as large with a smaller index.  Up to
+// kOrderMax events (beyond that the input order is kept).
+constexpr int kOrderMax = 4096;
+
+__global__ void __launch_bounds__(1024) k_event_order(const int *ev_off, int n_events, int *perm)
+{
+    __shared__ int s_size[kOrderMax];
+    if (n_events > kOrderMax) {
+        for (int e = threadIdx.x; e < n_events; e += blockDim.x) perm[e] = e;
+        return;
+    }
+    for (int e = threadIdx.x; e < n_events; e += blockDim.x) s_size[e] = ev_off[e + 1] - ev_off[e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < n_events; e += blockDim.x) {
+        const int se = s_size[e];
+        int rank = 0;
+        for (int f = 0; f < n_events; ++f) {
+            const int sf = s_size[f];
+            rank += sf > se || (sf == se && f < e);
+        }
+        perm[rank] = e;
+    }
+}
+
+// The bins of one event in one block (one block per event, events taken in the order perm),
+// with the event's bin counters in shared memory: (1) count the hits per (layer, eta bin, phi
+// bin) and reduce the largest variances per layer; (2) exclusive scan of the counts ->
+// bin_off (the event's hits keep their place [event_off[e], event_off[e+1]) in the index);
+// (3) place every hit into its bin (a shared-memory cursor per bin).  k_bin_sort then orders
+// the bins.  The same bins and offsets as the multi-launch path.
+constexpr int kEventThreads = 1024;
+constexpr int kEventWarps = kEventThreads / 32;
+constexpr int kEventUnroll = 4;
+
+__global__ void __launch_bounds__(kEventThreads)
+k_index_event(const IndexGeom g, const tkf_hits h, const int *perm, int n_bins_total, float4 *hxyzi, float2 *hvar,
+              int *bin_off, float2 *var_max, int *err)
+{
+    extern __shared__ int s_cnt[];  // [L * n_bins]: counts, then bin offsets / cursors
+    __shared__ int s_var[2 * TKF_MAX_LAYERS];
+    __shared__ int s_wvar[kEventWarps][2 * TKF_MAX_LAYERS];
+    __shared__ int s_part[kEventWarps];
+    const unsigned full = 0xffffffffu;
+    const int e = perm[blockIdx.x], tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (lane < 2 * TKF_MAX_LAYERS) s_wvar[w][lane] = 0;
+    const int nb_ev = g.L * g.n_bins;
+    const int h0 = h.event_off[e], h1 = h.event_off[e + 1];
+    for (int k = tid; k < nb_ev; k += kEventThreads) s_cnt[k] = 0;
+    if (tid < 2 * g.L) s_var[tid] = 0;
+    __syncthreads();
+    // (1) counts and variance maxima; kEventUnroll hits per thread and pass, loaded together
+    for (int i0 = h0; i0 < h1; i0 += kEventThreads * kEventUnroll) {
+        int l[kEventUnroll];
+        float x[kEventUnroll], y[kEventUnroll], z[kEventUnroll], vu[kEventUnroll], vv[kEventUnroll];
+#pragma unroll
+        for (int u = 0; u < kEventUnroll; ++u) {
+            const int i = i0 + tid + u * kEventThreads;
+            const int j = i < h1 ? i : h0;  // a valid index (the event is not empty here)
+            l[u] = h.layer[j];
+            x[u] = h.x[j];
+            y[u] = h.y[j];
+            z[u] = h.z[j];
+            vu[u] = h.var_u[j];
+            vv[u] = h.var_v[j];
+        }
+#pragma unroll
+        for (int u = 0; u < kEventUnroll; ++u) {
+            const bool in = i0 + tid + u * kEventThreads < h1;
+            const bool ok = in && l[u] >= 0 && l[u] < g.L;
+            if (ok) {
+                atomicAdd(&s_cnt[l[u] * g.n_bins + hit_bin(g, l[u], x[u], y[u], z[u])], 1);
+                atomicMax(&s_wvar[w][2 * l[u]], __float_as_int(fmaxf(vu[u], 0.f)));
+                atomicMax(&s_wvar[w][2 * l[u] + 1], __float_as_int(fmaxf(vv[u], 0.f)));
+            } else if (in) {
+                atomicOr(err, kErrBadLayer);
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < 2 * g.L) atomicMax(&s_var[lane], s_wvar[w][lane]);
+    __syncthreads();
+    // (2) exclusive scan: thread t owns the contiguous chunk [t * per, (t + 1) * per)
+    const int per = (nb_ev + kEventThreads - 1) / kEventThreads;
+    const int c0 = min(tid * per, nb_ev), c1 = min(c0 + per, nb_ev);
+    int sum = 0;
+    for (int k = c0; k < c1; ++k) sum += s_cnt[k];
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_part[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int x = lane < kEventWarps ? s_part[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(full, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane < kEventWarps) s_part[lane] = x;  // inclusive warp totals
+    }
+    __syncthreads();
+    int run = incl - sum + (w > 0 ? s_part[w - 1] : 0);
+    const size_t gb0 = (size_t)e * nb_ev;
+    for (int k = c0; k < c1; ++k) {
+        const int c = s_cnt[k];
+        s_cnt[k] = run;
+        bin_off[gb0 + k] = h0 + run;
+        run += c;
+    }
+    if (e == g.n_events - 1 && tid == kEventThreads - 1) bin_off[n_bins_total] = h0 + run;
+    if (tid < g.L)
+        var_max[(size_t)e * g.L + tid] = make_float2(__int_as_float(s_var[2 * tid]), __int_as_float(s_var[2 * tid + 1]));
+    __syncthreads();
+    // (3) place the hits, kEventUnroll per thread and pass
+    for (int i0 = h0; i0 < h1; i0 += kEventThreads * kEventUnroll) {
+        int l[kEventUnroll];
+        float x[kEventUnroll], y[kEventUnroll], z[kEventUnroll], vu[kEventUnroll], vv[kEventUnroll];
+#pragma unroll
+        for (int u = 0; u < kEventUnroll; ++u) {
+            const int i = i0 + tid + u * kEventThreads;
+            const int j = i < h1 ? i : h0;
+            l[u] = h.layer[j];
+            x[u] = h.x[j];
+            y[u] = h.y[j];
+            z[u] = h.z[j];
+            vu[u] = h.var_u[j];
+            vv[u] = h.var_v[j];
+        }
+#pragma unroll
+        for (int u = 0; u < kEventUnroll; ++u) {
+            const int i = i0 + tid + u * kEventThreads;
+            if (i >= h1 || l[u] < 0 || l[u] >= g.L) continue;
+            const int pos = h0 + atomicAdd(&s_cnt[l[u] * g.n_bins + hit_bin(g, l[u], x[u], y[u], z[u])], 1);
+            hxyzi[pos] = make_float4(x[u], y[u], z[u], __int_as_float(i - h0));
+            hvar[pos] = make_float2(vu[u], vv[u]);
+        }
+    }
+}
+
+// Dynamic shared memory of k_index_event (the event's bin counters) allowed next to its
+// static arrays within one block's 227 KB; an index whose event bins need more takes the
+// multi-launch path.
+constexpr size_t kEventStaticSmem = (size_t)kEventWarps * 4 + 2 * TKF_MAX_LAYERS * 4 * (kEventWarps + 1);
+constexpr size_t kEventMaxDynSmem = 227 * 1024 - kEventStaticSmem - 1024;
+
+size_t index_event_smem(int n_layers, int n_bins)
+{
+    const size_t bytes = (size_t)n_layers * n_bins * sizeof(int);
+    return bytes <= kEventMaxDynSmem ? bytes : 0;
+}
+
+// Allows k_index_event its dynamic shared memory on the current device.
+cudaError_t index_event_prepare()
+{
+    return cudaFuncSetAttribute(k_index_event, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEventMaxDynSmem);
 }
 
 unsigned sort_blocks(size_t n_bins)
@@ -713,6 +885,7 @@ int tkf_create(const tkf_config *cfg, tkf_ctx **out)
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_tile, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->d_err, sizeof(int));
+    if (e == cudaSuccess) e = index_event_prepare();
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
     if (e != cudaSuccess) {
         if (ctx->d_tile) cudaFree(ctx->d_tile);
@@ -798,10 +971,23 @@ int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out,
         g.eta_min = (float)c.eta_min;
         g.inv_eta_w = (float)(1.0 / c.eta_bin_w);
         g.phi_scale = (float)(c.n_phi_bins / (2.0 * kPi));
-        TKF_CUDA(ctx, cudaMemsetAsync(idx->counts, 0, n_bins * sizeof(int), s));
-        TKF_CUDA(ctx, cudaMemsetAsync(idx->var_max, 0, n_segs * sizeof(float2), s));
         TKF_CUDA(ctx, cudaMemcpyAsync(idx->ev_off, hits->event_off, (hits->n_events + 1) * sizeof(int),
                                       cudaMemcpyDeviceToDevice, s));
+        const size_t ev_smem = index_event_smem(L, NB);
+        if (ev_smem) {  // one block per event (k_index_event's shared memory is set up by tkf_create)
+            int *perm = idx->seg_base;  // >= n_events entries
+            k_event_order<<<1, 1024, 0, s>>>(hits->event_off, hits->n_events, perm);
+            k_index_event<<<(unsigned)hits->n_events, kEventThreads, ev_smem, s>>>(
+                g, *hits, perm, (int)n_bins, idx->hxyzi, idx->hvar, idx->bin_off, idx->var_max, ctx->d_err);
+            k_bin_sort<<<sort_blocks(n_bins), 32 * kSortWarps, 0, s>>>(g, idx->bin_off, idx->ev_off, (int)n_bins,
+                                                                       idx->hxyzi, idx->hvar, idx->bin_sub,
+                                                                       idx->pos_of_hit);
+            TKF_CUDA(ctx, cudaGetLastError());
+            *out = idx;
+            return TKF_OK;
+        }
+        TKF_CUDA(ctx, cudaMemsetAsync(idx->counts, 0, n_bins * sizeof(int), s));
+        TKF_CUDA(ctx, cudaMemsetAsync(idx->var_max, 0, n_segs * sizeof(float2), s));
         if (hits->n > 0) {
             const int nb = (hits->n + 255) / 256;
             k_hit_count<<<nb, 256, 0, s>>>(g, *hits, idx->keys, idx->counts, idx->seg_count, (int *)idx->var_max,
@@ -1060,6 +1246,7 @@ int noalloc_scratch(int **out)
     if (!g_noalloc_addr[dev]) {
         int *p = nullptr;
         if (cudaGetSymbolAddress((void **)&p, g_noalloc_scratch) != cudaSuccess || !p) return TKF_ERR_CUDA;
+        if (index_event_prepare() != cudaSuccess) return TKF_ERR_CUDA;
         g_noalloc_addr[dev] = p;
     }
     *out = g_noalloc_addr[dev];
@@ -1110,10 +1297,19 @@ extern "C" int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits
     cudaStream_t s = (cudaStream_t)stream;
     float4 *hxyzi = (float4 *)out->hit_xyzi;
     float2 *hvar = (float2 *)out->hit_var;
-    if (cudaMemsetAsync(counts, 0, n_bins * sizeof(int), s) != cudaSuccess ||
-        cudaMemsetAsync(out->var_max, 0, n_segs * 2 * sizeof(float), s) != cudaSuccess ||
-        cudaMemcpyAsync(out->event_off, hits->event_off, (hits->n_events + 1) * sizeof(int), cudaMemcpyDeviceToDevice,
+    if (cudaMemcpyAsync(out->event_off, hits->event_off, (hits->n_events + 1) * sizeof(int), cudaMemcpyDeviceToDevice,
                         s) != cudaSuccess)
+        return TKF_ERR_CUDA;
+    if (const size_t ev_smem = index_event_smem(L, NB)) {  // one block per event, nothing to clear
+        k_event_order<<<1, 1024, 0, s>>>(hits->event_off, hits->n_events, seg_base);
+        k_index_event<<<(unsigned)hits->n_events, kEventThreads, ev_smem, s>>>(
+            g, *hits, seg_base, (int)n_bins, hxyzi, hvar, out->bin_off, (float2 *)out->var_max, err);
+        k_bin_sort<<<sort_blocks(n_bins), 32 * kSortWarps, 0, s>>>(g, out->bin_off, out->event_off, (int)n_bins, hxyzi,
+                                                                   hvar, (uint4 *)out->bin_sub, out->pos_of_hit);
+        return cudaGetLastError() == cudaSuccess ? TKF_OK : TKF_ERR_CUDA;
+    }
+    if (cudaMemsetAsync(counts, 0, n_bins * sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(out->var_max, 0, n_segs * 2 * sizeof(float), s) != cudaSuccess)
         return TKF_ERR_CUDA;
     if (hits->n > 0)
         k_hit_count<<<(hits->n + 255) / 256, 256, 0, s>>>(g, *hits, keys, counts, seg_count, (int *)out->var_max, err);
