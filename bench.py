@@ -134,6 +134,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def efficiency(b, hit_idx):
+    """Fraction of seeds whose built track has >= 75 % of its hits from the seed's own simulated
+    track (hit_idx: [L, n_tracks] batch hit ids, -1 = hole)."""
+    h = np.asarray(hit_idx)
+    own = (h >= 0) & (b.mc[np.maximum(h, 0)] == np.arange(h.shape[1])[None, :])
+    nh = (h >= 0).sum(0)
+    return float(np.mean(own.sum(0) >= 0.75 * np.maximum(nh, 1)))
+
+
 # ----------------------------------------------------------------------------- replicas
 def job_rate(units, ms, dist=None, device="cpu"):
     """Whole-job throughput of independent replicas: the units of every rank summed, over the
@@ -422,6 +431,21 @@ def main():
         cn.close()
     n_grid[6] = {"tiles": tiles, "build_ms": [round(x, 4) for x in tile_ms], "best": best_tile}
     del scratch_out
+    # building efficiency at each N on this workload (the physics side of the N choice)
+    for n_cand in sorted(n_grid):
+        if n_cand == 6:
+            hid = tkf.tracks_tensors(pipe.outputs()[1], L)["hit_idx"][:, :n_tr]
+            n_grid[6]["efficiency"] = efficiency(b, hid.cpu().numpy())
+            continue
+        cn = tkf.Context(tkf.default_config(seed_order=a.seed_order, n_cand=n_cand,
+                                            seeds_per_block=n_grid[n_cand]["best"]))
+        pn = tkf.DevicePipeline(cn, n_hits, b.n_events, n_tr, use_graph=False)
+        pn.run(hits, d["seed_hits"], d["seed_event"], n_tr, stream=stream)
+        cn.sync_status(stream)
+        hid = tkf.tracks_tensors(pn.outputs()[1], L)["hit_idx"][:, :n_tr]
+        n_grid[n_cand]["efficiency"] = efficiency(b, hid.cpu().numpy())
+        pn.close()
+        cn.close()
     # the clock sampler starts before the warm-up: nvidia-smi's start-up must not fall in the
     # timed region
     clocks = ClockSampler(local).__enter__()
@@ -585,11 +609,20 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         ev, ntr = sample_events(a.seed, a.cpu_tracks)
-        tracks, wall = cpu_baseline(oracle_sample(b, ev), pool, cores)
+        sample = oracle_sample(b, ev)
+        tracks, wall = cpu_baseline(sample, pool, cores)
+        # one core: the same oracle in this process on the sample's first events (>= 20 000 tracks)
+        ev1 = ev[:max(1, next((k + 1 for k in range(len(ev)) if int(b.trk_off[ev[k] + 1] - b.trk_off[ev[0]]) >= 20000),
+                              len(ev)))]
+        t1 = time.perf_counter()
+        n1 = _oracle_events(sample[:len(ev1)])
+        wall1 = time.perf_counter() - t1
         cpu = {"value": ntr / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "events %d..%d of the same batch (%d tracks): index, seed, seed fit, build, final fit, "
                          "FP64, one process per core; inputs pickled to the workers inside the timed region"
-                         % (ev[0], ev[-1], ntr)}
+                         % (ev[0], ev[-1], ntr),
+               "single_core": {"value": n1 / wall1, "unit": UNIT, "cores": 1,
+                               "sample": "events %d..%d (%d tracks), one process" % (ev1[0], ev1[-1], n1)}}
     pool.close()
 
     achieved = FLOP_PER_SEED * n_tr / (build_ms / 1e3) / 1e12

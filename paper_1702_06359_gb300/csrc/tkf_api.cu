@@ -973,8 +973,11 @@ int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out,
         g.phi_scale = (float)(c.n_phi_bins / (2.0 * kPi));
         TKF_CUDA(ctx, cudaMemcpyAsync(idx->ev_off, hits->event_off, (hits->n_events + 1) * sizeof(int),
                                       cudaMemcpyDeviceToDevice, s));
-        const size_t ev_smem = index_event_smem(L, NB);
-        if (ev_smem) {  // one block per event (k_index_event's shared memory is set up by tkf_create)
+        // one block per event when the batch has enough events to fill the GPU and their bins fit
+        // a block's shared memory (set up by tkf_create); otherwise counts in global memory and
+        // every block on the hits of a few events
+        const size_t ev_smem = hits->n_events >= ctx->sm_count ? index_event_smem(L, NB) : 0;
+        if (ev_smem) {
             int *perm = idx->seg_base;  // >= n_events entries
             k_event_order<<<1, 1024, 0, s>>>(hits->event_off, hits->n_events, perm);
             k_index_event<<<(unsigned)hits->n_events, kEventThreads, ev_smem, s>>>(
@@ -1238,7 +1241,9 @@ static __device__ __align__(256) int g_noalloc_scratch[kNoallocWords];
 std::mutex g_noalloc_mutex;
 int *g_noalloc_addr[64] = {};
 
-int noalloc_scratch(int **out)
+int g_noalloc_sms[64] = {};
+
+int noalloc_scratch(int **out, int *sm_count)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TKF_ERR_CUDA;
@@ -1247,9 +1252,12 @@ int noalloc_scratch(int **out)
         int *p = nullptr;
         if (cudaGetSymbolAddress((void **)&p, g_noalloc_scratch) != cudaSuccess || !p) return TKF_ERR_CUDA;
         if (index_event_prepare() != cudaSuccess) return TKF_ERR_CUDA;
+        if (cudaDeviceGetAttribute(&g_noalloc_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return TKF_ERR_CUDA;
         g_noalloc_addr[dev] = p;
     }
     *out = g_noalloc_addr[dev];
+    *sm_count = g_noalloc_sms[dev];
     return TKF_OK;
 }
 
@@ -1276,8 +1284,8 @@ extern "C" int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits
     const size_t n_bins = n_segs * NB;
     if ((size_t)hits->n > TKF_NOALLOC_MAX_HITS || n_bins > TKF_NOALLOC_MAX_BINS || n_segs > TKF_NOALLOC_MAX_SEGMENTS)
         return TKF_ERR_TOO_LARGE;
-    int *scratch = nullptr;
-    int st = noalloc_scratch(&scratch);
+    int *scratch = nullptr, n_sm = 0;
+    int st = noalloc_scratch(&scratch, &n_sm);
     if (st) return st;
     int *keys = scratch;
     int *counts = keys + TKF_NOALLOC_MAX_HITS;
@@ -1300,7 +1308,7 @@ extern "C" int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits
     if (cudaMemcpyAsync(out->event_off, hits->event_off, (hits->n_events + 1) * sizeof(int), cudaMemcpyDeviceToDevice,
                         s) != cudaSuccess)
         return TKF_ERR_CUDA;
-    if (const size_t ev_smem = index_event_smem(L, NB)) {  // one block per event, nothing to clear
+    if (const size_t ev_smem = hits->n_events >= n_sm ? index_event_smem(L, NB) : 0) {  // one block per event
         k_event_order<<<1, 1024, 0, s>>>(hits->event_off, hits->n_events, seg_base);
         k_index_event<<<(unsigned)hits->n_events, kEventThreads, ev_smem, s>>>(
             g, *hits, seg_base, (int)n_bins, hxyzi, hvar, out->bin_off, (float2 *)out->var_max, err);

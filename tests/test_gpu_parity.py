@@ -95,6 +95,46 @@ def test_hit_index_matches_oracle_bins(det):
     assert n_edge <= 4
 
 
+def test_hit_index_one_block_per_event_equals_multi_launch_index(det):
+    """A batch with more events than SMs takes the one-block-per-event kernel, a smaller one the
+    multi-launch path (global counts and scans); the index of the whole batch must equal the
+    two halves' indices laid end to end, bit for bit."""
+    from synth import event_sizes
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    n_ev = sm + 40
+    sizes, noise = event_sizes(43, n_ev, median=120, lo=0, hi=900)
+    b = generate(EventSpec(seed=43, n_events=n_ev, n_tracks=sizes, noise_frac=noise), det)
+    ctx = _ctx()
+    L, NB = det.n_layers, ctx.cfg.n_eta_bins * ctx.cfg.n_phi_bins
+
+    def arrays(bb):
+        idx = ctx.build_hit_index(device_hits(bb))
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        v = idx.view()
+        n, nbt = bb.n_hits, bb.n_events * L * NB
+        out = dict(xyzi=_copy_dev(v.hit_xyzi, n * 4, torch.float32).cpu().numpy().view(np.int32),
+                   var=_copy_dev(v.hit_var, n * 2, torch.float32).cpu().numpy().view(np.int32),
+                   sub=_copy_dev(v.bin_sub, nbt * 4, torch.int32).cpu().numpy(),
+                   off=_copy_dev(v.bin_off, nbt + 1, torch.int32).cpu().numpy(),
+                   pos=_copy_dev(v.pos_of_hit, n, torch.int32).cpu().numpy(),
+                   vmax=_copy_dev(v.var_max, bb.n_events * L * 2, torch.float32).cpu().numpy().view(np.int32))
+        idx.free()
+        return out
+
+    full = arrays(b)
+    half = n_ev // 2
+    a1 = arrays(select_events(b, list(range(half))))
+    a2 = arrays(select_events(b, list(range(half, n_ev))))
+    n1 = int(b.hit_off[half])
+    assert np.array_equal(full["xyzi"], np.concatenate([a1["xyzi"], a2["xyzi"]]))
+    assert np.array_equal(full["var"], np.concatenate([a1["var"], a2["var"]]))
+    assert np.array_equal(full["sub"], np.concatenate([a1["sub"], a2["sub"]]))
+    assert np.array_equal(full["off"], np.concatenate([a1["off"][:-1], a2["off"] + n1]))
+    assert np.array_equal(full["pos"], np.concatenate([a1["pos"], a2["pos"] + n1]))
+    assert np.array_equal(full["vmax"], np.concatenate([a1["vmax"], a2["vmax"]]))
+
+
 def _copy_dev(ptr, count, dtype):
     """Copies `count` elements from a raw device pointer owned by the library."""
     class _Wrap:

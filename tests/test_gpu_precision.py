@@ -10,7 +10,8 @@ chi2 within the parity tolerance (1e-8 in FP64); a differing hit list is allowed
 layer where the oracle's own decision was fragile (two ranked totals within 1e-3, or a chi2
 within 1e-3 of the cut), and for at most 5% of seeds.  Reported per quantity and mode
 (printed, and written as JSON to $TKF_REPORT_DIR when set): relative error of each
-parameter, of each covariance diagonal element and of chi2, and the hit agreement."""
+parameter, of each covariance diagonal element and of chi2, the hit agreement, and the
+building efficiency next to the oracle's."""
 import json
 import os
 
@@ -78,6 +79,17 @@ def _gpu_path(b, det, prec):
     return out
 
 
+def _efficiency(hits_local, mc_local, n_tracks):
+    """Fraction of seeds whose track has >= 75 % of its hits from the seed's own simulated track,
+    and that fraction per number of hits on the track (3..10)."""
+    own = (mc_local[np.maximum(hits_local, 0)] == np.arange(n_tracks)[:, None]) & (hits_local >= 0)
+    nh = (hits_local >= 0).sum(1)
+    good = own.sum(1) / np.maximum(nh, 1) >= 0.75
+    per = {int(k): [int((nh == k).sum()), float(good[nh == k].mean()) if (nh == k).any() else None]
+           for k in range(3, hits_local.shape[1] + 1)}
+    return float(good.mean()), per
+
+
 def _stats(x):
     x = np.asarray(x)
     if not len(x):
@@ -92,11 +104,15 @@ def test_precision_sweep_whole_path(sweep_events, prec):
     name = {tkf.FP32: "fp32", tkf.MIXED: "mixed", tkf.FP64: "fp64"}[prec]
     n_same = n_div = n_lost = 0
     par_err, cov_err, chi2_err = [], [], []
+    eff_gpu, eff_orc = [], []
     for e, ref in enumerate(refs):
         t0, t1 = b.trk_off[e], b.trk_off[e + 1]
         h0 = b.hit_off[e]
         gh = got["hits"][t0:t1]
         gh = np.where(gh >= 0, gh - h0, -1)
+        mc = np.where(b.mc[h0:b.hit_off[e + 1]] >= 0, b.mc[h0:b.hit_off[e + 1]] - t0, -1)
+        eff_gpu.append(_efficiency(gh, mc, t1 - t0))
+        eff_orc.append(_efficiency(ref["hits"], mc, t1 - t0))
         lost = ref["n_cand"] == 0
         n_lost += int(lost.sum())
         assert np.all(got["built_nhits"][t0:t1][lost] == tkf.TRACK_LOST)
@@ -133,10 +149,57 @@ def test_precision_sweep_whole_path(sweep_events, prec):
         "param_rel_err_note": "|d| / max(|ref|, floor), floors (1, 1, 1 cm, 0.1 1/GeV, 1, 1 rad)",
         "cov_diag_rel_err": {NAMES[i]: _stats(cov_err[:, i]) for i in range(6)},
         "chi2_rel_err": _stats(chi2_err),
+        "efficiency": float(np.mean([e for e, _ in eff_gpu])),
+        "efficiency_oracle": float(np.mean([e for e, _ in eff_orc])),
+        "efficiency_note": "seeds whose track has >= 75 % of its hits from the seed's simulated track "
+                           "(mean over events)",
     }
+    assert report["efficiency"] > 0.97 and abs(report["efficiency"] - report["efficiency_oracle"]) < 0.005
     print(json.dumps(report))
     out_dir = os.environ.get("TKF_REPORT_DIR")
     if out_dir:
         os.makedirs(out_dir, exist_ok=True)
         with open(os.path.join(out_dir, "precision_sweep_%s.json" % name), "w") as f:
             json.dump(report, f, indent=1)
+
+
+@pytest.mark.parametrize("n_cand", [4, 6, 10])
+def test_efficiency_by_candidates_per_seed(n_cand):
+    """Building efficiency of the GPU path (FP32) for 4, 6 and 10 candidates per seed on the
+    plain building workload (20 x 5000 tracks, 20 % noise), per number of hits on the track;
+    the throughput side of the same choice is bench.py's autotune grid."""
+    det = Detector()
+    b = generate(EventSpec(seed=1, n_events=N_EVENTS, n_tracks=N_TRACKS, noise_frac=0.2), det)
+    from _gpu import device_hits
+    ctx = tkf.Context(tkf.default_config(n_cand=n_cand))
+    L = det.n_layers
+    sh = torch.as_tensor(np.ascontiguousarray(b.trk_hits[:, :3].T), dtype=torch.int32, device="cuda")
+    se = torch.as_tensor(b.trk_event, dtype=torch.int32, device="cuda")
+    pipe = tkf.DevicePipeline(ctx, b.n_hits, b.n_events, b.n_tracks, use_graph=False)
+    pipe.run(device_hits(b), sh, se, b.n_tracks)
+    ctx.sync_status()
+    _, built, _ = pipe.outputs()
+    hits = tkf.tracks_tensors(built, L)["hit_idx"][:, :b.n_tracks].T.cpu().numpy()
+    pipe.close()
+    ctx.close()
+    effs, per = [], {}
+    for e in range(b.n_events):
+        h0, h1, t0, t1 = b.hit_off[e], b.hit_off[e + 1], b.trk_off[e], b.trk_off[e + 1]
+        gh = np.where(hits[t0:t1] >= 0, hits[t0:t1] - h0, -1)
+        mc = np.where(b.mc[h0:h1] >= 0, b.mc[h0:h1] - t0, -1)
+        eff, p = _efficiency(gh, mc, t1 - t0)
+        effs.append(eff)
+        for k, (n, f) in p.items():
+            if n:
+                a = per.setdefault(k, [0, 0.0])
+                a[0] += n
+                a[1] += n * f
+    report = {"n_cand": n_cand, "efficiency": float(np.mean(effs)),
+              "by_hits": {k: [n, round(f / n, 5)] for k, (n, f) in sorted(per.items())}}
+    print(json.dumps(report))
+    out_dir = os.environ.get("TKF_REPORT_DIR")
+    if out_dir:
+        os.makedirs(out_dir, exist_ok=True)
+        with open(os.path.join(out_dir, "efficiency_n%d.json" % n_cand), "w") as f:
+            json.dump(report, f, indent=1)
+    assert report["efficiency"] > 0.95
