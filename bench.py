@@ -190,8 +190,13 @@ def oracle_sample(batch, events):
 
 
 def cpu_baseline(sample, pool, cores):
-    """The oracle on the sample's events, one worker process per core; (tracks, wall s)."""
-    chunks = [sample[i::cores] for i in range(cores)]
+    """The oracle on the sample's events, one worker process per core, events dealt largest
+    first to the least-loaded worker; (tracks, wall s)."""
+    chunks, load = [[] for _ in range(cores)], [0] * cores
+    for ev in sorted(sample, key=lambda e: -len(e[1])):
+        k = load.index(min(load))
+        chunks[k].append(ev)
+        load[k] += len(ev[1])
     chunks = [c for c in chunks if c]
     t0 = time.perf_counter()
     done = sum(pool.map(_oracle_events, chunks, chunksize=1))
@@ -350,7 +355,7 @@ def main():
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--plain-events", type=int, default=640, help="events timed one at a time")
     ap.add_argument("--cpu-tracks", type=int, default=200000, help="oracle CPU-baseline sample (tracks)")
-    ap.add_argument("--ref-tracks", type=int, default=60000, help="reference-arm sample per step (tracks)")
+    ap.add_argument("--ref-tracks", type=int, default=120000, help="reference-arm sample per step (tracks)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve", type=int, default=1, help="1: also measure the served stream")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
