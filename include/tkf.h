@@ -303,7 +303,8 @@ void tkf_server_default_options(tkf_server_options *opt);
  * Errors: TKF_ERR_INVALID (bad options, result_bytes below one batch), TKF_ERR_NOMEM,
  * TKF_ERR_CUDA. */
 int tkf_server_create(const tkf_config *cfg, const tkf_server_options *opt, tkf_server **out);
-/* Stops the worker after the batches in flight finish, and frees everything. */
+/* Stops the worker after the batches in flight finish, and frees everything (results not yet
+ * released included).  No other call on this server may overlap or follow it. */
 int tkf_server_destroy(tkf_server *server);
 
 /* Non-blocking submission.  Errors: TKF_ERR_AGAIN (host queue full: retry later),

@@ -30,8 +30,6 @@ __host__ __device__ __forceinline__ float at2(float y, float x) { return atan2f(
 __host__ __device__ __forceinline__ double at2(double y, double x) { return atan2(y, x); }
 __host__ __device__ __forceinline__ float asn(float a) { return asinf(a); }
 __host__ __device__ __forceinline__ double asn(double a) { return asin(a); }
-__host__ __device__ __forceinline__ float ash(float a) { return asinhf(a); }
-__host__ __device__ __forceinline__ double ash(double a) { return asinh(a); }
 __host__ __device__ __forceinline__ float ab(float a) { return fabsf(a); }
 __host__ __device__ __forceinline__ double ab(double a) { return fabs(a); }
 __host__ __device__ __forceinline__ float flr(float a) { return floorf(a); }
