@@ -264,6 +264,7 @@ class LentEvents:
             ev = tkf.Event(*[base[k] + 4 * h0 for k in ("x", "y", "z", "var_u", "var_v", "layer")], h1 - h0,
                            blk.ctypes.data, t1 - t0, 1)
             self.events.append(ev)
+        self.array = (tkf.Event * len(self.events))(*self.events)
         self.n_tracks = b.n_tracks
         # bytes the server moves per pass: hit planes, seed ids and two offsets per event in;
         # final parameters, covariance, chi2, nhits and hit ids out
@@ -272,16 +273,17 @@ class LentEvents:
 
 
 def server_pass(sv, lent):
-    """Submits every event of the batch, waits for all results; returns (seconds, tracks)."""
+    """Submits every event of the batch, waits for all results and releases them (one call
+    each); returns (seconds, tracks)."""
     t0 = time.perf_counter()
-    tickets = [sv.submit_struct(ev) for ev in lent.events]
-    tracks = 0
-    for t in tickets:
-        code, r = sv.poll(t, timeout_us=60_000_000, copy=False)
-        if code != 0:
-            raise RuntimeError("server pass: poll returned %d" % code)
-        tracks += r.n_tracks
-        sv.release(t)
+    code, tickets = sv.submit_many(lent.array)
+    if code != 0 or len(tickets) != len(lent.events):
+        raise RuntimeError("server pass: submission returned %d" % code)
+    code, res = sv.wait_all(tickets)
+    if code != 0:
+        raise RuntimeError("server pass: wait returned %d" % code)
+    tracks = sum(r.n_tracks for r in res)
+    sv.release_many(tickets)
     return time.perf_counter() - t0, tracks
 
 
@@ -361,7 +363,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--mixed", type=int, default=1, help="1: also time the batched step in MIXED precision")
     ap.add_argument("--tile", type=int, default=0, help="seeds per warp work tile (0: autotuned)")
-    ap.add_argument("--e2e-batch", type=int, default=128, help="events per server batch in the e2e measurement")
+    ap.add_argument("--e2e-batch", type=int, default=160, help="events per server batch in the e2e measurement")
+    ap.add_argument("--e2e-slots", type=int, default=4, help="server slots in the e2e measurement")
     ap.add_argument("--seed-order", type=int, default=1,
                     help="batched form: 1 = build seeds grouped by detector region (the per-event form keeps input order)")
     a = ap.parse_args()
@@ -510,7 +513,8 @@ def main():
 
     # ---------------- end to end through the public serving API (host buffers lent to tkf_server)
     lent = LentEvents(tkf, b, host, L)
-    e2e_opts = dict(n_slots=3, max_batch_events=a.e2e_batch, max_batch_hits=1 << 23, max_batch_tracks=1 << 19)
+    e2e_opts = dict(n_slots=a.e2e_slots, max_batch_events=a.e2e_batch, max_batch_hits=1 << 24,
+                    max_batch_tracks=1 << 20)
     sv = tkf.Server(ctx.cfg, **e2e_opts)
     for _ in range(max(1, a.warmup)):
         server_pass(sv, lent)
@@ -523,8 +527,9 @@ def main():
     e2e = {"value": job_rate(n_tr, 1e3 * statistics.mean(e2e_s), dist, dev)[2], "unit": UNIT,
            "h2d_bytes_per_step": lent.h2d,
            "d2h_bytes_per_step": lent.d2h, "ms_per_step": 1e3 * statistics.mean(e2e_s),
-           "form": "tkf_submit_event of all %d events (hit planes lent from pinned host memory) then tkf_poll of "
-                   "each; %d slots, batches of up to %d events; host wall clock" % (b.n_events, 3, a.e2e_batch)}
+           "form": "tkf_submit_events of all %d events (hit planes lent from pinned host memory), tkf_wait_all, "
+                   "tkf_release_many; %d slots, batches of up to %d events; host wall clock"
+                   % (b.n_events, a.e2e_slots, a.e2e_batch)}
 
     # ---------------- the same batched step in MIXED precision (FP64 inverse + Joseph update)
     mixed = None

@@ -322,6 +322,18 @@ int tkf_release(tkf_server *server, uint64_t ticket);
 
 int tkf_server_get_stats(tkf_server *server, tkf_server_stats *out);
 
+/* Batch forms for clients that move many events per call (the calls above, in a loop).
+ * tkf_submit_events submits events[0..n) in order and stops at the first refusal: returns
+ * that status (TKF_ERR_AGAIN: queue full) with *n_accepted events accepted and their tickets
+ * in tickets[0..*n_accepted).  tkf_wait_all fills results[k] for tickets[k], waiting up to
+ * timeout_us in total (0: do not wait); it returns the first error (TKF_ERR_TIMEOUT,
+ * TKF_ERR_NOTREADY, TKF_ERR_INVALID), the results before it being filled.  tkf_release_many
+ * releases every ticket given and returns the first error. */
+int tkf_submit_events(tkf_server *server, const tkf_event *events, int32_t n, uint64_t *tickets,
+                      int32_t *n_accepted);
+int tkf_wait_all(tkf_server *server, const uint64_t *tickets, int32_t n, tkf_result *results, int64_t timeout_us);
+int tkf_release_many(tkf_server *server, const uint64_t *tickets, int32_t n);
+
 /* ---------------------------------------------------------------- allocation-free variant */
 
 /* Caller-owned output arrays of tkf_build_hit_index_noalloc (device memory), laid out as in

@@ -632,6 +632,42 @@ int tkf_release(tkf_server *sv, uint64_t ticket)
     return TKF_OK;
 }
 
+int tkf_submit_events(tkf_server *sv, const tkf_event *events, int32_t n, uint64_t *tickets, int32_t *n_accepted)
+{
+    if (!sv || (n > 0 && (!events || !tickets)) || n < 0 || !n_accepted) return TKF_ERR_INVALID;
+    *n_accepted = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        const int st = tkf_submit_event(sv, &events[k], &tickets[k]);
+        if (st) return st;
+        *n_accepted = k + 1;
+    }
+    return TKF_OK;
+}
+
+int tkf_wait_all(tkf_server *sv, const uint64_t *tickets, int32_t n, tkf_result *results, int64_t timeout_us)
+{
+    if (!sv || n < 0 || (n > 0 && (!tickets || !results))) return TKF_ERR_INVALID;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(std::max<int64_t>(timeout_us, 0));
+    for (int32_t k = 0; k < n; ++k) {
+        const int64_t left = std::chrono::duration_cast<std::chrono::microseconds>(
+                                 deadline - std::chrono::steady_clock::now()).count();
+        const int st = tkf_poll(sv, tickets[k], &results[k], timeout_us == 0 ? 0 : std::max<int64_t>(left, 1));
+        if (st) return st;
+    }
+    return TKF_OK;
+}
+
+int tkf_release_many(tkf_server *sv, const uint64_t *tickets, int32_t n)
+{
+    if (!sv || n < 0 || (n > 0 && !tickets)) return TKF_ERR_INVALID;
+    int first = TKF_OK;
+    for (int32_t k = 0; k < n; ++k) {
+        const int st = tkf_release(sv, tickets[k]);
+        if (st && !first) first = st;
+    }
+    return first;
+}
+
 int tkf_server_get_stats(tkf_server *sv, tkf_server_stats *out)
 {
     if (!sv || !out) return TKF_ERR_INVALID;

@@ -139,6 +139,9 @@ def lib():
         L.tkf_poll.argtypes = [vp, C.c_uint64, C.POINTER(Result), C.c_int64]
         L.tkf_release.argtypes = [vp, C.c_uint64]
         L.tkf_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+        L.tkf_submit_events.argtypes = [vp, C.POINTER(Event), i32, C.POINTER(C.c_uint64), C.POINTER(i32)]
+        L.tkf_wait_all.argtypes = [vp, C.POINTER(C.c_uint64), i32, C.POINTER(Result), C.c_int64]
+        L.tkf_release_many.argtypes = [vp, C.POINTER(C.c_uint64), i32]
         L.tkf_build_hit_index_noalloc.argtypes = [C.POINTER(Config), C.POINTER(Hits), C.POINTER(HitIndexOut), vp]
         for name in declared_functions():
             if name not in ("tkf_last_error", "tkf_status_string", "tkf_default_config", "tkf_pipeline_index",
@@ -464,6 +467,26 @@ class Server:
         return code, t.value
 
     try_submit = submit
+
+    def submit_many(self, events):
+        """Submits a ctypes array of Event structs; returns (status, tickets accepted)."""
+        n = len(events)
+        tickets = (C.c_uint64 * n)()
+        acc = C.c_int32()
+        code = lib().tkf_submit_events(self.handle, events, n, tickets, C.byref(acc))
+        return code, list(tickets[:acc.value])
+
+    def wait_all(self, tickets, timeout_us=60_000_000):
+        """Waits for every ticket; returns (status, ctypes array of Result structs)."""
+        n = len(tickets)
+        t = (C.c_uint64 * n)(*tickets)
+        res = (Result * n)()
+        code = lib().tkf_wait_all(self.handle, t, n, res, int(timeout_us))
+        return code, res
+
+    def release_many(self, tickets):
+        n = len(tickets)
+        return lib().tkf_release_many(self.handle, (C.c_uint64 * n)(*tickets), n)
 
     def submit_struct(self, ev, retry_us=20):
         """Submits, waiting while the queue is full; returns the ticket, raises on errors."""

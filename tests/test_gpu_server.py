@@ -153,3 +153,27 @@ def test_unreleased_results_hold_back_new_batches():
         sv.release(t)
     assert sv.stats()["events_done"] == len(evs)
     sv.close()
+
+
+def test_batch_submit_wait_release_match_single_calls():
+    import ctypes as C
+    b, evs = _events(75, n_events=8)
+    sv = tkf.Server(n_slots=2, max_batch_events=4, max_batch_hits=1 << 20, max_batch_tracks=1 << 16)
+    single = []
+    for ev in evs:
+        code, t = sv.submit(ev)
+        single.append(_wait(sv, t))
+        sv.release(t)
+    arr = (tkf.Event * len(evs))(*[ev.struct for ev in evs])
+    code, tickets = sv.submit_many(arr)
+    assert code == tkf.OK and len(tickets) == len(evs)
+    code, res = sv.wait_all(tickets, timeout_us=10_000_000)
+    assert code == tkf.OK
+    for r, ref in zip(res, single):
+        assert r.status == tkf.OK and r.n_tracks == ref["n_tracks"]
+        n, st = r.n_tracks, r.stride
+        par = np.ctypeslib.as_array(C.cast(r.par, C.POINTER(C.c_float)), shape=(5 * st + n,))
+        assert np.array_equal(np.stack([par[k * st:k * st + n] for k in range(6)]), ref["par"])
+    assert sv.release_many(tickets) == tkf.OK
+    assert sv.release_many(tickets[:1]) == tkf.ERR_INVALID  # already released
+    sv.close()
