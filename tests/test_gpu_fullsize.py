@@ -1,0 +1,107 @@
+"""Parity at the full batched size, in the launch configuration bench.py times: the 640-event
+lognormal batch (2.6 M seeds, 35 M hits) through the graph-replayed pipeline with seed ordering
+and the autotuned work tile, compared with the oracle on a seeded sample of seeds (the oracle
+builds and fits them one event at a time), plus properties checked on every seed."""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from _gpu import chi2_violations, param_violations
+from synth import Detector
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1702_06359_gb300 import tkf  # noqa: E402
+
+N_SAMPLE_EVENTS, SEEDS_PER_EVENT = 48, 40
+
+
+@pytest.fixture(scope="module")
+def full_batch():
+    import bench
+    with mp.get_context("spawn").Pool(min(os.cpu_count() or 1, 16)) as pool:
+        b = bench.workload(3, 640, pool)
+    return b
+
+
+def test_full_batch_sampled_parity_and_properties(full_batch):
+    b = full_batch
+    det = Detector()
+    L = det.n_layers
+    dev = torch.device("cuda", 0)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(dev)
+    hits = tkf.DeviceHits(t(b.x, torch.float32), t(b.y, torch.float32), t(b.z, torch.float32),
+                          t(b.var_u, torch.float32), t(b.var_v, torch.float32), t(b.layer, torch.int32),
+                          t(b.hit_off, torch.int32))
+    sh, se = t(b.trk_hits[:, :3].T, torch.int32), t(b.trk_event, torch.int32)
+    n = b.n_tracks
+    ctx = tkf.Context(tkf.default_config(seed_order=1, seeds_per_block=5))
+    pipe = tkf.DevicePipeline(ctx, b.n_hits, b.n_events, n, use_graph=True)
+    for _ in range(2):  # capture, then a replay
+        pipe.run(hits, sh, se, n)
+    ctx.sync_status()
+    assert pipe.captures() == 1
+    _, built, fitted = pipe.outputs()
+    bt, ft = tkf.tracks_tensors(built, L), tkf.tracks_tensors(fitted, L)
+    hid = bt["hit_idx"][:, :n].T.cpu().numpy()
+    bnh = bt["nhits"][:n].cpu().numpy()
+    par = ft["par"][:, :n].double().T.cpu().numpy()
+    chi2 = ft["chi2"][:n].double().cpu().numpy()
+    fnh = ft["nhits"][:n].cpu().numpy()
+    cov_diag = ft["cov"][[0, 2, 5, 9, 14, 20], :n].double().cpu().numpy()
+
+    # properties of every seed
+    ev = b.trk_event
+    lo, hi = b.hit_off[ev], b.hit_off[ev + 1]
+    ok = (hid < 0) | ((hid >= lo[:, None]) & (hid < hi[:, None]))
+    assert ok.all(), "a hit id outside its seed's event"
+    assert np.array_equal(hid[:, :3], b.trk_hits[:, :3]), "seed hits must stay on layers 0-2"
+    live = bnh >= 0
+    assert live.mean() > 0.999
+    assert np.array_equal((hid[live] >= 0).sum(1), bnh[live]), "nhits counts the built hits"
+    assert np.all(chi2[live] >= 0) and np.all(cov_diag[:, live] > 0)
+    layers = np.where(hid >= 0, b.layer[np.maximum(hid, 0)], -1)
+    assert np.all((hid < 0) | (layers == np.arange(L)[None, :])), "hit of layer l in slot l"
+
+    # sampled seeds against the oracle, one event at a time
+    g = O.make_geom(det)
+    rng = np.random.default_rng(1702)
+    events = np.sort(rng.choice(b.n_events, N_SAMPLE_EVENTS, replace=False))
+    n_cmp = n_div = 0
+    for e in events:
+        h0, h1, t0, t1 = b.hit_off[e], b.hit_off[e + 1], b.trk_off[e], b.trk_off[e + 1]
+        if t1 == t0:
+            continue
+        s = np.sort(rng.choice(np.arange(t0, t1), min(SEEDS_PER_EVENT, t1 - t0), replace=False))
+        oh = O.hits_of(b, slice(h0, h1))
+        local = b.trk_hits[s] - h0
+        p0, c0 = O.seed_estimate(g, oh, local[:, :3])
+        ids = np.full((len(s), L), -1, dtype=np.int32)
+        ids[:, :3] = local[:, :3]
+        sp, sP, sc2, snh, _ = O.fit(g, oh, p0, c0, ids, 0, 2)
+        res = O.build(g, O.hit_index(g, oh), sp, sP, sc2, snh, ids)
+        rh = res.hits[:, 0, :]
+        gh = np.where(hid[s] >= 0, hid[s] - h0, -1)
+        lost = res.n_cand == 0
+        assert np.all(bnh[s[lost]] == tkf.TRACK_LOST)
+        same = np.all(gh == rh, axis=1) & ~lost
+        for k in np.nonzero(~same & ~lost)[0]:
+            d = int(np.argmax(gh[k] != rh[k]))
+            assert d >= res.fragile[k], ("hit list differs before any fragile decision", e, s[k], d)
+            n_div += 1
+        m = np.nonzero(same)[0]
+        fpar, fcov, fchi2, fn, _ = O.fit(g, oh, p0[m], c0[m], rh[m], 0, L - 1)
+        assert not param_violations(par[s[m]], fpar)[0].any()
+        assert not chi2_violations(chi2[s[m]], fchi2)[0].any()
+        assert np.array_equal(fnh[s[m]], fn)
+        n_cmp += len(s)
+    assert n_cmp > 1000 and n_div <= 0.05 * n_cmp, (n_cmp, n_div)
+    pipe.close()
+    ctx.close()
