@@ -111,3 +111,31 @@ def test_results_do_not_depend_on_the_work_tile():
         assert torch.equal(gb["hit_idx"], ref_b["hit_idx"]) and torch.equal(gb["par"], ref_b["par"]), tile
         assert torch.equal(gf["par"], ref_f["par"]), tile
         p2.close()
+
+
+@pytest.mark.parametrize("prec", [tkf.MIXED, tkf.FP64], ids=["mixed", "fp64"])
+def test_graph_replay_equals_direct_calls_other_precisions(prec):
+    b = _batch(64, n_events=6)
+    ctx = tkf.Context(tkf.default_config(precision=prec))
+    L, n = ctx.cfg.n_layers, b.n_tracks
+    dh = device_hits(b)
+    sh = torch.as_tensor(np.ascontiguousarray(b.trk_hits[:, :3].T), dtype=torch.int32, device="cuda")
+    se = torch.as_tensor(b.trk_event, dtype=torch.int32, device="cuda")
+    pipe = tkf.DevicePipeline(ctx, b.n_hits, b.n_events, n, use_graph=True)
+    for _ in range(2):
+        pipe.run(dh, sh, se, n)
+    ctx.sync_status()
+    assert pipe.captures() == 1
+    _, built, fitted = pipe.outputs()
+    gb, gf = tkf.tracks_tensors(built, L, prec), tkf.tracks_tensors(fitted, L, prec)
+    init, seeds, db, df = (tkf.DeviceTracks.empty(n, L, prec) for _ in range(4))
+    idx = ctx.build_hit_index(dh)
+    ctx.seed_state(dh, sh, init)
+    ctx.fit(dh, init, 0, 2, seeds)
+    seeds.event = se
+    ctx.build_tracks(idx, seeds, db)
+    ctx.fit(dh, init, 0, L - 1, df, hit_idx=db.hit_idx)
+    ctx.sync_status()
+    assert torch.equal(gb["hit_idx"][:, :n], db.hit_idx[:, :n])
+    assert torch.equal(gf["par"][:, :n], df.par[:, :n]) and torch.equal(gf["cov"][:, :n], df.cov[:, :n])
+    pipe.close()

@@ -177,3 +177,27 @@ def test_batch_submit_wait_release_match_single_calls():
     assert sv.release_many(tickets) == tkf.OK
     assert sv.release_many(tickets[:1]) == tkf.ERR_INVALID  # already released
     sv.close()
+
+
+def test_mixed_precision_server_equals_mixed_pipeline():
+    b, evs = _events(76, n_events=3)
+    cfg = tkf.default_config(precision=tkf.MIXED)
+    sv = tkf.Server(cfg, n_slots=2, max_batch_events=4, max_batch_hits=1 << 20, max_batch_tracks=1 << 16)
+    tickets = [sv.submit(ev)[1] for ev in evs]
+    res = [_wait(sv, t) for t in tickets]
+    sv.release_many(tickets)
+    sv.close()
+    e = 1
+    h0, h1, t0, t1 = b.hit_off[e], b.hit_off[e + 1], b.trk_off[e], b.trk_off[e + 1]
+    ctx = tkf.Context(tkf.default_config(precision=tkf.MIXED))
+    dh = device_hits(b)
+    dh = tkf.DeviceHits(dh.x[h0:h1], dh.y[h0:h1], dh.z[h0:h1], dh.var_u[h0:h1], dh.var_v[h0:h1], dh.layer[h0:h1],
+                        torch.tensor([0, h1 - h0], dtype=torch.int32, device="cuda"))
+    sh = torch.as_tensor(np.ascontiguousarray((b.trk_hits[t0:t1, :3] - h0).T), dtype=torch.int32, device="cuda")
+    pipe = tkf.DevicePipeline(ctx, h1 - h0, 1, t1 - t0, use_graph=False)
+    pipe.run(dh, sh, torch.zeros(t1 - t0, dtype=torch.int32, device="cuda"), t1 - t0)
+    torch.cuda.synchronize()
+    _, built, fitted = pipe.outputs()
+    assert np.array_equal(tkf.tracks_tensors(fitted, 10)["par"].cpu().numpy()[:, :t1 - t0], res[e]["par"])
+    assert np.array_equal(tkf.tracks_tensors(built, 10)["hit_idx"].cpu().numpy()[:, :t1 - t0], res[e]["hit_idx"])
+    pipe.close()
