@@ -57,6 +57,11 @@ cudaError_t launch_build_fp32(const BuildArgs &a, int nmax, int grid, cudaStream
 cudaError_t launch_build_mixed(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
 cudaError_t launch_build_fp64(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
 
+// tkf_fit, and its continued form (continue_fit: `init` lies on layer first_layer - 1, as a
+// fit of the earlier layers leaves it; the fit propagates before its first update).
+int fit_tracks(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx, int32_t first_layer,
+               int32_t last_layer, tkf_tracks *out, tkf_stream stream, bool continue_fit);
+
 // Allocates (or grows) `*idx` so that batches of up to max_hits hits and max_events events
 // need no further allocation (used before capturing the pipeline into a CUDA graph).
 int hit_index_reserve(tkf_ctx *ctx, tkf_hit_index **idx, size_t max_hits, size_t max_events);

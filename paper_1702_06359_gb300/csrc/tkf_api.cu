@@ -654,8 +654,10 @@ __global__ void k_seed(const FitGeom g, const tkf_hits h, const int *seed_hits, 
 }
 
 template <class R, class U>
+// prop_first = 0: the input state lies on layer `first` (its first step is the update there);
+// 1: it lies on the layer before (the fit continues a fit of the earlier layers).
 __global__ void k_fit(const FitGeom g, const tkf_hits h, const tkf_tracks in, const int *hit_idx, int first, int last,
-                      tkf_tracks out, int *err)
+                      int prop_first, tkf_tracks out, int *err)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= in.n) return;
@@ -671,7 +673,7 @@ __global__ void k_fit(const FitGeom g, const tkf_hits h, const tkf_tracks in, co
     int status = nh < 0 ? nh : 0;
     const R kb = gpick<R>(g.kb_f, g.kb), mass = gpick<R>(g.mass_f, g.mass);
     for (int l = first; l <= last && status == 0; ++l) {
-        if (l > first && !propagate<R>(p, P, gpick<R>(g.radius_f[l], g.radius[l]), kb)) {
+        if ((l > first || prop_first) && !propagate<R>(p, P, gpick<R>(g.radius_f[l], g.radius[l]), kb)) {
             status = TKF_TRACK_NOREACH;
             break;
         }
@@ -1072,7 +1074,16 @@ int tkf_seed_state(tkf_ctx *ctx, const tkf_hits *hits, const int32_t *seed_hits,
 int tkf_fit(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx, int32_t first_layer,
             int32_t last_layer, tkf_tracks *out, tkf_stream stream)
 {
+    return tkf::fit_tracks(ctx, hits, init, hit_idx, first_layer, last_layer, out, stream, false);
+}
+
+}  // extern "C"
+
+int tkf::fit_tracks(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx,
+                    int32_t first_layer, int32_t last_layer, tkf_tracks *out, tkf_stream stream, bool continue_fit)
+{
     if (!ctx) return TKF_ERR_INVALID;
+    if (continue_fit && first_layer < 1) return set_err(ctx, TKF_ERR_INVALID, "a continued fit starts at layer >= 1");
     int st = check_hits(ctx, hits);
     if (st || (st = check_tracks(ctx, init, hit_idx == nullptr, "init")) || (st = check_tracks(ctx, out, false, "out")))
         return st;
@@ -1084,14 +1095,23 @@ int tkf_fit(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const in
     const FitGeom g = fit_geom(ctx);
     const int nb = (init->n + 127) / 128;
     cudaStream_t s = (cudaStream_t)stream;
+    const int pf = continue_fit ? 1 : 0;
     switch (ctx->cfg.precision) {
-    case TKF_FP32: k_fit<float, float><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, *out, ctx->d_err); break;
-    case TKF_MIXED: k_fit<float, double><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, *out, ctx->d_err); break;
-    default: k_fit<double, double><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, *out, ctx->d_err); break;
+    case TKF_FP32:
+        k_fit<float, float><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, pf, *out, ctx->d_err);
+        break;
+    case TKF_MIXED:
+        k_fit<float, double><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, pf, *out, ctx->d_err);
+        break;
+    default:
+        k_fit<double, double><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, pf, *out, ctx->d_err);
+        break;
     }
     TKF_CUDA(ctx, cudaGetLastError());
     return TKF_OK;
 }
+
+extern "C" {
 
 int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *seeds, tkf_tracks *out,
                      tkf_tracks *out_all, int32_t *n_cand_out, tkf_stream stream)

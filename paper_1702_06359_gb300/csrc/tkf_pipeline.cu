@@ -87,6 +87,7 @@ int fail(tkf_ctx *ctx, int code, const std::string &m)
 }
 
 // the step: index -> seed estimate -> seed fit (layers 0..first-1) -> build -> final fit
+// (layers first..L-1, continuing the seed fit)
 int issue(tkf_pipeline *p, const tkf_hits *hits, const int32_t *seed_hits, const int32_t *seed_event, int n,
           cudaStream_t s, bool capturing)
 {
@@ -106,7 +107,9 @@ int issue(tkf_pipeline *p, const tkf_hits *hits, const int32_t *seed_hits, const
     if ((st = tkf_build_tracks(ctx, p->idx, &seeds, &built, nullptr, nullptr, (tkf_stream)s))) return st;
     if (cudaEventRecordWithFlags(p->build_ev[1], s, flag) != cudaSuccess)
         return fail(ctx, TKF_ERR_CUDA, "pipeline: cudaEventRecord");
-    return tkf_fit(ctx, hits, &init, built.hit_idx, 0, L - 1, &fin, (tkf_stream)s);
+    // final fit of the built hit list: layers 0..first-1 carry the seed's hits, so the seed fit
+    // already holds its state there (bit for bit); the fit continues from it on layer first
+    return tkf::fit_tracks(ctx, hits, &seeds, built.hit_idx, first, L - 1, &fin, (tkf_stream)s, true);
 }
 
 }  // namespace
