@@ -1,0 +1,71 @@
+"""Host-side logic of bench.py (no GPU): the building-efficiency measure, the layout of events
+lent to the server, the balanced dealing of oracle events to host cores, and the sample
+selection."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import bench
+from synth import Detector, EventSpec, generate
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    return generate(EventSpec(seed=5, n_events=3, n_tracks=[40, 0, 25], noise_frac=0.3), Detector())
+
+
+def test_efficiency_counts_tracks_with_three_quarters_own_hits(small_batch):
+    b = small_batch
+    truth = b.trk_hits.T.copy()  # [L, n]: every track its own simulated hits
+    assert bench.efficiency(b, truth) == 1.0
+    noise = np.nonzero(b.mc < 0)[0]
+    bad = truth.copy()
+    bad[3:6, 0] = noise[:3]  # 3 of 10 hits of track 0 from noise: 70 % own
+    bad[3:5, 1] = noise[3:5]  # 2 of 10 for track 1: 80 % own
+    bad[:, 2] = -1
+    bad[:3, 2] = truth[:3, 2]  # only the seed hits: 100 % own
+    eff = bench.efficiency(b, bad)
+    assert eff == pytest.approx((b.n_tracks - 1) / b.n_tracks)
+
+
+def test_lent_events_point_into_the_batch_planes(small_batch):
+    torch = pytest.importorskip("torch")
+    from paper_1702_06359_gb300 import tkf
+    b = small_batch
+    host = {k: torch.as_tensor(np.ascontiguousarray(getattr(b, k)), dtype=torch.int32 if k == "layer" else torch.float32)
+            for k in ("x", "y", "z", "var_u", "var_v", "layer")}
+    lent = bench.LentEvents(tkf, b, host, 10)
+    assert len(lent.events) == b.n_events and len(lent.array) == b.n_events
+    for e, ev in enumerate(lent.events):
+        h0, h1, t0, t1 = b.hit_off[e], b.hit_off[e + 1], b.trk_off[e], b.trk_off[e + 1]
+        assert ev.n_hits == h1 - h0 and ev.n_seeds == t1 - t0 and ev.borrow == 1
+        if ev.n_hits:
+            z = np.ctypeslib.as_array(C.cast(ev.z, C.POINTER(C.c_float)), shape=(ev.n_hits,))
+            assert np.array_equal(z, b.z[h0:h1])
+        if ev.n_seeds:
+            sd = np.ctypeslib.as_array(C.cast(ev.seed_hits, C.POINTER(C.c_int32)), shape=(3 * ev.n_seeds,))
+            assert np.array_equal(sd.reshape(3, -1), (b.trk_hits[t0:t1, :3] - h0).T)
+    assert lent.h2d == b.n_hits * 24 + b.n_tracks * 12 + b.n_events * 8
+
+
+def test_oracle_events_are_dealt_largest_first_to_the_least_loaded_core():
+    class _Pool:
+        def map(self, fn, chunks, chunksize=1):
+            self.chunks = chunks
+            return [sum(len(ev[1]) for ev in c) for c in chunks]
+    sizes = [50, 10, 40, 30, 20, 5]
+    sample = [(None, np.zeros((n, 10))) for n in sizes]
+    pool = _Pool()
+    done, wall = bench.cpu_baseline(sample, pool, 2)
+    assert done == sum(sizes) and wall >= 0
+    loads = sorted(sum(len(ev[1]) for ev in c) for c in pool.chunks)
+    assert loads == [75, 80]  # 50+20+5 and 40+30+10
+
+
+def test_sample_events_cover_the_requested_tracks():
+    ev, n = bench.sample_events(3, 20000)
+    from synth import event_sizes
+    sizes, _ = event_sizes(3, 640)
+    assert ev == list(range(len(ev))) and n == int(sizes[:len(ev)].sum()) >= 20000
+    assert int(sizes[:len(ev) - 1].sum()) < 20000
