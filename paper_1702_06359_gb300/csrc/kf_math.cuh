@@ -316,12 +316,11 @@ __host__ __device__ __forceinline__ bool kalman_update(R pR[6], R PR[21], R xh_,
 {
     const R irR = R(1) / sq(xh_ * xh_ + yh_ * yh_);
     const R shR = yh_ * irR, chR = xh_ * irR;
-    const U u = U(chR * (yh_ - pR[1]) - shR * (xh_ - pR[0]));
-    const U v = U(zh_ - pR[2]);
+    const R uR = chR * (yh_ - pR[1]) - shR * (xh_ - pR[0]);
+    const R vR = zh_ - pR[2];
+    const U u = U(uR), v = U(vR);
     const U sh = U(shR), ch = U(chR);
-    U p[6], P[21];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) p[i] = U(pR[i]);
+    U P[21];
 #pragma unroll
     for (int k = 0; k < 21; ++k) P[k] = U(PR[k]);
     U B0[6], B1[6];
@@ -343,17 +342,24 @@ __host__ __device__ __forceinline__ bool kalman_update(R pR[6], R PR[21], R xh_,
     for (int i = 0; i < 6; ++i) {
         K0[i] = B0[i] * i00 + B1[i] * i01;
         K1[i] = B0[i] * i01 + B1[i] * i11;
-        D0[i] = B0[i] - (K0[i] * Suu + K1[i] * Suv);
-        D1[i] = B1[i] - (K0[i] * Suv + K1[i] * Svv);
+        D0[i] = fma(-K1[i], Suv, fma(-K0[i], Suu, B0[i]));
+        D1[i] = fma(-K1[i], Svv, fma(-K0[i], Suv, B1[i]));
     }
+    // state update in the state's type (the gain rounded to it)
 #pragma unroll
-    for (int i = 0; i < 6; ++i) pR[i] = R(p[i] + K0[i] * u + K1[i] * v);
+    for (int i = 0; i < 6; ++i) pR[i] = pR[i] + R(K0[i]) * uR + R(K1[i]) * vR;
     pR[4] = wrap_phi(pR[4]);
+    // Joseph form, element by element: P - (K B + D K^T) in one fused chain
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
-        for (int j = 0; j <= i; ++j)
-            PR[sym(i, j)] = R(P[sym(i, j)] - (K0[i] * B0[j] + K1[i] * B1[j]) - (D0[i] * K0[j] + D1[i] * K1[j]));
+        for (int j = 0; j <= i; ++j) {
+            U t = K0[i] * B0[j];
+            t = fma(K1[i], B1[j], t);
+            t = fma(D0[i], K0[j], t);
+            t = fma(D1[i], K1[j], t);
+            PR[sym(i, j)] = R(P[sym(i, j)] - t);
+        }
     return true;
 }
 
