@@ -51,9 +51,9 @@ FLOP_PER_SEED = (PER_SEED["n_prop"] * (FLOP_PROPAGATE + FLOP_WINDOW) + PER_SEED[
 # FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # libtkf.so kernels per step: hit index (event order, per-event count/scan/place, bin sort),
-# seed estimate, seed fit, seed ordering (key, segment totals, segment scan, bin scan, place),
-# build, final fit
-KERNELS_PER_STEP = 12
+# seed estimate with seed fit, seed ordering (key, segment totals, segment scan, bin scan,
+# place), build, final fit
+KERNELS_PER_STEP = 11
 # DRAM bytes (read + write) per seed of the FP32 building kernel, from one ncu capture of the
 # kernel as built now (160-event case: 408.4 MB for 701 095 seeds; summary in profiles/);
 # None whenever the kernel changes until it is captured again

@@ -62,6 +62,11 @@ cudaError_t launch_build_fp64(const BuildArgs &a, int nmax, int grid, cudaStream
 int fit_tracks(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx, int32_t first_layer,
                int32_t last_layer, tkf_tracks *out, tkf_stream stream, bool continue_fit);
 
+// tkf_seed_state followed by tkf_fit over layers 0..last_layer in one kernel (the estimate is not
+// stored): the seed fit of the batched pipeline.
+int seed_and_fit(tkf_ctx *ctx, const tkf_hits *hits, const int32_t *seed_hits, int32_t last_layer, tkf_tracks *out,
+                 tkf_stream stream);
+
 // Allocates (or grows) `*idx` so that batches of up to max_hits hits and max_events events
 // need no further allocation (used before capturing the pipeline into a CUDA graph).
 int hit_index_reserve(tkf_ctx *ctx, tkf_hit_index **idx, size_t max_hits, size_t max_events);

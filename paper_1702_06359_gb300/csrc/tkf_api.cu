@@ -613,16 +613,9 @@ template <class R> __device__ __forceinline__ R asin_over(R x)
 // (positive for a counter-clockwise turn), tangent at P1 = chord direction P1->P2 turned back by
 // half the subtended angle, transverse arc P1->P3 = chord * asin(k c/2)/(k c/2).
 template <class R>
-__global__ void k_seed(const FitGeom g, const tkf_hits h, const int *seed_hits, tkf_tracks out, int *err)
+__device__ __forceinline__ void seed_estimate(const FitGeom &g, const tkf_hits &h, int h1, int h2, int h3, R p[6],
+                                              R P[21])
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= out.n) return;
-    const int h1 = seed_hits[i], h2 = seed_hits[out.stride + i], h3 = seed_hits[2 * out.stride + i];
-    if (h1 < 0 || h2 < 0 || h3 < 0 || h1 >= h.n || h2 >= h.n || h3 >= h.n) {
-        atomicOr(err, kErrBadHitId);
-        out.nhits[i] = TKF_TRACK_SINGULAR;
-        return;
-    }
     const R x1 = h.x[h1], y1 = h.y[h1], z1 = h.z[h1];
     const R x2 = h.x[h2], y2 = h.y[h2];
     const R x3 = h.x[h3], y3 = h.y[h3], z3 = h.z[h3];
@@ -636,21 +629,89 @@ __global__ void k_seed(const FitGeom g, const tkf_hits h, const int *seed_hits, 
     const R s13 = d13 * asin_over(h13);
     const R cot = (z3 - z1) / s13;
     const R kb = gpick<R>(g.kb_f, g.kb);
+    p[0] = x1;
+    p[1] = y1;
+    p[2] = z1;
+    p[3] = -kappa / kb;
+    p[4] = wrap_phi(phi);
+    p[5] = at2(R(1), cot);
+#pragma unroll
+    for (int k = 0; k < 21; ++k) P[k] = R(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) P[sym(k, k)] = R(g.prior[k] * g.prior[k]);
+}
+
+template <class R>
+__global__ void k_seed(const FitGeom g, const tkf_hits h, const int *seed_hits, tkf_tracks out, int *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= out.n) return;
+    const int h1 = seed_hits[i], h2 = seed_hits[out.stride + i], h3 = seed_hits[2 * out.stride + i];
+    if (h1 < 0 || h2 < 0 || h3 < 0 || h1 >= h.n || h2 >= h.n || h3 >= h.n) {
+        atomicOr(err, kErrBadHitId);
+        out.nhits[i] = TKF_TRACK_SINGULAR;
+        return;
+    }
+    R p[6], P[21];
+    seed_estimate<R>(g, h, h1, h2, h3, p, P);
     R *par = (R *)out.par, *cov = (R *)out.cov;
     const size_t st = out.stride;
-    par[0 * st + i] = x1;
-    par[1 * st + i] = y1;
-    par[2 * st + i] = z1;
-    par[3 * st + i] = -kappa / kb;
-    par[4 * st + i] = wrap_phi(phi);
-    par[5 * st + i] = at2(R(1), cot);
-    for (int k = 0; k < 21; ++k) cov[k * st + i] = R(0);
-    for (int k = 0; k < 6; ++k) cov[sym(k, k) * st + i] = R(g.prior[k] * g.prior[k]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) par[k * st + i] = p[k];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) cov[k * st + i] = P[k];
     ((R *)out.chi2)[i] = R(0);
     out.nhits[i] = 0;
     if (out.hit_idx) {
         for (int l = 0; l < g.L; ++l) out.hit_idx[l * st + i] = l < 3 ? seed_hits[l * st + i] : -1;
     }
+}
+
+// The Kalman fit over layers first..last of a state in registers: propagate (on the first
+// layer only when prop_first: the state then lies on the layer before), update with the
+// layer's hit (hit_at(l), -1 = none) and add the layer's scattering (all but the outermost
+// layer of the detector).  status: 0, or the track status that stopped the fit.
+template <class R, class U, class HitAt>
+__device__ __forceinline__ void fit_layers(const FitGeom &g, const tkf_hits &h, HitAt hit_at, int first, int last,
+                                           bool prop_first, R p[6], R P[21], R &chi2, int &nh, int &status, int *err)
+{
+    const R kb = gpick<R>(g.kb_f, g.kb), mass = gpick<R>(g.mass_f, g.mass);
+    for (int l = first; l <= last && status == 0; ++l) {
+        if ((l > first || prop_first) && !propagate<R>(p, P, gpick<R>(g.radius_f[l], g.radius[l]), kb)) {
+            status = TKF_TRACK_NOREACH;
+            break;
+        }
+        const int hid = hit_at(l);
+        if (hid >= h.n) {
+            atomicOr(err, kErrBadHitId);
+            status = TKF_TRACK_SINGULAR;
+            break;
+        }
+        if (hid >= 0) {
+            U dc2;
+            if (!kalman_update<U, R>(p, P, R(h.x[hid]), R(h.y[hid]), R(h.z[hid]), R(h.var_u[hid]), R(h.var_v[hid]),
+                                     &dc2)) {
+                status = TKF_TRACK_SINGULAR;
+                break;
+            }
+            chi2 += R(dc2);
+            nh += 1;
+        }
+        if (l < g.L - 1) scatter<R>(p, P, gpick<R>(g.xx0_f[l], g.xx0[l]), mass);
+    }
+}
+
+template <class R> __device__ __forceinline__ void store_fit(const tkf_tracks &out, int i, const R p[6], const R P[21],
+                                                             R chi2, int nhits)
+{
+    R *op = (R *)out.par, *oc = (R *)out.cov;
+    const size_t so = out.stride;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) op[k * so + i] = p[k];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) oc[k * so + i] = P[k];
+    ((R *)out.chi2)[i] = chi2;
+    out.nhits[i] = nhits;
 }
 
 template <class R, class U>
@@ -671,39 +732,40 @@ __global__ void k_fit(const FitGeom g, const tkf_hits h, const tkf_tracks in, co
     R chi2 = ((const R *)in.chi2)[i];
     int nh = in.nhits[i];
     int status = nh < 0 ? nh : 0;
-    const R kb = gpick<R>(g.kb_f, g.kb), mass = gpick<R>(g.mass_f, g.mass);
-    for (int l = first; l <= last && status == 0; ++l) {
-        if ((l > first || prop_first) && !propagate<R>(p, P, gpick<R>(g.radius_f[l], g.radius[l]), kb)) {
-            status = TKF_TRACK_NOREACH;
-            break;
-        }
-        const int hid = hit_idx[l * si + i];
-        if (hid >= h.n) {
-            atomicOr(err, kErrBadHitId);
-            status = TKF_TRACK_SINGULAR;
-            break;
-        }
-        if (hid >= 0) {
-            U dc2;
-            if (!kalman_update<U, R>(p, P, R(h.x[hid]), R(h.y[hid]), R(h.z[hid]), R(h.var_u[hid]), R(h.var_v[hid]),
-                                     &dc2)) {
-                status = TKF_TRACK_SINGULAR;
-                break;
-            }
-            chi2 += R(dc2);
-            nh += 1;
-        }
-        if (l < g.L - 1) scatter<R>(p, P, gpick<R>(g.xx0_f[l], g.xx0[l]), mass);
-    }
-    R *op = (R *)out.par, *oc = (R *)out.cov;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) op[k * so + i] = p[k];
-#pragma unroll
-    for (int k = 0; k < 21; ++k) oc[k * so + i] = P[k];
-    ((R *)out.chi2)[i] = chi2;
-    out.nhits[i] = status ? status : nh;
+    fit_layers<R, U>(
+        g, h, [&](int l) { return hit_idx[l * si + i]; }, first, last, prop_first != 0, p, P, chi2, nh, status, err);
+    store_fit<R>(out, i, p, P, chi2, status ? status : nh);
     if (out.hit_idx && out.hit_idx != hit_idx)
         for (int l = 0; l < g.L; ++l) out.hit_idx[l * so + i] = hit_idx[l * si + i];
+}
+
+// Seed estimate and its fit over layers 0..last in one pass (the first two steps of the
+// batched pipeline): the same values as k_seed followed by k_fit, without storing the estimate.
+template <class R, class U>
+__global__ void k_seed_fit(const FitGeom g, const tkf_hits h, const int *seed_hits, int last, tkf_tracks out, int *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= out.n) return;
+    const size_t st = out.stride;
+    const int h1 = seed_hits[i], h2 = seed_hits[st + i], h3 = seed_hits[2 * st + i];
+    R p[6], P[21], chi2 = R(0);
+    int nh = 0, status = 0;
+    if (h1 < 0 || h2 < 0 || h3 < 0 || h1 >= h.n || h2 >= h.n || h3 >= h.n) {
+        atomicOr(err, kErrBadHitId);
+        status = TKF_TRACK_SINGULAR;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) p[k] = R(0);
+#pragma unroll
+        for (int k = 0; k < 21; ++k) P[k] = R(0);
+    } else {
+        seed_estimate<R>(g, h, h1, h2, h3, p, P);
+        fit_layers<R, U>(
+            g, h, [&](int l) { return l < 3 ? seed_hits[l * st + i] : -1; }, 0, last, false, p, P, chi2, nh, status,
+            err);
+    }
+    store_fit<R>(out, i, p, P, chi2, status ? status : nh);
+    if (out.hit_idx)
+        for (int l = 0; l < g.L; ++l) out.hit_idx[l * st + i] = l < 3 ? seed_hits[l * st + i] : -1;
 }
 
 FitGeom fit_geom(const tkf_ctx *ctx)
@@ -1077,6 +1139,18 @@ int tkf_fit(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const in
     return tkf::fit_tracks(ctx, hits, init, hit_idx, first_layer, last_layer, out, stream, false);
 }
 
+int tkf_fit_continue(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx,
+                     int32_t first_layer, int32_t last_layer, tkf_tracks *out, tkf_stream stream)
+{
+    return tkf::fit_tracks(ctx, hits, init, hit_idx, first_layer, last_layer, out, stream, true);
+}
+
+int tkf_seed_fit(tkf_ctx *ctx, const tkf_hits *hits, const int32_t *seed_hits, int32_t last_layer, tkf_tracks *out,
+                 tkf_stream stream)
+{
+    return tkf::seed_and_fit(ctx, hits, seed_hits, last_layer, out, stream);
+}
+
 }  // extern "C"
 
 int tkf::fit_tracks(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx,
@@ -1106,6 +1180,28 @@ int tkf::fit_tracks(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, 
     default:
         k_fit<double, double><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, pf, *out, ctx->d_err);
         break;
+    }
+    TKF_CUDA(ctx, cudaGetLastError());
+    return TKF_OK;
+}
+
+int tkf::seed_and_fit(tkf_ctx *ctx, const tkf_hits *hits, const int32_t *seed_hits, int32_t last_layer,
+                      tkf_tracks *out, tkf_stream stream)
+{
+    if (!ctx) return TKF_ERR_INVALID;
+    int st = check_hits(ctx, hits);
+    if (st || (st = check_tracks(ctx, out, false, "out"))) return st;
+    if (out->n > 0 && !seed_hits) return set_err(ctx, TKF_ERR_INVALID, "seed_hits is null");
+    if (last_layer < 0 || last_layer >= ctx->cfg.n_layers)
+        return set_err(ctx, TKF_ERR_INVALID, "need 0 <= last_layer < n_layers");
+    if (out->n == 0) return TKF_OK;
+    const FitGeom g = fit_geom(ctx);
+    const int nb = (out->n + 127) / 128;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (ctx->cfg.precision) {
+    case TKF_FP32: k_seed_fit<float, float><<<nb, 128, 0, s>>>(g, *hits, seed_hits, last_layer, *out, ctx->d_err); break;
+    case TKF_MIXED: k_seed_fit<float, double><<<nb, 128, 0, s>>>(g, *hits, seed_hits, last_layer, *out, ctx->d_err); break;
+    default: k_seed_fit<double, double><<<nb, 128, 0, s>>>(g, *hits, seed_hits, last_layer, *out, ctx->d_err); break;
     }
     TKF_CUDA(ctx, cudaGetLastError());
     return TKF_OK;

@@ -67,7 +67,7 @@ struct tkf_pipeline {
     tkf_ctx *ctx = nullptr;
     int max_hits = 0, max_events = 0, max_tracks = 0, use_graph = 1;
     tkf_hit_index *idx = nullptr;
-    Buf init, seeds, built, final_;
+    Buf seeds, built, final_;
     cudaStream_t capture = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -86,8 +86,8 @@ int fail(tkf_ctx *ctx, int code, const std::string &m)
     return code;
 }
 
-// the step: index -> seed estimate -> seed fit (layers 0..first-1) -> build -> final fit
-// (layers first..L-1, continuing the seed fit)
+// the step: index -> seed estimate and seed fit (layers 0..first-1, one kernel) -> build ->
+// final fit (layers first..L-1, continuing the seed fit)
 int issue(tkf_pipeline *p, const tkf_hits *hits, const int32_t *seed_hits, const int32_t *seed_event, int n,
           cudaStream_t s, bool capturing)
 {
@@ -95,11 +95,10 @@ int issue(tkf_pipeline *p, const tkf_hits *hits, const int32_t *seed_hits, const
     const int L = ctx->cfg.n_layers, first = ctx->cfg.first_build_layer, stride = p->max_tracks;
     int st = tkf_build_hit_index(ctx, hits, &p->idx, (tkf_stream)s);
     if (st) return st;
-    tkf_tracks init = view(p->init, n, stride), seeds = view(p->seeds, n, stride), built = view(p->built, n, stride),
+    tkf_tracks seeds = view(p->seeds, n, stride), built = view(p->built, n, stride),
                fin = view(p->final_, n, stride);
     seeds.event = const_cast<int32_t *>(seed_event);
-    if ((st = tkf_seed_state(ctx, hits, seed_hits, &init, (tkf_stream)s))) return st;
-    if ((st = tkf_fit(ctx, hits, &init, nullptr, 0, first - 1, &seeds, (tkf_stream)s))) return st;
+    if ((st = tkf::seed_and_fit(ctx, hits, seed_hits, first - 1, &seeds, (tkf_stream)s))) return st;
     // events around the building kernel (event-record nodes when captured into the graph)
     const unsigned flag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (cudaEventRecordWithFlags(p->build_ev[0], s, flag) != cudaSuccess)
@@ -131,7 +130,7 @@ int tkf_pipeline_create(tkf_ctx *ctx, int32_t max_hits, int32_t max_events, int3
     const int L = ctx->cfg.n_layers;
     const size_t es = ctx->cfg.precision == TKF_FP64 ? sizeof(double) : sizeof(float);
     cudaError_t e = cudaSuccess;
-    for (Buf *b : {&p->init, &p->seeds, &p->built, &p->final_})
+    for (Buf *b : {&p->seeds, &p->built, &p->final_})
         if (e == cudaSuccess) e = alloc_buf(*b, max_tracks, L, es);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&p->build_ev[0]);
@@ -156,7 +155,7 @@ int tkf_pipeline_destroy(tkf_pipeline *p)
     for (cudaEvent_t ev : p->build_ev)
         if (ev) cudaEventDestroy(ev);
     if (p->idx) tkf_hit_index_free(p->idx);
-    for (Buf *b : {&p->init, &p->seeds, &p->built, &p->final_}) free_buf(*b);
+    for (Buf *b : {&p->seeds, &p->built, &p->final_}) free_buf(*b);
     delete p;
     return TKF_OK;
 }

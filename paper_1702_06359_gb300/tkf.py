@@ -122,6 +122,8 @@ def lib():
         L.tkf_hit_index_get_view.argtypes = [vp, C.POINTER(HitIndexView)]
         L.tkf_seed_state.argtypes = [vp, C.POINTER(Hits), vp, C.POINTER(Tracks), vp]
         L.tkf_fit.argtypes = [vp, C.POINTER(Hits), C.POINTER(Tracks), vp, i32, i32, C.POINTER(Tracks), vp]
+        L.tkf_fit_continue.argtypes = [vp, C.POINTER(Hits), C.POINTER(Tracks), vp, i32, i32, C.POINTER(Tracks), vp]
+        L.tkf_seed_fit.argtypes = [vp, C.POINTER(Hits), vp, i32, C.POINTER(Tracks), vp]
         L.tkf_build_tracks.argtypes = [vp, vp, C.POINTER(Tracks), C.POINTER(Tracks), C.POINTER(Tracks), vp, vp]
         L.tkf_sync_status.argtypes = [vp, vp]
         L.tkf_pipeline_create.argtypes = [vp, i32, i32, i32, i32, C.POINTER(vp)]
@@ -303,10 +305,18 @@ class Context:
         hs, ts = hits.struct(), out.struct()
         self._check(lib().tkf_seed_state(self.handle, C.byref(hs), _ptr(seed_hits), C.byref(ts), _stream(stream)))
 
-    def fit(self, hits: DeviceHits, init: DeviceTracks, first, last, out: DeviceTracks, hit_idx=None, stream=None):
+    def fit(self, hits: DeviceHits, init: DeviceTracks, first, last, out: DeviceTracks, hit_idx=None, stream=None,
+            continue_fit=False):
+        """tkf_fit; continue_fit: tkf_fit_continue (init lies on layer first - 1)."""
         hs, ti, to = hits.struct(), init.struct(), out.struct()
-        self._check(lib().tkf_fit(self.handle, C.byref(hs), C.byref(ti), _ptr(hit_idx), int(first), int(last),
-                                  C.byref(to), _stream(stream)))
+        fn = lib().tkf_fit_continue if continue_fit else lib().tkf_fit
+        self._check(fn(self.handle, C.byref(hs), C.byref(ti), _ptr(hit_idx), int(first), int(last), C.byref(to),
+                       _stream(stream)))
+
+    def seed_fit(self, hits: DeviceHits, seed_hits, last, out: DeviceTracks, stream=None):
+        hs, to = hits.struct(), out.struct()
+        self._check(lib().tkf_seed_fit(self.handle, C.byref(hs), _ptr(seed_hits), int(last), C.byref(to),
+                                       _stream(stream)))
 
     def build_tracks(self, index: HitIndex, seeds: DeviceTracks, out: DeviceTracks, out_all: DeviceTracks = None,
                      n_cand_out=None, stream=None):

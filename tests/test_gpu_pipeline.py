@@ -22,19 +22,17 @@ def _batch(seed, n_events=8):
 
 
 def _direct(ctx, b, dh, sh, se):
+    """The pipeline's step as separate C-ABI calls."""
     L = ctx.cfg.n_layers
     n = b.n_tracks
-    init = tkf.DeviceTracks.empty(n, L)
     seeds = tkf.DeviceTracks.empty(n, L)
     built = tkf.DeviceTracks.empty(n, L)
     final = tkf.DeviceTracks.empty(n, L)
-    seeds.event = se
     idx = ctx.build_hit_index(dh)
-    ctx.seed_state(dh, sh, init)
-    ctx.fit(dh, init, 0, 2, seeds)
+    ctx.seed_fit(dh, sh, 2, seeds)
     seeds.event = se
     ctx.build_tracks(idx, seeds, built)
-    ctx.fit(dh, init, 0, L - 1, final, hit_idx=built.hit_idx)
+    ctx.fit(dh, seeds, 3, L - 1, final, hit_idx=built.hit_idx, continue_fit=True)
     ctx.sync_status()
     return built, final
 
@@ -128,14 +126,43 @@ def test_graph_replay_equals_direct_calls_other_precisions(prec):
     assert pipe.captures() == 1
     _, built, fitted = pipe.outputs()
     gb, gf = tkf.tracks_tensors(built, L, prec), tkf.tracks_tensors(fitted, L, prec)
-    init, seeds, db, df = (tkf.DeviceTracks.empty(n, L, prec) for _ in range(4))
+    seeds, db, df = (tkf.DeviceTracks.empty(n, L, prec) for _ in range(3))
     idx = ctx.build_hit_index(dh)
-    ctx.seed_state(dh, sh, init)
-    ctx.fit(dh, init, 0, 2, seeds)
+    ctx.seed_fit(dh, sh, 2, seeds)
     seeds.event = se
     ctx.build_tracks(idx, seeds, db)
-    ctx.fit(dh, init, 0, L - 1, df, hit_idx=db.hit_idx)
+    ctx.fit(dh, seeds, 3, L - 1, df, hit_idx=db.hit_idx, continue_fit=True)
     ctx.sync_status()
     assert torch.equal(gb["hit_idx"][:, :n], db.hit_idx[:, :n])
     assert torch.equal(gf["par"][:, :n], df.par[:, :n]) and torch.equal(gf["cov"][:, :n], df.cov[:, :n])
     pipe.close()
+
+
+@pytest.mark.parametrize("prec", [tkf.FP32, tkf.FP64], ids=["fp32", "fp64"])
+def test_seed_fit_and_continued_fit_agree_with_the_separate_calls(prec):
+    """tkf_seed_fit equals tkf_seed_state + tkf_fit, and a fit continued over layers 3..9 from
+    the seed fit equals one fit over 0..9, within rounding of the fused arithmetic (bit for
+    bit is not promised: the compiler may fuse multiply-adds differently in the two kernels)."""
+    from _gpu import PAR_FLOOR
+    b = _batch(65, n_events=4)
+    ctx = tkf.Context(tkf.default_config(precision=prec))
+    L, n = ctx.cfg.n_layers, b.n_tracks
+    dh = device_hits(b)
+    sh = torch.as_tensor(np.ascontiguousarray(b.trk_hits[:, :3].T), dtype=torch.int32, device="cuda")
+    hid = torch.as_tensor(np.ascontiguousarray(b.trk_hits.T), dtype=torch.int32, device="cuda")
+    init, sep, fused, full, cont = (tkf.DeviceTracks.empty(n, L, prec) for _ in range(5))
+    ctx.seed_state(dh, sh, init)
+    ctx.fit(dh, init, 0, 2, sep)
+    ctx.seed_fit(dh, sh, 2, fused)
+    ctx.fit(dh, init, 0, L - 1, full, hit_idx=hid)
+    ctx.fit(dh, fused, 3, L - 1, cont, hit_idx=hid, continue_fit=True)
+    ctx.sync_status()
+    rel = 1e-5 if prec == tkf.FP32 else 1e-12
+    floor = torch.as_tensor(PAR_FLOOR, device="cuda", dtype=sep.par.dtype)[:, None]
+    for a_, b_ in ((sep, fused), (full, cont)):
+        assert torch.equal(a_.nhits, b_.nhits)
+        d = (a_.par - b_.par).abs() / torch.maximum(a_.par.abs(), floor)
+        d[4] = torch.remainder(d[4] + np.pi, 2 * np.pi) - np.pi
+        assert float(d.abs().max()) < rel
+        assert float(((a_.chi2 - b_.chi2).abs() / torch.clamp(a_.chi2.abs(), min=1.0)).max()) < 10 * rel
+    assert torch.equal(fused.hit_idx[:3], sh) and bool((fused.hit_idx[3:] == -1).all())
