@@ -166,6 +166,7 @@ __device__ __forceinline__ void scan_window(const BuildArgs &a, int ev, int l, R
             const int i1 = ob + sub_end(wb, ps1[part], ob1 - ob);
             for (int i = i0; i < i1; ++i) {
                 const float4 h = __ldg(&a.hxyzi[i]);
+                const float2 hv = __ldg(&a.hvar[i]);  // issued with the position: one round trip
                 const R hx = R(h.x), hy = R(h.y);
                 if (!(xp * hx + yp * hy > R(0))) continue;  // far half of the cylinder
                 // residual on the hit's tangent plane; |u| <= U and |v| <= W bound every hit
@@ -175,7 +176,6 @@ __device__ __forceinline__ void scan_window(const BuildArgs &a, int ev, int l, R
                 const R u = ch * (hy - yp) - sh * (hx - xp);
                 const R v = R(h.z) - zp;
                 if (ab(u) > U || ab(v) > W) continue;
-                const float2 hv = __ldg(&a.hvar[i]);
                 const R c2 = chi2_uv<R>(P, u, v, sh, ch, R(hv.x), R(hv.y));
                 if (c2 < cut) {
                     list_insert(list, make_key(nh + 1, to_f32(chi2 + c2), rank, __float_as_int(h.w)));
