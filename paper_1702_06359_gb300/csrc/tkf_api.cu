@@ -418,6 +418,15 @@ __global__ void __launch_bounds__(1024) k_event_order(const int *ev_off, int n_e
     }
 }
 
+// Folds a thread's running variance maxima of layer l (float bits of non-negative values, so
+// integer order is value order) into the block's maxima; l < 0: nothing held.
+__device__ __forceinline__ void var_flush(int *s_var, int l, int mu, int mv)
+{
+    if (l < 0) return;
+    atomicMax(&s_var[2 * l], mu);
+    atomicMax(&s_var[2 * l + 1], mv);
+}
+
 // The bins of one event in one block (one block per event, events taken in the order perm),
 // with the event's bin counters in shared memory: (1) count the hits per (layer, eta bin, phi
 // bin) and reduce the largest variances per layer; (2) exclusive scan of the counts ->
@@ -434,11 +443,10 @@ k_index_event(const IndexGeom g, const tkf_hits h, const int *perm, int n_bins_t
 {
     extern __shared__ int s_cnt[];  // [L * n_bins]: counts, then bin offsets / cursors
     __shared__ int s_var[2 * TKF_MAX_LAYERS];
-    __shared__ int s_wvar[kEventWarps][2 * TKF_MAX_LAYERS];
     __shared__ int s_part[kEventWarps];
     const unsigned full = 0xffffffffu;
     const int e = perm[blockIdx.x], tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if (lane < 2 * TKF_MAX_LAYERS) s_wvar[w][lane] = 0;
+    int cur_l = -1, mu = 0, mv = 0;  // this thread's layer and its largest variances (float bits)
     const int nb_ev = g.L * g.n_bins;
     const int h0 = h.event_off[e], h1 = h.event_off[e + 1];
     for (int k = tid; k < nb_ev; k += kEventThreads) s_cnt[k] = 0;
@@ -465,15 +473,23 @@ k_index_event(const IndexGeom g, const tkf_hits h, const int *perm, int n_bins_t
             const bool ok = in && l[u] >= 0 && l[u] < g.L;
             if (ok) {
                 atomicAdd(&s_cnt[l[u] * g.n_bins + hit_bin(g, l[u], x[u], y[u], z[u])], 1);
-                atomicMax(&s_wvar[w][2 * l[u]], __float_as_int(fmaxf(vu[u], 0.f)));
-                atomicMax(&s_wvar[w][2 * l[u] + 1], __float_as_int(fmaxf(vv[u], 0.f)));
+                if (l[u] != cur_l) {  // hits usually come grouped by layer: rare
+                    var_flush(s_var, cur_l, mu, mv);
+                    cur_l = l[u];
+                    mu = mv = 0;
+                }
+                mu = max(mu, __float_as_int(fmaxf(vu[u], 0.f)));
+                mv = max(mv, __float_as_int(fmaxf(vv[u], 0.f)));
             } else if (in) {
                 atomicOr(err, kErrBadLayer);
             }
         }
     }
-    __syncwarp();
-    if (lane < 2 * g.L) atomicMax(&s_var[lane], s_wvar[w][lane]);
+    {  // the last running maxima, one atomic per layer and warp
+        const unsigned grp = __match_any_sync(full, cur_l);
+        const int ru = __reduce_max_sync(grp, (unsigned)mu), rv = __reduce_max_sync(grp, (unsigned)mv);
+        if (lane == __ffs(grp) - 1) var_flush(s_var, cur_l, ru, rv);
+    }
     __syncthreads();
     // (2) exclusive scan: thread t owns the contiguous chunk [t * per, (t + 1) * per)
     const int per = (nb_ev + kEventThreads - 1) / kEventThreads;
@@ -539,7 +555,7 @@ k_index_event(const IndexGeom g, const tkf_hits h, const int *perm, int n_bins_t
 // Dynamic shared memory of k_index_event (the event's bin counters) allowed next to its
 // static arrays within one block's 227 KB; an index whose event bins need more takes the
 // multi-launch path.
-constexpr size_t kEventStaticSmem = (size_t)kEventWarps * 4 + 2 * TKF_MAX_LAYERS * 4 * (kEventWarps + 1);
+constexpr size_t kEventStaticSmem = (size_t)kEventWarps * 4 + 2 * TKF_MAX_LAYERS * 4;
 constexpr size_t kEventMaxDynSmem = 227 * 1024 - kEventStaticSmem - 1024;
 
 size_t index_event_smem(int n_layers, int n_bins)
