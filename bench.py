@@ -362,6 +362,8 @@ def main():
     ap.add_argument("--serve", type=int, default=1, help="1: also measure the served stream")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--mixed", type=int, default=1, help="1: also time the batched step in MIXED precision")
+    ap.add_argument("--backward", type=int, default=1,
+                    help="1: also time the backward pass of the final fit over the batch's fitted tracks")
     ap.add_argument("--tile", type=int, default=0, help="seeds per warp work tile (0: autotuned)")
     ap.add_argument("--e2e-batch", type=int, default=160, help="events per server batch in the e2e measurement")
     ap.add_argument("--e2e-slots", type=int, default=4, help="server slots in the e2e measurement")
@@ -485,6 +487,37 @@ def main():
     if dist:
         dist.barrier()
     total_tracks, ms_max, value = job_rate(n_tr, ms, dist, dev)
+
+    # ---------------- the backward pass of the final fit over every fitted track of the batch
+    backward = None
+    if a.backward:
+        _, built_t, fitted_t = pipe.outputs()
+        bhid = tkf.tracks_tensors(built_t, L)["hit_idx"]
+        back = tkf.DeviceTracks.empty(n_tr, L, device=dev)
+
+        def run_backward():
+            ctx.fit_backward(hits, _T(fitted_t), L - 1, 0, back, cov_scale=1e4, hit_idx=bhid, stream=stream)
+        for _ in range(max(3, a.warmup)):
+            run_backward()
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(a.steps):
+            run_backward()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        ctx.sync_status(stream)
+        bw_ms = b0.elapsed_time(b1) / a.steps
+        nh = back.nhits[:n_tr]
+        live = int((nh >= 0).sum())
+        bw_flop = (float(nh.clamp(min=0).sum()) * FLOP_UPDATE
+                   + live * ((L - 1) * FLOP_PROPAGATE + L * FLOP_SCATTER))
+        backward = {"ms": bw_ms, "tracks_per_s": n_tr / bw_ms * 1e3, "achieved_tflops": bw_flop / bw_ms / 1e9,
+                    "frac_fp32_peak": bw_flop / bw_ms / 1e9 / FP32_PEAK_TFLOPS, "kernel": "k_fit_backward<float,float>",
+                    "flop_per_track": bw_flop / max(live, 1),
+                    "form": "tkf_fit_backward over the pipeline's %d fitted tracks, layer 10 to layer 1, covariance "
+                            "scale 1e4, FP32; one launch per pass, CUDA events; inputs larger than L2" % n_tr}
+        del back
 
     # ---------------- end to end through host buffers
     _, built_t, fitted_t = pipe.outputs()
@@ -658,6 +691,7 @@ def main():
         "e2e": e2e,
         "e2e_pipeline": e2e_pipe,
         "mixed": mixed,
+        "backward_pass": backward,
         "plain": plain,
         "serve": serve,
         "autotune": {"grid": "seeds per warp tile x candidates per seed N (build launch ms)",

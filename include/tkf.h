@@ -185,6 +185,22 @@ int tkf_fit_continue(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init,
 int tkf_seed_fit(tkf_ctx *ctx, const tkf_hits *hits, const int32_t *seed_hits, int32_t last_layer, tkf_tracks *out,
                  tkf_stream stream);
 
+/* Backward pass of the final fit (Sec. 2: the final fit gives the best estimate of the track's
+ * parameters; this pass carries that estimate to the production point): an inward Kalman
+ * filter over each track's hits from layer last_layer down to first_layer.  `init` holds the
+ * states on layer last_layer (typically tkf_fit's output over 0..last_layer); their covariance
+ * is multiplied by cov_scale (> 0; a large factor such as 1e4 discounts the forward fit's
+ * information, so the pass is nearly an independent fit in the opposite direction).  Then, per
+ * layer from last_layer inward: the Kalman update with the layer's hit (hit_idx as for tkf_fit;
+ * -1 = none), the layer's scattering material, and the propagation to the next smaller
+ * cylinder (the outward propagation of the reversed track: same helix, opposite direction).
+ * `out` receives the states on first_layer after its update and material -- on layer 0, the
+ * track as it left the production region -- with this pass's chi2 and hit count (nhits < 0:
+ * enum tkf_track_status, also for inputs with nhits < 0).  hit_idx null: init->hit_idx.
+ * Errors: TKF_ERR_INVALID (also last_layer < first_layer, cov_scale not positive or finite). */
+int tkf_fit_backward(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx,
+                     int32_t last_layer, int32_t first_layer, double cov_scale, tkf_tracks *out, tkf_stream stream);
+
 /* Combinatorial track building (Sec. 2, Sec. 3.2): each seed (a state on layer
  * first_build_layer - 1, with chi2, nhits and the hit ids of the seeding layers) is extended
  * outward layer by layer: every candidate is propagated to the next cylinder, every hit of

@@ -108,6 +108,8 @@ def lib():
         L.orc_update.argtypes = [dp, dp, C.POINTER(Hit), dp]
         L.orc_seed_batch.argtypes = [C.POINTER(Geom), vp, C.c_int, ip, dp, dp]
         L.orc_fit_batch.argtypes = [C.POINTER(Geom), vp, C.c_int, dp, dp, ip, C.c_int, C.c_int, dp, dp, dp, ip, ip]
+        L.orc_fit_backward_batch.argtypes = [C.POINTER(Geom), vp, C.c_int, dp, dp, C.c_double, ip, C.c_int, C.c_int,
+                                             dp, dp, dp, ip, ip]
         L.orc_eta_bin.argtypes = [C.POINTER(Geom), C.c_int, C.c_double]
         L.orc_phi_bin.argtypes = [C.POINTER(Geom), C.c_double]
         L.orc_hit_index.argtypes = [C.POINTER(Geom), C.c_int, vp, ip, ip, ip]
@@ -213,6 +215,23 @@ def fit(g: Geom, hits: np.ndarray, par, cov, hit_ids, first, last):
     status = np.zeros(n, dtype=np.int32)
     lib().orc_fit_batch(C.byref(g), hits.ctypes.data, n, _d(par), _d(cov), _i(hit_ids), int(first), int(last),
                         _d(po), _d(co), _d(c2), _i(nh), _i(status))
+    return po, co.reshape(n, 6, 6), c2, nh, status
+
+
+def fit_backward(g: Geom, hits: np.ndarray, par, cov, hit_ids, last, first, cov_scale):
+    """Inward pass from layer `last` down to `first` (orc_fit_backward): par/cov are the states
+    on layer `last`; returns (par, cov, chi2, nhits, status) on layer `first`."""
+    par = np.ascontiguousarray(par, dtype=np.float64)
+    n = len(par)
+    cov = np.ascontiguousarray(cov, dtype=np.float64).reshape(n, 36)
+    hit_ids = np.ascontiguousarray(hit_ids, dtype=np.int32)
+    assert hit_ids.shape == (n, g.n_layers)
+    po, co = np.zeros((n, 6)), np.zeros((n, 36))
+    c2 = np.zeros(n)
+    nh = np.zeros(n, dtype=np.int32)
+    status = np.zeros(n, dtype=np.int32)
+    lib().orc_fit_backward_batch(C.byref(g), hits.ctypes.data, n, _d(par), _d(cov), float(cov_scale), _i(hit_ids),
+                                 int(last), int(first), _d(po), _d(co), _d(c2), _i(nh), _i(status))
     return po, co.reshape(n, 6, 6), c2, nh, status
 
 

@@ -368,6 +368,93 @@ int orc_fit_track(const orc_geom *g, const double pin[6], const double Pin[36], 
     return ORC_OK;
 }
 
+/* ------------------------------------------------------------------ backward pass (Sec. 2: final fit) */
+
+/*
+ * Inward Kalman filter over a track's hit list from layer `last` down to layer `first`
+ * (first <= last), refining the final fit's estimate towards the production point.  The state
+ * on layer `last` (typically the forward fit's result there) is taken with its covariance
+ * multiplied by cov_scale (>= 1: the forward information is mostly discounted, so the pass is
+ * nearly an independent fit in the opposite direction); then, layer by layer from `last` inward:
+ * the update with the layer's hit, the layer's material (the scattering kick that the forward
+ * fit adds on its way out of the layer), the propagation to the next smaller cylinder.  The
+ * result lies on layer `first` after its update and its material: the state on the track
+ * segment just inside that layer, which on layer 0 is the track as it left the production
+ * region (the generator's truth there, taken before the layer's kick); chi2 and nhits are the
+ * backward pass's own.
+ *
+ * Inward propagation is the outward propagation of the reversed track: the map
+ * (x, y, z, q/pT, phi, theta) -> (x, y, z, -q/pT, phi + pi, pi - theta) describes the same helix
+ * run backwards (transverse path s -> -s: the centre and radius of the track circle stay, the
+ * direction of motion flips), so the first crossing of the smaller cylinder along the reversed
+ * track is the previous crossing of the original one.  The map is its own inverse with the
+ * diagonal Jacobian D = diag(1, 1, 1, -1, 1, -1) (covariance D P D); the measurement depends on
+ * the position only, and the scattering noise of the reversed state is D Q D (its q/pT-theta
+ * term is odd in both), so the update and the scattering apply unchanged to the reversed state.
+ */
+static void reverse_track(const double a[6], double b[6])
+{
+    b[0] = a[0];
+    b[1] = a[1];
+    b[2] = a[2];
+    b[3] = -a[3];
+    b[4] = a[4] > 0.0 ? a[4] - ORC_PI : a[4] + ORC_PI;
+    b[5] = ORC_PI - a[5];
+}
+
+static void reverse_cov(const double A[36], double s, double B[36])
+{
+    static const double D[6] = {1.0, 1.0, 1.0, -1.0, 1.0, -1.0};
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) B[i * 6 + j] = s * D[i] * D[j] * A[i * 6 + j];
+}
+
+int orc_fit_backward(const orc_geom *g, const double pin[6], const double Pin[36], double cov_scale,
+                     const orc_hit *hits, const int *hit_of_layer, int last, int first, double pout[6],
+                     double Pout[36], double *chi2, int *nhits)
+{
+    double p[6], P[36], J[36], q[6], PJ[36];
+    if (first < 0 || last < first || last >= g->n_layers || !(cov_scale > 0.0)) return ORC_ERR_INVALID;
+    reverse_track(pin, p);
+    reverse_cov(Pin, cov_scale, P);
+    double c2 = 0.0;
+    int nh = 0;
+    for (int l = last; l >= first; --l) {
+        if (l < last) {
+            int st = orc_propagate(g, p, g->radius[l], q, J);
+            if (st != ORC_OK) return st;
+            sandwich6(J, P, PJ);
+            memcpy(p, q, sizeof p);
+            memcpy(P, PJ, sizeof P);
+        }
+        const int hid = hit_of_layer[l];
+        if (hid >= 0) {
+            double dc2;
+            int st = orc_update(p, P, &hits[hid], &dc2);
+            if (st != ORC_OK) return st;
+            c2 += dc2;
+            nh += 1;
+        }
+        orc_scatter(g, l, p, P);
+    }
+    reverse_track(p, pout);
+    reverse_cov(P, 1.0, Pout);
+    if (chi2) *chi2 = c2;
+    if (nhits) *nhits = nh;
+    return ORC_OK;
+}
+
+int orc_fit_backward_batch(const orc_geom *g, const orc_hit *hits, int n, const double *par_in,
+                           const double *cov_in, double cov_scale, const int *hit_ids, int last, int first,
+                           double *par_out, double *cov_out, double *chi2, int *nhits, int *status)
+{
+    for (int i = 0; i < n; ++i)
+        status[i] = orc_fit_backward(g, par_in + 6 * i, cov_in + 36 * i, cov_scale, hits,
+                                     hit_ids + g->n_layers * i, last, first, par_out + 6 * i, cov_out + 36 * i,
+                                     chi2 + i, nhits + i);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------ hit index (binning) */
 
 int orc_eta_bin(const orc_geom *g, int layer, double z)

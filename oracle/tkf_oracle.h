@@ -63,6 +63,10 @@ int orc_seed_estimate(const orc_geom *g, const orc_hit *h1, const orc_hit *h2, c
 int orc_fit_track(const orc_geom *g, const double pin[6], const double Pin[36], const orc_hit *hits,
                   const int *hit_of_layer, int first, int last, double pout[6], double Pout[36],
                   double *chi2, int *nhits);
+/* inward (backward) pass over layers last..first, first <= last; see tkf_oracle.c */
+int orc_fit_backward(const orc_geom *g, const double pin[6], const double Pin[36], double cov_scale,
+                     const orc_hit *hits, const int *hit_of_layer, int last, int first, double pout[6],
+                     double Pout[36], double *chi2, int *nhits);
 int orc_eta_bin(const orc_geom *g, int layer, double z);
 int orc_phi_bin(const orc_geom *g, double phi);
 int orc_hit_index(const orc_geom *g, int n, const orc_hit *hits, int *bin_of_hit, int *order, int *bin_off);
@@ -75,6 +79,9 @@ int orc_seed_batch(const orc_geom *g, const orc_hit *hits, int n, const int *see
 int orc_fit_batch(const orc_geom *g, const orc_hit *hits, int n, const double *par_in, const double *cov_in,
                   const int *hit_ids /*[n][n_layers]*/, int first, int last, double *par_out, double *cov_out,
                   double *chi2, int *nhits, int *status);
+int orc_fit_backward_batch(const orc_geom *g, const orc_hit *hits, int n, const double *par_in,
+                           const double *cov_in, double cov_scale, const int *hit_ids, int last, int first,
+                           double *par_out, double *cov_out, double *chi2, int *nhits, int *status);
 int orc_build_batch(const orc_geom *g, const orc_event *ev, int n, const double *sp, const double *sP,
                     const double *schi2, const int *snhits, const int *shits /*[n][n_layers]*/, int cap,
                     int *n_cand, double *par, double *cov, double *chi2, int *nhits, int *hits,

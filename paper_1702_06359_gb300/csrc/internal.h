@@ -67,6 +67,10 @@ int fit_tracks(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const
 int seed_and_fit(tkf_ctx *ctx, const tkf_hits *hits, const int32_t *seed_hits, int32_t last_layer, tkf_tracks *out,
                  tkf_stream stream);
 
+// tkf_fit_backward: the inward pass over layers last_layer..first_layer.
+int fit_backward(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx,
+                 int32_t last_layer, int32_t first_layer, double cov_scale, tkf_tracks *out, tkf_stream stream);
+
 // Allocates (or grows) `*idx` so that batches of up to max_hits hits and max_events events
 // need no further allocation (used before capturing the pipeline into a CUDA graph).
 int hit_index_reserve(tkf_ctx *ctx, tkf_hit_index **idx, size_t max_hits, size_t max_events);

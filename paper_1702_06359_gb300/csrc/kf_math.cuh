@@ -125,7 +125,15 @@ template <class R> __host__ __device__ __forceinline__ void helix_fn(R a, R &S, 
 // constraint r(s, p_in) = radius; P <- J P J^T uses its sparsity (rows of q/pT and theta are
 // unit rows, rows x, y, phi touch columns x, y, q/pT, phi only).
 // Returns false when the cylinder is not reached.
-template <class R> __host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R kb)
+//
+// kInward: the cylinder lies inside the state's radius (the backward pass runs the reversed
+// track outward-in).  The straight line then meets it twice ahead, and Newton starts from the
+// nearer root; when the tangent line misses the cylinder but the helix curves onto it, the start
+// is the exact crossing of the two circles: the track circle has centre c = p0 + (-sin phi,
+// cos phi)/k, and the position seen from c turns by k s, so s = (signed angle from p0 - c to
+// the crossing - c) / k, taken in (0, 2 pi/|k|].
+template <class R, bool kInward = false>
+__host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R kb)
 {
     const R x = p[0], y = p[1], z = p[2], w = p[3], phi = p[4], th = p[5];
     R sp, cp;
@@ -134,11 +142,39 @@ template <class R> __host__ __device__ __forceinline__ bool propagate(R p[6], R 
     const R A = x * cp + y * sp;
     const R r0 = sq(x * x + y * y);
     const R disc = A * A + (radius - r0) * (radius + r0);
-    if (!(disc >= R(0))) return false;
-    R s = -A + sq(disc);
-    R S, C, Sd, Cd;
+    R s;
+    if (!kInward) {
+        if (!(disc >= R(0))) return false;
+        s = -A + sq(disc);
+    } else if (disc >= R(0)) {
+        s = -A - sq(disc);
+    } else {
+        if (!(ab(kappa) > R(0))) return false;
+        const R ik = R(1) / kappa;
+        const R cx = x - sp * ik, cy = y + cp * ik;  // centre of the track circle
+        const R d2 = cx * cx + cy * cy, d = sq(d2);
+        const R a = (radius * radius - ik * ik + d2) / (R(2) * d);  // chord's distance from the origin
+        const R h2 = radius * radius - a * a;
+        if (!(h2 >= R(0)) || !(d > R(0))) return false;
+        const R h = sq(h2);
+        const R ux = x - cx, uy = y - cy;  // p0 - c
+        const R two_pi_rho = R(2.0 * kPi) * ab(ik);
+        s = R(-1);
 #pragma unroll
-    for (int it = 0; it < Lim<R>::newton; ++it) {
+        for (int k = 0; k < 2; ++k) {
+            const R sg = k ? R(-1) : R(1);
+            const R qx = (a * cx - sg * h * cy) / d - cx, qy = (a * cy + sg * h * cx) / d - cy;  // crossing - c
+            R sk = at2(ux * qy - uy * qx, ux * qx + uy * qy) * ik;
+            if (!(sk > R(0))) sk += two_pi_rho;
+            if (s < R(0) || sk < s) s = sk;
+        }
+    }
+    R S, C, Sd, Cd;
+    // inward starts can be far from the crossing (a grazing entry, the circle intersection's
+    // rounding): more steps
+    constexpr int n_newton = kInward ? 3 * Lim<R>::newton + 2 : Lim<R>::newton;
+#pragma unroll
+    for (int it = 0; it < n_newton; ++it) {
         const R a = kappa * s;
         helix_fn(a, S, C, Sd, Cd);
         const R sa = a * S, ca = R(1) - a * C;

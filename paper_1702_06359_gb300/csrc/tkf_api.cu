@@ -784,6 +784,77 @@ __global__ void k_seed_fit(const FitGeom g, const tkf_hits h, const int *seed_hi
         for (int l = 0; l < g.L; ++l) out.hit_idx[l * st + i] = l < 3 ? seed_hits[l * st + i] : -1;
 }
 
+// The reversed description of a track: (x, y, z, q/pT, phi, theta) -> (x, y, z, -q/pT, phi + pi,
+// pi - theta) is the same helix run backwards (transverse path s -> -s), so outward
+// propagation of the reversed state reaches the previous (inner) crossing.  The map is its own
+// inverse with Jacobian diag(1, 1, 1, -1, 1, -1): covariance elements pairing one of q/pT,
+// theta with one of x, y, z, phi change sign.  `scale` multiplies the covariance.
+template <class R> __device__ __forceinline__ void reverse_track(R p[6], R P[21], R scale)
+{
+    p[3] = -p[3];
+    p[4] = p[4] > R(0) ? p[4] - R(kPi) : p[4] + R(kPi);
+    p[5] = R(kPi) - p[5];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            const bool odd = ((i == 3 || i == 5) != (j == 3 || j == 5));
+            P[sym(i, j)] = (odd ? -scale : scale) * P[sym(i, j)];
+        }
+}
+
+// Backward (inward) pass over a fitted track's hits, layers last..first: the state on layer
+// `last` with its covariance times `scale`, then per layer from `last` inward the update with
+// the layer's hit, the layer's material, the propagation to the next smaller cylinder (as the
+// outward propagation of the reversed track).  The result lies on layer `first` after its
+// update and material; chi2 and nhits are the pass's own.
+template <class R, class U>
+__global__ void k_fit_backward(const FitGeom g, const tkf_hits h, const tkf_tracks in, const int *hit_idx, int last,
+                               int first, R scale, tkf_tracks out, int *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= in.n) return;
+    const size_t si = in.stride, so = out.stride;
+    R p[6], P[21];
+    const R *ip = (const R *)in.par, *ic = (const R *)in.cov;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[k] = ip[k * si + i];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) P[k] = ic[k * si + i];
+    const int nh_in = in.nhits[i];
+    int status = nh_in < 0 ? nh_in : 0, nh = 0;
+    R chi2 = R(0);
+    const R kb = gpick<R>(g.kb_f, g.kb), mass = gpick<R>(g.mass_f, g.mass);
+    reverse_track<R>(p, P, scale);
+    for (int l = last; l >= first && status == 0; --l) {
+        if (l < last && !propagate<R, true>(p, P, gpick<R>(g.radius_f[l], g.radius[l]), kb)) {
+            status = TKF_TRACK_NOREACH;
+            break;
+        }
+        const int hid = hit_idx[l * si + i];
+        if (hid >= h.n) {
+            atomicOr(err, kErrBadHitId);
+            status = TKF_TRACK_SINGULAR;
+            break;
+        }
+        if (hid >= 0) {
+            U dc2;
+            if (!kalman_update<U, R>(p, P, R(h.x[hid]), R(h.y[hid]), R(h.z[hid]), R(h.var_u[hid]), R(h.var_v[hid]),
+                                     &dc2)) {
+                status = TKF_TRACK_SINGULAR;
+                break;
+            }
+            chi2 += R(dc2);
+            nh += 1;
+        }
+        scatter<R>(p, P, gpick<R>(g.xx0_f[l], g.xx0[l]), mass);
+    }
+    reverse_track<R>(p, P, R(1));
+    store_fit<R>(out, i, p, P, chi2, status ? status : nh);
+    if (out.hit_idx && out.hit_idx != hit_idx)
+        for (int l = 0; l < g.L; ++l) out.hit_idx[l * so + i] = hit_idx[l * si + i];
+}
+
 FitGeom fit_geom(const tkf_ctx *ctx)
 {
     FitGeom g{};
@@ -1167,6 +1238,12 @@ int tkf_seed_fit(tkf_ctx *ctx, const tkf_hits *hits, const int32_t *seed_hits, i
     return tkf::seed_and_fit(ctx, hits, seed_hits, last_layer, out, stream);
 }
 
+int tkf_fit_backward(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx,
+                     int32_t last_layer, int32_t first_layer, double cov_scale, tkf_tracks *out, tkf_stream stream)
+{
+    return tkf::fit_backward(ctx, hits, init, hit_idx, last_layer, first_layer, cov_scale, out, stream);
+}
+
 }  // extern "C"
 
 int tkf::fit_tracks(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx,
@@ -1195,6 +1272,41 @@ int tkf::fit_tracks(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, 
         break;
     default:
         k_fit<double, double><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, pf, *out, ctx->d_err);
+        break;
+    }
+    TKF_CUDA(ctx, cudaGetLastError());
+    return TKF_OK;
+}
+
+int tkf::fit_backward(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx,
+                      int32_t last_layer, int32_t first_layer, double cov_scale, tkf_tracks *out, tkf_stream stream)
+{
+    if (!ctx) return TKF_ERR_INVALID;
+    int st = check_hits(ctx, hits);
+    if (st || (st = check_tracks(ctx, init, hit_idx == nullptr, "init")) || (st = check_tracks(ctx, out, false, "out")))
+        return st;
+    if (out->n != init->n) return set_err(ctx, TKF_ERR_INVALID, "out->n must equal init->n");
+    if (first_layer < 0 || last_layer < first_layer || last_layer >= ctx->cfg.n_layers)
+        return set_err(ctx, TKF_ERR_INVALID, "need 0 <= first_layer <= last_layer < n_layers");
+    if (!(cov_scale > 0.0) || !std::isfinite(cov_scale))
+        return set_err(ctx, TKF_ERR_INVALID, "cov_scale must be positive and finite");
+    if (init->n == 0) return TKF_OK;
+    const int32_t *hidx = hit_idx ? hit_idx : init->hit_idx;
+    const FitGeom g = fit_geom(ctx);
+    const int nb = (init->n + 127) / 128;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (ctx->cfg.precision) {
+    case TKF_FP32:
+        k_fit_backward<float, float><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, last_layer, first_layer,
+                                                         (float)cov_scale, *out, ctx->d_err);
+        break;
+    case TKF_MIXED:
+        k_fit_backward<float, double><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, last_layer, first_layer,
+                                                          (float)cov_scale, *out, ctx->d_err);
+        break;
+    default:
+        k_fit_backward<double, double><<<nb, 128, 0, s>>>(g, *hits, *init, hidx, last_layer, first_layer, cov_scale,
+                                                           *out, ctx->d_err);
         break;
     }
     TKF_CUDA(ctx, cudaGetLastError());

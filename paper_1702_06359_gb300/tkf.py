@@ -124,6 +124,8 @@ def lib():
         L.tkf_fit.argtypes = [vp, C.POINTER(Hits), C.POINTER(Tracks), vp, i32, i32, C.POINTER(Tracks), vp]
         L.tkf_fit_continue.argtypes = [vp, C.POINTER(Hits), C.POINTER(Tracks), vp, i32, i32, C.POINTER(Tracks), vp]
         L.tkf_seed_fit.argtypes = [vp, C.POINTER(Hits), vp, i32, C.POINTER(Tracks), vp]
+        L.tkf_fit_backward.argtypes = [vp, C.POINTER(Hits), C.POINTER(Tracks), vp, i32, i32, C.c_double,
+                                       C.POINTER(Tracks), vp]
         L.tkf_build_tracks.argtypes = [vp, vp, C.POINTER(Tracks), C.POINTER(Tracks), C.POINTER(Tracks), vp, vp]
         L.tkf_sync_status.argtypes = [vp, vp]
         L.tkf_pipeline_create.argtypes = [vp, i32, i32, i32, i32, C.POINTER(vp)]
@@ -312,6 +314,13 @@ class Context:
         fn = lib().tkf_fit_continue if continue_fit else lib().tkf_fit
         self._check(fn(self.handle, C.byref(hs), C.byref(ti), _ptr(hit_idx), int(first), int(last), C.byref(to),
                        _stream(stream)))
+
+    def fit_backward(self, hits: DeviceHits, init: DeviceTracks, last, first, out: DeviceTracks, cov_scale=1e4,
+                     hit_idx=None, stream=None):
+        """tkf_fit_backward: the inward pass from layer `last` down to `first`."""
+        hs, ti, to = hits.struct(), init.struct(), out.struct()
+        self._check(lib().tkf_fit_backward(self.handle, C.byref(hs), C.byref(ti), _ptr(hit_idx), int(last), int(first),
+                                           float(cov_scale), C.byref(to), _stream(stream)))
 
     def seed_fit(self, hits: DeviceHits, seed_hits, last, out: DeviceTracks, stream=None):
         hs, to = hits.struct(), out.struct()

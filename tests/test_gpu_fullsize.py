@@ -1,7 +1,8 @@
 """Parity at the full batched size, in the launch configuration bench.py times: the 640-event
 lognormal batch (2.6 M seeds, 35 M hits) through the graph-replayed pipeline with seed ordering
 and the autotuned work tile, compared with the oracle on a seeded sample of seeds (the oracle
-builds and fits them one event at a time), plus properties checked on every seed."""
+builds and fits them one event at a time), plus properties checked on every seed; then the
+backward pass (tkf_fit_backward) over every fitted track, sampled against the oracle's."""
 import multiprocessing as mp
 import os
 
@@ -9,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from _gpu import chi2_violations, param_violations
+from _gpu import chi2_violations, param_violations, unpack_cov
 from synth import Detector
 
 pytestmark = pytest.mark.gpu
@@ -75,6 +76,7 @@ def test_full_batch_sampled_parity_and_properties(full_batch):
     rng = np.random.default_rng(1702)
     events = np.sort(rng.choice(b.n_events, N_SAMPLE_EVENTS, replace=False))
     n_cmp = n_div = 0
+    bw_samples = []
     for e in events:
         h0, h1, t0, t1 = b.hit_off[e], b.hit_off[e + 1], b.trk_off[e], b.trk_off[e + 1]
         if t1 == t0:
@@ -102,6 +104,40 @@ def test_full_batch_sampled_parity_and_properties(full_batch):
         assert not chi2_violations(chi2[s[m]], fchi2)[0].any()
         assert np.array_equal(fnh[s[m]], fn)
         n_cmp += len(s)
+        bw_samples.append((oh, s[m], rh[m]))
     assert n_cmp > 1000 and n_div <= 0.05 * n_cmp, (n_cmp, n_div)
+
+    # the backward pass over every fitted track (tkf_fit_backward, layer 10 -> 1), the sampled
+    # seeds against the oracle's pass from the same (float32) states
+    class _Raw:  # the pipeline's output struct where the binding expects a DeviceTracks
+        def __init__(self, t):
+            self.t = t
+
+        def struct(self):
+            return self.t
+    back = tkf.DeviceTracks.empty(n, L)
+    ctx.fit_backward(hits, _Raw(fitted), L - 1, 0, back, cov_scale=1e4, hit_idx=bt["hit_idx"])
+    ctx.sync_status()
+    bk = dict(par=back.par, cov=back.cov, chi2=back.chi2, nhits=back.nhits)
+    bnh2 = bk["nhits"][:n].cpu().numpy()
+    live = fnh >= 0
+    assert np.array_equal(bnh2[live], fnh[live]) and np.all(bnh2[~live] < 0)
+    assert np.all(bk["chi2"][:n].cpu().numpy()[live] >= 0)
+    assert np.all(bk["cov"][[0, 2, 5, 9, 14, 20], :n].cpu().numpy()[:, live] > 0)
+    bpar = bk["par"][:, :n].double().T.cpu().numpy()
+    bchi2 = bk["chi2"][:n].double().cpu().numpy()
+    fcov_all = ft["cov"][:, :n]
+    n_bw = 0
+    for oh, idx, rh in bw_samples:
+        if not len(idx):
+            continue
+        init_cov = unpack_cov(fcov_all[:, idx].double().cpu().numpy())
+        rp, _, rc2, rn, rst = O.fit_backward(g, oh, par[idx], init_cov, rh, L - 1, 0, 1e4)
+        assert np.all(rst == 0)
+        assert np.array_equal(bnh2[idx], rn)
+        assert not param_violations(bpar[idx], rp)[0].any()
+        assert not chi2_violations(bchi2[idx], rc2)[0].any()
+        n_bw += len(idx)
+    assert n_bw > 1000
     pipe.close()
     ctx.close()
