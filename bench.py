@@ -178,6 +178,31 @@ def _oracle_events(chunk):
     return done
 
 
+def _oracle_backward(chunk):
+    """The oracle's backward pass on a few events, each (hit records, hit ids [n, L], states on
+    the outermost layer [n, 6], covariances [n, 6, 6])."""
+    import oracle as O
+    from synth import Detector
+    det = Detector()
+    g = O.make_geom(det)
+    done = 0
+    for hits, ids, par, cov in chunk:
+        O.fit_backward(g, hits, par, cov, ids, det.n_layers - 1, 0, 1e4)
+        done += len(ids)
+    return done
+
+
+def _unpack_cov(c21):
+    """[21, n] packed lower triangle (row order) -> [n, 6, 6]"""
+    out = np.zeros((c21.shape[1], 6, 6))
+    k = 0
+    for i in range(6):
+        for j in range(i + 1):
+            out[:, i, j] = out[:, j, i] = c21[k]
+            k += 1
+    return out
+
+
 def oracle_sample(batch, events):
     """Per-event oracle inputs for the listed events of a generated batch."""
     import oracle as O
@@ -666,6 +691,34 @@ def main():
                          % (ev[0], ev[-1], ntr),
                "single_core": {"value": n1 / wall1, "unit": UNIT, "cores": 1,
                                "sample": "events %d..%d (%d tracks), one process" % (ev1[0], ev1[-1], n1)}}
+        if backward is not None:
+            # the oracle's backward pass beside the GPU's, from the GPU's fitted states of the
+            # same sample events
+            _, built_t, fitted_t = pipe.outputs()
+            t_hi = int(b.trk_off[ev[-1] + 1])
+            hid = tkf.tracks_tensors(built_t, L)["hit_idx"][:, :t_hi].T.cpu().numpy()
+            fv = tkf.tracks_tensors(fitted_t, L)
+            fpar = fv["par"][:, :t_hi].double().T.cpu().numpy()
+            fcov = _unpack_cov(fv["cov"][:, :t_hi].double().cpu().numpy())
+            fnh = fv["nhits"][:t_hi].cpu().numpy()
+            bsample = []
+            for (hits_e, _), e in zip(sample, ev):
+                t0, t1, h0 = int(b.trk_off[e]), int(b.trk_off[e + 1]), int(b.hit_off[e])
+                live = np.nonzero(fnh[t0:t1] >= 0)[0] + t0
+                ids = np.where(hid[live] >= 0, hid[live] - h0, -1).astype(np.int32)
+                bsample.append((hits_e, ids, fpar[live], fcov[live]))
+            chunks, load = [[] for _ in range(cores)], [0] * cores
+            for item in sorted(bsample, key=lambda it: -len(it[1])):
+                k = load.index(min(load))
+                chunks[k].append(item)
+                load[k] += len(item[1])
+            tb = time.perf_counter()
+            nb = sum(pool.map(_oracle_backward, [c for c in chunks if c], chunksize=1))
+            backward["cpu_baseline"] = {
+                "value": nb / (time.perf_counter() - tb), "unit": "tracks/s", "cores": cores, "kind": "oracle",
+                "sample": "the backward pass of events %d..%d (%d tracks) from the GPU's fitted states, FP64, one "
+                          "process per core; inputs pickled to the workers inside the timed region"
+                          % (ev[0], ev[-1], nb)}
     pool.close()
 
     achieved = FLOP_PER_SEED * n_tr / (build_ms / 1e3) / 1e12

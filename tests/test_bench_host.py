@@ -69,3 +69,23 @@ def test_sample_events_cover_the_requested_tracks():
     sizes, _ = event_sizes(3, 640)
     assert ev == list(range(len(ev))) and n == int(sizes[:len(ev)].sum()) >= 20000
     assert int(sizes[:len(ev) - 1].sum()) < 20000
+
+
+def test_backward_baseline_helpers():
+    """The bench's covariance unpacking matches the test helpers' packing, and its oracle
+    backward-pass worker runs the oracle's pass on every track it is given."""
+    import oracle as O
+    from _gpu import pack_cov
+    from synth import Detector, EventSpec, generate
+    rng = np.random.default_rng(5)
+    a = rng.normal(size=(7, 6, 6))
+    cov = a @ np.transpose(a, (0, 2, 1))
+    assert np.array_equal(bench._unpack_cov(pack_cov(cov)), cov)
+    det = Detector()
+    b = generate(EventSpec(seed=9, n_tracks=40), det)
+    g = O.make_geom(det)
+    hits = O.hits_of(b)
+    p0, c0 = O.seed_estimate(g, hits, b.trk_hits[:, :3])
+    pf, cf, _, _, st = O.fit(g, hits, p0, c0, b.trk_hits, 0, det.n_layers - 1)
+    assert np.all(st == 0)
+    assert bench._oracle_backward([(hits, b.trk_hits, pf, cf), (hits, b.trk_hits[:5], pf[:5], cf[:5])]) == 45
