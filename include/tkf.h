@@ -169,16 +169,16 @@ int tkf_seed_state(tkf_ctx *ctx, const tkf_hits *hits, const int32_t *seed_hits,
 int tkf_fit(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx,
             int32_t first_layer, int32_t last_layer, tkf_tracks *out, tkf_stream stream);
 
-/* The same fit continued: `init` lies on layer first_layer - 1 (as tkf_fit or tkf_seed_fit
+/* The track fit of Sec. 2 continued: `init` lies on layer first_layer - 1 (as tkf_fit or tkf_seed_fit
  * leave it after that layer), so each track is propagated to first_layer before its first
  * update.  Fitting layers 0..k and then continuing over k+1..last gives the same result as one
  * fit over 0..last.  Errors: TKF_ERR_INVALID (also first_layer < 1). */
 int tkf_fit_continue(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, const int32_t *hit_idx,
                      int32_t first_layer, int32_t last_layer, tkf_tracks *out, tkf_stream stream);
 
-/* tkf_seed_state followed by tkf_fit over layers 0..last_layer with the seed hits (rows 0..2
- * of seed_hits, no hit on later layers) in one kernel, without storing the estimate: the seed
- * fit of the batched pipeline.  seed_hits: device int32 [3][out->stride].  out gets the fitted
+/* Seeding and fitting (Sec. 2): tkf_seed_state followed by tkf_fit over layers 0..last_layer
+ * with the seed hits (rows 0..2 of seed_hits, no hit on later layers) in one kernel, without
+ * storing the estimate: the seed fit of the batched pipeline.  seed_hits: device int32 [3][out->stride].  out gets the fitted
  * state, chi2, nhits and hit_idx (rows 0..2 the seed hits, others -1).  Seeds with a hit id out
  * of range get nhits = TKF_TRACK_SINGULAR and a zero state (and the kernel error bit).
  * Errors: TKF_ERR_INVALID. */

@@ -37,8 +37,6 @@ int cuda_err(tkf_ctx *ctx, cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return cuda_err(ctx, e_, #call); \
     } while (0)
 
-size_t elem_size(const tkf_ctx *ctx) { return ctx->cfg.precision == TKF_FP64 ? sizeof(double) : sizeof(float); }
-
 // ------------------------------------------------------------------ hit index kernels
 
 __device__ __forceinline__ int find_event(const int *off, int n_events, int i)
