@@ -221,7 +221,7 @@ __global__ void k_bin_scan(const int *counts, const int *seg_base, int *bin_off,
 
 // place each hit into its bin (order inside a bin fixed afterwards)
 __global__ void k_hit_scatter(const IndexGeom g, const tkf_hits h, const int *keys, int *counts, const int *bin_off,
-                              float4 *hxyzi, float2 *hvar)
+                              float4 *hxyzi, float2 *hvar, int *err)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= h.n) return;
@@ -231,6 +231,9 @@ __global__ void k_hit_scatter(const IndexGeom g, const tkf_hits h, const int *ke
     const int pos = bin_off[key] + slot;
     const int e = key / (g.L * g.n_bins);
     const int local = i - h.event_off[e];
+    // event-local ids travel in 23-bit fields (sort keys, branch keys): a larger event is an
+    // error (its ids wrap inside the event's own range, so no access leaves it)
+    if (local > kMaxHitsPerEvent) atomicOr(err, kErrTooManyHits);
     hxyzi[pos] = make_float4(h.x[i], h.y[i], h.z[i], __int_as_float(local));
     hvar[pos] = make_float2(h.var_u[i], h.var_v[i]);
 }
@@ -447,6 +450,7 @@ k_index_event(const IndexGeom g, const tkf_hits h, const int *perm, int n_bins_t
     int cur_l = -1, mu = 0, mv = 0;  // this thread's layer and its largest variances (float bits)
     const int nb_ev = g.L * g.n_bins;
     const int h0 = h.event_off[e], h1 = h.event_off[e + 1];
+    if (tid == 0 && h1 - h0 > kMaxHitsPerEvent) atomicOr(err, kErrTooManyHits);  // 23-bit local ids
     for (int k = tid; k < nb_ev; k += kEventThreads) s_cnt[k] = 0;
     if (tid < 2 * g.L) s_var[tid] = 0;
     __syncthreads();
@@ -1150,7 +1154,8 @@ int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out,
         k_bin_scan<<<(unsigned)n_segs, 256, 0, s>>>(idx->counts, idx->seg_base, idx->bin_off, NB, (int)n_segs);
         if (hits->n > 0) {
             const int nb = (hits->n + 255) / 256;
-            k_hit_scatter<<<nb, 256, 0, s>>>(g, *hits, idx->keys, idx->counts, idx->bin_off, idx->hxyzi, idx->hvar);
+            k_hit_scatter<<<nb, 256, 0, s>>>(g, *hits, idx->keys, idx->counts, idx->bin_off, idx->hxyzi, idx->hvar,
+                                              ctx->d_err);
         }
         k_bin_sort<<<sort_blocks(n_bins), 32 * kSortWarps, 0, s>>>(g, idx->bin_off, idx->ev_off, (int)n_bins,
                                                                    idx->hxyzi, idx->hvar, idx->bin_sub, idx->pos_of_hit);
@@ -1460,7 +1465,8 @@ int tkf_sync_status(tkf_ctx *ctx, tkf_stream stream)
     if (e) {
         TKF_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
         char buf[160];
-        std::snprintf(buf, sizeof buf, "kernel error bits 0x%x (1: hit layer out of range, 2: hit id out of range, 8: seed event out of range)", e);
+        std::snprintf(buf, sizeof buf, "kernel error bits 0x%x (1: hit layer out of range, 2: hit id out of range, 4: more than 8388606 hits "
+                      "in one event, 8: seed event out of range)", e);
         return set_err(ctx, TKF_ERR_KERNEL, buf);
     }
     return TKF_OK;
@@ -1567,7 +1573,7 @@ extern "C" int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits
     k_seg_scan<<<1, 1024, 0, s>>>(seg_count, seg_base, (int)n_segs);
     k_bin_scan<<<(unsigned)n_segs, 256, 0, s>>>(counts, seg_base, out->bin_off, NB, (int)n_segs);
     if (hits->n > 0)
-        k_hit_scatter<<<(hits->n + 255) / 256, 256, 0, s>>>(g, *hits, keys, counts, out->bin_off, hxyzi, hvar);
+        k_hit_scatter<<<(hits->n + 255) / 256, 256, 0, s>>>(g, *hits, keys, counts, out->bin_off, hxyzi, hvar, err);
     k_bin_sort<<<sort_blocks(n_bins), 32 * kSortWarps, 0, s>>>(g, out->bin_off, out->event_off, (int)n_bins, hxyzi,
                                                                hvar, (uint4 *)out->bin_sub, out->pos_of_hit);
     return cudaGetLastError() == cudaSuccess ? TKF_OK : TKF_ERR_CUDA;

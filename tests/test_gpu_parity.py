@@ -135,6 +135,42 @@ def test_hit_index_one_block_per_event_equals_multi_launch_index(det):
     assert np.array_equal(full["vmax"], np.concatenate([a1["vmax"], a2["vmax"]]))
 
 
+@pytest.mark.parametrize("n_events", [1, 160], ids=["multi_launch", "one_block_per_event"])
+def test_event_over_the_hit_limit_is_reported(n_events):
+    """Event-local hit ids are 23-bit fields: an event of 2^23 + 5 hits makes the index raise
+    its error bit (both index paths: one event takes the multi-launch path, 160 events the
+    one-block-per-event kernel); the ids wrap inside the event's own range, so nothing is
+    accessed outside it.  630 phi bins keep ~33 hits per bin."""
+    import math
+    big = (1 << 23) + 5
+    sizes = np.full(n_events, 10)
+    sizes[0] = big
+    n = int(sizes.sum())
+    cfg = tkf.default_config(n_phi_bins=630)
+    L = cfg.n_layers
+    rng = np.random.default_rng(7)
+    layer = rng.integers(0, L, n).astype(np.int32)
+    R = np.array([cfg.radius[l] for l in range(L)])[layer]
+    phi = rng.uniform(-math.pi, math.pi, n)
+    dev = torch.device("cuda", 0)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(dev)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    hits = tkf.DeviceHits(t(R * np.cos(phi), torch.float32), t(R * np.sin(phi), torch.float32),
+                          t(rng.uniform(-0.8, 0.8, n) * R, torch.float32), t(np.full(n, 1e-4), torch.float32),
+                          t(np.full(n, 1e-2), torch.float32), t(layer, torch.int32), t(off, torch.int32))
+    ctx = tkf.Context(cfg)
+    idx = ctx.build_hit_index(hits)
+    with pytest.raises(tkf.TkfError, match="8388606"):
+        ctx.sync_status()
+    idx.free()
+    # a batch within the limit on the same context reports nothing
+    ok = tkf.DeviceHits(*(getattr(hits, k)[:int(off[1]) - 6] for k in ("x", "y", "z", "var_u", "var_v", "layer")),
+                        t(np.array([0, int(off[1]) - 6]), torch.int32))
+    ctx.build_hit_index(ok).free()
+    ctx.sync_status()
+    ctx.close()
+
+
 def _copy_dev(ptr, count, dtype):
     """Copies `count` elements from a raw device pointer owned by the library."""
     class _Wrap:
