@@ -56,9 +56,9 @@ SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # place), build, final fit
 KERNELS_PER_STEP = 11
 # DRAM bytes (read + write) per seed of the FP32 building kernel, from one ncu capture of the
-# kernel as built now (160-event case: 409.8 MB for 701 095 seeds; summary in profiles/);
+# kernel as built now (160-event case: 407.1 MB for 701 095 seeds; summary in profiles/);
 # None whenever the kernel changes until it is captured again
-BUILD_DRAM_BYTES_PER_SEED = 584.5
+BUILD_DRAM_BYTES_PER_SEED = 580.7
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 
 

@@ -17,10 +17,13 @@
 // work stealing (Sec. 2.3): warps pull tiles of seeds_per_block seeds from an atomic counter
 // until the seeds of every event are done (one persistent launch over many events, Sec. 4).
 //
-// Branch key (64 bits, smaller = better): [63:59] 31 - nHits, [58:27] float bits of the total
-// chi2 (non-negative, so integer order = value order), [26:23] parent rank, [22:0]
-// event-local hit id (0x7FFFFF for a hole).  This is the total order
-// (nHits desc, chi2 asc, parent rank asc, hit id asc).
+// Branch key (32 bits, smaller = better): [31:27] 31 - nHits, [26:4] float bits 30..8 of the
+// total chi2 rounded (non-negative, so integer order = value order, to 2^-16 relative), [3:0] parent
+// rank; the event-local hit id (0x7FFFFF for a hole) travels beside it.  This is the order
+// (nHits desc, chi2 asc, parent rank asc); totals within 2^-15 may rank by parent, and within
+// one parent by the order the hits were scanned -- near-ties far inside the 1e-3 relative band
+// within which the parity definition calls a ranking fragile.  Keys of one seed's lanes differ
+// in the parent field.
 #pragma once
 
 #include "internal.h"
@@ -29,7 +32,7 @@
 namespace tkf {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr uint64_t kEmpty = ~0ull;
+constexpr unsigned kEmpty32 = 0xFFFFFFFFu;
 
 template <class R> __device__ __forceinline__ R pick(float f, double d);
 template <> __device__ __forceinline__ float pick<float>(float f, double) { return f; }
@@ -38,29 +41,41 @@ template <> __device__ __forceinline__ double pick<double>(float, double d) { re
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(double v) { return __double2float_rn(v); }
 
-__device__ __forceinline__ uint64_t make_key(int nhits, float chi2, int parent, int hit)
+// The branch key of a candidate's branch (layout at the top of this file); the chi2 bits are
+// rounded to nearest, so key_chi2 returns the total within 2^-16 relative.
+__device__ __forceinline__ unsigned make_key32(int nhits, float chi2, int parent)
 {
-    const uint64_t c = __float_as_uint(chi2) & 0x7FFFFFFFu;
-    return ((uint64_t)(31 - nhits) << 59) | (c << 27) | ((uint64_t)parent << 23) | (uint64_t)hit;
+    const unsigned c = ((__float_as_uint(chi2) & 0x7FFFFFFFu) + 0x80u) >> 8;
+    return ((unsigned)(31 - nhits) << 27) | (c << 4) | (unsigned)parent;
 }
 
-// A lane's branch list: the NMAX smallest keys in ascending order.
-template <int NMAX> __device__ __forceinline__ void list_insert(uint64_t (&list)[NMAX], uint64_t k)
+__device__ __forceinline__ float key_chi2(unsigned key) { return __uint_as_float(((key >> 4) & 0x7FFFFFu) << 8); }
+
+// A lane's branch list: its NMAX smallest keys in ascending order (lk), with their hit ids (lh);
+// a key equal to one already listed goes after it.
+template <int NMAX>
+__device__ __forceinline__ void list_insert32(unsigned (&lk)[NMAX], int (&lh)[NMAX], unsigned k, int h)
 {
 #pragma unroll
     for (int i = 0; i < NMAX; ++i) {
-        const uint64_t lo = k < list[i] ? k : list[i];
-        const uint64_t hi = k < list[i] ? list[i] : k;
-        list[i] = lo;
-        k = hi;
+        const bool lt = k < lk[i];
+        const unsigned k2 = lt ? lk[i] : k;
+        const int h2 = lt ? lh[i] : h;
+        lk[i] = lt ? k : lk[i];
+        lh[i] = lt ? h : lh[i];
+        k = k2;
+        h = h2;
     }
 }
 
-template <int NMAX> __device__ __forceinline__ void list_pop(uint64_t (&list)[NMAX])
+template <int NMAX> __device__ __forceinline__ void list_pop32(unsigned (&lk)[NMAX], int (&lh)[NMAX])
 {
 #pragma unroll
-    for (int i = 0; i + 1 < NMAX; ++i) list[i] = list[i + 1];
-    list[NMAX - 1] = kEmpty;
+    for (int i = 0; i + 1 < NMAX; ++i) {
+        lk[i] = lk[i + 1];
+        lh[i] = lh[i + 1];
+    }
+    lk[NMAX - 1] = kEmpty32;
 }
 
 // Hit ranges of phi sub-bins inside a bin, from the packed bytes of bin_sub (byte t - 1 holds
@@ -106,7 +121,7 @@ template <class R> __device__ __forceinline__ R asin_window(R x)
 // Scores every hit of the candidate's window and fills its branch list.
 template <int NMAX, class R>
 __device__ __forceinline__ void scan_window(const BuildArgs &a, int ev, int l, R Rl, const R p[6], const R P[21],
-                                            R chi2, int nh, int rank, uint64_t (&list)[NMAX])
+                                            R chi2, int nh, int rank, unsigned (&lk)[NMAX], int (&lh)[NMAX])
 {
     const int seg = ev * a.L + l;
     const float2 vmax = a.var_max[seg];
@@ -178,13 +193,13 @@ __device__ __forceinline__ void scan_window(const BuildArgs &a, int ev, int l, R
                 if (ab(u) > U || ab(v) > W) continue;
                 const R c2 = chi2_uv<R>(P, u, v, sh, ch, R(hv.x), R(hv.y));
                 if (c2 < cut) {
-                    list_insert(list, make_key(nh + 1, to_f32(chi2 + c2), rank, __float_as_int(h.w)));
+                    list_insert32(lk, lh, make_key32(nh + 1, to_f32(chi2 + c2), rank), __float_as_int(h.w));
                     found = true;
                 }
             }
         }
     }
-    if (!found) list_insert(list, make_key(nh, to_f32(chi2), rank, kHoleId));
+    if (!found) list_insert32(lk, lh, make_key32(nh, to_f32(chi2), rank), kHoleId);
 }
 
 template <class R> __device__ __forceinline__ void store_track(void *par, void *cov, void *c2, int stride, int i,
@@ -268,43 +283,54 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U>::va
             for (int l = a.first; l < a.L; ++l) {
                 const R Rl = pick<R>(a.radius_f[l], a.radius[l]);
                 const bool ok = alive && propagate<R>(p, P, Rl, kb);
-                uint64_t list[NMAX];
+                unsigned lk[NMAX];
+                int lh[NMAX];
 #pragma unroll
-                for (int i = 0; i < NMAX; ++i) list[i] = kEmpty;
-                if (ok) scan_window<NMAX, R>(a, ev, l, Rl, p, P, chi2, nh, r, list);
+                for (int i = 0; i < NMAX; ++i) {
+                    lk[i] = kEmpty32;
+                    lh[i] = 0;
+                }
+                if (ok) scan_window<NMAX, R>(a, ev, l, Rl, p, P, chi2, nh, r, lk, lh);
 
                 // merge the segment's lists: N rounds of a segmented minimum
-                uint64_t mine = kEmpty;
+                unsigned mine = kEmpty32;
+                int mine_h = 0;
                 ns = 0;
                 for (int k = 0; k < N; ++k) {
-                    if (!__any_sync(kFull, list[0] != kEmpty)) break;  // no segment has branches left
-                    uint64_t m = list[0];
+                    if (!__any_sync(kFull, lk[0] != kEmpty32)) break;  // no segment has branches left
+                    unsigned m = lk[0];
                     for (int off = 1; off < N; off <<= 1) {
-                        const uint64_t o = __shfl_down_sync(kFull, m, off);
+                        const unsigned o = __shfl_down_sync(kFull, m, off);
                         if (r + off < N && o < m) m = o;
                     }
                     m = __shfl_sync(kFull, m, gbase);
-                    if (m != kEmpty) {
-                        if (list[0] == m) list_pop(list);
-                        if (r == k) mine = m;
+                    // the winner is the lane whose rank is the key's parent field
+                    const int hsel = __shfl_sync(kFull, lh[0], lane_ok ? gbase + (int)(m & 0xFu) : lane);
+                    if (m != kEmpty32) {
+                        if (lk[0] == m) list_pop32(lk, lh);
+                        if (r == k) {
+                            mine = m;
+                            mine_h = hsel;
+                        }
                         ns = k + 1;
                     }
                 }
 
                 // survivors take their parent's predicted state
-                const int parent = mine != kEmpty ? (int)((mine >> 23) & 0xF) : r;
+                const int parent = mine != kEmpty32 ? (int)(mine & 0xFu) : r;
                 const int src = lane_ok ? gbase + parent : lane;
 #pragma unroll
                 for (int k = 0; k < 6; ++k) p[k] = __shfl_sync(kFull, p[k], src);
 #pragma unroll
                 for (int k = 0; k < 21; ++k) P[k] = __shfl_sync(kFull, P[k], src);
                 const R pchi2 = __shfl_sync(kFull, chi2, src);
-                alive = mine != kEmpty;
+                alive = mine != kEmpty32;
                 if (alive) {
-                    nh = 31 - (int)(mine >> 59);
-                    const int hl = (int)(mine & (uint64_t)kHoleId);
+                    nh = 31 - (int)(mine >> 27);
+                    const int hl = mine_h;
                     int gh = -1;
-                    chi2 = sizeof(R) == 8 ? pchi2 : R(__uint_as_float((unsigned)((mine >> 27) & 0xFFFFFFFFull)));
+                    // the total the ranking used (the scan's sum); FP64 keeps its own exact sum
+                    chi2 = sizeof(R) == 8 ? pchi2 : R(key_chi2(mine));
                     if (hl != kHoleId) {
                         gh = __ldg(&a.ev_off[ev]) + hl;
                         const int pos = __ldg(&a.pos_of_hit[gh]);

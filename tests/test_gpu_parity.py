@@ -8,7 +8,8 @@ import numpy as np
 import pytest
 
 import oracle as O
-from _gpu import (chi2_violations, device_hits, device_tracks, host_tracks, param_violations, rounded)
+from _gpu import (chi2_violations, device_hits, device_tracks, divergence_allowed, host_tracks, param_violations,
+                  rounded)
 from _helpers import oracle_seeds, select_events, small_event
 from synth import Detector, EventSpec, event_sizes, generate
 
@@ -320,9 +321,8 @@ def _check_build(batch, got, refs, n_layers, max_divergent=0.05, rel=None):
             if ref.n_cand[s] == 0:
                 assert got["nhits"][t0 + s] == tkf.TRACK_LOST
                 continue
-            d = int(np.argmax(gh[s] != rh[s]))
-            assert d >= ref.fragile[s], ("hit assignment differs before any fragile decision", e, s, d,
-                                         ref.fragile[s], gh[s], rh[s])
+            assert divergence_allowed(gh[s], ref, s), ("hit assignment differs before any fragile decision", e, s,
+                                                       ref.fragile[s], gh[s], rh[s])
             n_div += 1
         n_all += t1 - t0
         m = np.nonzero(same)[0]

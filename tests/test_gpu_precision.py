@@ -6,9 +6,10 @@ FP32, MIXED (FP64 innovation inverse and Joseph-form update, Sec. 3.2) and FP64,
 against the FP64 oracle's whole path on the same events.
 
 Gates: every seed whose final hit list equals the oracle's has its final-fit parameters and
-chi2 within the parity tolerance (1e-8 in FP64); a differing hit list is allowed only from a
-layer where the oracle's own decision was fragile (two ranked totals within 1e-3, or a chi2
-within 1e-3 of the cut), and for at most 5% of seeds.  Reported per quantity and mode
+chi2 within the parity tolerance (1e-8 in FP64); a differing hit list is allowed only where
+the oracle's own decision was fragile (two ranked totals within 1e-3, or a chi2 within 1e-3
+of the cut): from the first fragile layer on, or as one of the oracle's final candidates tied
+with its best, and for at most 5% of seeds.  Reported per quantity and mode
 (printed, and written as JSON to $TKF_REPORT_DIR when set): relative error of each
 parameter, of each covariance diagonal element and of chi2, the hit agreement, and the
 building efficiency next to the oracle's."""
@@ -19,7 +20,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from _gpu import PAR_FLOOR, chi2_violations, param_violations, unpack_cov
+from _gpu import PAR_FLOOR, chi2_violations, divergence_allowed, param_violations, unpack_cov
 from synth import Detector, EventSpec, generate
 
 pytestmark = pytest.mark.gpu
@@ -53,7 +54,7 @@ def sweep_events():
         res = O.build(g, O.hit_index(g, hits), sp, sP, sc2, snh, ids)
         fpar, fcov, fchi2, fnh, fst = O.fit(g, hits, p0, c0, res.hits[:, 0, :], 0, L - 1)
         refs.append(dict(hits=res.hits[:, 0, :], n_cand=res.n_cand, fragile=res.fragile, par=fpar, cov=fcov,
-                         chi2=fchi2, nhits=fnh))
+                         chi2=fchi2, nhits=fnh, res=res))
     return det, b, refs
 
 
@@ -118,8 +119,7 @@ def test_precision_sweep_whole_path(sweep_events, prec):
         assert np.all(got["built_nhits"][t0:t1][lost] == tkf.TRACK_LOST)
         same = np.all(gh == ref["hits"], axis=1) & ~lost
         for s in np.nonzero(~same & ~lost)[0]:
-            d = int(np.argmax(gh[s] != ref["hits"][s]))
-            assert d >= ref["fragile"][s], ("hit list differs before any fragile decision", name, e, s, d)
+            assert divergence_allowed(gh[s], ref["res"], s), ("hit list differs before any fragile decision", name, e, s)
             n_div += 1
         m = np.nonzero(same)[0]
         n_same += len(m)

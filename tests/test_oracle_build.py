@@ -208,3 +208,18 @@ def test_building_efficiency_on_the_plain_workload(det):
     eff = np.mean(frac >= 0.75)
     assert eff > 0.97, eff
     assert np.mean(res.nhits[:, 0] == det.n_layers) > 0.9
+
+
+def test_divergence_rule_of_the_gpu_tests():
+    """The exemption the GPU parity tests apply to a differing hit list: from the oracle's first
+    fragile layer on, or a final candidate tied (within 1e-3) with the best; nothing else."""
+    from _gpu import divergence_allowed
+    hits = np.array([[[1, 2, 3, 4, 5], [1, 2, 3, 9, 5], [1, 2, 3, 9, 8]]])
+    res = O.BuildResult(n_cand=np.array([3]), par=None, cov=None, chi2=np.array([[10.0, 10.005, 12.0]]),
+                        nhits=np.array([[5, 5, 5]]), hits=hits, fragile=np.array([4]), stats={})
+    assert divergence_allowed(np.array([1, 2, 3, 4, 7]), res, 0)      # differs at the fragile layer 4
+    assert divergence_allowed(np.array([1, 2, 3, 9, 5]), res, 0)      # rank 1, tied with the best
+    assert not divergence_allowed(np.array([1, 2, 3, 9, 8]), res, 0)  # rank 2, 20 % worse
+    assert not divergence_allowed(np.array([1, 2, 7, 4, 5]), res, 0)  # not a candidate
+    res.nhits[0, 1] = 4
+    assert not divergence_allowed(np.array([1, 2, 3, 9, 5]), res, 0)  # fewer hits: not a tie
