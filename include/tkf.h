@@ -49,9 +49,10 @@ enum tkf_status_code {
     TKF_ERR_TOO_LARGE = 8 /* input exceeds the fixed capacity of tkf_build_hit_index_noalloc */
 };
 
-/* Arithmetic of the KF steps.  FP32: everything in float.  MIXED: float, except the
- * innovation-covariance inverse and the Joseph-form covariance update, done in double and
- * rounded back.  FP64: everything in double (track arrays hold double). */
+/* Arithmetic of the KF steps (Sec. 3.2: the update's numerical stability).  FP32: everything
+ * in float.  MIXED: float, except the innovation covariance, its inverse, the gain and the
+ * Joseph-form covariance update, done in double and rounded back (the state update applies
+ * the rounded gain in float).  FP64: everything in double (track arrays hold double). */
 enum tkf_precision { TKF_FP32 = 0, TKF_MIXED = 1, TKF_FP64 = 2 };
 
 /* Per-track status written to tkf_tracks.nhits when a track fails (nhits < 0). */
