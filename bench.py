@@ -161,13 +161,15 @@ def job_rate(units, ms, dist=None, device="cpu"):
 # ----------------------------------------------------------------------------- CPU baseline (oracle)
 def _oracle_events(chunk):
     """Runs the oracle's whole path (index, seed, seed fit, build, final fit) on a few events,
-    each given as (oracle hit records, track hit ids [n, L])."""
+    each given as (oracle hit records, track hit ids [n, L]); returns (tracks, seconds spent
+    computing in this process)."""
     import oracle as O
     from synth import Detector
     det = Detector()
     g = O.make_geom(det)
     L = det.n_layers
     done = 0
+    t0 = time.perf_counter()
     for hits, local in chunk:
         p0, c0 = O.seed_estimate(g, hits, local[:, :3])
         ids = np.full((len(local), L), -1, dtype=np.int32)
@@ -176,21 +178,22 @@ def _oracle_events(chunk):
         res = O.build(g, O.hit_index(g, hits), sp, sP, sc2, snh, ids)
         O.fit(g, hits, p0, c0, res.hits[:, 0, :], 0, L - 1)
         done += len(local)
-    return done
+    return done, time.perf_counter() - t0
 
 
 def _oracle_backward(chunk):
     """The oracle's backward pass on a few events, each (hit records, hit ids [n, L], states on
-    the outermost layer [n, 6], covariances [n, 6, 6])."""
+    the outermost layer [n, 6], covariances [n, 6, 6]); returns (tracks, seconds computing)."""
     import oracle as O
     from synth import Detector
     det = Detector()
     g = O.make_geom(det)
     done = 0
+    t0 = time.perf_counter()
     for hits, ids, par, cov in chunk:
         O.fit_backward(g, hits, par, cov, ids, det.n_layers - 1, 0, 1e4)
         done += len(ids)
-    return done
+    return done, time.perf_counter() - t0
 
 
 def _unpack_cov(c21):
@@ -215,9 +218,10 @@ def oracle_sample(batch, events):
     return out
 
 
-def cpu_baseline(sample, pool, cores):
-    """The oracle on the sample's events, one worker process per core, events dealt largest
-    first to the least-loaded worker; (tracks, wall s)."""
+def cpu_baseline(sample, pool, cores, fn=_oracle_events):
+    """The oracle on the sample's items (events), one worker process per core, items dealt
+    largest first to the least-loaded worker; (tracks, seconds of the slowest worker's
+    computing, wall seconds including the transfer of the inputs to the workers)."""
     chunks, load = [[] for _ in range(cores)], [0] * cores
     for ev in sorted(sample, key=lambda e: -len(e[1])):
         k = load.index(min(load))
@@ -225,8 +229,9 @@ def cpu_baseline(sample, pool, cores):
         load[k] += len(ev[1])
     chunks = [c for c in chunks if c]
     t0 = time.perf_counter()
-    done = sum(pool.map(_oracle_events, chunks, chunksize=1))
-    return done, time.perf_counter() - t0
+    res = pool.map(fn, chunks, chunksize=1)
+    wall = time.perf_counter() - t0
+    return sum(r[0] for r in res), max(r[1] for r in res), wall
 
 
 def sample_events(seed, target_tracks):
@@ -256,10 +261,11 @@ def run_reference(a):
         sample = oracle_sample(workload(a.seed, ev[-1] + 1, pool), ev)
         for _ in range(a.warmup):
             cpu_baseline(sample, pool, cores)
-        times = []
+        times, walls = [], []
         for _ in range(a.steps):
-            tracks, wall = cpu_baseline(sample, pool, cores)
-            times.append(wall)
+            tracks, comp, wall = cpu_baseline(sample, pool, cores)
+            times.append(comp)
+            walls.append(wall)
     value = ntr / statistics.mean(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
@@ -268,7 +274,9 @@ def run_reference(a):
                                    "(%d tracks), oracle FP64 on host cores" % (ev[0], ev[-1], ntr),
                        "events": len(ev), "tracks": ntr},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d events, %d tracks per step" % (len(ev), ntr)},
+                             "sample": "%d events, %d tracks per step; time = the slowest worker's computing "
+                                       "(mean %.2f s; %.2f s wall with the transfer of the inputs)"
+                                       % (len(ev), ntr, statistics.mean(times), statistics.mean(walls))},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -382,7 +390,7 @@ def main():
     ap.add_argument("--events", type=int, default=640)
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--plain-events", type=int, default=640, help="events timed one at a time")
-    ap.add_argument("--cpu-tracks", type=int, default=200000, help="oracle CPU-baseline sample (tracks)")
+    ap.add_argument("--cpu-tracks", type=int, default=600000, help="oracle CPU-baseline sample (tracks)")
     ap.add_argument("--ref-tracks", type=int, default=120000, help="reference-arm sample per step (tracks)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve", type=int, default=1, help="1: also measure the served stream")
@@ -685,18 +693,18 @@ def main():
     if rank == 0 and world == 1 and not a.no_cpu:
         ev, ntr = sample_events(a.seed, a.cpu_tracks)
         sample = oracle_sample(b, ev)
-        tracks, wall = cpu_baseline(sample, pool, cores)
-        # one core: the same oracle in this process on the sample's first events (>= 20 000 tracks)
-        ev1 = ev[:max(1, next((k + 1 for k in range(len(ev)) if int(b.trk_off[ev[k] + 1] - b.trk_off[ev[0]]) >= 20000),
+        tracks, comp, wall = cpu_baseline(sample, pool, cores)
+        # one core: the same oracle in this process on the sample's first events (>= 100 000 tracks)
+        ev1 = ev[:max(1, next((k + 1 for k in range(len(ev)) if int(b.trk_off[ev[k] + 1] - b.trk_off[ev[0]]) >= 100000),
                               len(ev)))]
-        t1 = time.perf_counter()
-        n1 = _oracle_events(sample[:len(ev1)])
-        wall1 = time.perf_counter() - t1
-        cpu = {"value": ntr / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+        n1, comp1 = _oracle_events(sample[:len(ev1)])
+        cpu = {"value": tracks / comp, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "events %d..%d of the same batch (%d tracks): index, seed, seed fit, build, final fit, "
-                         "FP64, one process per core; inputs pickled to the workers inside the timed region"
-                         % (ev[0], ev[-1], ntr),
-               "single_core": {"value": n1 / wall1, "unit": UNIT, "cores": 1,
+                         "FP64, one process per core, events dealt largest first; time = the slowest worker's "
+                         "computing (%.2f s; %.2f s wall with the transfer of the inputs to the workers)"
+                         % (ev[0], ev[-1], tracks, comp, wall),
+               "wall_value": tracks / wall,
+               "single_core": {"value": n1 / comp1, "unit": UNIT, "cores": 1,
                                "sample": "events %d..%d (%d tracks), one process" % (ev1[0], ev1[-1], n1)}}
         if backward is not None:
             # the oracle's backward pass beside the GPU's, from the GPU's fitted states of the
@@ -714,18 +722,12 @@ def main():
                 live = np.nonzero(fnh[t0:t1] >= 0)[0] + t0
                 ids = np.where(hid[live] >= 0, hid[live] - h0, -1).astype(np.int32)
                 bsample.append((hits_e, ids, fpar[live], fcov[live]))
-            chunks, load = [[] for _ in range(cores)], [0] * cores
-            for item in sorted(bsample, key=lambda it: -len(it[1])):
-                k = load.index(min(load))
-                chunks[k].append(item)
-                load[k] += len(item[1])
-            tb = time.perf_counter()
-            nb = sum(pool.map(_oracle_backward, [c for c in chunks if c], chunksize=1))
+            nb, compb, wallb = cpu_baseline(bsample, pool, cores, fn=_oracle_backward)
             backward["cpu_baseline"] = {
-                "value": nb / (time.perf_counter() - tb), "unit": "tracks/s", "cores": cores, "kind": "oracle",
+                "value": nb / compb, "unit": "tracks/s", "cores": cores, "kind": "oracle",
                 "sample": "the backward pass of events %d..%d (%d tracks) from the GPU's fitted states, FP64, one "
-                          "process per core; inputs pickled to the workers inside the timed region"
-                          % (ev[0], ev[-1], nb)}
+                          "process per core; time = the slowest worker's computing (%.2f s; %.2f s wall with the "
+                          "transfer of the inputs)" % (ev[0], ev[-1], nb, compb, wallb)}
     pool.close()
 
     achieved = FLOP_PER_SEED * n_tr / (build_ms / 1e3) / 1e12

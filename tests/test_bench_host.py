@@ -53,12 +53,12 @@ def test_oracle_events_are_dealt_largest_first_to_the_least_loaded_core():
     class _Pool:
         def map(self, fn, chunks, chunksize=1):
             self.chunks = chunks
-            return [sum(len(ev[1]) for ev in c) for c in chunks]
+            return [(sum(len(ev[1]) for ev in c), 0.001 * sum(len(ev[1]) for ev in c)) for c in chunks]
     sizes = [50, 10, 40, 30, 20, 5]
     sample = [(None, np.zeros((n, 10))) for n in sizes]
     pool = _Pool()
-    done, wall = bench.cpu_baseline(sample, pool, 2)
-    assert done == sum(sizes) and wall >= 0
+    done, comp, wall = bench.cpu_baseline(sample, pool, 2)
+    assert done == sum(sizes) and wall >= 0 and abs(comp - 0.080) < 1e-12  # the slowest worker's computing
     loads = sorted(sum(len(ev[1]) for ev in c) for c in pool.chunks)
     assert loads == [75, 80]  # 50+20+5 and 40+30+10
 
@@ -88,4 +88,5 @@ def test_backward_baseline_helpers():
     p0, c0 = O.seed_estimate(g, hits, b.trk_hits[:, :3])
     pf, cf, _, _, st = O.fit(g, hits, p0, c0, b.trk_hits, 0, det.n_layers - 1)
     assert np.all(st == 0)
-    assert bench._oracle_backward([(hits, b.trk_hits, pf, cf), (hits, b.trk_hits[:5], pf[:5], cf[:5])]) == 45
+    done, secs = bench._oracle_backward([(hits, b.trk_hits, pf, cf), (hits, b.trk_hits[:5], pf[:5], cf[:5])])
+    assert done == 45 and secs > 0
