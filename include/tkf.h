@@ -231,9 +231,9 @@ typedef struct tkf_pipeline tkf_pipeline;
  * seeds: the whole chain of Sec. 2 -- hit index, seed estimate, KF fit of the seeding layers,
  * combinatorial building, final KF fit of the built hit lists -- over every event of a batch
  * at once (the multi-event packing of Sec. 4, with the building kernel's dynamic work tiles
- * standing for the TBB work stealing of Sec. 2.3).  All buffers (hit index, four track sets)
- * are allocated here, so a run allocates nothing.  With use_graph != 0 the first run with a
- * given input signature (hit pointers and sizes, seed pointers, n_tracks) is captured into a
+ * standing for the TBB work stealing of Sec. 2.3).  All buffers (hit index, the track sets)
+ * are allocated here or by tkf_pipeline_set_backward, so a run allocates nothing.  With
+ * use_graph != 0 the first run with a given input signature (hit pointers and sizes, seed pointers, n_tracks) is captured into a
  * CUDA graph on the pipeline's own stream and replayed by every later run with the same
  * signature (one cudaGraphLaunch); another signature re-captures.
  * Errors: TKF_ERR_INVALID, TKF_ERR_NOMEM, TKF_ERR_CUDA. */
@@ -252,6 +252,17 @@ int tkf_pipeline_run(tkf_pipeline *p, const tkf_hits *hits, const int32_t *seed_
  * `seeds` = states after the seeding layers (with their event ids), `built` = best candidate
  * per seed after building, `fitted` = its final fit (hit_idx = the built hit list). */
 int tkf_pipeline_outputs(const tkf_pipeline *p, tkf_tracks *seeds, tkf_tracks *built, tkf_tracks *fitted);
+
+/* Adds (cov_scale > 0) or removes (0) a last stage to every following run: the backward pass
+ * of the final fit (tkf_fit_backward from the fitted states on the outermost layer to layer 0,
+ * with this covariance scale) into a fifth, pipeline-owned track set; the next run captures
+ * its graph again.  The first enabling call allocates that set.
+ * Errors: TKF_ERR_INVALID (cov_scale negative or not finite), TKF_ERR_NOMEM, TKF_ERR_CUDA. */
+int tkf_pipeline_set_backward(tkf_pipeline *p, double cov_scale);
+
+/* View of the backward pass's track set of the last run (states on layer 0; hit_idx = the
+ * built hit list).  Errors: TKF_ERR_INVALID (no backward stage set). */
+int tkf_pipeline_backward_outputs(const tkf_pipeline *p, tkf_tracks *out);
 
 /* Number of graph captures so far (replays do not count); -1 for a null pipeline. */
 int tkf_pipeline_captures(const tkf_pipeline *p);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -58,6 +59,7 @@ struct Signature {
     tkf_hits hits;
     const int32_t *seed_hits, *seed_event;
     int32_t n_tracks, tile;
+    double back_scale;
     bool operator==(const Signature &o) const { return std::memcmp(this, &o, sizeof *this) == 0; }
 };
 
@@ -67,7 +69,8 @@ struct tkf_pipeline {
     tkf_ctx *ctx = nullptr;
     int max_hits = 0, max_events = 0, max_tracks = 0, use_graph = 1;
     tkf_hit_index *idx = nullptr;
-    Buf seeds, built, final_;
+    Buf seeds, built, final_, back;
+    double back_scale = 0.0;  // > 0: the step ends with the backward pass (covariance scale)
     cudaStream_t capture = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -108,7 +111,11 @@ int issue(tkf_pipeline *p, const tkf_hits *hits, const int32_t *seed_hits, const
         return fail(ctx, TKF_ERR_CUDA, "pipeline: cudaEventRecord");
     // final fit of the built hit list: layers 0..first-1 carry the seed's hits, so the seed fit
     // already holds its state there (bit for bit); the fit continues from it on layer first
-    return tkf::fit_tracks(ctx, hits, &seeds, built.hit_idx, first, L - 1, &fin, (tkf_stream)s, true);
+    if ((st = tkf::fit_tracks(ctx, hits, &seeds, built.hit_idx, first, L - 1, &fin, (tkf_stream)s, true))) return st;
+    if (!(p->back_scale > 0.0)) return TKF_OK;
+    // optional: the final fit's backward pass to the innermost layer
+    tkf_tracks bk = view(p->back, n, stride);
+    return tkf::fit_backward(ctx, hits, &fin, built.hit_idx, L - 1, 0, p->back_scale, &bk, (tkf_stream)s);
 }
 
 }  // namespace
@@ -155,7 +162,7 @@ int tkf_pipeline_destroy(tkf_pipeline *p)
     for (cudaEvent_t ev : p->build_ev)
         if (ev) cudaEventDestroy(ev);
     if (p->idx) tkf_hit_index_free(p->idx);
-    for (Buf *b : {&p->seeds, &p->built, &p->final_}) free_buf(*b);
+    for (Buf *b : {&p->seeds, &p->built, &p->final_, &p->back}) free_buf(*b);
     delete p;
     return TKF_OK;
 }
@@ -176,6 +183,7 @@ int tkf_pipeline_run(tkf_pipeline *p, const tkf_hits *hits, const int32_t *seed_
     sig.seed_event = seed_event;
     sig.n_tracks = n_tracks;
     sig.tile = ctx->cfg.seeds_per_block;
+    sig.back_scale = p->back_scale;
     if (!p->have_sig || !(sig == p->sig)) {
         if (p->exec) cudaGraphExecDestroy(p->exec);
         if (p->graph) cudaGraphDestroy(p->graph);
@@ -219,6 +227,33 @@ int tkf_pipeline_outputs(const tkf_pipeline *p, tkf_tracks *seeds, tkf_tracks *b
         *fitted = view(p->final_, n, p->max_tracks);
         fitted->hit_idx = p->built.hit_idx;  // the final fit uses the built hit list
     }
+    return TKF_OK;
+}
+
+int tkf_pipeline_set_backward(tkf_pipeline *p, double cov_scale)
+{
+    if (!p) return TKF_ERR_INVALID;
+    if (!(cov_scale >= 0.0) || !std::isfinite(cov_scale))
+        return fail(p->ctx, TKF_ERR_INVALID, "pipeline: cov_scale must be >= 0 and finite");
+    if (cov_scale > 0.0 && !p->back.par) {
+        const size_t es = p->ctx->cfg.precision == TKF_FP64 ? sizeof(double) : sizeof(float);
+        const cudaError_t e = alloc_buf(p->back, p->max_tracks, p->ctx->cfg.n_layers, es);
+        if (e != cudaSuccess) {
+            free_buf(p->back);
+            return fail(p->ctx, e == cudaErrorMemoryAllocation ? TKF_ERR_NOMEM : TKF_ERR_CUDA,
+                        "pipeline: backward buffers");
+        }
+    }
+    p->back_scale = cov_scale;  // a graph captured with another setting is captured again
+    return TKF_OK;
+}
+
+int tkf_pipeline_backward_outputs(const tkf_pipeline *p, tkf_tracks *out)
+{
+    if (!p || !out || !(p->back_scale > 0.0)) return TKF_ERR_INVALID;
+    const int n = p->have_sig ? p->sig.n_tracks : p->max_tracks;
+    *out = view(p->back, n, p->max_tracks);
+    out->hit_idx = p->built.hit_idx;
     return TKF_OK;
 }
 

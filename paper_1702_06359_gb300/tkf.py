@@ -133,6 +133,8 @@ def lib():
         L.tkf_pipeline_run.argtypes = [vp, C.POINTER(Hits), vp, vp, i32, vp]
         L.tkf_pipeline_outputs.argtypes = [vp, C.POINTER(Tracks), C.POINTER(Tracks), C.POINTER(Tracks)]
         L.tkf_pipeline_captures.argtypes = [vp]
+        L.tkf_pipeline_set_backward.argtypes = [vp, C.c_double]
+        L.tkf_pipeline_backward_outputs.argtypes = [vp, C.POINTER(Tracks)]
         L.tkf_pipeline_index.argtypes = [vp]
         L.tkf_pipeline_build_ms.argtypes = [vp, C.POINTER(C.c_float)]
         L.tkf_autotune_build.argtypes = [vp, vp, C.POINTER(Tracks), C.POINTER(Tracks), vp, i32, i32, vp, vp, vp]
@@ -393,6 +395,16 @@ class DevicePipeline:
         sd, b, f = Tracks(), Tracks(), Tracks()
         self.ctx._check(lib().tkf_pipeline_outputs(self.handle, C.byref(sd), C.byref(b), C.byref(f)))
         return sd, b, f
+
+    def set_backward(self, cov_scale=1e4):
+        """tkf_pipeline_set_backward: every following run ends with the backward pass (0: off)."""
+        self.ctx._check(lib().tkf_pipeline_set_backward(self.handle, float(cov_scale)))
+
+    def backward_outputs(self):
+        """The backward pass's states on layer 0 of the last run, as a tkf_tracks struct."""
+        t = Tracks()
+        self.ctx._check(lib().tkf_pipeline_backward_outputs(self.handle, C.byref(t)))
+        return t
 
     def captures(self):
         return lib().tkf_pipeline_captures(self.handle)

@@ -166,3 +166,50 @@ def test_seed_fit_and_continued_fit_agree_with_the_separate_calls(prec):
         assert float(d.abs().max()) < rel
         assert float(((a_.chi2 - b_.chi2).abs() / torch.clamp(a_.chi2.abs(), min=1.0)).max()) < 10 * rel
     assert torch.equal(fused.hit_idx[:3], sh) and bool((fused.hit_idx[3:] == -1).all())
+
+
+def test_backward_stage_equals_the_separate_call():
+    """tkf_pipeline_set_backward adds the backward pass as the step's last stage: its states on
+    layer 1 equal tkf_fit_backward on the pipeline's own fitted tracks (the same kernel, bit for
+    bit), in the graph and with direct launches; enabling and disabling each capture anew."""
+    b = _batch(64)
+    n = b.n_tracks
+    dh = device_hits(b)
+    sh = torch.as_tensor(np.ascontiguousarray(b.trk_hits[:, :3].T), dtype=torch.int32, device="cuda")
+    se = torch.as_tensor(b.trk_event, dtype=torch.int32, device="cuda")
+
+    class _Raw:
+        def __init__(self, t):
+            self.t = t
+
+        def struct(self):
+            return self.t
+    for use_graph in (True, False):
+        ctx = tkf.Context(tkf.default_config())
+        L = ctx.cfg.n_layers
+        pipe = tkf.DevicePipeline(ctx, b.n_hits, b.n_events, n, use_graph=use_graph)
+        with pytest.raises(tkf.TkfError):
+            pipe.backward_outputs()  # no backward stage yet
+        pipe.run(dh, sh, se, n)
+        pipe.set_backward(1e4)
+        for _ in range(2):
+            pipe.run(dh, sh, se, n)
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        if use_graph:
+            assert pipe.captures() == 2
+        got = tkf.tracks_tensors(pipe.backward_outputs(), L)
+        _, built, fitted = pipe.outputs()
+        ref = tkf.DeviceTracks.empty(n, L)
+        ctx.fit_backward(dh, _Raw(fitted), L - 1, 0, ref, cov_scale=1e4, hit_idx=tkf.tracks_tensors(built, L)["hit_idx"])
+        ctx.sync_status()
+        assert torch.equal(got["par"][:, :n], ref.par) and torch.equal(got["cov"][:, :n], ref.cov)
+        assert torch.equal(got["chi2"][:n], ref.chi2) and torch.equal(got["nhits"][:n], ref.nhits)
+        pipe.set_backward(0)
+        pipe.run(dh, sh, se, n)
+        if use_graph:
+            assert pipe.captures() == 3
+        with pytest.raises(tkf.TkfError):
+            pipe.set_backward(-1.0)
+        pipe.close()
+        ctx.close()
