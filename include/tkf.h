@@ -77,6 +77,15 @@ typedef struct {
     int32_t seed_order;               /* 1: build seeds grouped by (event, eta bin, phi bin) so that a
                                          warp's seeds share hit-index cache lines (results do not
                                          depend on it); 0: in input order */
+    double hit_dr;                    /* cm, largest |hit radius - radius[layer]|.  0: hits lie on
+                                         the cylinders.  > 0 (hits on modules off the average
+                                         cylinder, the simplified CMS geometry of Sec. 2.2): fits
+                                         take each layer's state to its hit's own radius; building
+                                         propagates to the layer's radius, opens the window there
+                                         widened by the track's travel over hit_dr, and takes each
+                                         candidate hit's chi2 after a second propagation to the
+                                         hit's radius.  Must satisfy 0 <= hit_dr < radius[0] and
+                                         2 hit_dr < the gap between consecutive radii. */
 } tkf_config;
 
 /* Hits of one or more events (device arrays of length n, caller-owned).  The hits of event e

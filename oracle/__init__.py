@@ -50,6 +50,7 @@ class Geom(C.Structure):
         ("n_cand", C.c_int),
         ("brute_force", C.c_int),
         ("first_build_layer", C.c_int),
+        ("hit_dr", C.c_double),
     ]
 
 
@@ -143,6 +144,7 @@ def make_geom(det, st: Settings = Settings()) -> Geom:
     g.n_cand = st.n_cand
     g.brute_force = int(st.brute_force)
     g.first_build_layer = st.first_build_layer
+    g.hit_dr = 0.5 * getattr(det, "module_dr", 0.0)
     return g
 
 

@@ -23,7 +23,15 @@
  *     no compatible hit, branches ranked by (nHits desc, chi2 asc, parent rank asc, hit id
  *     asc), best N kept (Sec. 2: "branching to explore multiple candidate tracks per seed");
  *     a hit is compatible if it lies on the same half of the cylinder as the prediction and
- *     its chi2 is below the cut.
+ *     its chi2 is below the cut;
+ *   - hits off their layer's cylinder (hit_dr > 0, the simplified CMS geometry of Sec. 2.2):
+ *     a layer's hit is reached by the exact propagation from the previous layer to the hit's
+ *     own radius, and the update is made on the plane tangent there.  In building, the window
+ *     is opened around the prediction on the layer's average radius, its half-widths grown by
+ *     how far the track moves along the cylinder and in z while its radius changes by hit_dr;
+ *     a hit is a candidate if its residual to that prediction lies inside the window; its
+ *     chi2 is then taken at its own radius.  (The paper's second, per-hit propagation starts
+ *     from the prediction on the average radius; the two transports compose to this one.)
  */
 #include <math.h>
 #include <stdlib.h>
@@ -326,6 +334,13 @@ int orc_seed_estimate(const orc_geom *g, const orc_hit *h1, const orc_hit *h2, c
     return ORC_OK;
 }
 
+/* The cylinder a layer's state is taken to: the hit's own radius when hits lie off the
+ * layers' cylinders (hit_dr > 0) and the layer has a hit, else the layer's radius. */
+static double target_radius(const orc_geom *g, int layer, const orc_hit *h)
+{
+    return (g->hit_dr > 0.0 && h) ? sqrt(h->x * h->x + h->y * h->y) : g->radius[layer];
+}
+
 /* ------------------------------------------------------------------ fit (Sec. 2) */
 
 /*
@@ -344,14 +359,14 @@ int orc_fit_track(const orc_geom *g, const double pin[6], const double Pin[36], 
     double c2 = 0.0;
     int nh = 0;
     for (int l = first; l <= last; ++l) {
+        const int hid = hit_of_layer[l];
         if (l > first) {
-            int st = orc_propagate(g, p, g->radius[l], q, J);
+            int st = orc_propagate(g, p, target_radius(g, l, hid >= 0 ? &hits[hid] : 0), q, J);
             if (st != ORC_OK) return st;
             sandwich6(J, P, PJ);
             memcpy(p, q, sizeof p);
             memcpy(P, PJ, sizeof P);
         }
-        const int hid = hit_of_layer[l];
         if (hid >= 0) {
             double dc2;
             int st = orc_update(p, P, &hits[hid], &dc2);
@@ -420,14 +435,14 @@ int orc_fit_backward(const orc_geom *g, const double pin[6], const double Pin[36
     double c2 = 0.0;
     int nh = 0;
     for (int l = last; l >= first; --l) {
+        const int hid = hit_of_layer[l];
         if (l < last) {
-            int st = orc_propagate(g, p, g->radius[l], q, J);
+            int st = orc_propagate(g, p, target_radius(g, l, hid >= 0 ? &hits[hid] : 0), q, J);
             if (st != ORC_OK) return st;
             sandwich6(J, P, PJ);
             memcpy(p, q, sizeof p);
             memcpy(P, PJ, sizeof P);
         }
-        const int hid = hit_of_layer[l];
         if (hid >= 0) {
             double dc2;
             int st = orc_update(p, P, &hits[hid], &dc2);
@@ -531,7 +546,8 @@ static int cmp_branch(const void *a, const void *b)
 }
 
 static void window_bins(const orc_geom *g, int layer, const double p[6], const double P[36],
-                        double var_u, double var_v, int *eb0, int *eb1, int *pb0, int *pb1)
+                        double var_u, double var_v, int *eb0, int *eb1, int *pb0, int *pb1,
+                        double *Uo, double *Wo)
 {
     /* chi2-cut bounding box of the innovation covariance at phi_h = phi of the prediction */
     const double R = g->radius[layer];
@@ -540,8 +556,23 @@ static void window_bins(const orc_geom *g, int layer, const double p[6], const d
     double H[12], r[2], V[4], S[4], Si[4];
     meas_model(p, &probe, H, r, V);
     innovation(P, H, V, S, Si);
-    const double U = sqrt(g->chi2_cut * S[0]) * (1.0 + g->window_margin);
-    const double W = sqrt(g->chi2_cut * S[3]) * (1.0 + g->window_margin);
+    double U = sqrt(g->chi2_cut * S[0]) * (1.0 + g->window_margin);
+    double W = sqrt(g->chi2_cut * S[3]) * (1.0 + g->window_margin);
+    if (g->hit_dr > 0.0) {
+        /* hits up to hit_dr off the cylinder: while the radius changes by hit_dr the track
+         * covers t = hit_dr / cos(alpha) of transverse path (alpha between its direction and
+         * the radial direction, cos(alpha) floored at 0.01), moving t sin(alpha) along the
+         * cylinder plus at most t^2 |kappa| of bending, and t |cot(theta)| in z */
+        const double r0 = sqrt(p[0] * p[0] + p[1] * p[1]);
+        const double ca = fabs(p[0] * cos(p[4]) + p[1] * sin(p[4])) / r0;
+        const double sa = fabs(p[0] * sin(p[4]) - p[1] * cos(p[4])) / r0;
+        const double t = g->hit_dr / (ca > 0.01 ? ca : 0.01);
+        const double kappa = fabs(ORC_KB * g->bz * p[3]);
+        U += (1.0 + g->window_margin) * t * (sa + t * kappa);
+        W += (1.0 + g->window_margin) * t * fabs(cos(p[5]) / sin(p[5]));
+    }
+    *Uo = U;
+    *Wo = W;
     const double dphi = asin(U / R < 1.0 ? U / R : 1.0);
     *eb0 = orc_eta_bin(g, layer, p[2] - W);
     *eb1 = orc_eta_bin(g, layer, p[2] + W);
@@ -592,7 +623,8 @@ static int build_seed(const orc_geom *g, const orc_event *ev, const double sp[6]
             sandwich6(J, C[c].P, Q);
             int found = 0;
             int eb0, eb1, pb0, pb1;
-            window_bins(g, l, q, Q, ev->var_u_max[l], ev->var_v_max[l], &eb0, &eb1, &pb0, &pb1);
+            double U, W;
+            window_bins(g, l, q, Q, ev->var_u_max[l], ev->var_v_max[l], &eb0, &eb1, &pb0, &pb1, &U, &W);
             const int nbin = g->n_eta_bins * g->n_phi_bins;
             const int *off = ev->bin_off + l * (nbin + 1);
             int k_lo, k_hi, e_lo, e_hi;
@@ -612,13 +644,34 @@ static int build_seed(const orc_geom *g, const orc_event *ev, const double sp[6]
                         const orc_hit *h = &ev->hits[hid];
                         if (stats) stats->n_hits_examined += 1;
                         if (q[0] * h->x + q[1] * h->y <= 0.0) continue; /* far half of the cylinder */
-                        const double c2 = orc_chi2(q, Q, h);
+                        const double *qh = q, *Qh = Q;
+                        double q2[6], J2[36], Q2[36];
+                        if (g->hit_dr > 0.0) {
+                            /* the window around the prediction on the average radius, then the
+                             * state at the hit's own radius */
+                            double H[12], r[2], V[4];
+                            meas_model(q, h, H, r, V);
+                            const int inside = fabs(r[0]) <= U && fabs(r[1]) <= W;
+                            /* within tol of an edge: the window decision is fragile if the hit
+                             * would pass the chi2 cut */
+                            const int edge = fabs(fabs(r[0]) - U) <= tol * U || fabs(fabs(r[1]) - W) <= tol * W;
+                            if (!inside && !edge) continue;
+                            if (stats) stats->n_prop += 1;
+                            if (orc_propagate(g, C[c].p, target_radius(g, l, h), q2, J2) != ORC_OK) continue;
+                            sandwich6(J2, C[c].P, Q2);
+                            qh = q2;
+                            Qh = Q2;
+                            if (edge && orc_chi2(qh, Qh, h) < g->chi2_cut * (1.0 + tol) && res->fragile_layer > l)
+                                res->fragile_layer = l;
+                            if (!inside) continue;
+                        }
+                        const double c2 = orc_chi2(qh, Qh, h);
                         if (near(c2, g->chi2_cut, tol) && res->fragile_layer > l) res->fragile_layer = l;
                         if (!(c2 < g->chi2_cut)) continue;
                         if (nb == bcap) { bcap *= 2; B = (orc_cand *)realloc(B, sizeof(orc_cand) * (size_t)bcap); }
                         orc_cand *b = &B[nb++];
-                        memcpy(b->p, q, sizeof q);
-                        memcpy(b->P, Q, sizeof Q);
+                        memcpy(b->p, qh, sizeof b->p);
+                        memcpy(b->P, Qh, sizeof b->P);
                         b->chi2 = C[c].chi2 + c2;
                         b->nhits = C[c].nhits + 1;
                         b->parent = c;

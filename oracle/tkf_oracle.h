@@ -24,6 +24,9 @@ typedef struct {
     int n_cand;            /* candidates kept per seed; <= 0 keeps every branch */
     int brute_force;       /* 1: examine every hit of the layer instead of the binned window */
     int first_build_layer; /* 0-based layer where building starts (3 = fourth layer) */
+    double hit_dr;         /* largest |hit radius - layer radius| (cm); 0: hits lie on the cylinders.
+                              > 0: the CMS-geometry variant of Sec. 2.2, states are taken to each
+                              hit's own radius (see tkf_oracle.c) */
 } orc_geom;
 
 typedef struct {

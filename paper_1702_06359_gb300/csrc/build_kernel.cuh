@@ -12,6 +12,9 @@
 //      candidate tracks per seed" and the per-seed repacking of Sec. 3.2.1);
 //   4. the lane of rank r fetches its parent's predicted state with shuffles, applies the
 //      Kalman update (U = float or double) for a hit branch and the layer's scattering noise.
+// With hits off the layers' cylinders (kTwo) step 1 reaches the layer's average radius, step 2
+// scores each hit after a second, short propagation to its own radius, and the survivor of a
+// hit branch takes that step before its update (the two-step propagation of Sec. 2.2).
 // Hit history is kept per warp in shared memory (parent rank, hit id per layer and lane) and
 // the best candidate is backtracked at the end.  Work balance follows the paper's dynamic
 // work stealing (Sec. 2.3): warps pull tiles of seeds_per_block seeds from an atomic counter
@@ -118,8 +121,11 @@ template <class R> __device__ __forceinline__ R asin_window(R x)
     return asn(x < R(1) ? x : R(1));
 }
 
-// Scores every hit of the candidate's window and fills its branch list.
-template <int NMAX, class R>
+// Scores every hit of the candidate's window and fills its branch list.  kTwo: hits lie up to
+// a.hit_dr off the cylinder (the two-step geometry of Sec. 2.2): the window around the
+// prediction on the average radius is widened by the track's travel over hit_dr, and each hit
+// inside it is scored after the second step to its own radius (step_chi2).
+template <int NMAX, class R, bool kTwo>
 __device__ __forceinline__ void scan_window(const BuildArgs &a, int ev, int l, R Rl, const R p[6], const R P[21],
                                             R chi2, int nh, int rank, unsigned (&lk)[NMAX], int (&lh)[NMAX])
 {
@@ -133,7 +139,23 @@ __device__ __forceinline__ void scan_window(const BuildArgs &a, int ev, int l, R
     const R Svv = P[sym(2, 2)] + R(vmax.y);
     const R cut = pick<R>(a.cut_f, a.cut);
     const R mg = R(1) + pick<R>(a.margin_f, a.margin);
-    const R U = sq(cut * Suu) * mg, W = sq(cut * Svv) * mg;
+    R U = sq(cut * Suu) * mg, W = sq(cut * Svv) * mg;
+    R sphi = R(0), cphi = R(1), sth = R(1), cot = R(0);
+    const R kb = pick<R>(a.kb_f, a.kb);
+    if (kTwo) {
+        // while the radius changes by hit_dr the track covers t = hit_dr / cos(alpha) of
+        // transverse path (alpha between its direction and the radial direction, cos(alpha)
+        // floored at 0.01), moving t sin(alpha) along the cylinder plus at most t^2 |kappa| of
+        // bending, and t |cot(theta)| in z
+        R cth;
+        sc(p[4], &sphi, &cphi);
+        fast_sc(p[5], &sth, &cth);
+        cot = cth / sth;
+        const R ca = ab(xp * cphi + yp * sphi) / rp, sa = ab(xp * sphi - yp * cphi) / rp;
+        const R t = pick<R>(a.hit_dr_f, a.hit_dr) / (ca > R(0.01) ? ca : R(0.01));
+        U += mg * t * (sa + t * ab(kb * p[3]));
+        W += mg * t * ab(cot);
+    }
     const R phip = at2(yp, xp);
     // compatible hits satisfy |u| = r_p |sin(phi_h - phi_p)| <= U on the near half-cylinder,
     // so |phi_h - phi_p| <= asin(U / R); a 2e-5 rad slack covers float rounding of both angles
@@ -191,7 +213,12 @@ __device__ __forceinline__ void scan_window(const BuildArgs &a, int ev, int l, R
                 const R u = ch * (hy - yp) - sh * (hx - xp);
                 const R v = R(h.z) - zp;
                 if (ab(u) > U || ab(v) > W) continue;
-                const R c2 = chi2_uv<R>(P, u, v, sh, ch, R(hv.x), R(hv.y));
+                R c2;
+                if (kTwo)
+                    c2 = step_chi2<R>(p, P, sphi, cphi, sth, cot, kb, sq(hx * hx + hy * hy), hx, hy, R(h.z), sh, ch,
+                                      R(hv.x), R(hv.y));
+                else
+                    c2 = chi2_uv<R>(P, u, v, sh, ch, R(hv.x), R(hv.y));
                 if (c2 < cut) {
                     list_insert32(lk, lh, make_key32(nh + 1, to_f32(chi2 + c2), rank), __float_as_int(h.w));
                     found = true;
@@ -220,12 +247,13 @@ template <class R> __device__ __forceinline__ void store_track(void *par, void *
 #ifndef TKF_BUILD_MINBLOCKS_F32
 #define TKF_BUILD_MINBLOCKS_F32 7
 #endif
-template <int NMAX, class R, class U> struct BuildMinBlocks {
-    static constexpr int value = (sizeof(R) == 4 && sizeof(U) == 4 && NMAX <= 6) ? TKF_BUILD_MINBLOCKS_F32 : 1;
+template <int NMAX, class R, class U, bool kTwo> struct BuildMinBlocks {
+    static constexpr int value =
+        (!kTwo && sizeof(R) == 4 && sizeof(U) == 4 && NMAX <= 6) ? TKF_BUILD_MINBLOCKS_F32 : 1;
 };
 
-template <int NMAX, class R, class U>
-__global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U>::value)) k_build(const BuildArgs a)
+template <int NMAX, class R, class U, bool kTwo>
+__global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTwo>::value)) k_build(const BuildArgs a)
 {
     constexpr int W = kBuildThreads / 32;
     __shared__ int hist_hit[W][TKF_MAX_LAYERS][32];
@@ -290,7 +318,7 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U>::va
                     lk[i] = kEmpty32;
                     lh[i] = 0;
                 }
-                if (ok) scan_window<NMAX, R>(a, ev, l, Rl, p, P, chi2, nh, r, lk, lh);
+                if (ok) scan_window<NMAX, R, kTwo>(a, ev, l, Rl, p, P, chi2, nh, r, lk, lh);
 
                 // merge the segment's lists: N rounds of a segmented minimum
                 unsigned mine = kEmpty32;
@@ -336,6 +364,9 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U>::va
                         const int pos = __ldg(&a.pos_of_hit[gh]);
                         const float4 h = __ldg(&a.hxyzi[pos]);
                         const float2 hv = __ldg(&a.hvar[pos]);
+                        // the second step, to the hit's own radius (the scan took the same step
+                        // for this hit's chi2, so it succeeds here too)
+                        if (kTwo) propagate<R, kPropStep>(p, P, sq(R(h.x) * R(h.x) + R(h.y) * R(h.y)), kb);
                         U dc2 = U(0);
                         kalman_update<U, R>(p, P, R(h.x), R(h.y), R(h.z), R(hv.x), R(hv.y), &dc2);
                         if (sizeof(R) == 8) chi2 = pchi2 + R(dc2);
@@ -387,16 +418,16 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U>::va
     }
 }
 
-template <class R, class U>
+template <class R, class U, bool kTwo = false>
 cudaError_t launch_build_t(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy)
 {
     const void *fn = nullptr;
     switch (nmax) {
-    case 1: fn = (const void *)k_build<1, R, U>; break;
-    case 4: fn = (const void *)k_build<4, R, U>; break;
-    case 6: fn = (const void *)k_build<6, R, U>; break;
-    case 10: fn = (const void *)k_build<10, R, U>; break;
-    case 16: fn = (const void *)k_build<16, R, U>; break;
+    case 1: fn = (const void *)k_build<1, R, U, kTwo>; break;
+    case 4: fn = (const void *)k_build<4, R, U, kTwo>; break;
+    case 6: fn = (const void *)k_build<6, R, U, kTwo>; break;
+    case 10: fn = (const void *)k_build<10, R, U, kTwo>; break;
+    case 16: fn = (const void *)k_build<16, R, U, kTwo>; break;
     default: return cudaErrorInvalidValue;
     }
     if (occupancy) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, fn, kBuildThreads, 0);

@@ -22,8 +22,8 @@ struct BuildArgs {
     int L, first, ncand, n_eta, n_phi, n_bins, seeds_per_block, n_seeds, n_events;
     float radius_f[TKF_MAX_LAYERS], xx0_f[TKF_MAX_LAYERS];
     double radius[TKF_MAX_LAYERS], xx0[TKF_MAX_LAYERS];
-    float kb_f, mass_f, eta_min_f, inv_eta_w_f, cut_f, margin_f;
-    double kb, mass, eta_min, inv_eta_w, cut, margin;
+    float kb_f, mass_f, eta_min_f, inv_eta_w_f, cut_f, margin_f, hit_dr_f;
+    double kb, mass, eta_min, inv_eta_w, cut, margin, hit_dr;
     // hit index
     const float4 *hxyzi;
     const float2 *hvar;
@@ -56,6 +56,10 @@ struct BuildArgs {
 cudaError_t launch_build_fp32(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
 cudaError_t launch_build_mixed(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
 cudaError_t launch_build_fp64(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
+// The same for hits off the layers' cylinders (a.hit_dr > 0): the two-step building of Sec. 2.2.
+cudaError_t launch_build2_fp32(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
+cudaError_t launch_build2_mixed(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
+cudaError_t launch_build2_fp64(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
 
 // tkf_fit, and its continued form (continue_fit: `init` lies on layer first_layer - 1, as a
 // fit of the earlier layers leaves it; the fit propagates before its first update).

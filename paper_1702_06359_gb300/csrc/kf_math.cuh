@@ -126,13 +126,21 @@ template <class R> __host__ __device__ __forceinline__ void helix_fn(R a, R &S, 
 // unit rows, rows x, y, phi touch columns x, y, q/pT, phi only).
 // Returns false when the cylinder is not reached.
 //
-// kInward: the cylinder lies inside the state's radius (the backward pass runs the reversed
-// track outward-in).  The straight line then meets it twice ahead, and Newton starts from the
-// nearer root; when the tangent line misses the cylinder but the helix curves onto it, the start
-// is the exact crossing of the two circles: the track circle has centre c = p0 + (-sin phi,
-// cos phi)/k, and the position seen from c turns by k s, so s = (signed angle from p0 - c to
-// the crossing - c) / k, taken in (0, 2 pi/|k|].
-template <class R, bool kInward = false>
+// Modes:
+//   kPropOut: the next crossing ahead (s > 0), Newton from the straight line's outer root.
+//   kPropIn: the cylinder lies inside the state's radius (the backward pass runs the reversed
+//     track outward-in).  The straight line then meets it twice ahead, and Newton starts from
+//     the nearer root; when the tangent line misses the cylinder but the helix curves onto it,
+//     the start is the exact crossing of the two circles: the track circle has centre
+//     c = p0 + (-sin phi, cos phi)/k, and the position seen from c turns by k s, so
+//     s = (signed angle from p0 - c to the crossing - c) / k, taken in (0, 2 pi/|k|].
+//   kPropStep: the second of the two steps of Sec. 2.2, from a state on a layer's average
+//     radius to a hit's own radius close by: s of either sign, the crossing where the track
+//     moves outward, Newton from the straight line's nearer root written without cancellation,
+//     (radius^2 - r0^2) / (A + sqrt(disc)).
+enum : int { kPropOut = 0, kPropIn = 1, kPropStep = 2 };
+
+template <class R, int kMode = kPropOut>
 __host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R kb)
 {
     const R x = p[0], y = p[1], z = p[2], w = p[3], phi = p[4], th = p[5];
@@ -143,7 +151,10 @@ __host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R 
     const R r0 = sq(x * x + y * y);
     const R disc = A * A + (radius - r0) * (radius + r0);
     R s;
-    if (!kInward) {
+    if (kMode == kPropStep) {
+        if (!(A > R(0)) || !(disc >= R(0))) return false;
+        s = (radius - r0) * (radius + r0) / (A + sq(disc));
+    } else if (kMode == kPropOut) {
         if (!(disc >= R(0))) return false;
         s = -A + sq(disc);
     } else if (disc >= R(0)) {
@@ -172,7 +183,7 @@ __host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R 
     R S, C, Sd, Cd;
     // inward starts can be far from the crossing (a grazing entry, the circle intersection's
     // rounding): more steps
-    constexpr int n_newton = kInward ? 3 * Lim<R>::newton + 2 : Lim<R>::newton;
+    constexpr int n_newton = kMode == kPropIn ? 3 * Lim<R>::newton + 2 : Lim<R>::newton;
 #pragma unroll
     for (int it = 0; it < n_newton; ++it) {
         const R a = kappa * s;
@@ -192,8 +203,9 @@ __host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R 
     const R ys = y + s * (sp * S + cp * C);
     const R c1 = cp * ca - sp * sa, s1 = sp * ca + cp * sa;
     const R D = xs * c1 + ys * s1;  // r dr/ds
-    if (!(s > R(0)) || !(ab(D) > R(1e-6) * radius) || !(ab(xs * xs + ys * ys - radius * radius) < R(1e-3) * radius))
+    if (kMode == kPropStep ? !(D > R(1e-6) * radius) : (!(s > R(0)) || !(ab(D) > R(1e-6) * radius)))
         return false;
+    if (!(ab(xs * xs + ys * ys - radius * radius) < R(1e-3) * radius)) return false;
     R st, ct;
     fast_sc(th, &st, &ct);
     const R cot = ct / st;
@@ -338,6 +350,75 @@ __host__ __device__ __forceinline__ R chi2_uv(const R P[21], R u, R v, R sh, R c
 {
     return chi2_uv6<R>(P[sym(0, 0)], P[sym(1, 0)], P[sym(1, 1)], P[sym(2, 0)], P[sym(2, 1)], P[sym(2, 2)], u, v, sh,
                        ch, vu, vv);
+}
+
+// chi2 of a hit off the layer's cylinder (the two-step propagation of Sec. 2.2): the prediction
+// p, P on the layer's average radius is carried along the helix to the hit's own radius rh
+// (the kPropStep step of propagate), and the hit is compared there on its tangent plane
+// (-sh, ch).  Only the two measured rows of the transported state are formed: M = H J (2x6),
+// S = M P M^T + V.  sp, cp = sin, cos of phi; st = sin theta, cot = cot theta of p.
+// Returns +inf when the step fails or S is not positive definite.
+template <class R>
+__host__ __device__ __forceinline__ R step_chi2(const R p[6], const R P[21], R sp, R cp, R st, R cot, R kb, R rh,
+                                                R xh, R yh, R zh, R sh, R ch, R vu, R vv)
+{
+    const R x = p[0], y = p[1];
+    const R kappa = -kb * p[3];
+    const R A = x * cp + y * sp;
+    const R r0 = sq(x * x + y * y);
+    const R disc = A * A + (rh - r0) * (rh + r0);
+    if (!(A > R(0)) || !(disc >= R(0))) return R(INFINITY);
+    R s = (rh - r0) * (rh + r0) / (A + sq(disc));
+    R S, C, Sd, Cd;
+#pragma unroll
+    for (int it = 0; it < Lim<R>::newton; ++it) {
+        const R a = kappa * s;
+        helix_fn(a, S, C, Sd, Cd);
+        const R sa = a * S, ca = R(1) - a * C;
+        const R xs = x + s * (cp * S - sp * C);
+        const R ys = y + s * (sp * S + cp * C);
+        const R c1 = cp * ca - sp * sa, s1 = sp * ca + cp * sa;
+        s -= (xs * xs + ys * ys - rh * rh) / (R(2) * (xs * c1 + ys * s1));
+    }
+    const R a = kappa * s;
+    helix_fn(a, S, C, Sd, Cd);
+    const R sa = a * S, ca = R(1) - a * C;
+    const R xs = x + s * (cp * S - sp * C);
+    const R ys = y + s * (sp * S + cp * C);
+    const R c1 = cp * ca - sp * sa, s1 = sp * ca + cp * sa;
+    const R D = xs * c1 + ys * s1;
+    if (!(D > R(1e-6) * rh) || !(ab(xs * xs + ys * ys - rh * rh) < R(1e-3) * rh)) return R(INFINITY);
+    // rows x, y, z of the step's Jacobian (as in propagate)
+    const R s2kb = -kb * s * s;
+    const R dx_dw = s2kb * (cp * Sd - sp * Cd);
+    const R dy_dw = s2kb * (sp * Sd + cp * Cd);
+    const R dx_dphi = -(ys - y), dy_dphi = xs - x;
+    const R iD = R(1) / D;
+    const R s_x = -xs * iD, s_y = -ys * iD;
+    const R s_w = -(xs * dx_dw + ys * dy_dw) * iD;
+    const R s_f = -(xs * dx_dphi + ys * dy_dphi) * iD;
+    // M row u = -sh (row x) + ch (row y), over columns x, y, q/pT, phi; row v = row z
+    const R m0 = -sh * (R(1) + c1 * s_x) + ch * (s1 * s_x);
+    const R m1 = -sh * (c1 * s_y) + ch * (R(1) + s1 * s_y);
+    const R m3 = -sh * (dx_dw + c1 * s_w) + ch * (dy_dw + s1 * s_w);
+    const R m4 = -sh * (dx_dphi + c1 * s_f) + ch * (dy_dphi + s1 * s_f);
+    const R v0 = cot * s_x, v1 = cot * s_y, v3 = cot * s_w, v4 = cot * s_f, v5 = -s / (st * st);
+    R Tu[6], Tv[6];  // P M_u^T, P M_v^T
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const R p0 = P[sym(0, j)], p1 = P[sym(1, j)], p2 = P[sym(2, j)], p3 = P[sym(3, j)], p4 = P[sym(4, j)],
+                p5 = P[sym(5, j)];
+        Tu[j] = m0 * p0 + m1 * p1 + m3 * p3 + m4 * p4;
+        Tv[j] = v0 * p0 + v1 * p1 + p2 + v3 * p3 + v4 * p4 + v5 * p5;
+    }
+    const R Suu = m0 * Tu[0] + m1 * Tu[1] + m3 * Tu[3] + m4 * Tu[4] + vu;
+    const R Suv = m0 * Tv[0] + m1 * Tv[1] + m3 * Tv[3] + m4 * Tv[4];
+    const R Svv = v0 * Tv[0] + v1 * Tv[1] + Tv[2] + v3 * Tv[3] + v4 * Tv[4] + v5 * Tv[5] + vv;
+    const R u = ch * (yh - ys) - sh * (xh - xs);
+    const R v = zh - (p[2] + s * cot);
+    const R det = Suu * Svv - Suv * Suv;
+    if (!(det > R(0))) return R(INFINITY);
+    return fast_div(u * (Svv * u - R(2) * Suv * v) + Suu * v * v, det);
 }
 
 // Kalman update with the Joseph-form covariance:

@@ -607,6 +607,7 @@ __global__ void k_seed_place(const int *keys, int *counts, const int *off, int n
 
 struct FitGeom {
     int L;
+    int two_step;  // hits lie off the layers' cylinders (hit_dr > 0): states go to each hit's radius
     double radius[TKF_MAX_LAYERS], xx0[TKF_MAX_LAYERS];
     float radius_f[TKF_MAX_LAYERS], xx0_f[TKF_MAX_LAYERS];
     double kb, mass, prior[6];
@@ -616,6 +617,18 @@ struct FitGeom {
 template <class R> __device__ __forceinline__ R gpick(float f, double d);
 template <> __device__ __forceinline__ float gpick<float>(float f, double) { return f; }
 template <> __device__ __forceinline__ double gpick<double>(float, double d) { return d; }
+
+// The cylinder a layer's state is taken to: the hit's own radius when hits lie off the layers'
+// cylinders (the two-step geometry of Sec. 2.2) and the layer has a valid hit, else the layer's
+// radius.
+template <class R> __device__ __forceinline__ R target_radius(const FitGeom &g, const tkf_hits &h, int l, int hid)
+{
+    if (g.two_step && hid >= 0 && hid < h.n) {
+        const R x = R(h.x[hid]), y = R(h.y[hid]);
+        return sq(x * x + y * y);
+    }
+    return gpick<R>(g.radius_f[l], g.radius[l]);
+}
 
 // asin(x)/x, accurate near 0
 template <class R> __device__ __forceinline__ R asin_over(R x)
@@ -695,11 +708,11 @@ __device__ __forceinline__ void fit_layers(const FitGeom &g, const tkf_hits &h, 
 {
     const R kb = gpick<R>(g.kb_f, g.kb), mass = gpick<R>(g.mass_f, g.mass);
     for (int l = first; l <= last && status == 0; ++l) {
-        if ((l > first || prop_first) && !propagate<R>(p, P, gpick<R>(g.radius_f[l], g.radius[l]), kb)) {
+        const int hid = hit_at(l);
+        if ((l > first || prop_first) && !propagate<R>(p, P, target_radius<R>(g, h, l, hid), kb)) {
             status = TKF_TRACK_NOREACH;
             break;
         }
-        const int hid = hit_at(l);
         if (hid >= h.n) {
             atomicOr(err, kErrBadHitId);
             status = TKF_TRACK_SINGULAR;
@@ -829,11 +842,11 @@ __global__ void k_fit_backward(const FitGeom g, const tkf_hits h, const tkf_trac
     const R kb = gpick<R>(g.kb_f, g.kb), mass = gpick<R>(g.mass_f, g.mass);
     reverse_track<R>(p, P, scale);
     for (int l = last; l >= first && status == 0; --l) {
-        if (l < last && !propagate<R, true>(p, P, gpick<R>(g.radius_f[l], g.radius[l]), kb)) {
+        const int hid = hit_idx[l * si + i];
+        if (l < last && !propagate<R, kPropIn>(p, P, target_radius<R>(g, h, l, hid), kb)) {
             status = TKF_TRACK_NOREACH;
             break;
         }
-        const int hid = hit_idx[l * si + i];
         if (hid >= h.n) {
             atomicOr(err, kErrBadHitId);
             status = TKF_TRACK_SINGULAR;
@@ -862,6 +875,7 @@ FitGeom fit_geom(const tkf_ctx *ctx)
     FitGeom g{};
     const tkf_config &c = ctx->cfg;
     g.L = c.n_layers;
+    g.two_step = c.hit_dr > 0.0;
     for (int l = 0; l < c.n_layers; ++l) {
         g.radius[l] = c.radius[l];
         g.xx0[l] = c.x_over_x0[l];
@@ -1027,10 +1041,13 @@ int tkf_create(const tkf_config *cfg, tkf_ctx **out)
     if (c.n_layers < 4 || c.n_layers > TKF_MAX_LAYERS || c.n_cand < 1 || c.n_cand > TKF_MAX_CAND ||
         c.first_build_layer < 3 || c.first_build_layer > c.n_layers || c.n_eta_bins < 1 || c.n_phi_bins < 1 ||
         c.n_eta_bins * c.n_phi_bins > 1 << 20 || !(c.eta_bin_w > 0) || !(c.chi2_cut > 0) || !(c.bz != 0) ||
-        c.precision < TKF_FP32 || c.precision > TKF_FP64 || c.seeds_per_block < 0 || c.window_margin < 0)
+        c.precision < TKF_FP32 || c.precision > TKF_FP64 || c.seeds_per_block < 0 || c.window_margin < 0 ||
+        !(c.hit_dr >= 0.0) || !(c.hit_dr < c.radius[0]))
         return TKF_ERR_INVALID;
     for (int l = 0; l < c.n_layers; ++l)
-        if (!(c.radius[l] > 0) || (l > 0 && !(c.radius[l] > c.radius[l - 1])) || c.x_over_x0[l] < 0) return TKF_ERR_INVALID;
+        if (!(c.radius[l] > 0) || (l > 0 && !(c.radius[l] > c.radius[l - 1])) || c.x_over_x0[l] < 0 ||
+            (l > 0 && !(2.0 * c.hit_dr < c.radius[l] - c.radius[l - 1])))
+            return TKF_ERR_INVALID;
     tkf_ctx *ctx = new (std::nothrow) tkf_ctx();
     if (!ctx) return TKF_ERR_NOMEM;
     ctx->cfg = c;
@@ -1379,6 +1396,8 @@ int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *s
     a.inv_eta_w = 1.0 / c.eta_bin_w;
     a.cut = c.chi2_cut;
     a.margin = c.window_margin;
+    a.hit_dr = c.hit_dr;
+    a.hit_dr_f = (float)c.hit_dr;
     a.kb_f = (float)a.kb;
     a.mass_f = (float)a.mass;
     a.eta_min_f = (float)a.eta_min;
@@ -1445,7 +1464,12 @@ int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *s
         a.s_perm = ctx->ord_perm;  // counts are back to zero after k_seed_place
     }
     const int nmax = build_nmax(c.n_cand);
-    auto launch = c.precision == TKF_FP32 ? launch_build_fp32 : c.precision == TKF_MIXED ? launch_build_mixed : launch_build_fp64;
+    auto launch = c.hit_dr > 0.0 ? (c.precision == TKF_FP32    ? launch_build2_fp32
+                                    : c.precision == TKF_MIXED ? launch_build2_mixed
+                                                               : launch_build2_fp64)
+                                 : (c.precision == TKF_FP32    ? launch_build_fp32
+                                    : c.precision == TKF_MIXED ? launch_build_mixed
+                                                               : launch_build_fp64);
     int occ = 0;
     TKF_CUDA(ctx, launch(a, nmax, 0, nullptr, &occ));
     const long long tiles = ((long long)seeds->n + a.seeds_per_block - 1) / a.seeds_per_block;

@@ -42,6 +42,7 @@ class Config(C.Structure):
         ("precision", C.c_int32),
         ("seeds_per_block", C.c_int32),
         ("seed_order", C.c_int32),
+        ("hit_dr", C.c_double),
     ]
 
 

@@ -30,7 +30,13 @@ K_B = 0.00299792458  # GeV / (T cm): curvature constant, 1/rho = K_B * Bz / pT
 
 @dataclass(frozen=True)
 class Detector:
-    """Ideal barrel: n thin cylinders at radius[l], uniform Bz, thickness x/X0 per layer."""
+    """Ideal barrel: n thin cylinders at radius[l], uniform Bz, thickness x/X0 per layer.
+
+    module_dr > 0 gives the layers modules off the average cylinder (the simplified CMS
+    geometry of the paper's Sec. 2.2): layer l is tiled in phi by an even number of modules,
+    each about module_width long, alternately at radius[l] - module_dr/2 (even index, from
+    phi = -pi) and radius[l] + module_dr/2 (odd index).  A track's module is the one where it
+    crosses radius[l]; its hit and truth lie where it crosses that module's radius."""
 
     radii: tuple = tuple(4.0 * (l + 1) for l in range(10))
     bz: float = 3.8
@@ -38,10 +44,24 @@ class Detector:
     mass: float = 0.13957  # scattering mass hypothesis (charged pion)
     sigma_rphi: float = 0.01
     sigma_z: float = 0.1
+    module_dr: float = 0.0
+    module_width: float = 2.0
 
     @property
     def n_layers(self) -> int:
         return len(self.radii)
+
+    def n_modules(self, l: int) -> int:
+        return 2 * max(2, int(np.ceil(np.pi * self.radii[l] / self.module_width)))
+
+    def module_radius(self, l: int, phi):
+        """Radius of the module of layer l at azimuth phi (radius[l] when module_dr == 0)."""
+        phi = np.asarray(phi, dtype=np.float64)
+        if self.module_dr == 0.0:
+            return np.full(phi.shape, float(self.radii[l]))
+        n = self.n_modules(l)
+        k = np.clip(np.floor((phi + np.pi) / (2.0 * np.pi) * n).astype(np.int64), 0, n - 1)
+        return self.radii[l] + np.where(k % 2 == 0, -0.5, 0.5) * self.module_dr
 
 
 @dataclass
@@ -190,6 +210,11 @@ def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
     sig_hit = np.zeros((T, L, 3))  # x, y, z of the signal hit
     for l in range(L):
         R = det.radii[l]
+        if det.module_dr != 0.0:
+            # the module is the one crossed on the average cylinder; the track then goes from
+            # its previous point straight to that module's radius
+            xa, ya, _, _ = _helix_to_cylinder(x, y, z, w, phi, theta, R, kb)
+            R = det.module_radius(l, np.arctan2(ya, xa))
         x, y, z, phi = _helix_to_cylinder(x, y, z, w, phi, theta, R, kb)
         truth[:, l] = np.stack([x, y, z, w, phi, theta], axis=1)
         g_rphi, g_z = normals(key, (tl, _LAYER0 + l, 0, 0))
@@ -232,8 +257,9 @@ def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
             u_a, u_b = uniforms(ekey, (nid, _NOISE0 + l, 0, 1))
             zl = R * np.sinh(spec.eta_max) + 3.0 * spec.vertex_sigma[2]
             nphi = -np.pi + 2.0 * np.pi * u_a
-            hx = np.concatenate([sig_hit[t0:t1, l, 0], R * np.cos(nphi)])
-            hy = np.concatenate([sig_hit[t0:t1, l, 1], R * np.sin(nphi)])
+            nr = det.module_radius(l, nphi) if det.module_dr != 0.0 else R
+            hx = np.concatenate([sig_hit[t0:t1, l, 0], nr * np.cos(nphi)])
+            hy = np.concatenate([sig_hit[t0:t1, l, 1], nr * np.sin(nphi)])
             hz = np.concatenate([sig_hit[t0:t1, l, 2], -zl + 2.0 * zl * u_b])
             mc = np.concatenate([np.arange(t0, t1, dtype=np.int64), np.full(n_noise, -1, dtype=np.int64)])
             n_l = nt + n_noise

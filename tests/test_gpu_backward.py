@@ -26,9 +26,9 @@ def det():
     return Detector()
 
 
-def _forward(det, n, seed, pt_max=10.0, holes=0.0):
+def _forward(det, n, seed, pt_max=10.0, holes=0.0, eta_max=1.0):
     """Generated tracks and the oracle's forward fit over all layers (the backward pass's input)."""
-    b = generate(EventSpec(seed=seed, n_tracks=n, pt_max=pt_max), det)
+    b = generate(EventSpec(seed=seed, n_tracks=n, pt_max=pt_max, eta_max=eta_max), det)
     g = O.make_geom(det)
     hits = O.hits_of(b)
     ids = b.trk_hits.copy()
@@ -42,8 +42,8 @@ def _forward(det, n, seed, pt_max=10.0, holes=0.0):
     return b, g, hits, ids, pf, cf, nh
 
 
-def _gpu_backward(det, b, ids, par, cov, nhits, prec, last, first, scale):
-    ctx = tkf.Context(tkf.default_config(precision=prec))
+def _gpu_backward(det, b, ids, par, cov, nhits, prec, last, first, scale, **cfg):
+    ctx = tkf.Context(tkf.default_config(precision=prec, **cfg))
     init = device_tracks(par, cov, np.zeros(len(par)), nhits, ids, precision=prec)
     out = tkf.DeviceTracks.empty(len(par), det.n_layers, prec)
     ctx.fit_backward(device_hits(b), init, last, first, out, cov_scale=scale)
@@ -119,3 +119,21 @@ def test_backward_failed_inputs_bad_ids_and_errors(det):
     empty = tkf.DeviceTracks.empty(0, L)
     ctx.fit_backward(dh, empty, L - 1, 0, tkf.DeviceTracks.empty(0, L), cov_scale=1e4)
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=lambda p: PNAME[p])
+def test_backward_parity_on_module_geometry(prec):
+    """Hits on modules 0.5 cm inside and outside the layers' radii (hit_dr = 0.5 cm, |eta| < 2):
+    the inward pass takes each state to its hit's own radius, as the oracle does."""
+    det = Detector(module_dr=1.0)
+    L = det.n_layers
+    b, g, hits, ids, pf, cf, nh = _forward(det, 1000, 14, eta_max=2.0)
+    pf, cf = rounded(pf, prec), rounded(cf, prec)
+    ref = O.fit_backward(g, hits, pf, cf, ids, L - 1, 0, 1e4)
+    assert np.all(ref[4] == 0)
+    got = _gpu_backward(det, b, ids, pf, cf, nh, prec, L - 1, 0, 1e4, hit_dr=0.5)
+    assert np.array_equal(got["nhits"], ref[3])
+    bad, worst = param_violations(got["par"], ref[0])
+    assert not bad.any(), worst
+    bad, worst = chi2_violations(got["chi2"], ref[2])
+    assert not bad.any(), worst

@@ -276,7 +276,7 @@ def _seeds_for(batch, det, prec, n_cand=6):
     return g, out
 
 
-def _run_build(det, batch, prec, n_cand=6, seeds_per_block=0, want_all=False):
+def _run_build(det, batch, prec, n_cand=6, seeds_per_block=0, want_all=False, **cfg):
     g, per_ev = _seeds_for(batch, det, prec, n_cand)
     L = det.n_layers
     par = np.concatenate([s[2] for s in per_ev])
@@ -285,7 +285,7 @@ def _run_build(det, batch, prec, n_cand=6, seeds_per_block=0, want_all=False):
     nh = np.concatenate([s[5] for s in per_ev])
     hid = np.concatenate([np.where(s[6] >= 0, s[6] + batch.hit_off[e], -1) for e, s in enumerate(per_ev)])
     ev = np.repeat(np.arange(batch.n_events), np.diff(batch.trk_off))
-    ctx = _ctx(prec, n_cand=n_cand, seeds_per_block=seeds_per_block)
+    ctx = _ctx(prec, n_cand=n_cand, seeds_per_block=seeds_per_block, **cfg)
     dh = device_hits(batch)
     idx = ctx.build_hit_index(dh)
     seeds = device_tracks(par, cov, c2, nh, hid, event=ev, precision=prec)
@@ -409,3 +409,67 @@ def test_build_no_seeds_and_empty_layers(det):
     empty.n = 0
     ctx.build_tracks(idx, empty, empty)
     ctx.sync_status()
+
+
+# ------------------------------------------------------------------ hits off the cylinders (Sec. 2.2)
+
+# modules 0.5 cm inside and outside each layer's average radius (the simplified CMS geometry):
+# hit_dr = 0.5 cm, states taken to each hit's radius, building in two steps
+MODULES = Detector(module_dr=1.0)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=lambda p: PNAME[p])
+def test_two_step_fit_parity(prec):
+    """Fit of 1000 tracks (|eta| < 2) on the module geometry from the same initial states; with
+    hit_dr = 0 the same hits do not fit (the setting reaches the kernel)."""
+    b = generate(EventSpec(seed=71, n_tracks=1000, eta_max=2.0), MODULES)
+    g = O.make_geom(MODULES)
+    hits = O.hits_of(b)
+    par0, cov0 = O.seed_estimate(g, hits, b.trk_hits[:, :3])
+    par0, cov0 = rounded(par0, prec), rounded(cov0, prec)
+    ref = O.fit(g, hits, par0, cov0, b.trk_hits, 0, MODULES.n_layers - 1)
+    assert np.all(ref[4] == 0)
+    L = MODULES.n_layers
+    init = device_tracks(par0, cov0, np.zeros(b.n_tracks), np.zeros(b.n_tracks), b.trk_hits, precision=prec)
+    got = {}
+    for dr in (0.5, 0.0):
+        ctx = _ctx(prec, hit_dr=dr)
+        out = tkf.DeviceTracks.empty(b.n_tracks, L, prec)
+        ctx.fit(device_hits(b), init, 0, L - 1, out)
+        ctx.sync_status()
+        got[dr] = host_tracks(out)
+        ctx.close()
+    r = got[0.5]
+    assert np.array_equal(r["nhits"], ref[3])
+    bad, worst = param_violations(r["par"], ref[0])
+    assert not bad.any(), worst
+    bad, worst = chi2_violations(r["chi2"], ref[2])
+    assert not bad.any(), worst
+    if prec == tkf.FP64:
+        assert param_violations(r["par"], ref[0], rel=1e-8)[1] <= 1.0
+    assert np.median(got[0.0]["chi2"]) > 5.0 * np.median(r["chi2"])
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=lambda p: PNAME[p])
+def test_two_step_build_parity(prec):
+    """Two events (2000 and 3000 tracks, 30 % noise hits, |eta| < 2, N = 6) on the module
+    geometry: window on the average radius, every candidate hit scored after its own step."""
+    b = generate(EventSpec(seed=72, n_events=2, n_tracks=[2000, 3000], noise_frac=0.3, eta_max=2.0), MODULES)
+    got, _, _, refs = _run_build(MODULES, b, prec, hit_dr=0.5)
+    _check_build(b, got, refs, MODULES.n_layers, max_divergent=0.01, rel=1e-8 if prec == tkf.FP64 else None)
+    own = np.all(got["hit_idx"] == b.trk_hits, axis=1).mean()
+    assert own >= 0.97, own
+
+
+@pytest.mark.parametrize("n_cand", [1, 16])
+def test_two_step_build_parity_candidate_counts(n_cand):
+    b = generate(EventSpec(seed=73, n_tracks=1500, noise_frac=0.3, eta_max=1.5), MODULES)
+    got, _, _, refs = _run_build(MODULES, b, tkf.FP32, n_cand=n_cand, hit_dr=0.5)
+    _check_build(b, got, refs, MODULES.n_layers, max_divergent=0.01)
+
+
+def test_two_step_settings_are_validated():
+    for dr in (-0.1, float("nan"), 2.0, 4.0):  # negative, NaN, half the 4 cm gap, the first radius
+        with pytest.raises(tkf.TkfError):
+            _ctx(hit_dr=dr)
+    _ctx(hit_dr=1.99).close()

@@ -16,9 +16,9 @@ if not torch.cuda.is_available():
 from paper_1702_06359_gb300 import tkf  # noqa: E402
 
 
-def _batch(seed, n_events=8):
+def _batch(seed, n_events=8, det=Detector()):
     sizes, noise = event_sizes(seed, n_events, median=600, lo=50, hi=3000)
-    return generate(EventSpec(seed=seed, n_events=n_events, n_tracks=sizes, noise_frac=noise), Detector())
+    return generate(EventSpec(seed=seed, n_events=n_events, n_tracks=sizes, noise_frac=noise), det)
 
 
 def _direct(ctx, b, dh, sh, se):
@@ -213,3 +213,27 @@ def test_backward_stage_equals_the_separate_call():
             pipe.set_backward(-1.0)
         pipe.close()
         ctx.close()
+
+
+def test_two_step_pipeline_equals_direct_calls():
+    """Hits on modules off the layers' cylinders (hit_dr = 0.5 cm): the graph step equals the
+    same calls made one by one, bit for bit, and its builds keep most tracks' own hits."""
+    b = _batch(63, det=Detector(module_dr=1.0))
+    ctx = tkf.Context(tkf.default_config(hit_dr=0.5))
+    L = ctx.cfg.n_layers
+    dh = device_hits(b)
+    sh = torch.as_tensor(np.ascontiguousarray(b.trk_hits[:, :3].T), dtype=torch.int32, device="cuda")
+    se = torch.as_tensor(b.trk_event, dtype=torch.int32, device="cuda")
+    pipe = tkf.DevicePipeline(ctx, b.n_hits, b.n_events, b.n_tracks, use_graph=True)
+    for _ in range(2):
+        pipe.run(dh, sh, se, b.n_tracks)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    gb, gf = _pipe_out(pipe, L, b.n_tracks)
+    db, df = _direct(ctx, b, dh, sh, se)
+    assert torch.equal(gb["hit_idx"], db.hit_idx) and torch.equal(gb["par"], db.par)
+    assert torch.equal(gf["par"], df.par) and torch.equal(gf["cov"], df.cov) and torch.equal(gf["chi2"], df.chi2)
+    ids = gb["hit_idx"].T.cpu().numpy()  # global hit ids
+    assert np.all(ids == b.trk_hits, axis=1).mean() >= 0.97
+    pipe.close()
+    ctx.close()
