@@ -49,6 +49,25 @@ FLOP_SCATTER = 30      # Highland width and the four covariance terms
 PER_SEED = dict(n_prop=19.2502, n_hits_examined=189.7167, n_updates=18.0985, n_kept=21.7897)
 FLOP_PER_SEED = (PER_SEED["n_prop"] * (FLOP_PROPAGATE + FLOP_WINDOW) + PER_SEED["n_hits_examined"] * FLOP_CHI2
                  + PER_SEED["n_updates"] * FLOP_UPDATE + PER_SEED["n_kept"] * 6.0 / 7.0 * FLOP_SCATTER)
+# Hits off the layers' cylinders (modules 0.5 cm inside and outside each radius, the two-step
+# building): per examined hit only the residual and window test (14) before the step; per hit
+# inside the window the short step to its radius with the two measured rows of the transported
+# covariance and chi2 (step_chi2, 405); per candidate window the widening by the radial offset
+# (15); per update a second propagation (FLOP_PROPAGATE) to the hit's radius.  Work per seed
+# from the oracle (python oracle/opcount.py --events 16 --module-dr 1.0, 53756 seeds):
+FLOP_RESIDUAL, FLOP_STEP_CHI2, FLOP_WIDEN = 14, 405, 15
+PER_SEED_TWO_STEP = dict(n_prop=19.5538, n_hits_examined=213.4334, n_updates=18.2336, n_kept=22.1408,
+                         n_steps=25.6186)
+FLOP_PER_SEED_TWO_STEP = (PER_SEED_TWO_STEP["n_prop"] * (FLOP_PROPAGATE + FLOP_WINDOW + FLOP_WIDEN)
+                          + PER_SEED_TWO_STEP["n_hits_examined"] * FLOP_RESIDUAL
+                          + PER_SEED_TWO_STEP["n_steps"] * FLOP_STEP_CHI2
+                          + PER_SEED_TWO_STEP["n_updates"] * (FLOP_UPDATE + FLOP_PROPAGATE)
+                          + PER_SEED_TWO_STEP["n_kept"] * 6.0 / 7.0 * FLOP_SCATTER)
+MODULE_DR = 1.0  # cm between the inner and outer module rows of a layer (hit_dr = 0.5 cm)
+# DRAM bytes (read + write) per seed of the two-step FP32 building kernel, from one ncu capture
+# of the kernel as built now (160-event case: 405.0 MB for 701 095 seeds; summary in profiles/);
+# None whenever the kernel changes until it is captured again
+BUILD2_DRAM_BYTES_PER_SEED = 577.7
 # FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # libtkf.so kernels per step: hit index (event order, per-event count/scan/place, bin sort),
@@ -63,20 +82,22 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 
 
 def _gen_chunk(args):
-    from synth import EventSpec, event_sizes, generate
-    seed, e0, e1 = args
+    from synth import Detector, EventSpec, event_sizes, generate
+    seed, e0, e1, module_dr = args
     n, f = event_sizes(seed, 640)
-    return generate(EventSpec(seed=seed, n_events=e1 - e0, n_tracks=n[e0:e1], noise_frac=f[e0:e1], first_event=e0))
+    return generate(EventSpec(seed=seed, n_events=e1 - e0, n_tracks=n[e0:e1], noise_frac=f[e0:e1], first_event=e0),
+                    Detector(module_dr=module_dr))
 
 
-def workload(seed: int, n_events: int, pool=None):
+def workload(seed: int, n_events: int, pool=None, module_dr=0.0):
     """The first n_events events of the 640-event batched workload (generated in parallel
-    chunks when a process pool is given; the result does not depend on the chunking)."""
+    chunks when a process pool is given; the result does not depend on the chunking);
+    module_dr > 0: the same events on modules off the layers' cylinders."""
     from synth import concat
     if pool is None or n_events < 32:
-        return _gen_chunk((seed, 0, n_events))
+        return _gen_chunk((seed, 0, n_events, module_dr))
     step = max(1, n_events // 64)
-    chunks = [(seed, e, min(e + step, n_events)) for e in range(0, n_events, step)]
+    chunks = [(seed, e, min(e + step, n_events), module_dr) for e in range(0, n_events, step)]
     return concat(pool.map(_gen_chunk, chunks, chunksize=1))
 
 
@@ -159,13 +180,13 @@ def job_rate(units, ms, dist=None, device="cpu"):
 
 
 # ----------------------------------------------------------------------------- CPU baseline (oracle)
-def _oracle_events(chunk):
+def _oracle_events(chunk, module_dr=0.0):
     """Runs the oracle's whole path (index, seed, seed fit, build, final fit) on a few events,
     each given as (oracle hit records, track hit ids [n, L]); returns (tracks, seconds spent
     computing in this process)."""
     import oracle as O
     from synth import Detector
-    det = Detector()
+    det = Detector(module_dr=module_dr)
     g = O.make_geom(det)
     L = det.n_layers
     done = 0
@@ -179,6 +200,11 @@ def _oracle_events(chunk):
         O.fit(g, hits, p0, c0, res.hits[:, 0, :], 0, L - 1)
         done += len(local)
     return done, time.perf_counter() - t0
+
+
+def _oracle_events_modules(chunk):
+    """_oracle_events on the module geometry (hits off the layers' cylinders)."""
+    return _oracle_events(chunk, MODULE_DR)
 
 
 def _oracle_backward(chunk):
@@ -398,6 +424,9 @@ def main():
     ap.add_argument("--mixed", type=int, default=1, help="1: also time the batched step in MIXED precision")
     ap.add_argument("--backward", type=int, default=1,
                     help="1: also time the backward pass of the final fit over the batch's fitted tracks")
+    ap.add_argument("--two-step", type=int, default=160,
+                    help="events of the batch also timed on modules off the layers' cylinders (two-step building); "
+                         "0: skip")
     ap.add_argument("--tile", type=int, default=0, help="seeds per warp work tile (0: autotuned)")
     ap.add_argument("--e2e-batch", type=int, default=160, help="events per server batch in the e2e measurement")
     ap.add_argument("--e2e-slots", type=int, default=4, help="server slots in the e2e measurement")
@@ -552,6 +581,72 @@ def main():
                     "form": "tkf_fit_backward over the pipeline's %d fitted tracks, layer 10 to layer 1, covariance "
                             "scale 1e4, FP32; one launch per pass, CUDA events; inputs larger than L2" % n_tr}
         del back
+
+    # ---------------- the same events on modules off the layers' cylinders (two-step building)
+    two_step = None
+    b2 = None
+    if a.two_step > 0:
+        n2 = min(a.two_step, a.events)
+        b2 = workload(a.seed + 1000 * rank, n2, pool, module_dr=MODULE_DR)
+        t2 = lambda arr, dt: torch.as_tensor(np.ascontiguousarray(arr), dtype=dt).to(dev)
+        d2 = {"x": t2(b2.x, torch.float32), "y": t2(b2.y, torch.float32), "z": t2(b2.z, torch.float32),
+              "var_u": t2(b2.var_u, torch.float32), "var_v": t2(b2.var_v, torch.float32),
+              "layer": t2(b2.layer, torch.int32), "event_off": t2(b2.hit_off, torch.int32),
+              "seed_hits": t2(b2.trk_hits[:, :3].T, torch.int32), "seed_event": t2(b2.trk_event, torch.int32)}
+        hits2 = tkf.DeviceHits(d2["x"], d2["y"], d2["z"], d2["var_u"], d2["var_v"], d2["layer"], d2["event_off"])
+        c2 = tkf.Context(tkf.default_config(seed_order=a.seed_order, hit_dr=0.5 * MODULE_DR,
+                                            seeds_per_block=max(a.tile, 0)))
+        n2t = b2.n_tracks
+        p2 = tkf.DevicePipeline(c2, b2.n_hits, b2.n_events, n2t, use_graph=True)
+        step2 = lambda: p2.run(hits2, d2["seed_hits"], d2["seed_event"], n2t, stream=stream)
+        step2()
+        s2t = p2.outputs()[0]
+        if a.tile > 0:
+            tile2, t2ms = a.tile, []
+        else:
+            sc2 = tkf.DeviceTracks.empty(n2t, L, device=dev)
+            tile2, t2ms = c2.autotune_build(p2.index(), _T(s2t), sc2, tiles, repeats=2, stream=stream)
+            del sc2
+            c2.close()
+            p2.close()
+            c2 = tkf.Context(tkf.default_config(seed_order=a.seed_order, hit_dr=0.5 * MODULE_DR,
+                                                seeds_per_block=tile2))
+            p2 = tkf.DevicePipeline(c2, b2.n_hits, b2.n_events, n2t, use_graph=True)
+            step2 = lambda: p2.run(hits2, d2["seed_hits"], d2["seed_event"], n2t, stream=stream)
+        for _ in range(max(3, a.warmup)):
+            step2()
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        qb = []
+        q0.record(stream)
+        for _ in range(a.steps):
+            step2()
+            qb.append(p2.build_ms())
+        q1.record(stream)
+        torch.cuda.synchronize()
+        c2.sync_status(stream)
+        q_ms = q0.elapsed_time(q1) / a.steps
+        q_build = statistics.mean(qb)
+        hid2 = tkf.tracks_tensors(p2.outputs()[1], L)["hit_idx"][:, :n2t].cpu().numpy()
+        ach2 = FLOP_PER_SEED_TWO_STEP * n2t / (q_build / 1e3) / 1e12
+        two_step = {
+            "value": n2t / (q_ms / 1e3), "unit": UNIT, "ms_per_step": q_ms, "build_ms": q_build,
+            "events": b2.n_events, "tracks": n2t, "hits": b2.n_hits, "efficiency": efficiency(b2, hid2),
+            "own_hit_lists": float(np.mean(np.all(hid2.T == b2.trk_hits, axis=1))),
+            "seeds_per_warp_tile": tile2, "autotune_build_ms": [round(x, 4) for x in t2ms],
+            "roofline": {"kernel": "k_build<6,float,float,two-step>", "bound": "alu", "achieved": ach2,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach2 / FP32_PEAK_TFLOPS,
+                         "traffic": None if BUILD2_DRAM_BYTES_PER_SEED is None else BUILD2_DRAM_BYTES_PER_SEED * n2t,
+                         "traffic_unit": "bytes per launch (ncu DRAM read + write of the 160-event case, per seed)",
+                         "launch_ms": q_build, "flop_per_seed": FLOP_PER_SEED_TWO_STEP,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+            "form": "events 0..%d of the batched workload with each layer's modules 0.5 cm inside and outside "
+                    "its radius (hit_dr = 0.5 cm): window on the average radius, a second propagation to each "
+                    "candidate hit's radius; fits to each hit's radius; FP32, N = 6, whole step replayed from a "
+                    "CUDA graph; inputs larger than L2" % (b2.n_events - 1)}
+        p2.close()
+        c2.close()
+        del d2, hits2
 
     # ---------------- end to end through host buffers
     _, built_t, fitted_t = pipe.outputs()
@@ -728,6 +823,15 @@ def main():
                 "sample": "the backward pass of events %d..%d (%d tracks) from the GPU's fitted states, FP64, one "
                           "process per core; time = the slowest worker's computing (%.2f s; %.2f s wall with the "
                           "transfer of the inputs)" % (ev[0], ev[-1], nb, compb, wallb)}
+        if two_step is not None:
+            # the oracle on the first events of the module-geometry batch (its share of the sample)
+            n2s = next((k + 1 for k in range(b2.n_events) if int(b2.trk_off[k + 1]) >= a.cpu_tracks // 4), b2.n_events)
+            tracks2, comp2, wall2 = cpu_baseline(oracle_sample(b2, range(n2s)), pool, cores, fn=_oracle_events_modules)
+            two_step["cpu_baseline"] = {
+                "value": tracks2 / comp2, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": "events 0..%d of the module-geometry batch (%d tracks): index, seed, seed fit, two-step "
+                          "build, final fit, FP64, one process per core; time = the slowest worker's computing "
+                          "(%.2f s; %.2f s wall)" % (n2s - 1, tracks2, comp2, wall2)}
     pool.close()
 
     achieved = FLOP_PER_SEED * n_tr / (build_ms / 1e3) / 1e12
@@ -754,6 +858,7 @@ def main():
         "e2e_pipeline": e2e_pipe,
         "mixed": mixed,
         "backward_pass": backward,
+        "two_step": two_step,
         "plain": plain,
         "serve": serve,
         "autotune": {"grid": "seeds per warp tile x candidates per seed N (build launch ms)",

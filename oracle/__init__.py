@@ -73,7 +73,7 @@ class Event(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("n_prop", C.c_longlong), ("n_hits_examined", C.c_longlong), ("n_updates", C.c_longlong),
-                ("n_kept", C.c_longlong)]
+                ("n_kept", C.c_longlong), ("n_steps", C.c_longlong)]
 
 
 @dataclass

@@ -2,7 +2,10 @@
 seed on a seeded sample of a workload by instrumenting the oracle: candidates propagated,
 hits scored, Kalman updates and kept branches (each kept branch gets the scattering noise).
 
-    python oracle/opcount.py [--events K] [--workload batched|plain]
+    python oracle/opcount.py [--events K] [--workload batched|plain] [--module-dr D]
+
+--module-dr D places each layer's modules D/2 inside and outside its radius (hits off the
+cylinders, the two-step building); n_steps then counts the hits taken to their own radius.
 
 The per-seed counts it prints, times the per-operation FP32 operation counts of the build
 kernel's arithmetic, give the algorithmic FLOP per built track used for the roofline.
@@ -24,7 +27,7 @@ from synth import Detector, EventSpec, event_sizes, generate  # noqa: E402
 
 def count(batch, det, settings=O.Settings()):
     g = O.make_geom(det, settings)
-    tot = dict(n_prop=0, n_hits_examined=0, n_updates=0, n_kept=0, seeds=0)
+    tot = dict(n_prop=0, n_hits_examined=0, n_updates=0, n_kept=0, n_steps=0, seeds=0)
     L = det.n_layers
     for e in range(batch.n_events):
         h0, h1 = batch.hit_off[e], batch.hit_off[e + 1]
@@ -38,7 +41,7 @@ def count(batch, det, settings=O.Settings()):
         ids[:, :3] = local[:, :3]
         sp, sP, sc2, snh, _ = O.fit(g, hits, p0, c0, ids, 0, 2)
         res = O.build(g, O.hit_index(g, hits), sp, sP, sc2, snh, ids)
-        for k in ("n_prop", "n_hits_examined", "n_updates", "n_kept"):
+        for k in ("n_prop", "n_hits_examined", "n_updates", "n_kept", "n_steps"):
             tot[k] += res.stats[k]
         tot["seeds"] += t1 - t0
     return {k: v / tot["seeds"] for k, v in tot.items() if k != "seeds"} | {"seeds": tot["seeds"]}
@@ -48,8 +51,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--events", type=int, default=16)
     ap.add_argument("--workload", choices=["batched", "plain"], default="batched")
+    ap.add_argument("--module-dr", type=float, default=0.0)
     a = ap.parse_args()
-    det = Detector()
+    det = Detector(module_dr=a.module_dr)
     if a.workload == "batched":
         n, f = event_sizes(3, 640)
         spec = EventSpec(seed=3, n_events=a.events, n_tracks=n[:a.events], noise_frac=f[:a.events])

@@ -656,7 +656,7 @@ static int build_seed(const orc_geom *g, const orc_event *ev, const double sp[6]
                              * would pass the chi2 cut */
                             const int edge = fabs(fabs(r[0]) - U) <= tol * U || fabs(fabs(r[1]) - W) <= tol * W;
                             if (!inside && !edge) continue;
-                            if (stats) stats->n_prop += 1;
+                            if (stats) stats->n_steps += 1;
                             if (orc_propagate(g, C[c].p, target_radius(g, l, h), q2, J2) != ORC_OK) continue;
                             sandwich6(J2, C[c].P, Q2);
                             qh = q2;

@@ -55,6 +55,7 @@ typedef struct {
 
 typedef struct {
     long long n_prop, n_hits_examined, n_updates, n_kept;
+    long long n_steps; /* hits off the cylinder (hit_dr > 0) taken to their own radius and scored */
 } orc_stats;
 
 int orc_propagate(const orc_geom *g, const double pin[6], double R, double pout[6], double J[36]);
