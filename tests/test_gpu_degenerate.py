@@ -130,3 +130,57 @@ def test_backward_pass_reports_a_circle_that_never_returns_inward(det, prec):
     assert np.all(got["nhits"][normal] == 0)
     assert not param_violations(got["par"][normal], ref[0][normal])[0].any()
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=lambda p: PNAME[p])
+def test_two_step_fit_reports_a_module_out_of_reach(prec):
+    """Hits on modules off the cylinders (hit_dr = 0.5 cm), layers at 6.9 and 8 cm: curlers of
+    radius 4.05 cm from the origin reach at most 8.1 cm, past the 8 cm layer's average radius
+    and its inner modules (7.5 cm) but short of its outer modules (8.5 cm).  A track whose
+    second hit lies on an outer module is reported TKF_TRACK_NOREACH, as the oracle finds no
+    crossing of the hit's radius; with the hit on an inner module it is fitted, at parity.
+    (The first layer sits close to the second so that the step stays within the straight-line
+    start of the GPU's Newton solve: a 4 cm radius of curvature is 46 MeV of pT.)"""
+    radii = (6.9,) + tuple(4.0 * (l + 1) for l in range(1, 10))
+    det = Detector(radii=radii, x_over_x0=(0.0,) * 10, module_dr=1.0)
+    g = O.make_geom(det)
+    L = det.n_layers
+    n = 64
+    w = 1.0 / (K_B * det.bz * 4.05)
+    start = np.zeros((n, 6))
+    hits = np.zeros(2 * n, dtype=O.HIT_DTYPE)
+    ids = np.full((n, L), -1, dtype=np.int32)
+    outer = np.arange(n) % 2 == 1
+    for t in range(n):
+        v = np.array([0.0, 0.0, 0.0, w if t % 4 < 2 else -w, -math.pi + 2 * math.pi * t / n, 1.2])
+        st, p1, _ = O.propagate(g, v, radii[0])
+        assert st == 0
+        start[t] = p1
+        st, p2, _ = O.propagate(g, p1, 7.5)  # the crossing of the inner module radius
+        assert st == 0
+        r2 = 8.5 if outer[t] else 7.5
+        ph = math.atan2(p2[1], p2[0])
+        hits[2 * t] = (p1[0], p1[1], p1[2], det.sigma_rphi ** 2, det.sigma_z ** 2, 0)
+        hits[2 * t + 1] = (r2 * math.cos(ph), r2 * math.sin(ph), p2[2], det.sigma_rphi ** 2, det.sigma_z ** 2, 1)
+        ids[t, 0], ids[t, 1] = 2 * t, 2 * t + 1
+    # the oracle on the float-rounded hits the GPU reads
+    for k in ("x", "y", "z", "var_u", "var_v"):
+        hits[k] = hits[k].astype(np.float32)
+    cov = np.tile(np.diag(np.square([0.01, 0.01, 0.1, 0.01, 0.001, 0.001])), (n, 1, 1))
+    start, cov = rounded(start, prec), rounded(cov, prec)
+    ref = O.fit(g, hits, start, cov, ids, 0, 1)
+    assert np.all(ref[4][outer] == 1) and np.all(ref[4][~outer] == 0)  # ORC_ERR_NOREACH
+
+    class _Hits:
+        x, y, z = hits["x"], hits["y"], hits["z"]
+        var_u, var_v, layer = hits["var_u"], hits["var_v"], hits["layer"]
+        hit_off = np.array([0, 2 * n])
+    ctx = tkf.Context(tkf.default_config(precision=prec, hit_dr=0.5, radius=radii, x_over_x0=det.x_over_x0))
+    out = tkf.DeviceTracks.empty(n, L, prec)
+    ctx.fit(device_hits(_Hits), device_tracks(start, cov, np.zeros(n), np.zeros(n), ids, precision=prec), 0, 1, out)
+    ctx.sync_status()
+    got = host_tracks(out)
+    assert np.all(got["nhits"][outer] == tkf.TRACK_NOREACH)
+    assert np.all(got["nhits"][~outer] == 2)
+    assert not param_violations(got["par"][~outer], ref[0][~outer])[0].any()
+    ctx.close()
