@@ -68,6 +68,11 @@ MODULE_DR = 1.0  # cm between the inner and outer module rows of a layer (hit_dr
 # of the kernel as built now (160-event case: 405.0 MB for 701 095 seeds; summary in profiles/);
 # None whenever the kernel changes until it is captured again
 BUILD2_DRAM_BYTES_PER_SEED = 577.7
+# Warp instructions per seed of the two build kernels (ncu smsp__inst_executed.sum of the same
+# captures: 2.01 G and 4.09 G for 701 095 seeds), for the instruction-issue roofline beside the
+# FP32 one: an SM sub-partition issues at most one warp instruction per cycle, 4 per SM;
+# None whenever a kernel changes until it is captured again
+BUILD_WARP_INST_PER_SEED, BUILD2_WARP_INST_PER_SEED = 2867.0, 5839.0
 # FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # libtkf.so kernels per step: hit index (event order, per-event count/scan/place, bin sort),
@@ -79,6 +84,7 @@ KERNELS_PER_STEP = 11
 # None whenever the kernel changes until it is captured again
 BUILD_DRAM_BYTES_PER_SEED = 580.7
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+ISSUE_PEAK_WARP_INST_PER_S = SM_COUNT * 4 * SM_MAX_GHZ * 1e9
 
 
 def _gen_chunk(args):
@@ -154,6 +160,17 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def issue_roofline(inst_per_seed, seeds, launch_ms):
+    """The build launch against the instruction-issue limit: warp instructions (ncu count per
+    seed x seeds) per second of the CUDA-event launch time, over 152 SMs x 4 x 2.07 GHz."""
+    if inst_per_seed is None:
+        return None
+    a = inst_per_seed * seeds / (launch_ms / 1e3)
+    return {"achieved": a, "peak": ISSUE_PEAK_WARP_INST_PER_S, "unit": "warp instructions/s",
+            "frac": a / ISSUE_PEAK_WARP_INST_PER_S, "inst_per_seed": inst_per_seed,
+            "source": "ncu smsp__inst_executed.sum per seed of the 160-event capture"}
 
 
 def efficiency(b, hit_idx):
@@ -639,7 +656,8 @@ def main():
                          "traffic": None if BUILD2_DRAM_BYTES_PER_SEED is None else BUILD2_DRAM_BYTES_PER_SEED * n2t,
                          "traffic_unit": "bytes per launch (ncu DRAM read + write of the 160-event case, per seed)",
                          "launch_ms": q_build, "flop_per_seed": FLOP_PER_SEED_TWO_STEP,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                         "issue": issue_roofline(BUILD2_WARP_INST_PER_SEED, n2t, q_build)},
             "form": "events 0..%d of the batched workload with each layer's modules 0.5 cm inside and outside "
                     "its radius (hit_dr = 0.5 cm): window on the average radius, a second propagation to each "
                     "candidate hit's radius; fits to each hit's radius; FP32, N = 6, whole step replayed from a "
@@ -852,7 +870,8 @@ def main():
                      "traffic": None if BUILD_DRAM_BYTES_PER_SEED is None else BUILD_DRAM_BYTES_PER_SEED * n_tr,
                      "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled by seeds from the 160-event case)",
                      "launch_ms": build_ms, "flop_per_seed": FLOP_PER_SEED,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "issue": issue_roofline(BUILD_WARP_INST_PER_SEED, n_tr, build_ms)},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "e2e_pipeline": e2e_pipe,
