@@ -2,7 +2,9 @@
 lognormal batch (2.6 M seeds, 35 M hits) through the graph-replayed pipeline with seed ordering
 and the autotuned work tile, compared with the oracle on a seeded sample of seeds (the oracle
 builds and fits them one event at a time), plus properties checked on every seed; then the
-backward pass (tkf_fit_backward) over every fitted track, sampled against the oracle's."""
+backward pass (tkf_fit_backward) over every fitted track, sampled against the oracle's.  The
+same for the bench's two-step case: the batch's first 160 events on modules 0.5 cm off the
+layers' cylinders (hit_dr = 0.5 cm)."""
 import multiprocessing as mp
 import os
 
@@ -24,17 +26,21 @@ from paper_1702_06359_gb300 import tkf  # noqa: E402
 N_SAMPLE_EVENTS, SEEDS_PER_EVENT = 48, 40
 
 
-@pytest.fixture(scope="module")
-def full_batch():
+def _batch(n_events, module_dr=0.0):
     import bench
     with mp.get_context("spawn").Pool(min(os.cpu_count() or 1, 16)) as pool:
-        b = bench.workload(3, 640, pool)
-    return b
+        return bench.workload(3, n_events, pool, module_dr=module_dr)
 
 
-def test_full_batch_sampled_parity_and_properties(full_batch):
-    b = full_batch
-    det = Detector()
+def test_full_batch_sampled_parity_and_properties():
+    _check_batch(_batch(640), Detector(), {}, N_SAMPLE_EVENTS)
+
+
+def test_two_step_batch_sampled_parity_and_properties():
+    _check_batch(_batch(160, module_dr=1.0), Detector(module_dr=1.0), {"hit_dr": 0.5}, 32)
+
+
+def _check_batch(b, det, cfg, n_sample_events):
     L = det.n_layers
     dev = torch.device("cuda", 0)
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(dev)
@@ -43,7 +49,7 @@ def test_full_batch_sampled_parity_and_properties(full_batch):
                           t(b.hit_off, torch.int32))
     sh, se = t(b.trk_hits[:, :3].T, torch.int32), t(b.trk_event, torch.int32)
     n = b.n_tracks
-    ctx = tkf.Context(tkf.default_config(seed_order=1, seeds_per_block=5))
+    ctx = tkf.Context(tkf.default_config(seed_order=1, seeds_per_block=5, **cfg))
     pipe = tkf.DevicePipeline(ctx, b.n_hits, b.n_events, n, use_graph=True)
     for _ in range(2):  # capture, then a replay
         pipe.run(hits, sh, se, n)
@@ -74,7 +80,7 @@ def test_full_batch_sampled_parity_and_properties(full_batch):
     # sampled seeds against the oracle, one event at a time
     g = O.make_geom(det)
     rng = np.random.default_rng(1702)
-    events = np.sort(rng.choice(b.n_events, N_SAMPLE_EVENTS, replace=False))
+    events = np.sort(rng.choice(b.n_events, n_sample_events, replace=False))
     n_cmp = n_div = 0
     bw_samples = []
     for e in events:
@@ -104,7 +110,7 @@ def test_full_batch_sampled_parity_and_properties(full_batch):
         assert np.array_equal(fnh[s[m]], fn)
         n_cmp += len(s)
         bw_samples.append((oh, s[m], rh[m]))
-    assert n_cmp > 1000 and n_div <= 0.05 * n_cmp, (n_cmp, n_div)
+    assert n_cmp > 25 * n_sample_events and n_div <= 0.05 * n_cmp, (n_cmp, n_div)
 
     # the backward pass over every fitted track (tkf_fit_backward, layer 10 -> 1), the sampled
     # seeds against the oracle's pass from the same (float32) states
@@ -137,6 +143,8 @@ def test_full_batch_sampled_parity_and_properties(full_batch):
         assert not param_violations(bpar[idx], rp)[0].any()
         assert not chi2_violations(bchi2[idx], rc2)[0].any()
         n_bw += len(idx)
-    assert n_bw > 1000
+    assert n_bw > 25 * n_sample_events
+    pipe.close()
+    ctx.close()
     pipe.close()
     ctx.close()
