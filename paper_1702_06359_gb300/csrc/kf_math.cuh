@@ -4,13 +4,16 @@
 //
 // State p = (x, y, z, w = q/pT, phi, theta); covariance P as the 21-element packed lower
 // triangle, row order.  Everything is written out with the sparsity of the Jacobian and of H
-// (the paper's Matriplex generator idea of skipping known zeros and ones, Sec. 2.1, done by
-// hand), so no 6x6 product is ever formed densely.  Templated on the real type R (float or
+// (the paper's Matriplex generator idea of skipping known zeros and ones, Sec. 2.1): the
+// congruence products J P J^T and M P M^T come from gen_sparse.py (sparse_gen.cuh), the rest is
+// written by hand, so no 6x6 product is ever formed densely.  Templated on the real type R (float or
 // double) so that one source serves the FP32, mixed and FP64 modes.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "sparse_gen.cuh"
 
 namespace tkf {
 
@@ -226,54 +229,9 @@ __host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R 
     const R c0 = cot * s_x, cc1 = cot * s_y, c3 = cot * s_w, c4 = cot * s_f, c5 = -s / (st * st); // z (c2 = 1)
     const R f0 = kappa * s_x, f1 = kappa * s_y, f3 = -kb * s + kappa * s_w, f4 = R(1) + kappa * s_f; // phi
 
-    // T = J P (rows x, y, z, phi; rows w, theta of T are rows 3, 5 of P)
-    R Tx[6], Ty[6], Tz[6], Tf[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        const R p0 = P[sym(0, j)], p1 = P[sym(1, j)], p2 = P[sym(2, j)], p3 = P[sym(3, j)], p4 = P[sym(4, j)],
-                p5 = P[sym(5, j)];
-        Tx[j] = a0 * p0 + a1 * p1 + a3 * p3 + a4 * p4;
-        Ty[j] = b0 * p0 + b1 * p1 + b3 * p3 + b4 * p4;
-        Tz[j] = c0 * p0 + cc1 * p1 + p2 + c3 * p3 + c4 * p4 + c5 * p5;
-        Tf[j] = f0 * p0 + f1 * p1 + f3 * p3 + f4 * p4;
-    }
-    R Tw[6], Tt[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        Tw[j] = P[sym(3, j)];
-        Tt[j] = P[sym(5, j)];
-    }
-    // P' = T J^T, lower triangle
-#define TKF_DOT_X(T) (T[0] * a0 + T[1] * a1 + T[3] * a3 + T[4] * a4)
-#define TKF_DOT_Y(T) (T[0] * b0 + T[1] * b1 + T[3] * b3 + T[4] * b4)
-#define TKF_DOT_Z(T) (T[0] * c0 + T[1] * cc1 + T[2] + T[3] * c3 + T[4] * c4 + T[5] * c5)
-#define TKF_DOT_F(T) (T[0] * f0 + T[1] * f1 + T[3] * f3 + T[4] * f4)
+    // P' = J P J^T from J's sparsity pattern (generated: sparse_gen.cuh)
     R Q[21];
-    Q[sym(0, 0)] = TKF_DOT_X(Tx);
-    Q[sym(1, 0)] = TKF_DOT_X(Ty);
-    Q[sym(1, 1)] = TKF_DOT_Y(Ty);
-    Q[sym(2, 0)] = TKF_DOT_X(Tz);
-    Q[sym(2, 1)] = TKF_DOT_Y(Tz);
-    Q[sym(2, 2)] = TKF_DOT_Z(Tz);
-    Q[sym(3, 0)] = TKF_DOT_X(Tw);
-    Q[sym(3, 1)] = TKF_DOT_Y(Tw);
-    Q[sym(3, 2)] = TKF_DOT_Z(Tw);
-    Q[sym(3, 3)] = Tw[3];
-    Q[sym(4, 0)] = TKF_DOT_X(Tf);
-    Q[sym(4, 1)] = TKF_DOT_Y(Tf);
-    Q[sym(4, 2)] = TKF_DOT_Z(Tf);
-    Q[sym(4, 3)] = Tf[3];
-    Q[sym(4, 4)] = TKF_DOT_F(Tf);
-    Q[sym(5, 0)] = TKF_DOT_X(Tt);
-    Q[sym(5, 1)] = TKF_DOT_Y(Tt);
-    Q[sym(5, 2)] = TKF_DOT_Z(Tt);
-    Q[sym(5, 3)] = Tt[3];
-    Q[sym(5, 4)] = TKF_DOT_F(Tt);
-    Q[sym(5, 5)] = Tt[5];
-#undef TKF_DOT_X
-#undef TKF_DOT_Y
-#undef TKF_DOT_Z
-#undef TKF_DOT_F
+    transport_cov<R>(a0, a1, a3, a4, b0, b1, b3, b4, c0, cc1, c3, c4, c5, f0, f1, f3, f4, P, Q);
 #pragma unroll
     for (int k = 0; k < 21; ++k) P[k] = Q[k];
     p[0] = xs;
@@ -403,17 +361,9 @@ __host__ __device__ __forceinline__ R step_chi2(const R p[6], const R P[21], R s
     const R m3 = -sh * (dx_dw + c1 * s_w) + ch * (dy_dw + s1 * s_w);
     const R m4 = -sh * (dx_dphi + c1 * s_f) + ch * (dy_dphi + s1 * s_f);
     const R v0 = cot * s_x, v1 = cot * s_y, v3 = cot * s_w, v4 = cot * s_f, v5 = -s / (st * st);
-    R Tu[6], Tv[6];  // P M_u^T, P M_v^T
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-        const R p0 = P[sym(0, j)], p1 = P[sym(1, j)], p2 = P[sym(2, j)], p3 = P[sym(3, j)], p4 = P[sym(4, j)],
-                p5 = P[sym(5, j)];
-        Tu[j] = m0 * p0 + m1 * p1 + m3 * p3 + m4 * p4;
-        Tv[j] = v0 * p0 + v1 * p1 + p2 + v3 * p3 + v4 * p4 + v5 * p5;
-    }
-    const R Suu = m0 * Tu[0] + m1 * Tu[1] + m3 * Tu[3] + m4 * Tu[4] + vu;
-    const R Suv = m0 * Tv[0] + m1 * Tv[1] + m3 * Tv[3] + m4 * Tv[4];
-    const R Svv = v0 * Tv[0] + v1 * Tv[1] + Tv[2] + v3 * Tv[3] + v4 * Tv[4] + v5 * Tv[5] + vv;
+    R Sm[3];  // M P M^T from M's sparsity pattern (generated: sparse_gen.cuh)
+    measured_cov<R>(m0, m1, m3, m4, v0, v1, v3, v4, v5, P, Sm);
+    const R Suu = Sm[0] + vu, Suv = Sm[1], Svv = Sm[2] + vv;
     const R u = ch * (yh - ys) - sh * (xh - xs);
     const R v = zh - (p[2] + s * cot);
     const R det = Suu * Svv - Suv * Suv;
