@@ -19,9 +19,9 @@ if not torch.cuda.is_available():
 from paper_1702_06359_gb300 import tkf  # noqa: E402
 
 
-def _events(seed, n_events=12):
+def _events(seed, n_events=12, det=Detector()):
     sizes, noise = event_sizes(seed, n_events, median=800, lo=100, hi=4000)
-    b = generate(EventSpec(seed=seed, n_events=n_events, n_tracks=sizes, noise_frac=noise), Detector())
+    b = generate(EventSpec(seed=seed, n_events=n_events, n_tracks=sizes, noise_frac=noise), det)
     evs = []
     for e in range(n_events):
         h0, h1 = b.hit_off[e], b.hit_off[e + 1]
@@ -179,9 +179,13 @@ def test_batch_submit_wait_release_match_single_calls():
     sv.close()
 
 
-def test_mixed_precision_server_equals_mixed_pipeline():
-    b, evs = _events(76, n_events=3)
-    cfg = tkf.default_config(precision=tkf.MIXED)
+@pytest.mark.parametrize("prec,module_dr", [(tkf.MIXED, 0.0), (tkf.FP32, 1.0)], ids=["mixed", "two_step"])
+def test_server_equals_the_pipeline_of_its_configuration(prec, module_dr):
+    """The server's results equal the plain pipeline's under the same configuration, bit for bit:
+    MIXED precision, and hits on modules 0.5 cm off the layers' cylinders (hit_dr = 0.5 cm)."""
+    b, evs = _events(76, n_events=3, det=Detector(module_dr=module_dr))
+    kw = dict(precision=prec, hit_dr=0.5 * module_dr)
+    cfg = tkf.default_config(**kw)
     sv = tkf.Server(cfg, n_slots=2, max_batch_events=4, max_batch_hits=1 << 20, max_batch_tracks=1 << 16)
     tickets = [sv.submit(ev)[1] for ev in evs]
     res = [_wait(sv, t) for t in tickets]
@@ -189,7 +193,7 @@ def test_mixed_precision_server_equals_mixed_pipeline():
     sv.close()
     e = 1
     h0, h1, t0, t1 = b.hit_off[e], b.hit_off[e + 1], b.trk_off[e], b.trk_off[e + 1]
-    ctx = tkf.Context(tkf.default_config(precision=tkf.MIXED))
+    ctx = tkf.Context(tkf.default_config(**kw))
     dh = device_hits(b)
     dh = tkf.DeviceHits(dh.x[h0:h1], dh.y[h0:h1], dh.z[h0:h1], dh.var_u[h0:h1], dh.var_v[h0:h1], dh.layer[h0:h1],
                         torch.tensor([0, h1 - h0], dtype=torch.int32, device="cuda"))
