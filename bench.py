@@ -441,6 +441,8 @@ def main():
     ap.add_argument("--mixed", type=int, default=1, help="1: also time the batched step in MIXED precision")
     ap.add_argument("--backward", type=int, default=1,
                     help="1: also time the backward pass of the final fit over the batch's fitted tracks")
+    ap.add_argument("--batch-scan", type=str, default="10,40,160",
+                    help="also time the step on the batch's first K events for each K (comma list; empty: skip)")
     ap.add_argument("--two-step", type=int, default=160,
                     help="events of the batch also timed on modules off the layers' cylinders (two-step building); "
                          "0: skip")
@@ -598,6 +600,33 @@ def main():
                     "form": "tkf_fit_backward over the pipeline's %d fitted tracks, layer 10 to layer 1, covariance "
                             "scale 1e4, FP32; one launch per pass, CUDA events; inputs larger than L2" % n_tr}
         del back
+
+    # ---------------- throughput against batch size: the step on the batch's first K events
+    batch_scan = None
+    if a.batch_scan:
+        batch_scan = []
+        for k in sorted({int(x) for x in a.batch_scan.split(",") if x.strip()}):
+            if not 0 < k < b.n_events:
+                continue
+            nh_k, nt_k = int(b.hit_off[k]), int(b.trk_off[k])
+            hk = tkf.DeviceHits(d["x"][:nh_k], d["y"][:nh_k], d["z"][:nh_k], d["var_u"][:nh_k], d["var_v"][:nh_k],
+                                d["layer"][:nh_k], d["event_off"][:k + 1])
+            sk = d["seed_hits"][:, :nt_k].contiguous()  # [3][K's tracks]: rows strided by the pipeline's capacity
+            pk = tkf.DevicePipeline(ctx, nh_k, k, nt_k, use_graph=True)
+            for _ in range(max(3, a.warmup)):
+                pk.run(hk, sk, d["seed_event"], nt_k, stream=stream)
+            torch.cuda.synchronize()
+            k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
+            for _ in range(a.steps):
+                pk.run(hk, sk, d["seed_event"], nt_k, stream=stream)
+            k1.record(stream)
+            torch.cuda.synchronize()
+            ctx.sync_status(stream)
+            kms = k0.elapsed_time(k1) / a.steps
+            batch_scan.append({"events": k, "tracks": nt_k, "ms_per_step": kms, "tracks_per_s": nt_k / (kms / 1e3)})
+            pk.close()
+        batch_scan.append({"events": b.n_events, "tracks": n_tr, "ms_per_step": ms, "tracks_per_s": n_tr / (ms / 1e3)})
 
     # ---------------- the same events on modules off the layers' cylinders (two-step building)
     two_step = None
@@ -878,6 +907,7 @@ def main():
         "mixed": mixed,
         "backward_pass": backward,
         "two_step": two_step,
+        "batch_scan": batch_scan,
         "plain": plain,
         "serve": serve,
         "autotune": {"grid": "seeds per warp tile x candidates per seed N (build launch ms)",
