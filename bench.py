@@ -44,6 +44,10 @@ FLOP_WINDOW = 40       # chi2 bounding box -> eta/phi bin ranges
 FLOP_CHI2 = 39         # one hit: tangent-plane residual, 2x2 S, chi2, half-cylinder test
 FLOP_UPDATE = 335      # Kalman gain, state update, Joseph-form covariance
 FLOP_SCATTER = 30      # Highland width and the four covariance terms
+# FP64 operations of one MIXED Kalman update (kalman_update<double, float>): B = H P (18), S and
+# its determinant (11), the inverse's three terms (3), chi2 (9), gain (36), D = B^T - K S (48),
+# Joseph form (168); conversions and the division are not counted
+FLOP_UPDATE_FP64 = 290
 # Work per seed on the batched workload, counted with the oracle's instrumentation
 # (python oracle/opcount.py --events 16 --workload batched, 53756 seeds):
 PER_SEED = dict(n_prop=19.2502, n_hits_examined=189.7167, n_updates=18.0985, n_kept=21.7897)
@@ -215,6 +219,23 @@ def _oracle_events(chunk, module_dr=0.0):
         sp, sP, sc2, snh, _ = O.fit(g, hits, p0, c0, ids, 0, 2)
         res = O.build(g, O.hit_index(g, hits), sp, sP, sc2, snh, ids)
         O.fit(g, hits, p0, c0, res.hits[:, 0, :], 0, L - 1)
+        done += len(local)
+    return done, time.perf_counter() - t0
+
+
+def _oracle_fit(chunk):
+    """The oracle's plain fit on a few events, each (hit records, track hit ids [n, L]): the
+    three-hit estimate and the Kalman fit over every layer with the known hits; returns
+    (tracks, seconds computing)."""
+    import oracle as O
+    from synth import Detector
+    det = Detector()
+    g = O.make_geom(det)
+    done = 0
+    t0 = time.perf_counter()
+    for hits, local in chunk:
+        p0, c0 = O.seed_estimate(g, hits, local[:, :3])
+        O.fit(g, hits, p0, c0, local, 0, det.n_layers - 1)
         done += len(local)
     return done, time.perf_counter() - t0
 
@@ -441,6 +462,9 @@ def main():
     ap.add_argument("--mixed", type=int, default=1, help="1: also time the batched step in MIXED precision")
     ap.add_argument("--backward", type=int, default=1,
                     help="1: also time the backward pass of the final fit over the batch's fitted tracks")
+    ap.add_argument("--fit", type=int, default=1,
+                    help="1: also time the plain fit (known hits, all layers) over every track of the batch")
+    ap.add_argument("--probe", type=int, default=1, help="1: measure the SMs' FP32/FP64/SFU throughput")
     ap.add_argument("--batch-scan", type=str, default="10,40,160",
                     help="also time the step on the batch's first K events for each K (comma list; empty: skip)")
     ap.add_argument("--two-step", type=int, default=160,
@@ -600,6 +624,40 @@ def main():
                     "form": "tkf_fit_backward over the pipeline's %d fitted tracks, layer 10 to layer 1, covariance "
                             "scale 1e4, FP32; one launch per pass, CUDA events; inputs larger than L2" % n_tr}
         del back
+
+    # ---------------- the plain fit: three-hit estimate and KF fit over all layers with the
+    # known hit assignment, every track of the batch (the fit configuration at 2.6 M tracks)
+    fit_leg = None
+    if a.fit:
+        true_ids = torch.as_tensor(np.ascontiguousarray(b.trk_hits.T), dtype=torch.int32).to(dev)
+        f_init = tkf.DeviceTracks.empty(n_tr, L, device=dev)
+        f_out = tkf.DeviceTracks.empty(n_tr, L, device=dev)
+
+        def run_fit():
+            ctx.seed_state(hits, d["seed_hits"], f_init, stream=stream)
+            ctx.fit(hits, f_init, 0, L - 1, f_out, hit_idx=true_ids, stream=stream)
+        for _ in range(max(3, a.warmup)):
+            run_fit()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(a.steps):
+            run_fit()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ctx.sync_status(stream)
+        f_ms = f0.elapsed_time(f1) / a.steps
+        n_full = int((f_out.nhits[:n_tr] == L).sum())  # tracks fitted through every layer's hit
+        f_flop = n_tr * ((L - 1) * FLOP_PROPAGATE + L * FLOP_UPDATE + (L - 1) * FLOP_SCATTER)
+        fit_leg = {"ms": f_ms, "tracks_per_s": n_tr / f_ms * 1e3, "achieved_tflops": f_flop / f_ms / 1e9,
+                   "frac_fp32_peak": f_flop / f_ms / 1e9 / FP32_PEAK_TFLOPS, "flop_per_track": f_flop / n_tr,
+                   "kernels": "k_seed<float>, k_fit<float,float>", "tracks_with_all_hits": n_full,
+                   "form": "tkf_seed_state + tkf_fit (layers 1..10, the known hit lists) over the batch's %d tracks, "
+                           "FP32; CUDA events over %d passes; inputs larger than L2" % (n_tr, a.steps)}
+        del f_init, f_out, true_ids
+
+    # ---------------- the SMs' arithmetic throughput (measured roofline denominators)
+    alu = tkf.probe_alu(stream) if a.probe else None
 
     # ---------------- throughput against batch size: the step on the batch's first K events
     batch_scan = None
@@ -766,11 +824,22 @@ def main():
         torch.cuda.synchronize()
         mctx.sync_status(stream)
         mms = m0.elapsed_time(m1) / a.steps
-        mixed = {"value": n_tr / (mms / 1e3), "unit": UNIT, "ms_per_step": mms, "build_ms": statistics.mean(mb),
+        mb_ms = statistics.mean(mb)
+        m_fp64 = PER_SEED["n_updates"] * FLOP_UPDATE_FP64 * n_tr / (mb_ms / 1e3) / 1e12
+        mixed = {"value": n_tr / (mms / 1e3), "unit": UNIT, "ms_per_step": mms, "build_ms": mb_ms,
+                 "roofline": {"kernel": "k_build<6,float,double>", "bound": "fp64", "achieved": m_fp64,
+                              "peak": None, "unit": "TFLOP/s", "frac": None,
+                              "flop_per_seed_fp64": PER_SEED["n_updates"] * FLOP_UPDATE_FP64,
+                              "note": "FP64 arithmetic of the updates against the measured FP64 multiply-add "
+                                      "rate (alu_peaks); ncu shows the FP64 pipe 87 % busy, most of it with the "
+                                      "float/double conversions and the division of each update"},
                  "precision": "mixed: FP32 propagation, window and chi2; FP64 innovation inverse and Joseph update",
                  "seeds_per_warp_tile": best_tile}
         mpipe.close()
         mctx.close()
+        if alu is not None:
+            mixed["roofline"]["peak"] = alu["fp64_tflops"]
+            mixed["roofline"]["frac"] = m_fp64 / alu["fp64_tflops"]
 
     # ---------------- plain form: one event per pass (direct launches), per-event latency
     plain = None
@@ -870,6 +939,12 @@ def main():
                 "sample": "the backward pass of events %d..%d (%d tracks) from the GPU's fitted states, FP64, one "
                           "process per core; time = the slowest worker's computing (%.2f s; %.2f s wall with the "
                           "transfer of the inputs)" % (ev[0], ev[-1], nb, compb, wallb)}
+        if fit_leg is not None:
+            nf, compf, wallf = cpu_baseline(sample, pool, cores, fn=_oracle_fit)
+            fit_leg["cpu_baseline"] = {
+                "value": nf / compf, "unit": "tracks/s", "cores": cores, "kind": "oracle",
+                "sample": "the plain fit of events %d..%d (%d tracks), FP64, one process per core; time = the "
+                          "slowest worker's computing (%.2f s; %.2f s wall)" % (ev[0], ev[-1], nf, compf, wallf)}
         if two_step is not None:
             # the oracle on the first events of the module-geometry batch (its share of the sample)
             n2s = next((k + 1 for k in range(b2.n_events) if int(b2.trk_off[k + 1]) >= a.cpu_tracks // 4), b2.n_events)
@@ -900,7 +975,9 @@ def main():
                      "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled by seeds from the 160-event case)",
                      "launch_ms": build_ms, "flop_per_seed": FLOP_PER_SEED,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                     "issue": issue_roofline(BUILD_WARP_INST_PER_SEED, n_tr, build_ms)},
+                     "issue": issue_roofline(BUILD_WARP_INST_PER_SEED, n_tr, build_ms),
+                     "measured_peak": None if alu is None else alu["fp32_tflops"],
+                     "frac_of_measured": None if alu is None else achieved / alu["fp32_tflops"]},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "e2e_pipeline": e2e_pipe,
@@ -908,6 +985,9 @@ def main():
         "backward_pass": backward,
         "two_step": two_step,
         "batch_scan": batch_scan,
+        "fit": fit_leg,
+        "alu_peaks": None if alu is None else dict(alu, source="tkf_probe_alu: independent FMA / __sinf chains, "
+                                                               "2048 threads per SM, best of 3 launches"),
         "plain": plain,
         "serve": serve,
         "autotune": {"grid": "seeds per warp tile x candidates per seed N (build launch ms)",

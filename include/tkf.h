@@ -429,6 +429,16 @@ typedef struct {
 int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits *hits, const tkf_hit_index_out *out,
                                 tkf_stream stream);
 
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Measures the arithmetic throughput of the current device's SMs, the denominators of the
+ * rooflines of the ALU-bound kernels: FP32 and FP64 fused multiply-add (TFLOP/s, 2 per FMA) and
+ * the special-function unit (__sinf, tera-operations/s).  Each probe runs independent
+ * dependency chains in 2048 threads per SM for about a millisecond; the best of three timed
+ * launches (after an untimed one) on `stream` is reported.  Synchronous: it returns after the
+ * last probe.  Errors: TKF_ERR_INVALID (a null output), TKF_ERR_NOMEM, TKF_ERR_CUDA. */
+int tkf_probe_alu(tkf_stream stream, double *fp32_tflops, double *fp64_tflops, double *sfu_tops);
+
 #ifdef __cplusplus
 }
 #endif

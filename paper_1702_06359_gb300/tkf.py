@@ -136,6 +136,7 @@ def lib():
         L.tkf_pipeline_captures.argtypes = [vp]
         L.tkf_pipeline_set_backward.argtypes = [vp, C.c_double]
         L.tkf_pipeline_backward_outputs.argtypes = [vp, C.POINTER(Tracks)]
+        L.tkf_probe_alu.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.tkf_pipeline_index.argtypes = [vp]
         L.tkf_pipeline_build_ms.argtypes = [vp, C.POINTER(C.c_float)]
         L.tkf_autotune_build.argtypes = [vp, vp, C.POINTER(Tracks), C.POINTER(Tracks), vp, i32, i32, vp, vp, vp]
@@ -361,6 +362,16 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def probe_alu(stream=None) -> dict:
+    """tkf_probe_alu: measured FP32 / FP64 multiply-add throughput (TFLOP/s) and special-function
+    throughput (tera-ops/s) of the current device."""
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    rc = lib().tkf_probe_alu(_stream(stream), C.byref(a), C.byref(b), C.byref(c))
+    if rc:
+        raise TkfError(rc, "tkf_probe_alu failed")
+    return {"fp32_tflops": a.value, "fp64_tflops": b.value, "sfu_tops": c.value}
 
 
 def build_hit_index_noalloc(cfg: Config, hits: DeviceHits, out: dict, stream=None):
