@@ -458,7 +458,8 @@ def main():
     ap.add_argument("--ref-tracks", type=int, default=120000, help="reference-arm sample per step (tracks)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve", type=int, default=1, help="1: also measure the served stream")
-    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="arrival window per rate; each rate runs for this long or 20000 events, whichever is fewer")
     ap.add_argument("--mixed", type=int, default=1, help="1: also time the batched step in MIXED precision")
     ap.add_argument("--backward", type=int, default=1,
                     help="1: also time the backward pass of the final fit over the batch's fitted tracks")
@@ -890,7 +891,7 @@ def main():
         mcfg = tkf.default_config(precision=tkf.MIXED)
         serve = {"batched": served_stream(tkf, lent, rates, a.serve_seconds, 20000, a.seed, cfg=mcfg, **opts),
                  "batched_fp32": served_stream(tkf, lent, rates, a.serve_seconds, 20000, a.seed, **opts),
-                 "plain": served_stream(tkf, lent, rates, a.serve_seconds, 4000, a.seed, n_slots=1,
+                 "plain": served_stream(tkf, lent, rates, a.serve_seconds, 20000, a.seed, n_slots=1,
                                         max_batch_events=1, max_batch_hits=max(hmax, 1), max_batch_tracks=1 << 16),
                  "batched_form": "MIXED precision, continuous batching over 3 slots, up to 64 events per batch "
                                  "(batched_fp32: the same in FP32)",
