@@ -177,6 +177,37 @@ def issue_roofline(inst_per_seed, seeds, launch_ms):
             "source": "ncu smsp__inst_executed.sum per seed of the 160-event capture"}
 
 
+def physics(b, hit_idx, par, nhits):
+    """Physics performance of the built and fitted tracks, the quantities of the paper's figure on
+    track-building physics: the fraction of seeds whose track has k hits (k = 0..10, the track
+    building's own count), the fraction carrying all ten of their own hits, the transverse
+    momentum resolution (pT_fit - pT_true) / pT_true against the generator's truth on the last
+    layer for those tracks (half-width of the central 68 % and RMS, in bins of true pT), and the
+    fraction with the wrong charge.  hit_idx: [L, n] batch hit ids; par: [6, n]; nhits: [n]."""
+    h = np.asarray(hit_idx)
+    L, n = h.shape
+    nh = np.asarray(nhits)
+    frac = {int(k): float(np.mean(nh == k)) for k in range(0, L + 1)}
+    own = np.all(h.T == b.trk_hits, axis=1)
+    w_fit, w_true = np.asarray(par)[3], b.truth[:, -1, 3]
+    pt_fit, pt_true = 1.0 / np.abs(w_fit), 1.0 / np.abs(w_true)
+    res = (pt_fit - pt_true) / pt_true
+    bins = [(0.5, 1.0), (1.0, 2.0), (2.0, 5.0), (5.0, 10.0)]
+    by_pt = []
+    for lo, hi in bins:
+        m = own & (pt_true >= lo) & (pt_true < hi)
+        r = res[m]
+        q16, q84 = np.percentile(r, [16, 84]) if len(r) else (np.nan, np.nan)
+        by_pt.append({"pt_gev": [lo, hi], "tracks": int(m.sum()), "sigma68": float(0.5 * (q84 - q16)),
+                      "rms": float(np.sqrt(np.mean(r * r))) if len(r) else None,
+                      "mean": float(np.mean(r)) if len(r) else None})
+    r = res[own]
+    return {"fraction_by_nhits": frac, "own_ten_hits": float(own.mean()),
+            "pt_resolution": {"sigma68": float(0.5 * np.subtract(*np.percentile(r, [84, 16]))),
+                              "rms": float(np.sqrt(np.mean(r * r))), "by_pt": by_pt},
+            "charge_misid": float(np.mean(np.sign(w_fit[own]) != np.sign(w_true[own])))}
+
+
 def efficiency(b, hit_idx):
     """Fraction of seeds whose built track has >= 75 % of its hits from the seed's own simulated
     track (hit_idx: [L, n_tracks] batch hit ids, -1 = hole)."""
@@ -595,6 +626,13 @@ def main():
         dist.barrier()
     total_tracks, ms_max, value = job_rate(n_tr, ms, dist, dev)
 
+    # ---------------- physics performance of the step's tracks
+    _, built_t, fitted_t = pipe.outputs()
+    fv_ph = tkf.tracks_tensors(fitted_t, L)
+    phys = physics(b, tkf.tracks_tensors(built_t, L)["hit_idx"][:, :n_tr].cpu().numpy(),
+                   fv_ph["par"][:, :n_tr].double().cpu().numpy(), fv_ph["nhits"][:n_tr].cpu().numpy())
+    del fv_ph
+
     # ---------------- the backward pass of the final fit over every fitted track of the batch
     backward = None
     if a.backward:
@@ -986,6 +1024,7 @@ def main():
         "backward_pass": backward,
         "two_step": two_step,
         "batch_scan": batch_scan,
+        "physics": phys,
         "fit": fit_leg,
         "alu_peaks": None if alu is None else dict(alu, source="tkf_probe_alu: independent FMA / __sinf chains, "
                                                                "2048 threads per SM, best of 3 launches"),
