@@ -69,9 +69,9 @@ FLOP_PER_SEED_TWO_STEP = (PER_SEED_TWO_STEP["n_prop"] * (FLOP_PROPAGATE + FLOP_W
                           + PER_SEED_TWO_STEP["n_kept"] * 6.0 / 7.0 * FLOP_SCATTER)
 MODULE_DR = 1.0  # cm between the inner and outer module rows of a layer (hit_dr = 0.5 cm)
 # DRAM bytes (read + write) per seed of the two-step FP32 building kernel, from one ncu capture
-# of the kernel as built now (160-event case: 405.0 MB for 701 095 seeds; summary in profiles/);
+# of the kernel as built now (160-event case: 404.6 MB for 701 095 seeds; summary in profiles/);
 # None whenever the kernel changes until it is captured again
-BUILD2_DRAM_BYTES_PER_SEED = 577.7
+BUILD2_DRAM_BYTES_PER_SEED = 577.1
 # Warp instructions per seed of the two build kernels (ncu smsp__inst_executed.sum of the same
 # captures: 2.01 G and 4.09 G for 701 095 seeds), for the instruction-issue roofline beside the
 # FP32 one: an SM sub-partition issues at most one warp instruction per cycle, 4 per SM;
@@ -84,9 +84,9 @@ SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # place), build, final fit
 KERNELS_PER_STEP = 11
 # DRAM bytes (read + write) per seed of the FP32 building kernel, from one ncu capture of the
-# kernel as built now (160-event case: 407.1 MB for 701 095 seeds; summary in profiles/);
+# kernel as built now (160-event case: 407.5 MB for 701 095 seeds; summary in profiles/);
 # None whenever the kernel changes until it is captured again
-BUILD_DRAM_BYTES_PER_SEED = 580.7
+BUILD_DRAM_BYTES_PER_SEED = 581.3
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 ISSUE_PEAK_WARP_INST_PER_S = SM_COUNT * 4 * SM_MAX_GHZ * 1e9
 
