@@ -80,7 +80,7 @@ def chi2_violations(got, ref, rel=CHI2_REL):
 
 def divergence_allowed(got_hits, ref, s, tol=1e-3):
     """Whether a GPU hit list that differs from the oracle's best for seed s is explained by a
-    fragile decision (the benchmark spec's exemption: two chi2 values within `tol` of each other or
+    fragile decision (the parity definition's exemption: two chi2 values within `tol` of each other or
     of the cut).  `ref` is the oracle's BuildResult.  Either the lists first differ at or after
     the oracle's first fragile layer, or the GPU's track is one of the oracle's final candidates
     with as many hits as the best and a total chi2 within `tol` of it (a near-tie in the final
