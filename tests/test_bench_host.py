@@ -90,3 +90,35 @@ def test_backward_baseline_helpers():
     assert np.all(st == 0)
     done, secs = bench._oracle_backward([(hits, b.trk_hits, pf, cf), (hits, b.trk_hits[:5], pf[:5], cf[:5])])
     assert done == 45 and secs > 0
+
+
+def test_physics_of_a_perfect_reconstruction_and_of_planted_errors(small_batch):
+    """Own hits and true states on the last layer: every track has ten own hits, the pT
+    resolution is zero and no charge is wrong; a track given a hole and another with its charge
+    flipped and pT 10 % high move exactly those figures."""
+    b = small_batch
+    L = b.detector.n_layers
+    hid = b.trk_hits.T.copy()
+    par = b.truth[:, -1].T.copy()  # [6, n]
+    nh = np.full(b.n_tracks, L)
+    ph = bench.physics(b, hid, par, nh)
+    assert ph["own_ten_hits"] == 1.0 and ph["charge_misid"] == 0.0
+    assert ph["fraction_by_nhits"][L] == 1.0
+    assert ph["pt_resolution"]["rms"] == pytest.approx(0.0, abs=1e-12)
+    hid[5, 0] = -1
+    nh[0] = L - 1
+    par[3, 1] = -par[3, 1] / 1.1  # flipped charge, pT 10 % high
+    ph = bench.physics(b, hid, par, nh)
+    n = b.n_tracks
+    assert ph["own_ten_hits"] == pytest.approx((n - 1) / n)
+    assert ph["fraction_by_nhits"][L - 1] == pytest.approx(1 / n)
+    assert ph["charge_misid"] == pytest.approx(1 / (n - 1))
+    assert ph["pt_resolution"]["rms"] == pytest.approx(0.1 / np.sqrt(n - 1), rel=1e-9)
+
+
+def test_issue_roofline_arithmetic():
+    r = bench.issue_roofline(2867.0, 1_000_000, 4.0)
+    assert r["achieved"] == pytest.approx(2867.0 * 1e6 / 4e-3)
+    assert r["peak"] == pytest.approx(152 * 4 * 2.07e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert bench.issue_roofline(None, 1, 1.0) is None
