@@ -88,7 +88,7 @@ class Settings:
     window_margin: float = 1e-3
     tie_tol: float = 1e-3
     n_cand: int = 6
-    brute_force: bool = False
+    brute_force: int = 0  # 1: every hit of the layer; 2: also no residual window (hit_dr > 0)
     first_build_layer: int = 3
     prior_sigma: tuple = (0.1, 0.1, 1.0, 0.5, 0.05, 0.05)
 

@@ -570,6 +570,21 @@ static void window_bins(const orc_geom *g, int layer, const double p[6], const d
         const double kappa = fabs(ORC_KB * g->bz * p[3]);
         U += (1.0 + g->window_margin) * t * (sa + t * kappa);
         W += (1.0 + g->window_margin) * t * fabs(cos(p[5]) / sin(p[5]));
+        /* that travel is uncertain too: to first order the crossing moves along the cylinder by
+         * hit_dr tan(alpha) and in z by t cot(theta), so the state's spread in
+         * alpha = phi - phi_pos (phi_pos = u / R) and in theta spreads the prediction at the
+         * hit's radius by (t / cos alpha) sigma_alpha along the cylinder and by
+         * t (sigma_theta / sin^2 theta + tan(alpha) |cot theta| sigma_alpha) in z.  The standard
+         * deviation of a sum is at most the sum of the standard deviations, so adding
+         * sqrt(cut) times these to U and W makes the window contain the chi2 < cut ellipse at the
+         * hit's own radius as well. */
+        const double cfl = ca > 0.01 ? ca : 0.01;
+        const double sig_alpha = sqrt(P[4 * 6 + 4]) + sqrt(S[0]) / R;
+        const double sig_theta = sqrt(P[5 * 6 + 5]);
+        const double st = sin(p[5]);
+        U += (1.0 + g->window_margin) * sqrt(g->chi2_cut) * t / cfl * sig_alpha;
+        W += (1.0 + g->window_margin) * sqrt(g->chi2_cut) * t *
+             (sig_theta / (st * st) + sa / cfl * fabs(cos(p[5]) / st) * sig_alpha);
     }
     *Uo = U;
     *Wo = W;
@@ -592,7 +607,8 @@ static int near(double a, double b, double tol)
 /*
  * Combinatorial building of one seed through layers first..n_layers-1.
  * For each layer and each candidate in rank order: propagate; collect every compatible hit
- * of the window (or of the whole layer when brute_force) as a branch; a candidate with no
+ * of the window (or of the whole layer when brute_force; brute_force = 2 also drops the
+ * residual window of hits off the cylinder) as a branch; a candidate with no
  * compatible hit yields one hole branch.  All branches of the seed are ranked and the best
  * n_cand kept (n_cand <= 0: keep all); hit branches get the Kalman update, then every kept
  * branch gets the scattering noise of the layer (except on the outermost layer).
@@ -651,10 +667,13 @@ static int build_seed(const orc_geom *g, const orc_event *ev, const double sp[6]
                              * state at the hit's own radius */
                             double H[12], r[2], V[4];
                             meas_model(q, h, H, r, V);
-                            const int inside = fabs(r[0]) <= U && fabs(r[1]) <= W;
+                            /* brute_force 2: no window at all, every hit of the layer is
+                             * scored at its own radius (the check that the window loses none) */
+                            const int inside = g->brute_force == 2 || (fabs(r[0]) <= U && fabs(r[1]) <= W);
                             /* within tol of an edge: the window decision is fragile if the hit
                              * would pass the chi2 cut */
-                            const int edge = fabs(fabs(r[0]) - U) <= tol * U || fabs(fabs(r[1]) - W) <= tol * W;
+                            const int edge = g->brute_force != 2 &&
+                                             (fabs(fabs(r[0]) - U) <= tol * U || fabs(fabs(r[1]) - W) <= tol * W);
                             if (!inside && !edge) continue;
                             if (stats) stats->n_steps += 1;
                             if (orc_propagate(g, C[c].p, target_radius(g, l, h), q2, J2) != ORC_OK) continue;

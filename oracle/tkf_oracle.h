@@ -22,7 +22,9 @@ typedef struct {
     double window_margin;
     double tie_tol;        /* relative closeness that marks a ranking or cut decision fragile */
     int n_cand;            /* candidates kept per seed; <= 0 keeps every branch */
-    int brute_force;       /* 1: examine every hit of the layer instead of the binned window */
+    int brute_force;       /* 1: examine every hit of the layer instead of the binned window;
+                              2 (hit_dr > 0): also without the residual window, every hit of the
+                              layer scored at its own radius */
     int first_build_layer; /* 0-based layer where building starts (3 = fourth layer) */
     double hit_dr;         /* largest |hit radius - layer radius| (cm); 0: hits lie on the cylinders.
                               > 0: the CMS-geometry variant of Sec. 2.2, states are taken to each

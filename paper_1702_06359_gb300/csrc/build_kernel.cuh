@@ -152,9 +152,19 @@ __device__ __forceinline__ void scan_window(const BuildArgs &a, int ev, int l, R
         fast_sc(p[5], &sth, &cth);
         cot = cth / sth;
         const R ca = ab(xp * cphi + yp * sphi) / rp, sa = ab(xp * sphi - yp * cphi) / rp;
-        const R t = pick<R>(a.hit_dr_f, a.hit_dr) / (ca > R(0.01) ? ca : R(0.01));
+        const R cfl = ca > R(0.01) ? ca : R(0.01);
+        const R t = pick<R>(a.hit_dr_f, a.hit_dr) / cfl;
         U += mg * t * (sa + t * ab(kb * p[3]));
         W += mg * t * ab(cot);
+        // the spread of that travel over the state's covariance: sigma of alpha = phi - phi_pos
+        // (phi_pos = u / R) and of theta move the crossing at the hit's radius by
+        // (t / cos alpha) sigma_alpha along the cylinder and t (sigma_theta / sin^2 theta +
+        // tan(alpha) |cot theta| sigma_alpha) in z; sqrt(cut) times these keeps the chi2 < cut
+        // ellipse at the hit's own radius inside the window
+        const R sig_a = sq(P[sym(4, 4)]) + sq(Suu) / Rl;
+        const R rc = sq(cut) * mg * t;
+        U += rc / cfl * sig_a;
+        W += rc * (sq(P[sym(5, 5)]) / (sth * sth) + sa / cfl * ab(cot) * sig_a);
     }
     const R phip = at2(yp, xp);
     // compatible hits satisfy |u| = r_p |sin(phi_h - phi_p)| <= U on the near half-cylinder,

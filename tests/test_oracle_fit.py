@@ -7,6 +7,7 @@ Kalman filter must reproduce it), symmetric positive-definite covariances, unit-
 and a flat chi2 p-value on simulated tracks, and the generator's simulated scattering kicks.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -214,3 +215,31 @@ def test_scattering_noise_matches_simulated_kicks():
     cot = 1.0 / np.tan(before[:, 5])
     m = np.abs(cot) > 0.2
     assert np.corrcoef(zw[m], zth[m])[0, 1] > 0.999
+
+
+HIGHLAND = os.path.join(os.path.dirname(__file__), "golden", "highland.txt")
+
+
+def test_scattering_width_hand_worked():
+    """The width and the covariance terms of the scattering noise against cases worked by hand
+    from the PDG's Highland formula (tests/golden/highland.txt, every step shown there): theta0 =
+    sqrt(Q_theta_theta), and each of the four non-zero terms, to 1e-12 relative."""
+    n = 0
+    for line in open(HIGHLAND):
+        if line.startswith("#") or not line.strip():
+            continue
+        x, y, z, w, phi, th, xx0, mass, th0, qww, qtw, qpp, qtt = (float(v) for v in line.split())
+        det = Detector(x_over_x0=(xx0,) * 10, mass=mass)
+        g = O.make_geom(det)
+        Q = O.scatter(g, 4, np.array([x, y, z, w, phi, th]), np.zeros((6, 6)))
+        assert math.sqrt(Q[5, 5]) == pytest.approx(th0, rel=1e-12, abs=0), line
+        for (i, j), ref in (((3, 3), qww), ((5, 3), qtw), ((4, 4), qpp), ((5, 5), qtt)):
+            assert Q[i, j] == pytest.approx(ref, rel=1e-12, abs=1e-43), (line, i, j)
+            assert Q[j, i] == Q[i, j]
+        # nothing else is touched: position rows and the phi-(w, theta) terms stay zero
+        mask = np.ones((6, 6), bool)
+        for i, j in ((3, 3), (5, 3), (3, 5), (4, 4), (5, 5)):
+            mask[i, j] = False
+        assert np.all(Q[mask] == 0.0)
+        n += 1
+    assert n == 4
