@@ -420,11 +420,15 @@ typedef struct {
  * than that capacity are rejected with TKF_ERR_TOO_LARGE before any work is queued.
  *
  * The first call on a device looks up the device address of that array (with that device
- * current); make that first call before capturing a stream into a CUDA graph.  All calls
- * share the one array and the call clears what must start at zero, so calls may follow each
- * other freely on one stream, but calls whose work overlaps on the GPU (other streams, other
- * host threads) race on it and must be serialised by the caller.  Kernel-side errors (a hit
- * layer out of range) are not reported; validate inputs beforehand.
+ * current) and keeps it for the life of the process; make that first call before capturing a
+ * stream into a CUDA graph.  The kept address belongs to the device's primary context: after
+ * cudaDeviceReset (or any reset of that context) it no longer points at the array, so a
+ * process that resets a device must not call this function on it again.  All calls share the
+ * one array and each call clears the counters that must start at zero, so calls may follow
+ * each other freely on one stream, but calls whose work overlaps on the GPU (other streams,
+ * other host threads) race on it and must be serialised by the caller.  The array also holds
+ * an error word that the kernels set (a hit layer out of range) but that is never cleared nor
+ * read: kernel-side errors are not reported, so validate inputs beforehand.
  * Errors: TKF_ERR_INVALID (bad configuration or arguments), TKF_ERR_TOO_LARGE, TKF_ERR_CUDA. */
 int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits *hits, const tkf_hit_index_out *out,
                                 tkf_stream stream);

@@ -31,19 +31,38 @@ def test_noalloc_rejects_inputs_beyond_its_capacity():
 
 
 @pytest.mark.gpu
-def test_noalloc_index_equals_allocating_index_on_consecutive_calls():
+@pytest.mark.parametrize("branch", ["multi_launch", "block_per_event"])
+def test_noalloc_index_equals_allocating_index_on_consecutive_calls(branch):
+    """Two calls in a row against tkf_build_hit_index, bit for bit.  "multi_launch": a few
+    events on the ten-layer barrel (fewer events than SMs: the index is built by kernels that
+    spread one event over the GPU).  "block_per_event": 200 events (more than the SMs) on a
+    four-layer barrel with 8 x 8 bins (800 segments, 51 200 bins, inside the fixed capacity),
+    which takes the one-block-per-event kernels."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
     from _gpu import device_hits
     from synth import Detector, EventSpec, generate
 
-    det = Detector()
-    cfg = tkf.default_config()
+    if branch == "multi_launch":
+        det = Detector()
+        cfg = tkf.default_config()
+        batches = [generate(EventSpec(seed=51, n_events=3, n_tracks=[2000, 0, 1500], noise_frac=0.3), det),
+                   generate(EventSpec(seed=52, n_events=2, n_tracks=[800, 3000], noise_frac=0.5), det)]
+    else:
+        det = Detector(radii=(4.0, 8.0, 12.0, 16.0), x_over_x0=(0.03,) * 4)
+        cfg = tkf.default_config(n_layers=4, radius=det.radii, x_over_x0=det.x_over_x0, n_eta_bins=8,
+                                 n_phi_bins=8, eta_min=-1.6, eta_bin_w=0.4)
+        rng = np.random.default_rng(53)
+        batches = [generate(EventSpec(seed=53, n_events=200, n_tracks=rng.integers(0, 400, 200).tolist(),
+                                      noise_frac=0.3), det),
+                   generate(EventSpec(seed=54, n_events=200, n_tracks=rng.integers(0, 300, 200).tolist(),
+                                      noise_frac=0.5), det)]
+        props = torch.cuda.get_device_properties(0)
+        assert all(b.n_events >= props.multi_processor_count for b in batches)
+        assert 200 * 4 <= tkf.NOALLOC_MAX_SEGMENTS and 200 * 4 * 64 <= tkf.NOALLOC_MAX_BINS
     ctx = tkf.Context(cfg)
     L, NB = cfg.n_layers, cfg.n_eta_bins * cfg.n_phi_bins
-    batches = [generate(EventSpec(seed=51, n_events=3, n_tracks=[2000, 0, 1500], noise_frac=0.3), det),
-               generate(EventSpec(seed=52, n_events=2, n_tracks=[800, 3000], noise_frac=0.5), det)]
 
     def raw(ptr, count, dtype):
         class _Wrap:
@@ -79,3 +98,4 @@ def test_noalloc_index_equals_allocating_index_on_consecutive_calls():
         assert torch.equal(out["event_off"], raw(v.event_off, E + 1, torch.int32))
         assert int(out["bin_off"][-1]) == n
         ref.free()
+    ctx.close()
