@@ -142,8 +142,12 @@ def test_graph_replay_equals_direct_calls_other_precisions(prec):
 def test_seed_fit_and_continued_fit_agree_with_the_separate_calls(prec):
     """tkf_seed_fit equals tkf_seed_state + tkf_fit, and a fit continued over layers 3..9 from
     the seed fit equals one fit over 0..9, within rounding of the fused arithmetic (bit for
-    bit is not promised: the compiler may fuse multiply-adds differently in the two kernels)."""
-    from _gpu import PAR_FLOOR
+    bit is not promised: the compiler may fuse multiply-adds differently in the two kernels).
+    In FP32 each form carries its own rounding error against the exact fit, up to about 5e-5
+    relative in q/pT on the precision sweep, so two forms may differ by the parity tolerance
+    (1e-4) on a few tracks (up to 2e-5 here); nearly all tracks agree far closer (99 % within
+    1e-5), which a dropped layer, update or scattering term would not give."""
+    from _gpu import CHI2_REL, PAR_FLOOR, PAR_REL
     b = _batch(65, n_events=4)
     ctx = tkf.Context(tkf.default_config(precision=prec))
     L, n = ctx.cfg.n_layers, b.n_tracks
@@ -157,14 +161,17 @@ def test_seed_fit_and_continued_fit_agree_with_the_separate_calls(prec):
     ctx.fit(dh, init, 0, L - 1, full, hit_idx=hid)
     ctx.fit(dh, fused, 3, L - 1, cont, hit_idx=hid, continue_fit=True)
     ctx.sync_status()
-    rel = 1e-5 if prec == tkf.FP32 else 1e-12
+    rel = PAR_REL if prec == tkf.FP32 else 1e-12
     floor = torch.as_tensor(PAR_FLOOR, device="cuda", dtype=sep.par.dtype)[:, None]
     for a_, b_ in ((sep, fused), (full, cont)):
         assert torch.equal(a_.nhits, b_.nhits)
         d = (a_.par - b_.par).abs() / torch.maximum(a_.par.abs(), floor)
         d[4] = torch.remainder(d[4] + np.pi, 2 * np.pi) - np.pi
         assert float(d.abs().max()) < rel
-        assert float(((a_.chi2 - b_.chi2).abs() / torch.clamp(a_.chi2.abs(), min=1.0)).max()) < 10 * rel
+        if prec == tkf.FP32:
+            assert float(torch.quantile(d.abs().max(dim=0).values.double(), 0.99)) < 1e-5
+        dc = (a_.chi2 - b_.chi2).abs() / torch.clamp(a_.chi2.abs(), min=1.0)
+        assert float(dc.max()) < (CHI2_REL if prec == tkf.FP32 else 1e-11)
     assert torch.equal(fused.hit_idx[:3], sh) and bool((fused.hit_idx[3:] == -1).all())
 
 
