@@ -266,7 +266,9 @@ template <int NMAX, class R, class U, bool kTwo> struct BuildMinBlocks {
                                      : 1;
 };
 
-template <int NMAX, class R, class U, bool kTwo>
+// kExactN: the candidates kept per seed equal NMAX, so the segment width and the merge's loops
+// are compile-time constants (unrolled); otherwise N = a.ncand <= NMAX at run time.
+template <int NMAX, class R, class U, bool kTwo, bool kExactN>
 __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTwo>::value)) k_build(const BuildArgs a)
 {
     constexpr int W = kBuildThreads / 32;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTw
     __shared__ signed char hist_par[W][TKF_MAX_LAYERS][32];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int N = a.ncand;
+    const int N = kExactN ? NMAX : a.ncand;
     const int spw = 32 / N;
     const int grp = lane / N;
     const int r = lane - grp * N;
@@ -432,16 +434,24 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTw
     }
 }
 
+#ifndef TKF_BUILD_EXACT_N
+#define TKF_BUILD_EXACT_N 1
+#endif
 template <class R, class U, bool kTwo = false>
 cudaError_t launch_build_t(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy)
 {
     const void *fn = nullptr;
+    const bool exact = TKF_BUILD_EXACT_N && a.ncand == nmax;
     switch (nmax) {
-    case 1: fn = (const void *)k_build<1, R, U, kTwo>; break;
-    case 4: fn = (const void *)k_build<4, R, U, kTwo>; break;
-    case 6: fn = (const void *)k_build<6, R, U, kTwo>; break;
-    case 10: fn = (const void *)k_build<10, R, U, kTwo>; break;
-    case 16: fn = (const void *)k_build<16, R, U, kTwo>; break;
+    case 1: fn = (const void *)k_build<1, R, U, kTwo, true>; break;
+    case 4: fn = exact ? (const void *)k_build<4, R, U, kTwo, true> : (const void *)k_build<4, R, U, kTwo, false>; break;
+    case 6: fn = exact ? (const void *)k_build<6, R, U, kTwo, true> : (const void *)k_build<6, R, U, kTwo, false>; break;
+    case 10:
+        fn = exact ? (const void *)k_build<10, R, U, kTwo, true> : (const void *)k_build<10, R, U, kTwo, false>;
+        break;
+    case 16:
+        fn = exact ? (const void *)k_build<16, R, U, kTwo, true> : (const void *)k_build<16, R, U, kTwo, false>;
+        break;
     default: return cudaErrorInvalidValue;
     }
     if (occupancy) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, fn, kBuildThreads, 0);
