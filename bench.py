@@ -379,10 +379,15 @@ def run_reference(a):
 # ----------------------------------------------------------------------------- served stream
 class LentEvents:
     """Every event of a batch as a tkf_event lent to the server (borrow = 1): hit planes are
-    slices of the batch's pinned host planes, seed ids event-local [3][n] blocks."""
+    slices of the batch's pinned host planes, seed ids event-local [3][n] blocks of one pinned
+    array."""
 
     def __init__(self, tkf, b, host, n_layers):
-        self.seeds = np.empty(3 * b.n_tracks, dtype=np.int32)
+        import torch
+        self._seeds_t = torch.empty(3 * b.n_tracks, dtype=torch.int32)
+        if torch.cuda.is_available():
+            self._seeds_t = self._seeds_t.pin_memory()  # pinned like the hit planes
+        self.seeds = self._seeds_t.numpy()
         self.events = []
         base = {k: host[k].data_ptr() for k in ("x", "y", "z", "var_u", "var_v", "layer")}
         for e in range(b.n_events):
@@ -834,8 +839,10 @@ def main():
 
     # ---------------- end to end through the public serving API (host buffers lent to tkf_server)
     lent = LentEvents(tkf, b, host, L)
+    # pinned result memory for two passes' worth of batches: after the warm-up passes every batch
+    # finds a free result buffer and nothing is allocated or freed while timing
     e2e_opts = dict(n_slots=a.e2e_slots, max_batch_events=a.e2e_batch, max_batch_hits=1 << 24,
-                    max_batch_tracks=1 << 20)
+                    max_batch_tracks=1 << 20, result_bytes=2 << 30)
     sv = tkf.Server(ctx.cfg, **e2e_opts)
     for _ in range(max(1, a.warmup)):
         server_pass(sv, lent)
@@ -854,6 +861,8 @@ def main():
            "h2d_bytes_per_step": lent.h2d,
            "d2h_bytes_per_step": lent.d2h, "ms_per_step": 1e3 * statistics.mean(e2e_s),
            "ms_per_step_median": 1e3 * statistics.median(e2e_s), "ms_per_step_max": 1e3 * max(e2e_s),
+           "ms_per_step_p99": 1e3 * float(np.percentile(e2e_s, 99)),
+           "passes_ms": [round(1e3 * x, 3) for x in e2e_s],
            "form": "tkf_submit_events of all %d events (hit planes lent from pinned host memory), tkf_wait_all, "
                    "tkf_release_many; %d slots, batches of up to %d events; host wall clock, mean over the "
                    "timed passes (Python garbage collection off during them)" % (b.n_events, a.e2e_slots, a.e2e_batch)}
@@ -1046,7 +1055,11 @@ def main():
         "plain": plain,
         "serve": serve,
         "autotune": {"grid": "seeds per warp tile x candidates per seed N (build launch ms)",
-                     "by_n_cand": n_grid, "best": best_tile, "n_cand": 6},
+                     "by_n_cand": n_grid, "best": best_tile, "n_cand": 6,
+                     "hit_tile": None,
+                     "hit_tile_note": "no hit-tile axis: the build kernel stages no hit tiles in shared memory; each "
+                                      "candidate's window is a few short index ranges (about 3 hits) read through "
+                                      "L1/L2, so there is no tile size to tune"},
         "gpu_launches": KERNELS_PER_STEP * a.steps,
         "clocks": clocks.summary(),
     }

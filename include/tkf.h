@@ -336,12 +336,16 @@ typedef struct {
 /* Result of one event (pinned host memory owned by the server, valid until tkf_release): the
  * final fit of the best built candidate of every seed -- par [6][stride], cov [21][stride],
  * chi2, nhits, first n_tracks columns -- and its hit ids [n_layers][stride] (event-local,
- * -1 = hole); timestamps (steady clock, ns) of submission, batch launch and completion. */
+ * -1 = hole); timestamps (steady clock, ns) of submission, batch launch and completion; and
+ * the device interval of the event's batch, from before its first input copy to after its
+ * last result copy on the slot's stream (CUDA event times in ms since the server's creation,
+ * -1 if unavailable): two batches whose intervals intersect were in flight on the GPU at once. */
 typedef struct {
     int32_t status, n_tracks, stride;
     const float *par, *cov, *chi2;
     const int32_t *nhits, *hit_idx;
     int64_t t_submit_ns, t_start_ns, t_done_ns;
+    float gpu_start_ms, gpu_done_ms;
 } tkf_result;
 
 typedef struct {
@@ -375,10 +379,11 @@ int tkf_release(tkf_server *server, uint64_t ticket);
 
 int tkf_server_get_stats(tkf_server *server, tkf_server_stats *out);
 
-/* Batch forms for clients that move many events per call (the calls above, in a loop).
- * tkf_submit_events submits events[0..n) in order and stops at the first refusal: returns
- * that status (TKF_ERR_AGAIN: queue full) with *n_accepted events accepted and their tickets
- * in tickets[0..*n_accepted).  tkf_wait_all fills results[k] for tickets[k], waiting up to
+/* Batch forms for clients that move many events per call.  tkf_submit_events submits
+ * events[0..n) in order, each as its own arrival (the worker may start a batch with the first
+ * events while the rest are queued), and stops at the first refusal: returns that status
+ * (TKF_ERR_AGAIN: queue full; TKF_ERR_INVALID: a malformed event) with *n_accepted events
+ * accepted and their tickets in tickets[0..*n_accepted).  tkf_wait_all fills results[k] for tickets[k], waiting up to
  * timeout_us in total (0: do not wait); it returns the first error (TKF_ERR_TIMEOUT,
  * TKF_ERR_NOTREADY, TKF_ERR_INVALID), the results before it being filled.  tkf_release_many
  * releases every ticket given and returns the first error. */

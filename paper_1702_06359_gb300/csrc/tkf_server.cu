@@ -61,6 +61,7 @@ struct Done {
     OutBuf *buf = nullptr;  // results at column trk0 of the batch's planes (stride buf->cap)
     int trk0 = 0;
     int64_t t_submit = 0, t_start = 0, t_done = 0;
+    float gpu_start_ms = 0.f, gpu_done_ms = 0.f;  // the batch's device interval (server clock)
     int status = TKF_OK;
     int n = 0;
     bool done = false;
@@ -92,6 +93,7 @@ struct Slot {
     tkf_pipeline *pipe = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t t_begin = nullptr, t_end = nullptr;  // timed: the batch's first and last device work
     // host staging (pinned) for copied events, and the per-batch event offsets
     Pinned<float> hx, hy, hz, hvu, hvv;
     Pinned<int> hlayer, hraw, hoff, htoff;
@@ -128,6 +130,7 @@ struct tkf_server {
     int worker_error = TKF_OK;
     std::vector<OutBuf *> free_bufs;  // result buffers no event holds
     size_t result_bytes = 0;          // pinned bytes of all result buffers, free or held
+    cudaEvent_t t_ref = nullptr;      // device time zero of the batches' intervals
 };
 
 namespace {
@@ -138,6 +141,8 @@ void free_slot(Slot &s)
     if (s.ctx) tkf_destroy(s.ctx);
     if (s.stream) cudaStreamDestroy(s.stream);
     if (s.done) cudaEventDestroy(s.done);
+    if (s.t_begin) cudaEventDestroy(s.t_begin);
+    if (s.t_end) cudaEventDestroy(s.t_end);
     for (void *p : {(void *)s.dx, (void *)s.dy, (void *)s.dz, (void *)s.dvu, (void *)s.dvv, (void *)s.dlayer,
                     (void *)s.draw, (void *)s.doff, (void *)s.dtoff, (void *)s.dseeds, (void *)s.dsev, (void *)s.dlocal})
         cudaFree(p);
@@ -164,12 +169,18 @@ OutBuf *get_outbuf(tkf_server *sv, int trk)
     int cap = 1024;
     while (cap < trk) cap *= 2;
     cap = std::min(cap, std::max(sv->opt.max_batch_tracks, trk));
+    // the smallest free buffer that holds the batch (of its size class or larger): after the
+    // first batches every launch reuses pinned memory, with no allocation (cudaMallocHost) or
+    // free (cudaFreeHost synchronises the device) on the serving path
+    size_t best = sv->free_bufs.size();
     for (size_t k = 0; k < sv->free_bufs.size(); ++k)
-        if (sv->free_bufs[k]->cap == cap) {
-            OutBuf *b = sv->free_bufs[k];
-            sv->free_bufs.erase(sv->free_bufs.begin() + k);
-            return b;
-        }
+        if (sv->free_bufs[k]->cap >= trk && (best == sv->free_bufs.size() || sv->free_bufs[k]->cap < sv->free_bufs[best]->cap))
+            best = k;
+    if (best < sv->free_bufs.size()) {
+        OutBuf *b = sv->free_bufs[best];
+        sv->free_bufs.erase(sv->free_bufs.begin() + best);
+        return b;
+    }
     const size_t bytes = outbuf_bytes(sv, cap);
     while (sv->result_bytes + bytes > sv->opt.result_bytes && !sv->free_bufs.empty()) {
         free_outbuf(sv, sv->free_bufs.back());
@@ -205,6 +216,8 @@ int init_slot(tkf_server *sv, Slot &s)
     if ((st = tkf_pipeline_create(s.ctx, (int)H, (int)E, (int)T, 0, &s.pipe))) return st;
     cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (!e) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+    if (!e) e = cudaEventCreate(&s.t_begin);
+    if (!e) e = cudaEventCreate(&s.t_end);
     if (!e) e = s.hx.alloc(H); if (!e) e = s.hy.alloc(H); if (!e) e = s.hz.alloc(H);
     if (!e) e = s.hvu.alloc(H); if (!e) e = s.hvv.alloc(H); if (!e) e = s.hlayer.alloc(H);
     if (!e) e = s.hraw.alloc(3 * T); if (!e) e = s.hoff.alloc(E + 1); if (!e) e = s.htoff.alloc(E + 1);
@@ -292,6 +305,7 @@ int launch_batch(tkf_server *sv, Slot &s, std::vector<Pending> &evs)
     CopyRun run[7];
     int hit = 0, trk = 0;
     s.evs.clear();
+    if (cudaEventRecord(s.t_begin, st) != cudaSuccess) return TKF_ERR_CUDA;
     for (size_t k = 0; k < evs.size(); ++k) {
         Pending &p = evs[k];
         const size_t nb = (size_t)p.n_hits * 4, sb = (size_t)p.n_seeds * 12;
@@ -353,6 +367,7 @@ int launch_batch(tkf_server *sv, Slot &s, std::vector<Pending> &evs)
         if (!e) e = cudaMemcpyAsync(o->nhits, fitted.nhits, trk * 4, cudaMemcpyDeviceToHost, st);
         if (!e) e = cudaMemcpy2DAsync(o->hit, hp, s.dlocal, T * 4, trk * 4, L, cudaMemcpyDeviceToHost, st);
     }
+    if (!e) e = cudaEventRecord(s.t_end, st);
     if (!e) e = cudaEventRecord(s.done, st);
     if (e) return TKF_ERR_CUDA;
     s.t_start = now_ns();
@@ -364,6 +379,10 @@ int launch_batch(tkf_server *sv, Slot &s, std::vector<Pending> &evs)
 void harvest(tkf_server *sv, Slot &s)
 {
     const int64_t t_done = now_ns();
+    float g0 = 0.f, g1 = 0.f;  // the batch's device interval against the server's time zero
+    if (cudaEventElapsedTime(&g0, sv->t_ref, s.t_begin) != cudaSuccess ||
+        cudaEventElapsedTime(&g1, sv->t_ref, s.t_end) != cudaSuccess)
+        g0 = g1 = -1.f;
     OutBuf *o = s.out;
     o->refs = 1;  // held by this function until the end
     for (const EvInfo &ev : s.evs) {
@@ -377,6 +396,8 @@ void harvest(tkf_server *sv, Slot &s)
         d.t_submit = ev.t_submit;
         d.t_start = s.t_start;
         d.t_done = t_done;
+        d.gpu_start_ms = g0;
+        d.gpu_done_ms = g1;
         d.status = TKF_OK;
         d.done = true;
         sv->stats.events_done += 1;
@@ -509,6 +530,13 @@ int tkf_server_create(const tkf_config *cfg, const tkf_server_options *opt, tkf_
             return st;
         }
     }
+    if (cudaEventCreate(&sv->t_ref) != cudaSuccess || cudaEventRecord(sv->t_ref, sv->slots[0].stream) != cudaSuccess ||
+        cudaEventSynchronize(sv->t_ref) != cudaSuccess) {
+        for (Slot &t : sv->slots) free_slot(t);
+        if (sv->t_ref) cudaEventDestroy(sv->t_ref);
+        delete sv;
+        return TKF_ERR_CUDA;
+    }
     sv->worker = std::thread(worker_loop, sv);
     *out = sv;
     return TKF_OK;
@@ -530,14 +558,19 @@ int tkf_server_destroy(tkf_server *sv)
             held.push_back(kv.second.buf);
     for (OutBuf *b : held) free_outbuf(sv, b);
     for (OutBuf *b : sv->free_bufs) free_outbuf(sv, b);
+    if (sv->t_ref) cudaEventDestroy(sv->t_ref);
     delete sv;
     return TKF_OK;
 }
 
-int tkf_submit_event(tkf_server *sv, const tkf_event *ev, uint64_t *ticket)
+}  // extern "C"
+
+namespace {
+
+// Checks one event; TKF_OK or TKF_ERR_INVALID.
+int check_event(const tkf_server *sv, const tkf_event *ev)
 {
-    const int64_t t_submit = now_ns();
-    if (!sv || !ev || !ticket || ev->n_hits < 0 || ev->n_seeds < 0) return TKF_ERR_INVALID;
+    if (!ev || ev->n_hits < 0 || ev->n_seeds < 0) return TKF_ERR_INVALID;
     if (ev->n_hits > 0 && (!ev->x || !ev->y || !ev->z || !ev->var_u || !ev->var_v || !ev->layer)) return TKF_ERR_INVALID;
     if (ev->n_seeds > 0 && !ev->seed_hits) return TKF_ERR_INVALID;
     if (ev->n_hits > sv->opt.max_batch_hits || ev->n_seeds > sv->opt.max_batch_tracks) return TKF_ERR_INVALID;
@@ -547,16 +580,17 @@ int tkf_submit_event(tkf_server *sv, const tkf_event *ev, uint64_t *ticket)
         hi = std::max(hi, ev->seed_hits[t]);
     }
     if (lo < 0 || (ev->n_seeds > 0 && hi >= ev->n_hits)) return TKF_ERR_INVALID;
-    const size_t bytes = ev->borrow ? 64 : (size_t)ev->n_hits * 24 + (size_t)ev->n_seeds * 12;
-    {
-        std::lock_guard<std::mutex> lk(sv->mu);
-        if (sv->worker_error) return sv->worker_error;
-        if (sv->queued_bytes + bytes > sv->opt.queue_bytes) {
-            sv->stats.rejected += 1;
-            return TKF_ERR_AGAIN;
-        }
-        sv->queued_bytes += bytes;  // reserve before copying outside the lock
-    }
+    return TKF_OK;
+}
+
+size_t event_bytes(const tkf_event *ev)
+{
+    return ev->borrow ? 64 : (size_t)ev->n_hits * 24 + (size_t)ev->n_seeds * 12;
+}
+
+// The queue entry of a checked event (copies its arrays unless it is lent).
+Pending make_pending(const tkf_event *ev, int64_t t_submit)
+{
     Pending p;
     p.n_hits = ev->n_hits;
     p.n_seeds = ev->n_seeds;
@@ -574,18 +608,63 @@ int tkf_submit_event(tkf_server *sv, const tkf_event *ev, uint64_t *ticket)
         p.layer.assign(ev->layer, ev->layer + ev->n_hits);
         p.seeds.assign(ev->seed_hits, ev->seed_hits + 3 * ev->n_seeds);
     }
-    p.bytes = bytes;
+    p.bytes = event_bytes(ev);
     p.t_submit = t_submit;
+    return p;
+}
+
+// Submits events[0..n): the checked prefix that fits the queue budget is reserved, copied
+// outside the lock, then queued in one piece with one wake-up of the worker (n = 1: one
+// arrival).
+int submit_some(tkf_server *sv, const tkf_event *events, int32_t n, uint64_t *tickets, int32_t *n_accepted)
+{
+    const int64_t t_submit = now_ns();
+    *n_accepted = 0;
+    int32_t m = 0;
+    int first_err = TKF_OK;
+    while (m < n && (first_err = check_event(sv, &events[m])) == TKF_OK) ++m;
+    int32_t k = 0;
+    size_t bytes = 0;
     {
         std::lock_guard<std::mutex> lk(sv->mu);
-        p.ticket = sv->next_ticket++;
-        *ticket = p.ticket;
-        sv->results.emplace(p.ticket, Done());
-        sv->queue.push_back(std::move(p));
-        sv->stats.submitted += 1;
+        if (sv->worker_error) return sv->worker_error;
+        while (k < m && sv->queued_bytes + bytes + event_bytes(&events[k]) <= sv->opt.queue_bytes) {
+            bytes += event_bytes(&events[k]);
+            ++k;
+        }
+        if (k < m) {
+            sv->stats.rejected += 1;
+            first_err = TKF_ERR_AGAIN;
+        }
+        sv->queued_bytes += bytes;  // reserved before copying outside the lock
     }
-    sv->cv_work.notify_one();
-    return TKF_OK;
+    std::vector<Pending> ps;
+    ps.reserve(k);
+    for (int32_t i = 0; i < k; ++i) ps.push_back(make_pending(&events[i], t_submit));
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (int32_t i = 0; i < k; ++i) {
+            ps[i].ticket = sv->next_ticket++;
+            tickets[i] = ps[i].ticket;
+            sv->results.emplace(ps[i].ticket, Done());
+            sv->queue.push_back(std::move(ps[i]));
+            sv->stats.submitted += 1;
+        }
+    }
+    if (k) sv->cv_work.notify_one();
+    *n_accepted = k;
+    return first_err;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tkf_submit_event(tkf_server *sv, const tkf_event *ev, uint64_t *ticket)
+{
+    if (!sv || !ev || !ticket) return TKF_ERR_INVALID;
+    int32_t n_acc = 0;
+    return submit_some(sv, ev, 1, ticket, &n_acc);
 }
 
 int tkf_poll(tkf_server *sv, uint64_t ticket, tkf_result *r, int64_t timeout_us)
@@ -617,6 +696,8 @@ int tkf_poll(tkf_server *sv, uint64_t ticket, tkf_result *r, int64_t timeout_us)
     r->t_submit_ns = d.t_submit;
     r->t_start_ns = d.t_start;
     r->t_done_ns = d.t_done;
+    r->gpu_start_ms = d.gpu_start_ms;
+    r->gpu_done_ms = d.gpu_done_ms;
     return TKF_OK;
 }
 
@@ -636,8 +717,12 @@ int tkf_submit_events(tkf_server *sv, const tkf_event *events, int32_t n, uint64
 {
     if (!sv || (n > 0 && (!events || !tickets)) || n < 0 || !n_accepted) return TKF_ERR_INVALID;
     *n_accepted = 0;
+    // one event at a time, as separate arrivals: the worker starts a batch with the first events
+    // while the rest are still being queued, so the first copies and kernels overlap the
+    // submission of the burst and the batches that follow grow to max_batch_events
     for (int32_t k = 0; k < n; ++k) {
-        const int st = tkf_submit_event(sv, &events[k], &tickets[k]);
+        int32_t one = 0;
+        const int st = submit_some(sv, &events[k], 1, &tickets[k], &one);
         if (st) return st;
         *n_accepted = k + 1;
     }

@@ -82,7 +82,8 @@ class Event(C.Structure):
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_tracks", C.c_int32), ("stride", C.c_int32), ("par", C.c_void_p), ("cov", C.c_void_p),
                 ("chi2", C.c_void_p), ("nhits", C.c_void_p), ("hit_idx", C.c_void_p), ("t_submit_ns", C.c_int64),
-                ("t_start_ns", C.c_int64), ("t_done_ns", C.c_int64)]
+                ("t_start_ns", C.c_int64), ("t_done_ns", C.c_int64), ("gpu_start_ms", C.c_float),
+                ("gpu_done_ms", C.c_float)]
 
 
 class ServerStats(C.Structure):
@@ -561,7 +562,8 @@ class Server:
         return code, dict(status=r.status, n_tracks=n, par=arr(r.par, 6, C.c_float),
                           cov=arr(r.cov, 21, C.c_float), chi2=arr(r.chi2, 0, C.c_float),
                           nhits=arr(r.nhits, 0, C.c_int32), hit_idx=arr(r.hit_idx, L, C.c_int32),
-                          t_submit_ns=r.t_submit_ns, t_start_ns=r.t_start_ns, t_done_ns=r.t_done_ns)
+                          t_submit_ns=r.t_submit_ns, t_start_ns=r.t_start_ns, t_done_ns=r.t_done_ns,
+                          gpu_start_ms=r.gpu_start_ms, gpu_done_ms=r.gpu_done_ms)
 
     def release(self, ticket):
         return lib().tkf_release(self.handle, int(ticket))

@@ -83,6 +83,46 @@ def test_result_is_the_same_alone_and_in_the_mix():
     sv.close()
 
 
+def test_batches_overlap_on_the_device_and_each_result_equals_its_alone_run():
+    """Continuous batching with three slots of two events: submitted together, the events run
+    as several batches in flight at once -- at least two batches' launch-to-completion host
+    intervals intersect, and so do their device intervals (CUDA event times from before the
+    first input copy to after the last result copy on each slot's stream) -- and every event's
+    result is bit for bit the one it gets alone (one event per batch, one slot)."""
+    b, evs = _events(74, n_events=18)
+    sv1 = tkf.Server(n_slots=1, max_batch_events=1, max_batch_hits=1 << 20, max_batch_tracks=1 << 16)
+    alone = []
+    for ev in evs:
+        code, t = sv1.submit(ev)
+        assert code == tkf.OK
+        alone.append(_wait(sv1, t))
+        sv1.release(t)
+    sv1.close()
+    sv = tkf.Server(n_slots=3, max_batch_events=2, max_batch_hits=1 << 20, max_batch_tracks=1 << 16)
+    arr = (tkf.Event * len(evs))(*[ev.struct for ev in evs])
+    code, tickets = sv.submit_many(arr)
+    assert code == tkf.OK and len(tickets) == len(evs)
+    results = [_wait(sv, t) for t in tickets]
+    for r, r0 in zip(results, alone):
+        for k in ("par", "cov", "chi2", "nhits", "hit_idx"):
+            assert np.array_equal(r[k], r0[k]), k
+    batches = {}
+    for r in results:
+        assert r["gpu_start_ms"] >= 0 and r["gpu_done_ms"] >= r["gpu_start_ms"]
+        batches[(r["t_start_ns"], r["gpu_start_ms"])] = (r["t_start_ns"], r["t_done_ns"], r["gpu_start_ms"],
+                                                         r["gpu_done_ms"])
+    iv = sorted(batches.values())
+    assert len(iv) >= len(evs) // 2
+    host = [(a, c) for a in range(len(iv)) for c in range(a + 1, len(iv))
+            if iv[a][0] < iv[c][1] and iv[c][0] < iv[a][1]]
+    dev = [(a, c) for a, c in host if iv[a][2] < iv[c][3] and iv[c][2] < iv[a][3]]
+    assert host, "no two batches were in flight at once"
+    assert dev, "no two batches overlapped on the device"
+    for t in tickets:
+        sv.release(t)
+    sv.close()
+
+
 def test_borrowed_inputs_give_the_same_results():
     b, evs = _events(73, n_events=6)
     sv = tkf.Server(n_slots=2, max_batch_events=8, max_batch_hits=1 << 20, max_batch_tracks=1 << 16)
