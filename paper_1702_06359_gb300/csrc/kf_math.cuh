@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ieee_cvt.cuh"
 #include "sparse_gen.cuh"
 
 namespace tkf {
@@ -371,6 +372,52 @@ __host__ __device__ __forceinline__ R step_chi2(const R p[6], const R P[21], R s
     return fast_div(u * (Svv * u - R(2) * Suv * v) + Suu * v * v, det);
 }
 
+// ------------------------------------------------------------------ float <-> double without the FP64 unit
+// (ieee_cvt.cuh): the mixed-precision update converts with integer operations on the bit fields.
+#ifndef TKF_INT_CVT
+#define TKF_INT_CVT 1
+#endif
+
+// cvt_up<U>(x): x (float or double) as U; cvt_down<R>(x): x (double) as R (float or double).
+template <class U> __device__ __forceinline__ U cvt_up(float x)
+{
+#if TKF_INT_CVT
+    if constexpr (sizeof(U) == 8) return f32_to_f64_bits(x);
+#endif
+    return U(x);
+}
+template <class U> __device__ __forceinline__ U cvt_up(double x) { return U(x); }
+template <class R> __device__ __forceinline__ R cvt_down(float x) { return R(x); }
+template <class R> __device__ __forceinline__ R cvt_down(double x)
+{
+#if TKF_INT_CVT
+    if constexpr (sizeof(R) == 4) return f64_to_f32_bits(x);
+#endif
+    return R(x);
+}
+
+// 1/x for x > 0: in float the approximate division; in double Newton's iteration for the
+// reciprocal, y <- y (2 - x y) written as y + y (1 - x y), from the correctly rounded
+// single-precision reciprocal of x rounded to float (relative error below 2^-23; each step
+// squares it, so two steps reach double rounding) -- four double operations where the IEEE
+// division takes about three times as many on the scarce double-precision units.  An x outside
+// the float range takes the IEEE division.
+template <class U> __device__ __forceinline__ U recip(U x) { return U(1) / x; }
+template <> __device__ __forceinline__ double recip<double>(double x)
+{
+#if TKF_INT_CVT
+    const float xf = f64_to_f32_bits(x);
+    const float yf = __frcp_rn(xf);
+    if (!(xf > 1e-37f && xf < 1e37f)) return 1.0 / x;
+    double y = f32_to_f64_bits(yf);
+    y = fma(y, fma(-x, y, 1.0), y);
+    y = fma(y, fma(-x, y, 1.0), y);
+    return y;
+#else
+    return 1.0 / x;
+#endif
+}
+
 // Kalman update with the Joseph-form covariance:
 //   B = H P (2x6), S = B H^T + V, K = B^T S^-1, p += K r,
 //   P' = (I - K H) P (I - K H)^T + K V K^T = P - K B - (B^T - K S) K^T   (element-wise below).
@@ -379,29 +426,29 @@ __host__ __device__ __forceinline__ R step_chi2(const R p[6], const R P[21], R s
 // are computed in U (double in the mixed mode).  Returns false when S is not positive definite;
 // writes the hit's chi2 to *chi2.
 template <class U, class R>
-__host__ __device__ __forceinline__ bool kalman_update(R pR[6], R PR[21], R xh_, R yh_, R zh_, R vu_, R vv_, U *chi2)
+__device__ __forceinline__ bool kalman_update(R pR[6], R PR[21], R xh_, R yh_, R zh_, R vu_, R vv_, U *chi2)
 {
     const R irR = R(1) / sq(xh_ * xh_ + yh_ * yh_);
     const R shR = yh_ * irR, chR = xh_ * irR;
     const R uR = chR * (yh_ - pR[1]) - shR * (xh_ - pR[0]);
     const R vR = zh_ - pR[2];
-    const U u = U(uR), v = U(vR);
-    const U sh = U(shR), ch = U(chR);
+    const U u = cvt_up<U>(uR), v = cvt_up<U>(vR);
+    const U sh = cvt_up<U>(shR), ch = cvt_up<U>(chR);
     U P[21];
 #pragma unroll
-    for (int k = 0; k < 21; ++k) P[k] = U(PR[k]);
+    for (int k = 0; k < 21; ++k) P[k] = cvt_up<U>(PR[k]);
     U B0[6], B1[6];
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
         B0[j] = ch * P[sym(1, j)] - sh * P[sym(0, j)];
         B1[j] = P[sym(2, j)];
     }
-    const U Suu = ch * B0[1] - sh * B0[0] + U(vu_);
+    const U Suu = ch * B0[1] - sh * B0[0] + cvt_up<U>(vu_);
     const U Suv = B0[2];
-    const U Svv = B1[2] + U(vv_);
+    const U Svv = B1[2] + cvt_up<U>(vv_);
     const U det = Suu * Svv - Suv * Suv;
     if (!(det > U(0))) return false;
-    const U id = U(1) / det;
+    const U id = recip<U>(det);
     const U i00 = Svv * id, i01 = -Suv * id, i11 = Suu * id;
     *chi2 = u * (i00 * u + i01 * v) + v * (i01 * u + i11 * v);
     U K0[6], K1[6], D0[6], D1[6];
@@ -414,7 +461,7 @@ __host__ __device__ __forceinline__ bool kalman_update(R pR[6], R PR[21], R xh_,
     }
     // state update in the state's type (the gain rounded to it)
 #pragma unroll
-    for (int i = 0; i < 6; ++i) pR[i] = pR[i] + R(K0[i]) * uR + R(K1[i]) * vR;
+    for (int i = 0; i < 6; ++i) pR[i] = pR[i] + cvt_down<R>(K0[i]) * uR + cvt_down<R>(K1[i]) * vR;
     pR[4] = wrap_phi(pR[4]);
     // Joseph form, element by element: P - (K B + D K^T) in one fused chain
 #pragma unroll
@@ -425,7 +472,7 @@ __host__ __device__ __forceinline__ bool kalman_update(R pR[6], R PR[21], R xh_,
             t = fma(K1[i], B1[j], t);
             t = fma(D0[i], K0[j], t);
             t = fma(D1[i], K1[j], t);
-            PR[sym(i, j)] = R(P[sym(i, j)] - t);
+            PR[sym(i, j)] = cvt_down<R>(P[sym(i, j)] - t);
         }
     return true;
 }
