@@ -51,16 +51,17 @@ class Geom(C.Structure):
         ("brute_force", C.c_int),
         ("first_build_layer", C.c_int),
         ("hit_dr", C.c_double),
+        ("disk_z", C.c_double * MAX_LAYERS),
     ]
 
 
 HIT_DTYPE = np.dtype([("x", "f8"), ("y", "f8"), ("z", "f8"), ("var_u", "f8"), ("var_v", "f8"),
-                      ("layer", "i4")], align=True)
+                      ("layer", "i4"), ("disk", "i4")], align=True)
 
 
 class Hit(C.Structure):
     _fields_ = [("x", C.c_double), ("y", C.c_double), ("z", C.c_double), ("var_u", C.c_double),
-                ("var_v", C.c_double), ("layer", C.c_int)]
+                ("var_v", C.c_double), ("layer", C.c_int), ("disk", C.c_int)]
 
 
 assert C.sizeof(Hit) == HIT_DTYPE.itemsize
@@ -102,6 +103,8 @@ def lib():
         L = C.CDLL(compile_library())
         dp, ip, vp = C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p
         L.orc_propagate.argtypes = [C.POINTER(Geom), dp, C.c_double, dp, dp]
+        L.orc_propagate_plane.argtypes = [C.POINTER(Geom), dp, C.c_double, dp, dp]
+        L.orc_hit_eta_bin.argtypes = [C.POINTER(Geom), C.POINTER(Hit)]
         L.orc_scatter.argtypes = [C.POINTER(Geom), C.c_int, dp, dp]
         L.orc_scatter.restype = None
         L.orc_chi2.argtypes = [dp, dp, C.POINTER(Hit)]
@@ -145,6 +148,8 @@ def make_geom(det, st: Settings = Settings()) -> Geom:
     g.brute_force = int(st.brute_force)
     g.first_build_layer = st.first_build_layer
     g.hit_dr = 0.5 * getattr(det, "module_dr", 0.0)
+    for l in range(det.n_layers):
+        g.disk_z[l] = det.disk_z[l] if getattr(det, "disk_z", ()) else 0.0
     return g
 
 
@@ -159,11 +164,23 @@ def hits_of(batch, sl=slice(None), exact=False) -> np.ndarray:
         h["x"], h["y"], h["z"] = batch.x[sl], batch.y[sl], batch.z[sl]
     h["var_u"], h["var_v"] = batch.var_u[sl], batch.var_v[sl]
     h["layer"] = batch.layer[sl]
+    dz = getattr(batch.detector, "disk_z", ())
+    if dz:
+        h["disk"] = (np.asarray(dz) > 0.0)[h["layer"]].astype(np.int32)
     return h
 
 
-def make_hit(x, y, z, var_u, var_v, layer=0) -> Hit:
-    return Hit(float(x), float(y), float(z), float(var_u), float(var_v), int(layer))
+def make_hit(x, y, z, var_u, var_v, layer=0, disk=0) -> Hit:
+    return Hit(float(x), float(y), float(z), float(var_u), float(var_v), int(layer), int(disk))
+
+
+def propagate_plane(g: Geom, p, Zp):
+    """Propagation to the plane z = Zp (an endcap disk): (status, state, Jacobian)."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    out = np.zeros(6)
+    J = np.zeros(36)
+    st = lib().orc_propagate_plane(C.byref(g), _d(p), float(Zp), _d(out), _d(J))
+    return st, out, J.reshape(6, 6)
 
 
 def propagate(g: Geom, p, R):

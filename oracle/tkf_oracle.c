@@ -32,6 +32,13 @@
  *     a hit is a candidate if its residual to that prediction lies inside the window; its
  *     chi2 is then taken at its own radius.  (The paper's second, per-hit propagation starts
  *     from the prediction on the average radius; the two transports compose to this one.)
+ *   - endcap disks (disk_z[l] > 0; the "endcap z" of Sec. 2.2): a layer is a pair of planes
+ *     z = +-disk_z[l]; a state goes to the one on the side of its z by the exact helix/plane
+ *     intersection; a disk hit is measured on the disk's plane in r-phi (u, along the tangent
+ *     (-sin phi_h, cos phi_h, 0)) and r (v, along (cos phi_h, sin phi_h, 0)); the window is the
+ *     chi2-cut box in (u, v) mapped to phi and to the eta bins of the radii it spans, eta of a
+ *     disk hit being asinh(z / r_hit); a compatible hit lies on the disk the state reached (not
+ *     the opposite endcap's, which the (u, v) measurement alone cannot tell apart).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -110,11 +117,12 @@ static double dsinc(double x)
  * The transport Jacobian J = dp_out/dp_in is the analytic derivative at fixed s plus
  * (dp_out/ds)(ds/dp_in), with ds/dp_in = -(dr/dp_in)/(dr/ds) from the constraint r(s, p_in) = R.
  */
+static int helix_at(const orc_geom *g, const double pin[6], double s, int plane, double pout[6], double J[36]);
+
 int orc_propagate(const orc_geom *g, const double pin[6], double R, double pout[6], double J[36])
 {
-    const double x0 = pin[0], y0 = pin[1], z0 = pin[2], w = pin[3], phi0 = pin[4], th = pin[5];
+    const double x0 = pin[0], y0 = pin[1], w = pin[3], phi0 = pin[4];
     const double kappa = -ORC_KB * g->bz * w;
-    const double cot_th = cos(th) / sin(th);
     const double nx = -sin(phi0), ny = cos(phi0);
     double s;
 
@@ -149,6 +157,20 @@ int orc_propagate(const orc_geom *g, const double pin[6], double R, double pout[
         s = best;
     }
 
+    return helix_at(g, pin, s, 0, pout, J);
+}
+
+/*
+ * The state at transverse path s along the helix of pin, and the transport Jacobian for a
+ * crossing defined by the constraint c(s, p_in) = 0 with c = r - R (plane = 0: a cylinder) or
+ * c = z - Zp (plane = 1): J = dp_out/dp_in at fixed s plus (dp_out/ds)(ds/dp_in), with
+ * ds/dp_in = -(dc/dp_in)/(dc/ds).
+ */
+static int helix_at(const orc_geom *g, const double pin[6], double s, int plane, double pout[6], double J[36])
+{
+    const double x0 = pin[0], y0 = pin[1], z0 = pin[2], w = pin[3], phi0 = pin[4], th = pin[5];
+    const double kappa = -ORC_KB * g->bz * w;
+    const double cot_th = cos(th) / sin(th);
     const double half = 0.5 * kappa * s, mid = phi0 + half;
     const double sn = sinc(half);
     const double x1 = x0 + s * cos(mid) * sn;
@@ -177,14 +199,39 @@ int orc_propagate(const orc_geom *g, const double pin[6], double R, double pout[
 
     /* derivative along the path */
     double dp_ds[6] = {cos(phi1), sin(phi1), cot_th, 0.0, kappa, 0.0};
-    /* constraint r^2 = x^2 + y^2 = R^2:  ds/dp_j = -(x dx/dp_j + y dy/dp_j) / (x dx/ds + y dy/ds) */
-    const double drds = x1 * dp_ds[0] + y1 * dp_ds[1];
-    if (drds == 0.0) return ORC_ERR_NOREACH;
     double ds_dp[6];
-    for (int j = 0; j < 6; ++j) ds_dp[j] = -(x1 * F[0 * 6 + j] + y1 * F[1 * 6 + j]) / drds;
+    if (plane) {
+        /* constraint z = Zp:  ds/dp_j = -(dz/dp_j) / (dz/ds) */
+        if (cot_th == 0.0) return ORC_ERR_NOREACH;
+        for (int j = 0; j < 6; ++j) ds_dp[j] = -F[2 * 6 + j] / cot_th;
+    } else {
+        /* constraint r^2 = x^2 + y^2 = R^2:  ds/dp_j = -(x dx/dp_j + y dy/dp_j) / (x dx/ds + y dy/ds) */
+        const double drds = x1 * dp_ds[0] + y1 * dp_ds[1];
+        if (drds == 0.0) return ORC_ERR_NOREACH;
+        for (int j = 0; j < 6; ++j) ds_dp[j] = -(x1 * F[0 * 6 + j] + y1 * F[1 * 6 + j]) / drds;
+    }
     for (int i = 0; i < 6; ++i)
         for (int j = 0; j < 6; ++j) J[i * 6 + j] = F[i * 6 + j] + dp_ds[i] * ds_dp[j];
     return ORC_OK;
+}
+
+/*
+ * Exact propagation of the helix to the plane z = Zp (an endcap disk, Sec. 2.2): z(s) =
+ * z0 + s cot(theta) = Zp gives s = (Zp - z0) tan(theta), which must be positive (the plane lies
+ * ahead); the state there is the helix at that s.  A track that would turn through more than a
+ * full circle before reaching the plane (a looper) does not reach it.
+ */
+int orc_propagate_plane(const orc_geom *g, const double pin[6], double Zp, double pout[6], double J[36])
+{
+    const double th = pin[5];
+    const double cot_th = cos(th) / sin(th);
+    if (cot_th == 0.0) return ORC_ERR_NOREACH;
+    const double s = (Zp - pin[2]) / cot_th;
+    if (!(s > 0.0)) return ORC_ERR_NOREACH;
+    if (!(fabs(ORC_KB * g->bz * pin[3]) * s <= 2.0 * ORC_PI)) return ORC_ERR_NOREACH;
+    const int st = helix_at(g, pin, s, 1, pout, J);
+    pout[2] = Zp; /* z0 + s cot(theta) is the plane up to rounding */
+    return st;
 }
 
 /* ------------------------------------------------------------------ multiple scattering */
@@ -192,7 +239,8 @@ int orc_propagate(const orc_geom *g, const double pin[6], double R, double pout[
 /*
  * Thin-scatterer process noise at layer l (Highland width, unit charge, mass hypothesis m):
  *   theta0 = 0.0136/(beta p) sqrt(t) (1 + 0.038 ln(t / beta^2)),  t = (x/X0) / |cos alpha|,
- * alpha the angle between the direction and the cylinder normal.  Two independent kicks of
+ * alpha the angle between the direction and the layer's normal (radial on a cylinder, z on
+ * a disk).  Two independent kicks of
  * width theta0 orthogonal to the direction change theta by d1 and phi by d2/sin(theta); with
  * |p| fixed, q/pT changes by -(q/pT) cot(theta) d1.
  */
@@ -205,7 +253,8 @@ void orc_scatter(const orc_geom *g, int layer, const double p[6], double P[36])
     const double beta = mom / sqrt(mom * mom + g->mass * g->mass);
     const double r = sqrt(p[0] * p[0] + p[1] * p[1]);
     const double d[3] = {sin(th) * cos(phi), sin(th) * sin(phi), cos(th)};
-    const double nrm[3] = {p[0] / r, p[1] / r, 0.0};
+    const int disk = g->disk_z[layer] > 0.0;                        /* a disk's normal is the z axis */
+    const double nrm[3] = {disk ? 0.0 : p[0] / r, disk ? 0.0 : p[1] / r, disk ? 1.0 : 0.0};
     const double cos_a = fabs(d[0] * nrm[0] + d[1] * nrm[1] + d[2] * nrm[2]);
     const double t = xt / cos_a;
     const double th0 = 0.0136 / (beta * mom) * sqrt(t) * (1.0 + 0.038 * log(t / (beta * beta)));
@@ -220,15 +269,23 @@ void orc_scatter(const orc_geom *g, int layer, const double p[6], double P[36])
 /* ------------------------------------------------------------------ Kalman update (Sec. 2.2) */
 
 /* Measurement model on the plane tangent to the cylinder at the hit: rows of H are the
- * tangent direction (-sin phi_h, cos phi_h, 0) and the z axis. */
+ * tangent direction (-sin phi_h, cos phi_h, 0) and the z axis.  On an endcap disk the plane is
+ * the disk's own: rows (-sin phi_h, cos phi_h, 0) (r-phi) and the radial direction
+ * (cos phi_h, sin phi_h, 0) (r). */
 static void meas_model(const double p[6], const orc_hit *h, double H[12], double r[2], double V[4])
 {
     const double ph = atan2(h->y, h->x);
     const double sh = sin(ph), ch = cos(ph);
     memset(H, 0, 12 * sizeof(double));
-    H[0] = -sh; H[1] = ch; H[6 + 2] = 1.0;
+    H[0] = -sh; H[1] = ch;
     r[0] = -sh * (h->x - p[0]) + ch * (h->y - p[1]);
-    r[1] = h->z - p[2];
+    if (h->disk) {
+        H[6 + 0] = ch; H[6 + 1] = sh;
+        r[1] = ch * (h->x - p[0]) + sh * (h->y - p[1]);
+    } else {
+        H[6 + 2] = 1.0;
+        r[1] = h->z - p[2];
+    }
     V[0] = h->var_u; V[1] = 0.0; V[2] = 0.0; V[3] = h->var_v;
 }
 
@@ -331,6 +388,7 @@ int orc_seed_estimate(const orc_geom *g, const orc_hit *h1, const orc_hit *h2, c
     p[5] = atan2(1.0, cot);
     memset(P, 0, 36 * sizeof(double));
     for (int i = 0; i < 6; ++i) P[i * 6 + i] = g->prior_sigma[i] * g->prior_sigma[i];
+    if (h1->disk) P[2 * 6 + 2] = 0.0; /* on an endcap disk z is the disk's, known exactly */
     return ORC_OK;
 }
 
@@ -339,6 +397,16 @@ int orc_seed_estimate(const orc_geom *g, const orc_hit *h1, const orc_hit *h2, c
 static double target_radius(const orc_geom *g, int layer, const orc_hit *h)
 {
     return (g->hit_dr > 0.0 && h) ? sqrt(h->x * h->x + h->y * h->y) : g->radius[layer];
+}
+
+/* Propagation to layer l: its cylinder (at target_radius), or for an endcap layer the disk on
+ * the side of the state's z (states between two disks of one side stay on that side). */
+static int propagate_layer(const orc_geom *g, int layer, const double p[6], const orc_hit *h, double q[6],
+                           double J[36])
+{
+    if (g->disk_z[layer] > 0.0)
+        return orc_propagate_plane(g, p, p[2] >= 0.0 ? g->disk_z[layer] : -g->disk_z[layer], q, J);
+    return orc_propagate(g, p, target_radius(g, layer, h), q, J);
 }
 
 /* ------------------------------------------------------------------ fit (Sec. 2) */
@@ -361,7 +429,7 @@ int orc_fit_track(const orc_geom *g, const double pin[6], const double Pin[36], 
     for (int l = first; l <= last; ++l) {
         const int hid = hit_of_layer[l];
         if (l > first) {
-            int st = orc_propagate(g, p, target_radius(g, l, hid >= 0 ? &hits[hid] : 0), q, J);
+            int st = propagate_layer(g, l, p, hid >= 0 ? &hits[hid] : 0, q, J);
             if (st != ORC_OK) return st;
             sandwich6(J, P, PJ);
             memcpy(p, q, sizeof p);
@@ -437,7 +505,7 @@ int orc_fit_backward(const orc_geom *g, const double pin[6], const double Pin[36
     for (int l = last; l >= first; --l) {
         const int hid = hit_of_layer[l];
         if (l < last) {
-            int st = orc_propagate(g, p, target_radius(g, l, hid >= 0 ? &hits[hid] : 0), q, J);
+            int st = propagate_layer(g, l, p, hid >= 0 ? &hits[hid] : 0, q, J);
             if (st != ORC_OK) return st;
             sandwich6(J, P, PJ);
             memcpy(p, q, sizeof p);
@@ -481,6 +549,16 @@ int orc_eta_bin(const orc_geom *g, int layer, double z)
     return b;
 }
 
+int orc_hit_eta_bin(const orc_geom *g, const orc_hit *h)
+{
+    if (g->disk_z[h->layer] <= 0.0) return orc_eta_bin(g, h->layer, h->z);
+    const double eta = asinh(h->z / sqrt(h->x * h->x + h->y * h->y));
+    int b = (int)floor((eta - g->eta_min) / g->eta_bin_w);
+    if (b < 0) b = 0;
+    if (b >= g->n_eta_bins) b = g->n_eta_bins - 1;
+    return b;
+}
+
 int orc_phi_bin(const orc_geom *g, double phi)
 {
     int b = (int)floor((phi + ORC_PI) / (2.0 * ORC_PI) * g->n_phi_bins);
@@ -509,7 +587,7 @@ int orc_hit_index(const orc_geom *g, int n, const orc_hit *hits, int *bin_of_hit
     for (int i = 0; i < n; ++i) {
         const orc_hit *h = &hits[i];
         if (h->layer < 0 || h->layer >= g->n_layers) return ORC_ERR_INVALID;
-        bin_of_hit[i] = orc_eta_bin(g, h->layer, h->z) * g->n_phi_bins + orc_phi_bin(g, atan2(h->y, h->x));
+        bin_of_hit[i] = orc_hit_eta_bin(g, h) * g->n_phi_bins + orc_phi_bin(g, atan2(h->y, h->x));
         order[i] = i;
     }
     g_sort_hits = hits;
@@ -545,14 +623,64 @@ static int cmp_branch(const void *a, const void *b)
     return hx < hy ? -1 : (hx > hy);
 }
 
+static int eta_to_bin(const orc_geom *g, double eta)
+{
+    const double f = floor((eta - g->eta_min) / g->eta_bin_w);
+    if (!(f >= 0.0)) return 0; /* also -inf */
+    if (f >= g->n_eta_bins - 1) return g->n_eta_bins - 1;
+    return (int)f;
+}
+
+static void phi_bins(const orc_geom *g, double ph, double dphi, int *pb0, int *pb1)
+{
+    const double f0 = (ph - dphi + ORC_PI) / (2.0 * ORC_PI) * g->n_phi_bins;
+    const double f1 = (ph + dphi + ORC_PI) / (2.0 * ORC_PI) * g->n_phi_bins;
+    *pb0 = (int)floor(f0);
+    *pb1 = (int)floor(f1);
+    if (*pb1 - *pb0 + 1 >= g->n_phi_bins) { *pb0 = 0; *pb1 = g->n_phi_bins - 1; }
+}
+
+/* Window on an endcap disk: the chi2-cut box |u| <= U (r-phi), |v| <= W (r) of the innovation
+ * covariance at phi_h = phi of the prediction.  A hit at (r_h, phi_p + d) has
+ * u = r_p sin(d) and v = r_h - r_p cos(d), so the box holds |d| <= asin(U / r_p) and radii from
+ * r_p cos(asin(U / r_p)) - W to r_p + W, whose eta bins (eta = asinh(z / r) on the disk at z)
+ * are scanned. */
+static void disk_window_bins(const orc_geom *g, int layer, const double p[6], const double P[36],
+                             double var_u, double var_v, int *eb0, int *eb1, int *pb0, int *pb1,
+                             double *Uo, double *Wo)
+{
+    const double rp = sqrt(p[0] * p[0] + p[1] * p[1]);
+    const double ph = atan2(p[1], p[0]);
+    orc_hit probe = {p[0], p[1], p[2], var_u, var_v, layer, 1};
+    double H[12], r[2], V[4], S[4], Si[4];
+    meas_model(p, &probe, H, r, V);
+    innovation(P, H, V, S, Si);
+    const double U = sqrt(g->chi2_cut * S[0]) * (1.0 + g->window_margin);
+    const double W = sqrt(g->chi2_cut * S[3]) * (1.0 + g->window_margin);
+    *Uo = U;
+    *Wo = W;
+    const double dphi = asin(U / rp < 1.0 ? U / rp : 1.0);
+    const double r_lo = rp * cos(dphi) - W, r_hi = rp + W;
+    const double zd = p[2];
+    const double e_far = asinh(zd / r_hi);                                   /* the largest radius */
+    const double e_near = r_lo > 0.0 ? asinh(zd / r_lo) : (zd > 0.0 ? INFINITY : -INFINITY);
+    *eb0 = eta_to_bin(g, zd > 0.0 ? e_far : e_near);
+    *eb1 = eta_to_bin(g, zd > 0.0 ? e_near : e_far);
+    phi_bins(g, ph, dphi, pb0, pb1);
+}
+
 static void window_bins(const orc_geom *g, int layer, const double p[6], const double P[36],
                         double var_u, double var_v, int *eb0, int *eb1, int *pb0, int *pb1,
                         double *Uo, double *Wo)
 {
+    if (g->disk_z[layer] > 0.0) {
+        disk_window_bins(g, layer, p, P, var_u, var_v, eb0, eb1, pb0, pb1, Uo, Wo);
+        return;
+    }
     /* chi2-cut bounding box of the innovation covariance at phi_h = phi of the prediction */
     const double R = g->radius[layer];
     const double ph = atan2(p[1], p[0]);
-    orc_hit probe = {R * cos(ph), R * sin(ph), p[2], var_u, var_v, layer};
+    orc_hit probe = {R * cos(ph), R * sin(ph), p[2], var_u, var_v, layer, 0};
     double H[12], r[2], V[4], S[4], Si[4];
     meas_model(p, &probe, H, r, V);
     innovation(P, H, V, S, Si);
@@ -631,11 +759,10 @@ static int build_seed(const orc_geom *g, const orc_event *ev, const double sp[6]
     for (int l = g->first_build_layer; l < g->n_layers; ++l) {
         int nb = 0, bcap = 16;
         orc_cand *B = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)bcap);
-        const double R = g->radius[l];
         for (int c = 0; c < n; ++c) {
             double q[6], J[36], Q[36];
             if (stats) stats->n_prop += 1;
-            if (orc_propagate(g, C[c].p, R, q, J) != ORC_OK) continue; /* dropped */
+            if (propagate_layer(g, l, C[c].p, 0, q, J) != ORC_OK) continue; /* dropped */
             sandwich6(J, C[c].P, Q);
             int found = 0;
             int eb0, eb1, pb0, pb1;
@@ -660,9 +787,10 @@ static int build_seed(const orc_geom *g, const orc_event *ev, const double sp[6]
                         const orc_hit *h = &ev->hits[hid];
                         if (stats) stats->n_hits_examined += 1;
                         if (q[0] * h->x + q[1] * h->y <= 0.0) continue; /* far half of the cylinder */
+                        if (h->disk && h->z * q[2] <= 0.0) continue;    /* the other endcap's disk */
                         const double *qh = q, *Qh = Q;
                         double q2[6], J2[36], Q2[36];
-                        if (g->hit_dr > 0.0) {
+                        if (g->hit_dr > 0.0 && g->disk_z[l] <= 0.0) {
                             /* the window around the prediction on the average radius, then the
                              * state at the hit's own radius */
                             double H[12], r[2], V[4];

@@ -29,11 +29,15 @@ typedef struct {
     double hit_dr;         /* largest |hit radius - layer radius| (cm); 0: hits lie on the cylinders.
                               > 0: the CMS-geometry variant of Sec. 2.2, states are taken to each
                               hit's own radius (see tkf_oracle.c) */
+    double disk_z[ORC_MAX_LAYERS]; /* > 0: layer l is a pair of endcap disks at z = +-disk_z[l]
+                                      (Sec. 2.2, "or endcap z"); 0: a cylinder of radius[l] */
 } orc_geom;
 
 typedef struct {
     double x, y, z, var_u, var_v;
     int layer;
+    int disk; /* 1: a hit on an endcap disk, measured in r-phi (var_u) and r (var_v); 0: on a
+                 cylinder, measured in r-phi and z */
 } orc_hit;
 
 typedef struct {
@@ -61,6 +65,8 @@ typedef struct {
 } orc_stats;
 
 int orc_propagate(const orc_geom *g, const double pin[6], double R, double pout[6], double J[36]);
+/* to the plane z = Zp (an endcap disk) */
+int orc_propagate_plane(const orc_geom *g, const double pin[6], double Zp, double pout[6], double J[36]);
 void orc_scatter(const orc_geom *g, int layer, const double p[6], double P[36]);
 double orc_chi2(const double p[6], const double P[36], const orc_hit *h);
 int orc_update(double p[6], double P[36], const orc_hit *h, double *chi2);
@@ -74,6 +80,8 @@ int orc_fit_backward(const orc_geom *g, const double pin[6], const double Pin[36
                      const orc_hit *hits, const int *hit_of_layer, int last, int first, double pout[6],
                      double Pout[36], double *chi2, int *nhits);
 int orc_eta_bin(const orc_geom *g, int layer, double z);
+/* the eta bin of a hit: asinh(z / R) on a cylinder of radius R, asinh(z / r_hit) on a disk */
+int orc_hit_eta_bin(const orc_geom *g, const orc_hit *h);
 int orc_phi_bin(const orc_geom *g, double phi);
 int orc_hit_index(const orc_geom *g, int n, const orc_hit *hits, int *bin_of_hit, int *order, int *bin_off);
 int orc_build_seed(const orc_geom *g, const orc_event *ev, const double sp[6], const double sP[36],

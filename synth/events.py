@@ -43,13 +43,21 @@ class Detector:
     x_over_x0: tuple = tuple(0.03 for _ in range(10))
     mass: float = 0.13957  # scattering mass hypothesis (charged pion)
     sigma_rphi: float = 0.01
-    sigma_z: float = 0.1
+    sigma_z: float = 0.1    # second measured coordinate: z on a cylinder, r on a disk
     module_dr: float = 0.0
     module_width: float = 2.0
+    # Endcap disks (the "endcap z" of the paper's Sec. 2.2): disk_z[l] > 0 makes layer l a pair
+    # of disks at z = +-disk_z[l] (a track crosses the one on its side), radii[l] its outer
+    # radius; () or 0 keeps the layer a cylinder of radius radii[l].
+    disk_z: tuple = ()
+    disk_rmin: float = 1.0
 
     @property
     def n_layers(self) -> int:
         return len(self.radii)
+
+    def is_disk(self, l: int) -> bool:
+        return bool(self.disk_z) and self.disk_z[l] > 0.0
 
     def n_modules(self, l: int) -> int:
         return 2 * max(2, int(np.ceil(np.pi * self.radii[l] / self.module_width)))
@@ -74,6 +82,7 @@ class EventSpec:
     pt_min: float = 0.5
     pt_max: float = 10.0
     eta_max: float = 1.0
+    eta_min: float = 0.0  # > 0: |eta| uniform in [eta_min, eta_max], either sign (forward tracks)
     noise_frac: object = 0.0
     vertex_sigma: tuple = (0.01, 0.01, 1.0)
     scatter: bool = True
@@ -168,6 +177,34 @@ def _helix_to_cylinder(x, y, z, w, phi, theta, radius, kb):
     return xs, ys, zs, phi_new
 
 
+def _helix_to_plane(x, y, z, w, phi, theta, zplane, kb):
+    """Exact helix crossing of the plane z = zplane: the transverse path is (zplane - z) tan(theta)."""
+    kappa = -kb * w
+    s = (zplane - z) * np.tan(theta)
+    if not np.all(s > 0):
+        raise RuntimeError("a generated track does not move towards its disk")
+    ang = phi + kappa * s
+    xs = x + (np.sin(ang) - np.sin(phi)) / kappa
+    ys = y - (np.cos(ang) - np.cos(phi)) / kappa
+    return xs, ys, np.full_like(x, 0.0) + zplane, np.arctan2(np.sin(ang), np.cos(ang))
+
+
+def _scatter(key, tl, l, q, w, phi, theta, cos_inc, det):
+    """Thin-scatterer kick on layer l: two Gaussian angles of Highland width for the path
+    x/X0 / cos_inc, orthogonal to the direction, |p| kept.  Returns (theta, phi, q/pT)."""
+    a1, a2 = normals(key, (tl, _LAYER0 + l, 1, 0))
+    p = 1.0 / (np.abs(w) * np.sin(theta))
+    d = np.stack([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)], axis=1)
+    th0 = highland_theta0(p, det.mass, det.x_over_x0[l] / cos_inc)
+    e_th = np.stack([np.cos(theta) * np.cos(phi), np.cos(theta) * np.sin(phi), -np.sin(theta)], axis=1)
+    e_ph = np.stack([-np.sin(phi), np.cos(phi), np.zeros_like(phi)], axis=1)
+    dn = d + (th0 * a1)[:, None] * e_th + (th0 * a2)[:, None] * e_ph
+    dn /= np.linalg.norm(dn, axis=1)[:, None]
+    theta = np.arccos(np.clip(dn[:, 2], -1.0, 1.0))
+    phi = np.arctan2(dn[:, 1], dn[:, 0])
+    return theta, phi, q / (p * np.sin(theta))
+
+
 def highland_theta0(p, mass, thickness):
     """Highland width of the projected scattering angle for unit charge (PDG form)."""
     beta = p / np.sqrt(p * p + mass * mass)
@@ -195,7 +232,11 @@ def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
     gvx, gvy = normals(key, (tl, _KIN, 2, 0))
     gvz, _ = normals(key, (tl, _KIN, 3, 0))
     pt = spec.pt_min + (spec.pt_max - spec.pt_min) * u_pt
-    eta = -spec.eta_max + 2.0 * spec.eta_max * u_eta
+    if spec.eta_min > 0.0:
+        a = 2.0 * np.abs(u_eta - 0.5)
+        eta = np.where(u_eta < 0.5, -1.0, 1.0) * (spec.eta_min + (spec.eta_max - spec.eta_min) * a)
+    else:
+        eta = -spec.eta_max + 2.0 * spec.eta_max * u_eta
     theta = 2.0 * np.arctan(np.exp(-eta))
     phi = -np.pi + 2.0 * np.pi * u_phi
     q = np.where(u_q < 0.5, 1.0, -1.0)
@@ -210,6 +251,22 @@ def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
     sig_hit = np.zeros((T, L, 3))  # x, y, z of the signal hit
     for l in range(L):
         R = det.radii[l]
+        if det.is_disk(l):
+            x, y, z, phi = _helix_to_plane(x, y, z, w, phi, theta, np.where(np.cos(theta) > 0, 1.0, -1.0) * det.disk_z[l], kb)
+            truth[:, l] = np.stack([x, y, z, w, phi, theta], axis=1)
+            g_rphi, g_r = normals(key, (tl, _LAYER0 + l, 0, 0))
+            phi_pos = np.arctan2(y, x)
+            r_pos = np.hypot(x, y)
+            if spec.smear:
+                phi_h = phi_pos + det.sigma_rphi * g_rphi / r_pos
+                r_h = r_pos + det.sigma_z * g_r
+            else:
+                phi_h, r_h = phi_pos, r_pos
+            sig_hit[:, l] = np.stack([r_h * np.cos(phi_h), r_h * np.sin(phi_h), z], axis=1)
+            if spec.scatter and det.x_over_x0[l] > 0.0:
+                theta, phi, w = _scatter(key, tl, l, q, w, phi, theta, np.abs(np.cos(theta)), det)
+            truth_after[:, l] = np.stack([x, y, z, w, phi, theta], axis=1)
+            continue
         if det.module_dr != 0.0:
             # the module is the one crossed on the average cylinder; the track then goes from
             # its previous point straight to that module's radius
@@ -226,19 +283,10 @@ def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
             phi_h, z_h = phi_pos, z.copy()
         sig_hit[:, l] = np.stack([R * np.cos(phi_h), R * np.sin(phi_h), z_h], axis=1)
         if spec.scatter and det.x_over_x0[l] > 0.0:
-            a1, a2 = normals(key, (tl, _LAYER0 + l, 1, 0))
-            p = 1.0 / (np.abs(w) * np.sin(theta))
             d = np.stack([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), np.cos(theta)], axis=1)
             radial = np.stack([np.cos(phi_pos), np.sin(phi_pos), np.zeros_like(phi_pos)], axis=1)
             cos_inc = np.abs(np.sum(d * radial, axis=1))
-            th0 = highland_theta0(p, det.mass, det.x_over_x0[l] / cos_inc)
-            e_th = np.stack([np.cos(theta) * np.cos(phi), np.cos(theta) * np.sin(phi), -np.sin(theta)], axis=1)
-            e_ph = np.stack([-np.sin(phi), np.cos(phi), np.zeros_like(phi)], axis=1)
-            dn = d + (th0 * a1)[:, None] * e_th + (th0 * a2)[:, None] * e_ph
-            dn /= np.linalg.norm(dn, axis=1)[:, None]
-            theta = np.arccos(np.clip(dn[:, 2], -1.0, 1.0))
-            phi = np.arctan2(dn[:, 1], dn[:, 0])
-            w = q / (p * np.sin(theta))
+            theta, phi, w = _scatter(key, tl, l, q, w, phi, theta, cos_inc, det)
         truth_after[:, l] = np.stack([x, y, z, w, phi, theta], axis=1)
 
     # --- assemble hits event by event: layer-major, signal then noise, then shuffled
@@ -255,12 +303,20 @@ def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
             n_noise = int(np.rint(noise_frac[e] * nt))
             nid = np.arange(n_noise, dtype=np.uint64)
             u_a, u_b = uniforms(ekey, (nid, _NOISE0 + l, 0, 1))
-            zl = R * np.sinh(spec.eta_max) + 3.0 * spec.vertex_sigma[2]
             nphi = -np.pi + 2.0 * np.pi * u_a
-            nr = det.module_radius(l, nphi) if det.module_dr != 0.0 else R
+            if det.is_disk(l):
+                # uniform in phi and in |eta| over the acceptance widened by 0.2, either disk
+                u_c, _ = uniforms(ekey, (nid, _NOISE0 + l, 1, 1))
+                e_lo, e_hi = max(spec.eta_min - 0.2, 0.05), spec.eta_max + 0.2
+                nr = det.disk_z[l] / np.sinh(e_lo + (e_hi - e_lo) * u_b)
+                nz = np.where(u_c < 0.5, -1.0, 1.0) * det.disk_z[l]
+            else:
+                zl = R * np.sinh(spec.eta_max) + 3.0 * spec.vertex_sigma[2]
+                nr = det.module_radius(l, nphi) if det.module_dr != 0.0 else R
+                nz = -zl + 2.0 * zl * u_b
             hx = np.concatenate([sig_hit[t0:t1, l, 0], nr * np.cos(nphi)])
             hy = np.concatenate([sig_hit[t0:t1, l, 1], nr * np.sin(nphi)])
-            hz = np.concatenate([sig_hit[t0:t1, l, 2], -zl + 2.0 * zl * u_b])
+            hz = np.concatenate([sig_hit[t0:t1, l, 2], nz])
             mc = np.concatenate([np.arange(t0, t1, dtype=np.int64), np.full(n_noise, -1, dtype=np.int64)])
             n_l = nt + n_noise
             if spec.shuffle_hits:
@@ -315,3 +371,19 @@ def concat(batches):
         trk_hits=np.concatenate([np.where(b.trk_hits >= 0, b.trk_hits + hb, -1) for b, hb in zip(batches, hit_base)]),
         truth=cat("truth"), truth_after=cat("truth_after"), vertex_state=cat("vertex_state"), extras=extras,
     )
+
+
+def forward_detector(n_layers: int = 10, spacing: float = 8.0, x_over_x0: float = 0.03, **kw) -> Detector:
+    """An endcap-only tracker (the "endcap z" geometry of the paper's Sec. 2.2): n_layers pairs of
+    disks at z = +-spacing, +-2 spacing, ... with outer radius 40 cm and inner radius 1 cm, in the
+    same 3.8 T field; hits measured in r-phi (sigma_rphi) and r (sigma_z, 0.1 cm).  Tracks with
+    1.7 <= |eta| <= 2.5 cross every disk of their side."""
+    return Detector(radii=(40.0,) * n_layers, x_over_x0=(x_over_x0,) * n_layers,
+                    disk_z=tuple(spacing * (l + 1) for l in range(n_layers)), disk_rmin=1.0, **kw)
+
+
+FORWARD_ETA = (1.7, 2.5)
+# Seed prior (cm, cm, cm, GeV^-1, rad, rad) for the endcap tracker: three hits on the first disks
+# span a few cm of arc, so their curvature estimate is poorer than in the barrel and the prior on
+# q/pT must be wider to stay uninformative (z is the first disk's, known exactly).
+FORWARD_PRIOR = (0.3, 0.3, 1.0, 5.0, 0.1, 0.1)
