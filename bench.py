@@ -68,15 +68,27 @@ FLOP_PER_SEED_TWO_STEP = (PER_SEED_TWO_STEP["n_prop"] * (FLOP_PROPAGATE + FLOP_W
                           + PER_SEED_TWO_STEP["n_updates"] * (FLOP_UPDATE + FLOP_PROPAGATE)
                           + PER_SEED_TWO_STEP["n_kept"] * 6.0 / 7.0 * FLOP_SCATTER)
 MODULE_DR = 1.0  # cm between the inner and outer module rows of a layer (hit_dr = 0.5 cm)
+# Endcap disks (the forward tracker): per propagation to a plane 296 (closed-form path, one
+# helix evaluation, the plane's J P J^T from plane_cov); per window 57 (r-phi and r extents, the
+# eta bins of the radii); per examined hit 57 (r-phi and r residuals, the disk's 2x2 S, chi2,
+# half-disk and endcap-side tests); per update 359 (the radial row of H adds 24); per kept
+# branch's scattering 23.  Work per seed from the oracle on the forward workload (a quarter of
+# each event's tracks; python oracle/opcount.py --events 64 --forward, 69674 seeds):
+FLOP_PROPAGATE_PLANE, FLOP_WINDOW_DISK, FLOP_CHI2_DISK, FLOP_UPDATE_DISK, FLOP_SCATTER_DISK = 296, 57, 57, 359, 23
+PER_SEED_DISK = dict(n_prop=25.7421, n_hits_examined=218.2409, n_updates=26.9508, n_kept=29.2005)
+FLOP_PER_SEED_DISK = (PER_SEED_DISK["n_prop"] * (FLOP_PROPAGATE_PLANE + FLOP_WINDOW_DISK)
+                      + PER_SEED_DISK["n_hits_examined"] * FLOP_CHI2_DISK
+                      + PER_SEED_DISK["n_updates"] * FLOP_UPDATE_DISK
+                      + PER_SEED_DISK["n_kept"] * 6.0 / 7.0 * FLOP_SCATTER_DISK)
 # DRAM bytes (read + write) per seed of the two-step FP32 building kernel, from one ncu capture
 # of the kernel as built now (160-event case: 404.6 MB for 701 095 seeds; summary in profiles/);
 # None whenever the kernel changes until it is captured again
 BUILD2_DRAM_BYTES_PER_SEED = 577.1
 # Warp instructions per seed of the two build kernels (ncu smsp__inst_executed.sum of the same
-# captures: 2.01 G and 4.09 G for 701 095 seeds), for the instruction-issue roofline beside the
+# captures: 1.822 G and 4.066 G for 701 095 seeds), for the instruction-issue roofline beside the
 # FP32 one: an SM sub-partition issues at most one warp instruction per cycle, 4 per SM;
 # None whenever a kernel changes until it is captured again
-BUILD_WARP_INST_PER_SEED, BUILD2_WARP_INST_PER_SEED = 2867.0, 5839.0
+BUILD_WARP_INST_PER_SEED, BUILD2_WARP_INST_PER_SEED = 2599.2, 5798.8
 # FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # libtkf.so kernels per step: hit index (event order, per-event count/scan/place, bin sort),
@@ -84,30 +96,34 @@ SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # place), build, final fit
 KERNELS_PER_STEP = 11
 # DRAM bytes (read + write) per seed of the FP32 building kernel, from one ncu capture of the
-# kernel as built now (160-event case: 407.5 MB for 701 095 seeds; summary in profiles/);
+# kernel as built now (160-event case: 406.3 MB for 701 095 seeds; summary in profiles/);
 # None whenever the kernel changes until it is captured again
-BUILD_DRAM_BYTES_PER_SEED = 581.3
+BUILD_DRAM_BYTES_PER_SEED = 579.6
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 ISSUE_PEAK_WARP_INST_PER_S = SM_COUNT * 4 * SM_MAX_GHZ * 1e9
 
 
 def _gen_chunk(args):
-    from synth import Detector, EventSpec, event_sizes, generate
-    seed, e0, e1, module_dr = args
+    from synth import FORWARD_ETA, Detector, EventSpec, event_sizes, forward_detector, generate
+    seed, e0, e1, module_dr, forward = args
     n, f = event_sizes(seed, 640)
-    return generate(EventSpec(seed=seed, n_events=e1 - e0, n_tracks=n[e0:e1], noise_frac=f[e0:e1], first_event=e0),
-                    Detector(module_dr=module_dr))
+    eta = dict(eta_min=FORWARD_ETA[0], eta_max=FORWARD_ETA[1]) if forward else {}
+    if forward:  # the endcaps' share: a quarter of each event's tracks
+        n = np.maximum(1, np.rint(0.25 * n)).astype(np.int64)
+    return generate(EventSpec(seed=seed, n_events=e1 - e0, n_tracks=n[e0:e1], noise_frac=f[e0:e1], first_event=e0,
+                              **eta), forward_detector() if forward else Detector(module_dr=module_dr))
 
 
-def workload(seed: int, n_events: int, pool=None, module_dr=0.0):
+def workload(seed: int, n_events: int, pool=None, module_dr=0.0, forward=False):
     """The first n_events events of the 640-event batched workload (generated in parallel
     chunks when a process pool is given; the result does not depend on the chunking);
-    module_dr > 0: the same events on modules off the layers' cylinders."""
+    module_dr > 0: the same events on modules off the layers' cylinders; forward: a quarter of each
+    event's tracks on the endcap tracker (ten pairs of disks), with 1.7 <= |eta| <= 2.5."""
     from synth import concat
     if pool is None or n_events < 32:
-        return _gen_chunk((seed, 0, n_events, module_dr))
+        return _gen_chunk((seed, 0, n_events, module_dr, forward))
     step = max(1, n_events // 64)
-    chunks = [(seed, e, min(e + step, n_events), module_dr) for e in range(0, n_events, step)]
+    chunks = [(seed, e, min(e + step, n_events), module_dr, forward) for e in range(0, n_events, step)]
     return concat(pool.map(_gen_chunk, chunks, chunksize=1))
 
 
@@ -232,14 +248,15 @@ def job_rate(units, ms, dist=None, device="cpu"):
 
 
 # ----------------------------------------------------------------------------- CPU baseline (oracle)
-def _oracle_events(chunk, module_dr=0.0):
+def _oracle_events(chunk, module_dr=0.0, forward=False):
     """Runs the oracle's whole path (index, seed, seed fit, build, final fit) on a few events,
     each given as (oracle hit records, track hit ids [n, L]); returns (tracks, seconds spent
     computing in this process)."""
     import oracle as O
-    from synth import Detector
-    det = Detector(module_dr=module_dr)
-    g = O.make_geom(det)
+    from synth import FORWARD_PRIOR, Detector, forward_detector
+    det = forward_detector() if forward else Detector(module_dr=module_dr)
+    g = O.make_geom(det, O.Settings(eta_min=-3.0, n_eta_bins=60, prior_sigma=FORWARD_PRIOR) if forward
+                    else O.Settings())
     L = det.n_layers
     done = 0
     t0 = time.perf_counter()
@@ -274,6 +291,19 @@ def _oracle_fit(chunk):
 def _oracle_events_modules(chunk):
     """_oracle_events on the module geometry (hits off the layers' cylinders)."""
     return _oracle_events(chunk, MODULE_DR)
+
+
+def _oracle_events_forward(chunk):
+    """_oracle_events on the endcap tracker."""
+    return _oracle_events(chunk, forward=True)
+
+
+def forward_config(tkf, **kw):
+    """The library configuration of the endcap tracker (ten pairs of disks at z = +-8..80 cm)."""
+    from synth import FORWARD_PRIOR, forward_detector
+    det = forward_detector()
+    return tkf.default_config(radius=det.radii, x_over_x0=det.x_over_x0, disk_z=det.disk_z, eta_min=-3.0,
+                              n_eta_bins=60, prior_sigma=FORWARD_PRIOR, **kw)
 
 
 def _oracle_backward(chunk):
@@ -417,6 +447,7 @@ def server_pass(sv, lent):
     if code != 0:
         raise RuntimeError("server pass: wait returned %d" % code)
     tracks = sum(r.n_tracks for r in res)
+    server_pass.gpu_span_ms = max(r.gpu_done_ms for r in res) - min(r.gpu_start_ms for r in res)
     sv.release_many(tickets)
     return time.perf_counter() - t0, tracks
 
@@ -508,6 +539,9 @@ def main():
     ap.add_argument("--two-step", type=int, default=160,
                     help="events of the batch also timed on modules off the layers' cylinders (two-step building); "
                          "0: skip")
+    ap.add_argument("--disks", type=int, default=640,
+                    help="events of the batch also timed on the endcap tracker, each with a quarter of its tracks "
+                         "(forward tracks on disks); 0: skip")
     ap.add_argument("--tile", type=int, default=0, help="seeds per warp work tile (0: autotuned)")
     ap.add_argument("--e2e-batch", type=int, default=160, help="events per server batch in the e2e measurement")
     ap.add_argument("--e2e-slots", type=int, default=4, help="server slots in the e2e measurement")
@@ -812,6 +846,67 @@ def main():
         c2.close()
         del d2, hits2
 
+    # ---------------- forward tracks on the endcap disks (the "endcap z" geometry)
+    disks = None
+    b3 = None
+    if a.disks > 0:
+        n3 = min(a.disks, 640)
+        b3 = workload(a.seed + 1000 * rank, n3, pool, forward=True)
+        t3 = lambda arr, dt: torch.as_tensor(np.ascontiguousarray(arr), dtype=dt).to(dev)
+        d3 = {"x": t3(b3.x, torch.float32), "y": t3(b3.y, torch.float32), "z": t3(b3.z, torch.float32),
+              "var_u": t3(b3.var_u, torch.float32), "var_v": t3(b3.var_v, torch.float32),
+              "layer": t3(b3.layer, torch.int32), "event_off": t3(b3.hit_off, torch.int32),
+              "seed_hits": t3(b3.trk_hits[:, :3].T, torch.int32), "seed_event": t3(b3.trk_event, torch.int32)}
+        hits3 = tkf.DeviceHits(d3["x"], d3["y"], d3["z"], d3["var_u"], d3["var_v"], d3["layer"], d3["event_off"])
+        n3t = b3.n_tracks
+        c3 = tkf.Context(forward_config(tkf, seed_order=a.seed_order, seeds_per_block=max(a.tile, 0)))
+        p3 = tkf.DevicePipeline(c3, b3.n_hits, b3.n_events, n3t, use_graph=True)
+        p3.run(hits3, d3["seed_hits"], d3["seed_event"], n3t, stream=stream)
+        if a.tile > 0:
+            tile3, t3ms = a.tile, []
+        else:
+            sc3 = tkf.DeviceTracks.empty(n3t, L, device=dev)
+            tile3, t3ms = c3.autotune_build(p3.index(), _T(p3.outputs()[0]), sc3, tiles, repeats=2, stream=stream)
+            del sc3
+            p3.close()
+            c3.close()
+            c3 = tkf.Context(forward_config(tkf, seed_order=a.seed_order, seeds_per_block=tile3))
+            p3 = tkf.DevicePipeline(c3, b3.n_hits, b3.n_events, n3t, use_graph=True)
+        step3 = lambda: p3.run(hits3, d3["seed_hits"], d3["seed_event"], n3t, stream=stream)
+        for _ in range(max(3, a.warmup)):
+            step3()
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        qb = []
+        q0.record(stream)
+        for _ in range(a.steps):
+            step3()
+            qb.append(p3.build_ms())
+        q1.record(stream)
+        torch.cuda.synchronize()
+        c3.sync_status(stream)
+        d_ms = q0.elapsed_time(q1) / a.steps
+        d_build = statistics.mean(qb)
+        hid3 = tkf.tracks_tensors(p3.outputs()[1], L)["hit_idx"][:, :n3t].cpu().numpy()
+        own3 = (hid3.T == b3.trk_hits).sum(axis=1)
+        ach3 = FLOP_PER_SEED_DISK * n3t / (d_build / 1e3) / 1e12
+        disks = {
+            "value": n3t / (d_ms / 1e3), "unit": UNIT, "ms_per_step": d_ms, "build_ms": d_build,
+            "events": b3.n_events, "tracks": n3t, "hits": b3.n_hits, "efficiency": efficiency(b3, hid3),
+            "own_hit_lists": float(np.mean(own3 == L)), "seeds_per_warp_tile": tile3,
+            "autotune_build_ms": [round(x, 4) for x in t3ms],
+            "roofline": {"kernel": "k_build<6,float,float,disks>", "bound": "alu", "achieved": ach3,
+                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach3 / FP32_PEAK_TFLOPS,
+                         "traffic": None, "launch_ms": d_build, "flop_per_seed": FLOP_PER_SEED_DISK,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+            "form": "events 0..%d of the batched workload, each with a quarter of its tracks (the endcaps' "
+                    "share) and its noise fraction, on the endcap tracker (ten pairs of disks at z = +-8..80 cm, "
+                    "tracks with 1.7 <= |eta| <= 2.5, hits in r-phi and r); FP32, N = 6, whole step replayed from "
+                    "a CUDA graph" % (b3.n_events - 1)}
+        p3.close()
+        c3.close()
+        del d3, hits3
+
     # ---------------- end to end through host buffers
     _, built_t, fitted_t = pipe.outputs()
     fv = tkf.tracks_tensors(fitted_t, L)
@@ -847,15 +942,19 @@ def main():
     for _ in range(max(1, a.warmup)):
         server_pass(sv, lent)
     e2e_s = []
+    allocs0 = sv.stats()["result_allocs"]
     gc.collect()
     gc.disable()  # a serving host does not collect garbage between a batch's submission and its results
+    gpu_spans = []
     try:
         for _ in range(a.steps):
             dt, nt = server_pass(sv, lent)
             assert nt == n_tr
             e2e_s.append(dt)
+            gpu_spans.append(server_pass.gpu_span_ms)
     finally:
         gc.enable()
+    e2e_allocs = sv.stats()["result_allocs"] - allocs0
     sv.close()
     e2e = {"value": job_rate(n_tr, 1e3 * statistics.mean(e2e_s), dist, dev)[2], "unit": UNIT,
            "h2d_bytes_per_step": lent.h2d,
@@ -863,9 +962,13 @@ def main():
            "ms_per_step_median": 1e3 * statistics.median(e2e_s), "ms_per_step_max": 1e3 * max(e2e_s),
            "ms_per_step_p99": 1e3 * float(np.percentile(e2e_s, 99)),
            "passes_ms": [round(1e3 * x, 3) for x in e2e_s],
+           "result_buffer_allocations_while_timed": e2e_allocs,
+           "gpu_span_ms": [round(x, 3) for x in gpu_spans],
            "form": "tkf_submit_events of all %d events (hit planes lent from pinned host memory), tkf_wait_all, "
                    "tkf_release_many; %d slots, batches of up to %d events; host wall clock, mean over the "
-                   "timed passes (Python garbage collection off during them)" % (b.n_events, a.e2e_slots, a.e2e_batch)}
+                   "timed passes (Python garbage collection off during them); gpu_span_ms: per pass, the device "
+                   "time from the first batch's first copy to the last batch's last copy"
+                   % (b.n_events, a.e2e_slots, a.e2e_batch)}
 
     # ---------------- the same batched step in MIXED precision (FP64 inverse + Joseph update)
     mixed = None
@@ -1017,6 +1120,14 @@ def main():
                 "sample": "events 0..%d of the module-geometry batch (%d tracks): index, seed, seed fit, two-step "
                           "build, final fit, FP64, one process per core; time = the slowest worker's computing "
                           "(%.2f s; %.2f s wall)" % (n2s - 1, tracks2, comp2, wall2)}
+        if disks is not None:
+            n3s = next((k + 1 for k in range(b3.n_events) if int(b3.trk_off[k + 1]) >= a.cpu_tracks // 4), b3.n_events)
+            tracks3, comp3, wall3 = cpu_baseline(oracle_sample(b3, range(n3s)), pool, cores, fn=_oracle_events_forward)
+            disks["cpu_baseline"] = {
+                "value": tracks3 / comp3, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": "events 0..%d of the endcap batch (%d tracks): index, seed, seed fit, build, final fit, "
+                          "FP64, one process per core; time = the slowest worker's computing (%.2f s; %.2f s wall)"
+                          % (n3s - 1, tracks3, comp3, wall3)}
     pool.close()
 
     achieved = FLOP_PER_SEED * n_tr / (build_ms / 1e3) / 1e12
@@ -1047,6 +1158,7 @@ def main():
         "mixed": mixed,
         "backward_pass": backward,
         "two_step": two_step,
+        "disks": disks,
         "batch_scan": batch_scan,
         "physics": phys,
         "fit": fit_leg,

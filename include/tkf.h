@@ -86,6 +86,15 @@ typedef struct {
                                          candidate hit's chi2 after a second propagation to the
                                          hit's radius.  Must satisfy 0 <= hit_dr < radius[0] and
                                          2 hit_dr < the gap between consecutive radii. */
+    double disk_z[TKF_MAX_LAYERS];    /* cm.  0: layer l is the cylinder of radius[l].  > 0: layer l
+                                         is a pair of endcap disks at z = +-disk_z[l] (the "endcap
+                                         z" of Sec. 2.2; radius[l] is then the disk's outer
+                                         radius): a state goes to the disk on the side of its z by
+                                         the exact helix/plane crossing, a hit there is measured in
+                                         r-phi (var_u) and r (var_v), its eta bin is
+                                         asinh(z / r_hit), and the seed's z on a first-layer disk
+                                         is exact (zero prior variance).  Consecutive disk layers
+                                         need increasing disk_z; disks exclude hit_dr > 0. */
 } tkf_config;
 
 /* Hits of one or more events (device arrays of length n, caller-owned).  The hits of event e
@@ -304,7 +313,10 @@ int tkf_autotune_build(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks 
  * the device memory in use is fixed by those limits (events are admitted into a batch only if
  * they fit its buffers).  Results land in pinned host buffers drawn from a pool bounded by
  * result_bytes; while unreleased results hold all of it, no new batch starts (the queue then
- * fills and submissions get TKF_ERR_AGAIN), so callers release results promptly.  Results of
+ * fills and submissions get TKF_ERR_AGAIN), so callers release results promptly.  The pool
+ * starts with one full-size buffer per slot, made at creation (pinned allocation can wait for
+ * the device); a batch takes the smallest free buffer that holds it, and new buffers are made
+ * only while more results are held than the pool has buffers.  Results of
  * an event do not depend on the batch it ran in. */
 typedef struct tkf_server tkf_server;
 
@@ -350,6 +362,7 @@ typedef struct {
 
 typedef struct {
     int64_t submitted, rejected, events_done, tracks_done, batches, max_batch_events;
+    int64_t result_allocs; /* pinned result buffers allocated so far (each takes milliseconds) */
 } tkf_server_stats;
 
 /* Defaults: 3 slots, 64 events, 4 Mi hits and 256 Ki seeds per batch, 1 GiB host queue,

@@ -22,7 +22,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # arithmetic is not affected.
 FAST_MATH = ["-use_fast_math"]
 SOURCES = ["tkf_api.cu", "tkf_build_fp32.cu", "tkf_build_mixed.cu", "tkf_build_fp64.cu", "tkf_build2_fp32.cu",
-           "tkf_build2_mixed.cu", "tkf_build2_fp64.cu", "tkf_pipeline.cu", "tkf_server.cu", "tkf_probe.cu"]
+           "tkf_build2_mixed.cu", "tkf_build2_fp64.cu", "tkf_build3_fp32.cu", "tkf_build3_mixed.cu",
+           "tkf_build3_fp64.cu", "tkf_pipeline.cu", "tkf_server.cu", "tkf_probe.cu"]
 
 
 def nvcc() -> str:

@@ -14,7 +14,9 @@
 //      Kalman update (U = float or double) for a hit branch and the layer's scattering noise.
 // With hits off the layers' cylinders (kTwo) step 1 reaches the layer's average radius, step 2
 // scores each hit after a second, short propagation to its own radius, and the survivor of a
-// hit branch takes that step before its update (the two-step propagation of Sec. 2.2).
+// hit branch takes that step before its update (the two-step propagation of Sec. 2.2).  With
+// endcap disks (kDisk) a disk layer is reached by the helix/plane crossing, its window is taken
+// in r-phi and r, and its hits are measured on the disk's plane (the "endcap z" of Sec. 2.2).
 // Hit history is kept per warp in shared memory (parent rank, hit id per layer and lane) and
 // the best candidate is backtracked at the end.  Work balance follows the paper's dynamic
 // work stealing (Sec. 2.3): warps pull tiles of seeds_per_block seeds from an atomic counter
@@ -239,6 +241,96 @@ __device__ __forceinline__ void scan_window(const BuildArgs &a, int ev, int l, R
     if (!found) list_insert32(lk, lh, make_key32(nh, to_f32(chi2), rank), kHoleId);
 }
 
+// The same on an endcap disk (the "endcap z" of Sec. 2.2): the chi2-cut box |u| <= U (r-phi),
+// |v| <= W (r) of the innovation covariance at phi_h = phi of the prediction.  A hit at
+// (r_h, phi_p + d) has u = r_p sin(d) and v = r_h - r_p cos(d): the box holds |d| <= asin(U / r_p)
+// and radii from r_p cos(asin(U / r_p)) - W to r_p + W, whose eta bins (eta = asinh(z / r) on the
+// disk at z) are scanned.  A compatible hit lies on the disk the state reached.
+template <int NMAX, class R>
+__device__ __forceinline__ void scan_window_disk(const BuildArgs &a, int ev, int l, const R p[6], const R P[21],
+                                                 R chi2, int nh, int rank, unsigned (&lk)[NMAX], int (&lh)[NMAX])
+{
+    const int seg = ev * a.L + l;
+    const float2 vmax = a.var_max[seg];
+    const R xp = p[0], yp = p[1], zp = p[2];
+    const R rp = sq(xp * xp + yp * yp);
+    const R sf = yp / rp, cf = xp / rp;
+    const R p00 = P[sym(0, 0)], p10 = P[sym(1, 0)], p11 = P[sym(1, 1)];
+    const R Suu = sf * (sf * p00 - cf * p10) + cf * (cf * p11 - sf * p10) + R(vmax.x);
+    const R Svv = cf * (cf * p00 + sf * p10) + sf * (sf * p11 + cf * p10) + R(vmax.y);
+    const R cut = pick<R>(a.cut_f, a.cut);
+    const R mg = R(1) + pick<R>(a.margin_f, a.margin);
+    const R U = sq(cut * Suu) * mg, W = sq(cut * Svv) * mg;
+    const R phip = at2(yp, xp);
+    const R dphi = asin_window(U / rp) + R(2e-5);
+    const R bscale = R(a.n_phi) / R(2.0 * kPi);
+    const R xlo = (phip - dphi + R(kPi)) * bscale, xhi = (phip + dphi + R(kPi)) * bscale;
+    const int k0 = (int)flr(xlo), k1 = (int)flr(xhi);
+    int s0 = (int)flr((xlo - R(k0)) * R(kSubBins)), s1 = (int)flr((xhi - R(k1)) * R(kSubBins));
+    s0 = s0 < 0 ? 0 : (s0 >= kSubBins ? kSubBins - 1 : s0);
+    s1 = s1 < 0 ? 0 : (s1 >= kSubBins ? kSubBins - 1 : s1);
+    const int nphi = a.n_phi;
+    const R emin = pick<R>(a.eta_min_f, a.eta_min), iw = pick<R>(a.inv_eta_w_f, a.inv_eta_w);
+    // eta bins of the radii r_p cos(dphi) - W .. r_p + W on this disk (eta falls with the radius
+    // for z > 0, rises for z < 0; a range reaching r = 0 extends to the last or first row)
+    R cdp, sdp;
+    sc(dphi < R(1.5707963) ? dphi : R(1.5707963), &sdp, &cdp);
+    const R r_lo = rp * cdp - W, r_hi = rp + W;
+    const int e_far = eta_bin_window(zp, R(1) / r_hi, emin, iw, a.n_eta, zp > R(0) ? R(-1e-4) : R(1e-4));
+    int e_near;
+    if (r_lo > R(0))
+        e_near = eta_bin_window(zp, R(1) / r_lo, emin, iw, a.n_eta, zp > R(0) ? R(1e-4) : R(-1e-4));
+    else
+        e_near = zp > R(0) ? a.n_eta - 1 : 0;
+    const int e0 = zp > R(0) ? e_far : e_near, e1 = zp > R(0) ? e_near : e_far;
+    int pb0[2], ps0[2], pb1[2], ps1[2];
+    if (k1 - k0 + 1 >= nphi) {
+        pb0[0] = 0; ps0[0] = 0; pb1[0] = nphi - 1; ps1[0] = kSubBins - 1;
+        pb0[1] = 0; ps0[1] = 0; pb1[1] = -1; ps1[1] = 0;
+    } else if (k0 < 0) {
+        pb0[0] = k0 + nphi; ps0[0] = s0; pb1[0] = nphi - 1; ps1[0] = kSubBins - 1;
+        pb0[1] = 0; ps0[1] = 0; pb1[1] = k1; ps1[1] = s1;
+    } else if (k1 >= nphi) {
+        pb0[0] = k0; ps0[0] = s0; pb1[0] = nphi - 1; ps1[0] = kSubBins - 1;
+        pb0[1] = 0; ps0[1] = 0; pb1[1] = k1 - nphi; ps1[1] = s1;
+    } else {
+        pb0[0] = k0; ps0[0] = s0; pb1[0] = k1; ps1[0] = s1;
+        pb0[1] = 0; ps0[1] = 0; pb1[1] = -1; ps1[1] = 0;
+    }
+    bool found = false;
+    const int row0 = seg * a.n_bins;
+    for (int e = e0; e <= e1; ++e) {
+        const int row = row0 + e * nphi;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            if (pb1[part] < pb0[part]) continue;
+            const int ba = row + pb0[part], bb = row + pb1[part];
+            const int oa = __ldg(&a.bin_off[ba]);
+            const int ob = __ldg(&a.bin_off[bb]), ob1 = __ldg(&a.bin_off[bb + 1]);
+            const uint4 wa = __ldg(&a.bin_sub[ba]), wb = __ldg(&a.bin_sub[bb]);
+            const int i0 = oa + sub_first(wa, ps0[part]);
+            const int i1 = ob + sub_end(wb, ps1[part], ob1 - ob);
+            for (int i = i0; i < i1; ++i) {
+                const float4 h = __ldg(&a.hxyzi[i]);
+                const float2 hv = __ldg(&a.hvar[i]);
+                const R hx = R(h.x), hy = R(h.y);
+                if (!(xp * hx + yp * hy > R(0)) || !(R(h.z) * zp > R(0))) continue;  // far half; other endcap
+                const R ir = fast_rsqrt(hx * hx + hy * hy);
+                const R sh = hy * ir, ch = hx * ir;
+                const R u = ch * (hy - yp) - sh * (hx - xp);
+                const R v = ch * (hx - xp) + sh * (hy - yp);
+                if (ab(u) > U || ab(v) > W) continue;
+                const R c2 = chi2_disk<R>(p00, p10, p11, u, v, sh, ch, R(hv.x), R(hv.y));
+                if (c2 < cut) {
+                    list_insert32(lk, lh, make_key32(nh + 1, to_f32(chi2 + c2), rank), __float_as_int(h.w));
+                    found = true;
+                }
+            }
+        }
+    }
+    if (!found) list_insert32(lk, lh, make_key32(nh, to_f32(chi2), rank), kHoleId);
+}
+
 template <class R> __device__ __forceinline__ void store_track(void *par, void *cov, void *c2, int stride, int i,
                                                                   const R p[6], const R P[21], R chi2)
 {
@@ -273,7 +365,8 @@ template <int NMAX, class R, class U, bool kTwo> struct BuildMinBlocks {
 
 // kExactN: the candidates kept per seed equal NMAX, so the segment width and the merge's loops
 // are compile-time constants (unrolled); otherwise N = a.ncand <= NMAX at run time.
-template <int NMAX, class R, class U, bool kTwo, bool kExactN>
+// kDisk: the configuration has endcap disks; each layer then goes by its kind (cylinder or disk).
+template <int NMAX, class R, class U, bool kTwo, bool kExactN, bool kDisk>
 __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTwo>::value)) k_build(const BuildArgs a)
 {
     constexpr int W = kBuildThreads / 32;
@@ -331,7 +424,10 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTw
             int ns = 0;
             for (int l = a.first; l < a.L; ++l) {
                 const R Rl = pick<R>(a.radius_f[l], a.radius[l]);
-                const bool ok = alive && propagate<R>(p, P, Rl, kb);
+                const bool disk = kDisk && ((a.disk_mask >> l) & 1u);
+                const R zd = pick<R>(a.disk_z_f[l], a.disk_z[l]);
+                const bool ok = alive && (disk ? propagate_plane<R>(p, P, p[2] >= R(0) ? zd : -zd, kb)
+                                               : propagate<R>(p, P, Rl, kb));
                 unsigned lk[NMAX];
                 int lh[NMAX];
 #pragma unroll
@@ -339,7 +435,12 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTw
                     lk[i] = kEmpty32;
                     lh[i] = 0;
                 }
-                if (ok) scan_window<NMAX, R, kTwo>(a, ev, l, Rl, p, P, chi2, nh, r, lk, lh);
+                if (ok) {
+                    if (disk)
+                        scan_window_disk<NMAX, R>(a, ev, l, p, P, chi2, nh, r, lk, lh);
+                    else
+                        scan_window<NMAX, R, kTwo>(a, ev, l, Rl, p, P, chi2, nh, r, lk, lh);
+                }
 
                 // merge the segment's lists: N rounds of a segmented minimum
                 unsigned mine = kEmpty32;
@@ -389,10 +490,13 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTw
                         // for this hit's chi2, so it succeeds here too)
                         if (kTwo) propagate<R, kPropStep>(p, P, sq(R(h.x) * R(h.x) + R(h.y) * R(h.y)), kb);
                         U dc2 = U(0);
-                        kalman_update<U, R>(p, P, R(h.x), R(h.y), R(h.z), R(hv.x), R(hv.y), &dc2);
+                        if (disk)
+                            kalman_update<U, R, true>(p, P, R(h.x), R(h.y), R(h.z), R(hv.x), R(hv.y), &dc2);
+                        else
+                            kalman_update<U, R, false>(p, P, R(h.x), R(h.y), R(h.z), R(hv.x), R(hv.y), &dc2);
                         if (sizeof(R) == 8) chi2 = pchi2 + R(dc2);
                     }
-                    if (l < a.L - 1) scatter<R>(p, P, pick<R>(a.xx0_f[l], a.xx0[l]), mass);
+                    if (l < a.L - 1) scatter<R>(p, P, pick<R>(a.xx0_f[l], a.xx0[l]), mass, disk);
                     hist_hit[warp][l][lane] = gh;
                     hist_par[warp][l][lane] = (signed char)parent;
                 }
@@ -442,23 +546,21 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTw
 #ifndef TKF_BUILD_EXACT_N
 #define TKF_BUILD_EXACT_N 1
 #endif
-template <class R, class U, bool kTwo = false>
+template <class R, class U, bool kTwo = false, bool kDisk = false>
 cudaError_t launch_build_t(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy)
 {
     const void *fn = nullptr;
     const bool exact = TKF_BUILD_EXACT_N && a.ncand == nmax;
+#define TKF_K(n, e) (const void *)k_build<n, R, U, kTwo, e, kDisk>
     switch (nmax) {
-    case 1: fn = (const void *)k_build<1, R, U, kTwo, true>; break;
-    case 4: fn = exact ? (const void *)k_build<4, R, U, kTwo, true> : (const void *)k_build<4, R, U, kTwo, false>; break;
-    case 6: fn = exact ? (const void *)k_build<6, R, U, kTwo, true> : (const void *)k_build<6, R, U, kTwo, false>; break;
-    case 10:
-        fn = exact ? (const void *)k_build<10, R, U, kTwo, true> : (const void *)k_build<10, R, U, kTwo, false>;
-        break;
-    case 16:
-        fn = exact ? (const void *)k_build<16, R, U, kTwo, true> : (const void *)k_build<16, R, U, kTwo, false>;
-        break;
+    case 1: fn = TKF_K(1, true); break;
+    case 4: fn = exact ? TKF_K(4, true) : TKF_K(4, false); break;
+    case 6: fn = exact ? TKF_K(6, true) : TKF_K(6, false); break;
+    case 10: fn = exact ? TKF_K(10, true) : TKF_K(10, false); break;
+    case 16: fn = exact ? TKF_K(16, true) : TKF_K(16, false); break;
     default: return cudaErrorInvalidValue;
     }
+#undef TKF_K
     if (occupancy) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, fn, kBuildThreads, 0);
     void *args[] = {(void *)&a};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kBuildThreads), args, 0, s);

@@ -3,7 +3,8 @@ matrix A of known sparsity, written out term by term -- known zeros skipped, kno
 multiplied.  This is the Matriplex code-generator idea of Sec. 2.1 of arXiv:1702.06359, for
 the products of the Kalman-filter kernels:
 
-  transport_cov   P' = J P J^T with the helix transport Jacobian J (propagation);
+  transport_cov   P' = J P J^T with the helix transport Jacobian J (propagation to a cylinder);
+  plane_cov       P' = J P J^T for the propagation to a plane z = const (an endcap disk);
   measured_cov    the 2x2 block M P M^T with M = H J, the two measured rows of the transported
                   state (the two-step propagation's per-hit chi2).
 
@@ -13,7 +14,7 @@ the products of the Kalman-filter kernels:
 An entry of a pattern is "0", "1" or the name of a scalar argument.  P and S are packed lower
 triangles in row order (element (i, j), i >= j, at i (i + 1) / 2 + j).  For each row i of A
 that is not a unit row, the generated code forms the row T_i = A_i P, summing over the nonzero
-entries in column order; a unit row e_m takes row m of P.  It then forms S_ik = T_i . A_k over
+entries in column order; a unit row e_m takes row m of P; a zero row gives zeros.  It then forms S_ik = T_i . A_k over
 the nonzero entries of A_k in column order, and a unit row A_k = e_m takes T_i[m].  Products
 are written as (entry) * (operand), left to right, so that the compiler's multiply-add
 contraction sees the same expression trees as a hand-written form in that order.
@@ -36,6 +37,17 @@ TRANSPORT = [
     ["f0", "f1", "0", "f3", "f4", "0"],      # phi
     ["0", "0", "0", "0", "0", "1"],          # theta
 ]
+# helix transport to a plane z = const (an endcap disk): the path depends on z and theta only,
+# so rows x, y, phi gain columns z and theta and lose the x, y dependence of the path; row z is
+# zero (the plane's z is fixed)
+PLANE = [
+    ["1", "0", "a2", "a3", "a4", "a5"],      # x
+    ["0", "1", "b2", "b3", "b4", "b5"],      # y
+    ["0", "0", "0", "0", "0", "0"],          # z
+    ["0", "0", "0", "1", "0", "0"],          # q/pT
+    ["0", "0", "f2", "f3", "1", "f5"],       # phi
+    ["0", "0", "0", "0", "0", "1"],          # theta
+]
 # the two measured rows of the transported state: u (along the hit's tangent) and z
 MEASURED = [
     ["m0", "m1", "0", "m3", "m4", "0"],      # u = -sin(phi_h) x + cos(phi_h) y
@@ -45,6 +57,10 @@ MEASURED = [
 
 def _sym(i, j):
     return i * (i + 1) // 2 + j if i >= j else j * (j + 1) // 2 + i
+
+
+def _zero(row):
+    return all(e == "0" for e in row)
 
 
 def _unit(row):
@@ -73,6 +89,9 @@ def sandwich(name, pattern, doc):
     # T_i = A_i P for the non-unit rows
     trow = {}
     for i, row in enumerate(pattern):
+        if _zero(row):
+            trow[i] = ("Z", i)
+            continue
         m = _unit(row)
         if m is not None:
             trow[i] = ("P", m)
@@ -95,6 +114,9 @@ def sandwich(name, pattern, doc):
     # S_ik = T_i . A_k, lower triangle
     for i in range(rows):
         for k in range(i + 1):
+            if _zero(pattern[i]) or _zero(pattern[k]):  # a zero row of A gives a zero row of S
+                lines.append("    S[%d] = R(0);" % _sym(i, k))
+                continue
 
             def t_at(m):
                 kind, idx = trow[i]
@@ -137,6 +159,9 @@ TKF_HD constexpr int tkf_gen_sym(int i, int j) { return i >= j ? i * (i + 1) / 2
         sandwich("transport_cov", TRANSPORT,
                  "P' = J P J^T for the helix transport Jacobian J: rows x, y, phi have entries in columns\n"
                  "x, y, q/pT, phi; row z also in columns z (1) and theta; rows q/pT and theta are unit rows."),
+        sandwich("plane_cov", PLANE,
+                 "P' = J P J^T for the transport to a plane z = const: rows x, y, phi have entries in\n"
+                 "columns z, q/pT, phi, theta (x, y on their own column); row z is zero; q/pT, theta unit rows."),
         sandwich("measured_cov", MEASURED,
                  "[[Suu], [Suv, Svv]] = M P M^T for the two measured rows M of a transported state: u in\n"
                  "columns x, y, q/pT, phi; v = z in every column, 1 in column z."),

@@ -24,6 +24,9 @@ struct BuildArgs {
     double radius[TKF_MAX_LAYERS], xx0[TKF_MAX_LAYERS];
     float kb_f, mass_f, eta_min_f, inv_eta_w_f, cut_f, margin_f, hit_dr_f;
     double kb, mass, eta_min, inv_eta_w, cut, margin, hit_dr;
+    float disk_z_f[TKF_MAX_LAYERS];
+    double disk_z[TKF_MAX_LAYERS];
+    unsigned disk_mask;  // bit l: layer l is a pair of endcap disks at z = +-disk_z[l]
     // hit index
     const float4 *hxyzi;
     const float2 *hvar;
@@ -60,6 +63,10 @@ cudaError_t launch_build_fp64(const BuildArgs &a, int nmax, int grid, cudaStream
 cudaError_t launch_build2_fp32(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
 cudaError_t launch_build2_mixed(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
 cudaError_t launch_build2_fp64(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
+// The same for configurations with endcap disks (a.disk_mask != 0; the "endcap z" of Sec. 2.2).
+cudaError_t launch_build3_fp32(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
+cudaError_t launch_build3_mixed(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
+cudaError_t launch_build3_fp64(const BuildArgs &a, int nmax, int grid, cudaStream_t s, int *occupancy);
 
 // tkf_fit, and its continued form (continue_fit: `init` lies on layer first_layer - 1, as a
 // fit of the earlier layers leaves it; the fit propagates before its first update).

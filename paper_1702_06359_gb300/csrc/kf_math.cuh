@@ -242,12 +242,55 @@ __host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R 
     return true;
 }
 
+// Propagation to the plane z = zp (an endcap disk, the "endcap z" of Sec. 2.2): from
+// z(s) = z + s cot(theta) the transverse path is s = (zp - z) tan(theta) in closed form; the state
+// is the helix there.  The Jacobian adds (dp/ds)(ds/dp_in) to the derivatives at fixed s, with
+// ds/dz = -1/cot(theta) and ds/dtheta = s / (sin^2(theta) cot(theta)) from z(s, p_in) = zp (the
+// path does not depend on x, y, q/pT, phi); P <- J P J^T from that sparsity (plane_cov).
+// Returns false when the plane is behind, parallel, or more than a full turn away (a looper).
+template <class R> __host__ __device__ __forceinline__ bool propagate_plane(R p[6], R P[21], R zp, R kb)
+{
+    const R x = p[0], y = p[1], z = p[2], w = p[3], phi = p[4], th = p[5];
+    R st, ct;
+    sc(th, &st, &ct);
+    const R cot = ct / st;
+    if (!(ab(cot) > R(0))) return false;
+    const R s = (zp - z) / cot;
+    const R kappa = -kb * w;
+    if (!(s > R(0)) || !(ab(kappa) * s <= R(2.0 * kPi))) return false;
+    R sp, cp;
+    sc(phi, &sp, &cp);
+    const R a = kappa * s;
+    R S, C, Sd, Cd;
+    helix_fn(a, S, C, Sd, Cd);
+    const R sa = a * S, ca = R(1) - a * C;
+    const R xs = x + s * (cp * S - sp * C);
+    const R ys = y + s * (sp * S + cp * C);
+    const R c1 = cp * ca - sp * sa, s1 = sp * ca + cp * sa;  // direction at the plane
+    const R s2kb = -kb * s * s;
+    const R dx_dw = s2kb * (cp * Sd - sp * Cd);
+    const R dy_dw = s2kb * (sp * Sd + cp * Cd);
+    const R sz = -R(1) / cot, sth = s / (st * st * cot);  // ds/dz, ds/dtheta
+    R Q[21];
+    plane_cov<R>(c1 * sz, dx_dw, -(ys - y), c1 * sth, s1 * sz, dy_dw, xs - x, s1 * sth, kappa * sz, -kb * s,
+                 kappa * sth, P, Q);
+#pragma unroll
+    for (int k = 0; k < 21; ++k) P[k] = Q[k];
+    p[0] = xs;
+    p[1] = ys;
+    p[2] = zp;
+    p[4] = wrap_phi(phi + a);
+    return true;
+}
+
 // ------------------------------------------------------------------ scattering noise
-// Thin scatterer of thickness x/X0 crossed at angle alpha to the cylinder normal: Highland
+// Thin scatterer of thickness x/X0 crossed at angle alpha to the layer's normal: Highland
 // width theta0 = 0.0136/(beta p) sqrt(t) (1 + 0.038 ln(t/beta^2)), t = (x/X0)/|cos alpha|;
 // two kicks orthogonal to the direction add theta0^2 to theta, theta0^2/sin^2(theta) to phi,
 // and (through pT = p sin(theta) at fixed p) the q/pT terms.
-template <class R> __host__ __device__ __forceinline__ void scatter(const R p[6], R P[21], R xx0, R mass)
+// disk: the layer is an endcap disk, whose normal is the z axis (|cos alpha| = |cos theta|).
+template <class R>
+__host__ __device__ __forceinline__ void scatter(const R p[6], R P[21], R xx0, R mass, bool disk = false)
 {
     if (!(xx0 > R(0))) return;
     R st, ct, sp, cp;
@@ -257,8 +300,13 @@ template <class R> __host__ __device__ __forceinline__ void scatter(const R p[6]
     const R mom = R(1) / (ab(w) * st);
     const R beta2 = mom * mom / (mom * mom + mass * mass);
     const R beta = sq(beta2);
-    const R r = sq(p[0] * p[0] + p[1] * p[1]);
-    const R cosa = ab(st * (p[0] * cp + p[1] * sp) / r);
+    R cosa;
+    if (disk) {
+        cosa = ab(ct);
+    } else {
+        const R r = sq(p[0] * p[0] + p[1] * p[1]);
+        cosa = ab(st * (p[0] * cp + p[1] * sp) / r);
+    }
     const R t = xx0 / cosa;
     const R th0 = R(0.0136) / (beta * mom) * sq(t) * (R(1) + R(0.038) * fast_log(t / beta2));
     const R v = th0 * th0;
@@ -299,6 +347,19 @@ __host__ __device__ __forceinline__ R chi2_uv6(R p00, R p10, R p11, R p20, R p21
     const R Suu = sh * (sh * p00 - ch * p10) + ch * (ch * p11 - sh * p10) + vu;
     const R Suv = ch * p21 - sh * p20;
     const R Svv = p22 + vv;
+    const R det = Suu * Svv - Suv * Suv;
+    if (!(det > R(0))) return R(INFINITY);
+    return fast_div(u * (Svv * u - R(2) * Suv * v) + Suu * v * v, det);
+}
+
+// On an endcap disk (the hit measured in r-phi and r): rows u = (-sh, ch, 0) and
+// v = (ch, sh, 0) of the x, y block of P; (u, v) already formed on the disk's plane.
+template <class R>
+__host__ __device__ __forceinline__ R chi2_disk(R p00, R p10, R p11, R u, R v, R sh, R ch, R vu, R vv)
+{
+    const R Suu = sh * (sh * p00 - ch * p10) + ch * (ch * p11 - sh * p10) + vu;
+    const R Suv = sh * ch * (p11 - p00) + (ch * ch - sh * sh) * p10;
+    const R Svv = ch * (ch * p00 + sh * p10) + sh * (sh * p11 + ch * p10) + vv;
     const R det = Suu * Svv - Suv * Suv;
     if (!(det > R(0))) return R(INFINITY);
     return fast_div(u * (Svv * u - R(2) * Suv * v) + Suu * v * v, det);
@@ -425,13 +486,15 @@ template <> __device__ __forceinline__ double recip<double>(double x)
 // formed in the state's type R; S, its inverse, the gain, the state update and the Joseph form
 // are computed in U (double in the mixed mode).  Returns false when S is not positive definite;
 // writes the hit's chi2 to *chi2.
-template <class U, class R>
+// kDisk: the hit lies on an endcap disk and is measured on the disk's plane: the second row of
+// H is the radial direction (cos phi_h, sin phi_h, 0) instead of z.
+template <class U, class R, bool kDisk = false>
 __device__ __forceinline__ bool kalman_update(R pR[6], R PR[21], R xh_, R yh_, R zh_, R vu_, R vv_, U *chi2)
 {
     const R irR = R(1) / sq(xh_ * xh_ + yh_ * yh_);
     const R shR = yh_ * irR, chR = xh_ * irR;
     const R uR = chR * (yh_ - pR[1]) - shR * (xh_ - pR[0]);
-    const R vR = zh_ - pR[2];
+    const R vR = kDisk ? chR * (xh_ - pR[0]) + shR * (yh_ - pR[1]) : zh_ - pR[2];
     const U u = cvt_up<U>(uR), v = cvt_up<U>(vR);
     const U sh = cvt_up<U>(shR), ch = cvt_up<U>(chR);
     U P[21];
@@ -441,11 +504,11 @@ __device__ __forceinline__ bool kalman_update(R pR[6], R PR[21], R xh_, R yh_, R
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
         B0[j] = ch * P[sym(1, j)] - sh * P[sym(0, j)];
-        B1[j] = P[sym(2, j)];
+        B1[j] = kDisk ? ch * P[sym(0, j)] + sh * P[sym(1, j)] : P[sym(2, j)];
     }
     const U Suu = ch * B0[1] - sh * B0[0] + cvt_up<U>(vu_);
-    const U Suv = B0[2];
-    const U Svv = B1[2] + cvt_up<U>(vv_);
+    const U Suv = kDisk ? ch * B0[0] + sh * B0[1] : B0[2];
+    const U Svv = (kDisk ? ch * B1[0] + sh * B1[1] : B1[2]) + cvt_up<U>(vv_);
     const U det = Suu * Svv - Suv * Suv;
     if (!(det > U(0))) return false;
     const U id = recip<U>(det);

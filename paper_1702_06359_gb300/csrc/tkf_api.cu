@@ -53,8 +53,27 @@ struct IndexGeom {
     int L, n_eta, n_phi, n_bins, n_events;
     float radius[TKF_MAX_LAYERS];
     float eta_min, inv_eta_w;
-    float phi_scale;  // n_phi / (2 pi), rounded once on the host
+    float phi_scale;     // n_phi / (2 pi), rounded once on the host
+    unsigned disk_mask;  // bit l: layer l is an endcap disk (eta = asinh(z / r_hit))
 };
+
+IndexGeom index_geom(const tkf_config &c, int n_events)
+{
+    IndexGeom g{};
+    g.L = c.n_layers;
+    g.n_eta = c.n_eta_bins;
+    g.n_phi = c.n_phi_bins;
+    g.n_bins = c.n_eta_bins * c.n_phi_bins;
+    g.n_events = n_events;
+    for (int l = 0; l < c.n_layers; ++l) {
+        g.radius[l] = (float)c.radius[l];
+        if (c.disk_z[l] > 0.0) g.disk_mask |= 1u << l;
+    }
+    g.eta_min = (float)c.eta_min;
+    g.inv_eta_w = (float)(1.0 / c.eta_bin_w);
+    g.phi_scale = (float)(c.n_phi_bins / (2.0 * kPi));
+    return g;
+}
 
 // continuous phi-bin coordinate (phi + pi) * n_phi / (2 pi); its floor is the phi bin
 __device__ __forceinline__ float phi_coord(const IndexGeom &g, float x, float y)
@@ -73,7 +92,9 @@ __device__ __forceinline__ float eta_of(float z, float r)
 
 __device__ __forceinline__ int hit_bin(const IndexGeom &g, int l, float x, float y, float z)
 {
-    int eb = (int)floorf((eta_of(z, g.radius[l]) - g.eta_min) * g.inv_eta_w);
+    // on a cylinder eta of the layer's radius; on an endcap disk of the hit's own radius
+    const float r = (g.disk_mask >> l) & 1u ? sqrtf(x * x + y * y) : g.radius[l];
+    int eb = (int)floorf((eta_of(z, r) - g.eta_min) * g.inv_eta_w);
     eb = eb < 0 ? 0 : (eb >= g.n_eta ? g.n_eta - 1 : eb);
     int pb = (int)floorf(phi_coord(g, x, y));
     pb = pb < 0 ? 0 : (pb >= g.n_phi ? g.n_phi - 1 : pb);
@@ -605,18 +626,41 @@ __global__ void k_seed_place(const int *keys, int *counts, const int *off, int n
 
 // ------------------------------------------------------------------ seed estimate and fit
 
+template <class R> __device__ __forceinline__ R gpick(float f, double d);
+template <> __device__ __forceinline__ float gpick<float>(float f, double) { return f; }
+template <> __device__ __forceinline__ double gpick<double>(float, double d) { return d; }
+
 struct FitGeom {
     int L;
     int two_step;  // hits lie off the layers' cylinders (hit_dr > 0): states go to each hit's radius
-    double radius[TKF_MAX_LAYERS], xx0[TKF_MAX_LAYERS];
-    float radius_f[TKF_MAX_LAYERS], xx0_f[TKF_MAX_LAYERS];
+    double radius[TKF_MAX_LAYERS], xx0[TKF_MAX_LAYERS], disk_z[TKF_MAX_LAYERS];
+    float radius_f[TKF_MAX_LAYERS], xx0_f[TKF_MAX_LAYERS], disk_z_f[TKF_MAX_LAYERS];
+    unsigned disk_mask;  // bit l: layer l is a pair of endcap disks at z = +-disk_z[l]
     double kb, mass, prior[6];
     float kb_f, mass_f;
 };
 
-template <class R> __device__ __forceinline__ R gpick(float f, double d);
-template <> __device__ __forceinline__ float gpick<float>(float f, double) { return f; }
-template <> __device__ __forceinline__ double gpick<double>(float, double d) { return d; }
+// The state's move to layer l (kDisk: the kernel serves configurations with endcap disks):
+// the layer's cylinder (at target_radius), or the disk on the side of the state's z.
+template <class R, bool kDisk, int kMode = kPropOut>
+__device__ __forceinline__ bool to_layer(const FitGeom &g, int l, R p[6], R P[21], R radius, R kb)
+{
+    if (kDisk && ((g.disk_mask >> l) & 1u)) {
+        const R zd = gpick<R>(g.disk_z_f[l], g.disk_z[l]);
+        return propagate_plane<R>(p, P, p[2] >= R(0) ? zd : -zd, kb);
+    }
+    return propagate<R, kMode>(p, P, radius, kb);
+}
+
+// The Kalman update with the layer's measurement model (r-phi and z on a cylinder, r-phi and r
+// on a disk).
+template <class U, class R, bool kDisk>
+__device__ __forceinline__ bool update_at(const FitGeom &g, int l, R p[6], R P[21], R x, R y, R z, R vu, R vv, U *c2)
+{
+    if (kDisk && ((g.disk_mask >> l) & 1u)) return kalman_update<U, R, true>(p, P, x, y, z, vu, vv, c2);
+    return kalman_update<U, R, false>(p, P, x, y, z, vu, vv, c2);
+}
+
 
 // asin(x)/x, accurate near 0
 template <class R> __device__ __forceinline__ R asin_over(R x)
@@ -658,6 +702,7 @@ __device__ __forceinline__ void seed_estimate(const FitGeom &g, const tkf_hits &
     for (int k = 0; k < 21; ++k) P[k] = R(0);
 #pragma unroll
     for (int k = 0; k < 6; ++k) P[sym(k, k)] = R(g.prior[k] * g.prior[k]);
+    if (g.disk_mask & 1u) P[sym(2, 2)] = R(0);  // on an endcap disk z is the disk's, known exactly
 }
 
 template <class R>
@@ -731,7 +776,7 @@ __device__ __forceinline__ R target_radius(const FitGeom &g, const tkf_hits &h, 
 // The reads are software-pipelined: while a layer is processed, the next layer's hit and the
 // id of the one after are already on their way, so the loads' latency hides behind a layer's
 // arithmetic instead of stalling each step.
-template <class R, class U, class HitAt>
+template <class R, class U, bool kDisk, class HitAt>
 __device__ __forceinline__ void fit_layers(const FitGeom &g, const tkf_hits &h, HitAt hit_at, int first, int last,
                                            bool prop_first, R p[6], R P[21], R &chi2, int &nh, int &status, int *err)
 {
@@ -742,7 +787,7 @@ __device__ __forceinline__ void fit_layers(const FitGeom &g, const tkf_hits &h, 
     for (int l = first; l <= last && status == 0; ++l) {
         const HitRec<R> nxt = load_hit<R>(h, hid1);
         const int hid2 = l + 2 <= last ? hit_at(l + 2) : -1;
-        if ((l > first || prop_first) && !propagate<R>(p, P, target_radius<R>(g, h, l, hid, cur), kb)) {
+        if ((l > first || prop_first) && !to_layer<R, kDisk>(g, l, p, P, target_radius<R>(g, h, l, hid, cur), kb)) {
             status = TKF_TRACK_NOREACH;
             break;
         }
@@ -753,14 +798,15 @@ __device__ __forceinline__ void fit_layers(const FitGeom &g, const tkf_hits &h, 
         }
         if (hid >= 0) {
             U dc2;
-            if (!kalman_update<U, R>(p, P, cur.x, cur.y, cur.z, cur.vu, cur.vv, &dc2)) {
+            if (!update_at<U, R, kDisk>(g, l, p, P, cur.x, cur.y, cur.z, cur.vu, cur.vv, &dc2)) {
                 status = TKF_TRACK_SINGULAR;
                 break;
             }
             chi2 += R(dc2);
             nh += 1;
         }
-        if (l < g.L - 1) scatter<R>(p, P, gpick<R>(g.xx0_f[l], g.xx0[l]), mass);
+        if (l < g.L - 1)
+            scatter<R>(p, P, gpick<R>(g.xx0_f[l], g.xx0[l]), mass, kDisk && ((g.disk_mask >> l) & 1u));
         cur = nxt;
         hid = hid1;
         hid1 = hid2;
@@ -782,7 +828,7 @@ template <class R> __device__ __forceinline__ void store_fit(const tkf_tracks &o
 
 // prop_first = 0: the input state lies on layer `first` (its first step is the update there);
 // 1: it lies on the layer before (the fit continues a fit of the earlier layers).
-template <class R, class U>
+template <class R, class U, bool kDisk>
 __global__ void __launch_bounds__(kFitThreads, (FitMinBlocks<R, U>::value)) k_fit(const FitGeom g, const tkf_hits h, const tkf_tracks in, const int *hit_idx, int first, int last,
                       int prop_first, tkf_tracks out, int *err)
 {
@@ -798,7 +844,7 @@ __global__ void __launch_bounds__(kFitThreads, (FitMinBlocks<R, U>::value)) k_fi
     R chi2 = ((const R *)in.chi2)[i];
     int nh = in.nhits[i];
     int status = nh < 0 ? nh : 0;
-    fit_layers<R, U>(
+    fit_layers<R, U, kDisk>(
         g, h, [&](int l) { return hit_idx[l * si + i]; }, first, last, prop_first != 0, p, P, chi2, nh, status, err);
     store_fit<R>(out, i, p, P, chi2, status ? status : nh);
     if (out.hit_idx && out.hit_idx != hit_idx)
@@ -807,7 +853,7 @@ __global__ void __launch_bounds__(kFitThreads, (FitMinBlocks<R, U>::value)) k_fi
 
 // Seed estimate and its fit over layers 0..last in one pass (the first two steps of the
 // batched pipeline): the same values as k_seed followed by k_fit, without storing the estimate.
-template <class R, class U>
+template <class R, class U, bool kDisk>
 __global__ void __launch_bounds__(kFitThreads, (FitMinBlocks<R, U>::value)) k_seed_fit(const FitGeom g, const tkf_hits h, const int *seed_hits, int last, tkf_tracks out, int *err)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -825,7 +871,7 @@ __global__ void __launch_bounds__(kFitThreads, (FitMinBlocks<R, U>::value)) k_se
         for (int k = 0; k < 21; ++k) P[k] = R(0);
     } else {
         seed_estimate<R>(g, h, h1, h2, h3, p, P);
-        fit_layers<R, U>(
+        fit_layers<R, U, kDisk>(
             g, h, [&](int l) { return l < 3 ? seed_hits[l * st + i] : -1; }, 0, last, false, p, P, chi2, nh, status,
             err);
     }
@@ -858,7 +904,7 @@ template <class R> __device__ __forceinline__ void reverse_track(R p[6], R P[21]
 // the layer's hit, the layer's material, the propagation to the next smaller cylinder (as the
 // outward propagation of the reversed track).  The result lies on layer `first` after its
 // update and material; chi2 and nhits are the pass's own.
-template <class R, class U>
+template <class R, class U, bool kDisk>
 __global__ void __launch_bounds__(kFitThreads, (FitMinBlocks<R, U>::value)) k_fit_backward(const FitGeom g, const tkf_hits h, const tkf_tracks in, const int *hit_idx, int last,
                                int first, R scale, tkf_tracks out, int *err)
 {
@@ -883,7 +929,7 @@ __global__ void __launch_bounds__(kFitThreads, (FitMinBlocks<R, U>::value)) k_fi
     for (int l = last; l >= first && status == 0; --l) {
         const HitRec<R> nxt = load_hit<R>(h, hid1);
         const int hid2 = l - 2 >= first ? hit_idx[(l - 2) * si + i] : -1;
-        if (l < last && !propagate<R, kPropIn>(p, P, target_radius<R>(g, h, l, hid, cur), kb)) {
+        if (l < last && !to_layer<R, kDisk, kPropIn>(g, l, p, P, target_radius<R>(g, h, l, hid, cur), kb)) {
             status = TKF_TRACK_NOREACH;
             break;
         }
@@ -894,14 +940,14 @@ __global__ void __launch_bounds__(kFitThreads, (FitMinBlocks<R, U>::value)) k_fi
         }
         if (hid >= 0) {
             U dc2;
-            if (!kalman_update<U, R>(p, P, cur.x, cur.y, cur.z, cur.vu, cur.vv, &dc2)) {
+            if (!update_at<U, R, kDisk>(g, l, p, P, cur.x, cur.y, cur.z, cur.vu, cur.vv, &dc2)) {
                 status = TKF_TRACK_SINGULAR;
                 break;
             }
             chi2 += R(dc2);
             nh += 1;
         }
-        scatter<R>(p, P, gpick<R>(g.xx0_f[l], g.xx0[l]), mass);
+        scatter<R>(p, P, gpick<R>(g.xx0_f[l], g.xx0[l]), mass, kDisk && ((g.disk_mask >> l) & 1u));
         cur = nxt;
         hid = hid1;
         hid1 = hid2;
@@ -923,6 +969,9 @@ FitGeom fit_geom(const tkf_ctx *ctx)
         g.xx0[l] = c.x_over_x0[l];
         g.radius_f[l] = (float)c.radius[l];
         g.xx0_f[l] = (float)c.x_over_x0[l];
+        g.disk_z[l] = c.disk_z[l];
+        g.disk_z_f[l] = (float)c.disk_z[l];
+        if (c.disk_z[l] > 0.0) g.disk_mask |= 1u << l;
     }
     g.kb = kCurv * c.bz;
     g.kb_f = (float)g.kb;
@@ -1086,10 +1135,20 @@ int tkf_create(const tkf_config *cfg, tkf_ctx **out)
         c.precision < TKF_FP32 || c.precision > TKF_FP64 || c.seeds_per_block < 0 || c.window_margin < 0 ||
         !(c.hit_dr >= 0.0) || !(c.hit_dr < c.radius[0]))
         return TKF_ERR_INVALID;
-    for (int l = 0; l < c.n_layers; ++l)
-        if (!(c.radius[l] > 0) || (l > 0 && !(c.radius[l] > c.radius[l - 1])) || c.x_over_x0[l] < 0 ||
-            (l > 0 && !(2.0 * c.hit_dr < c.radius[l] - c.radius[l - 1])))
+    bool any_disk = false;
+    for (int l = 0; l < c.n_layers; ++l) {
+        if (!(c.disk_z[l] >= 0.0) || !(c.disk_z[l] < 1e6)) return TKF_ERR_INVALID;
+        any_disk |= c.disk_z[l] > 0.0;
+    }
+    if (any_disk && c.hit_dr > 0.0) return TKF_ERR_INVALID;
+    for (int l = 0; l < c.n_layers; ++l) {
+        if (!(c.radius[l] > 0) || c.x_over_x0[l] < 0) return TKF_ERR_INVALID;
+        if (l == 0) continue;
+        const bool d0 = c.disk_z[l - 1] > 0.0, d1 = c.disk_z[l] > 0.0;
+        if (!d0 && !d1 && (!(c.radius[l] > c.radius[l - 1]) || !(2.0 * c.hit_dr < c.radius[l] - c.radius[l - 1])))
             return TKF_ERR_INVALID;
+        if (d0 && d1 && !(c.disk_z[l] > c.disk_z[l - 1])) return TKF_ERR_INVALID;
+    }
     tkf_ctx *ctx = new (std::nothrow) tkf_ctx();
     if (!ctx) return TKF_ERR_NOMEM;
     ctx->cfg = c;
@@ -1173,16 +1232,7 @@ int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out,
         idx->n_layers = L;
         idx->n_bins = NB;
         cudaStream_t s = (cudaStream_t)stream;
-        IndexGeom g{};
-        g.L = L;
-        g.n_eta = c.n_eta_bins;
-        g.n_phi = c.n_phi_bins;
-        g.n_bins = NB;
-        g.n_events = hits->n_events;
-        for (int l = 0; l < L; ++l) g.radius[l] = (float)c.radius[l];
-        g.eta_min = (float)c.eta_min;
-        g.inv_eta_w = (float)(1.0 / c.eta_bin_w);
-        g.phi_scale = (float)(c.n_phi_bins / (2.0 * kPi));
+        const IndexGeom g = index_geom(c, hits->n_events);
         TKF_CUDA(ctx, cudaMemcpyAsync(idx->ev_off, hits->event_off, (hits->n_events + 1) * sizeof(int),
                                       cudaMemcpyDeviceToDevice, s));
         // one block per event when the batch has enough events to fill the GPU and their bins fit
@@ -1325,16 +1375,14 @@ int tkf::fit_tracks(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init, 
     const int nb = (init->n + 127) / 128;
     cudaStream_t s = (cudaStream_t)stream;
     const int pf = continue_fit ? 1 : 0;
+    auto go = [&](auto kern) {
+        kern<<<nb, kFitThreads, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, pf, *out, ctx->d_err);
+    };
+    const bool dk = g.disk_mask != 0;
     switch (ctx->cfg.precision) {
-    case TKF_FP32:
-        k_fit<float, float><<<nb, kFitThreads, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, pf, *out, ctx->d_err);
-        break;
-    case TKF_MIXED:
-        k_fit<float, double><<<nb, kFitThreads, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, pf, *out, ctx->d_err);
-        break;
-    default:
-        k_fit<double, double><<<nb, kFitThreads, 0, s>>>(g, *hits, *init, hidx, first_layer, last_layer, pf, *out, ctx->d_err);
-        break;
+    case TKF_FP32: dk ? go(k_fit<float, float, true>) : go(k_fit<float, float, false>); break;
+    case TKF_MIXED: dk ? go(k_fit<float, double, true>) : go(k_fit<float, double, false>); break;
+    default: dk ? go(k_fit<double, double, true>) : go(k_fit<double, double, false>); break;
     }
     TKF_CUDA(ctx, cudaGetLastError());
     return TKF_OK;
@@ -1357,18 +1405,18 @@ int tkf::fit_backward(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init
     const FitGeom g = fit_geom(ctx);
     const int nb = (init->n + 127) / 128;
     cudaStream_t s = (cudaStream_t)stream;
+    auto go = [&](auto kern, auto scale) {
+        kern<<<nb, kFitThreads, 0, s>>>(g, *hits, *init, hidx, last_layer, first_layer, scale, *out, ctx->d_err);
+    };
+    const bool dk = g.disk_mask != 0;
+    const float sf = (float)cov_scale;
     switch (ctx->cfg.precision) {
-    case TKF_FP32:
-        k_fit_backward<float, float><<<nb, kFitThreads, 0, s>>>(g, *hits, *init, hidx, last_layer, first_layer,
-                                                         (float)cov_scale, *out, ctx->d_err);
-        break;
+    case TKF_FP32: dk ? go(k_fit_backward<float, float, true>, sf) : go(k_fit_backward<float, float, false>, sf); break;
     case TKF_MIXED:
-        k_fit_backward<float, double><<<nb, kFitThreads, 0, s>>>(g, *hits, *init, hidx, last_layer, first_layer,
-                                                          (float)cov_scale, *out, ctx->d_err);
+        dk ? go(k_fit_backward<float, double, true>, sf) : go(k_fit_backward<float, double, false>, sf);
         break;
     default:
-        k_fit_backward<double, double><<<nb, kFitThreads, 0, s>>>(g, *hits, *init, hidx, last_layer, first_layer, cov_scale,
-                                                           *out, ctx->d_err);
+        dk ? go(k_fit_backward<double, double, true>, cov_scale) : go(k_fit_backward<double, double, false>, cov_scale);
         break;
     }
     TKF_CUDA(ctx, cudaGetLastError());
@@ -1388,10 +1436,12 @@ int tkf::seed_and_fit(tkf_ctx *ctx, const tkf_hits *hits, const int32_t *seed_hi
     const FitGeom g = fit_geom(ctx);
     const int nb = (out->n + 127) / 128;
     cudaStream_t s = (cudaStream_t)stream;
+    auto go = [&](auto kern) { kern<<<nb, kFitThreads, 0, s>>>(g, *hits, seed_hits, last_layer, *out, ctx->d_err); };
+    const bool dk = g.disk_mask != 0;
     switch (ctx->cfg.precision) {
-    case TKF_FP32: k_seed_fit<float, float><<<nb, kFitThreads, 0, s>>>(g, *hits, seed_hits, last_layer, *out, ctx->d_err); break;
-    case TKF_MIXED: k_seed_fit<float, double><<<nb, kFitThreads, 0, s>>>(g, *hits, seed_hits, last_layer, *out, ctx->d_err); break;
-    default: k_seed_fit<double, double><<<nb, kFitThreads, 0, s>>>(g, *hits, seed_hits, last_layer, *out, ctx->d_err); break;
+    case TKF_FP32: dk ? go(k_seed_fit<float, float, true>) : go(k_seed_fit<float, float, false>); break;
+    case TKF_MIXED: dk ? go(k_seed_fit<float, double, true>) : go(k_seed_fit<float, double, false>); break;
+    default: dk ? go(k_seed_fit<double, double, true>) : go(k_seed_fit<double, double, false>); break;
     }
     TKF_CUDA(ctx, cudaGetLastError());
     return TKF_OK;
@@ -1440,6 +1490,11 @@ int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *s
     a.margin = c.window_margin;
     a.hit_dr = c.hit_dr;
     a.hit_dr_f = (float)c.hit_dr;
+    for (int l = 0; l < c.n_layers; ++l) {
+        a.disk_z[l] = c.disk_z[l];
+        a.disk_z_f[l] = (float)c.disk_z[l];
+        if (c.disk_z[l] > 0.0) a.disk_mask |= 1u << l;
+    }
     a.kb_f = (float)a.kb;
     a.mass_f = (float)a.mass;
     a.eta_min_f = (float)a.eta_min;
@@ -1481,16 +1536,7 @@ int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *s
     if (c.seed_order) {
         // counting sort of the seeds by (event, eta bin, phi bin) on the last seeding layer
         if ((st = tkf::seed_order_reserve(ctx, (size_t)seeds->n, (size_t)idx->n_events))) return st;
-        IndexGeom g{};
-        g.L = c.n_layers;
-        g.n_eta = c.n_eta_bins;
-        g.n_phi = c.n_phi_bins;
-        g.n_bins = c.n_eta_bins * c.n_phi_bins;
-        g.n_events = idx->n_events;
-        for (int l = 0; l < c.n_layers; ++l) g.radius[l] = (float)c.radius[l];
-        g.eta_min = (float)c.eta_min;
-        g.inv_eta_w = (float)(1.0 / c.eta_bin_w);
-        g.phi_scale = (float)(c.n_phi_bins / (2.0 * kPi));
+        const IndexGeom g = index_geom(c, idx->n_events);
         const int nb = (seeds->n + 255) / 256, layer = c.first_build_layer - 1;
         if (c.precision == TKF_FP64)
             k_seed_key<double><<<nb, 256, 0, s>>>(g, layer, (const double *)seeds->par, seeds->stride, seeds->event,
@@ -1506,10 +1552,13 @@ int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *s
         a.s_perm = ctx->ord_perm;  // counts are back to zero after k_seed_place
     }
     const int nmax = build_nmax(c.n_cand);
-    auto launch = c.hit_dr > 0.0 ? (c.precision == TKF_FP32    ? launch_build2_fp32
+    auto launch = a.disk_mask    ? (c.precision == TKF_FP32    ? launch_build3_fp32
+                                    : c.precision == TKF_MIXED ? launch_build3_mixed
+                                                               : launch_build3_fp64)
+                  : c.hit_dr > 0.0 ? (c.precision == TKF_FP32    ? launch_build2_fp32
                                     : c.precision == TKF_MIXED ? launch_build2_mixed
                                                                : launch_build2_fp64)
-                                 : (c.precision == TKF_FP32    ? launch_build_fp32
+                                   : (c.precision == TKF_FP32    ? launch_build_fp32
                                     : c.precision == TKF_MIXED ? launch_build_mixed
                                                                : launch_build_fp64);
     int occ = 0;
@@ -1606,16 +1655,7 @@ extern "C" int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits
     int *seg_count = counts + TKF_NOALLOC_MAX_BINS;
     int *seg_base = seg_count + TKF_NOALLOC_MAX_SEGMENTS;
     int *err = seg_base + TKF_NOALLOC_MAX_SEGMENTS;
-    IndexGeom g{};
-    g.L = L;
-    g.n_eta = c.n_eta_bins;
-    g.n_phi = c.n_phi_bins;
-    g.n_bins = NB;
-    g.n_events = hits->n_events;
-    for (int l = 0; l < L; ++l) g.radius[l] = (float)c.radius[l];
-    g.eta_min = (float)c.eta_min;
-    g.inv_eta_w = (float)(1.0 / c.eta_bin_w);
-    g.phi_scale = (float)(c.n_phi_bins / (2.0 * kPi));
+    const IndexGeom g = index_geom(c, hits->n_events);
     cudaStream_t s = (cudaStream_t)stream;
     float4 *hxyzi = (float4 *)out->hit_xyzi;
     float2 *hvar = (float2 *)out->hit_var;

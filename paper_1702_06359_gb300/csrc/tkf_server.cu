@@ -164,28 +164,12 @@ void free_outbuf(tkf_server *sv, OutBuf *b)
 // batch's size class (the next power of two from 1024, at most max_batch_tracks), else a new
 // one within the pinned-memory budget opt.result_bytes, freeing idle buffers of other sizes
 // first.  nullptr when the budget is held by unreleased results (the batch waits).
-OutBuf *get_outbuf(tkf_server *sv, int trk)
+// A new pinned result buffer of `cap` tracks within the budget (nullptr if it does not fit or the
+// allocation fails).  cudaMallocHost can wait for the device, so the server makes n_slots of them
+// when it is created and allocates more only when results held by the client exceed them.
+OutBuf *new_outbuf(tkf_server *sv, int cap)
 {
-    int cap = 1024;
-    while (cap < trk) cap *= 2;
-    cap = std::min(cap, std::max(sv->opt.max_batch_tracks, trk));
-    // the smallest free buffer that holds the batch (of its size class or larger): after the
-    // first batches every launch reuses pinned memory, with no allocation (cudaMallocHost) or
-    // free (cudaFreeHost synchronises the device) on the serving path
-    size_t best = sv->free_bufs.size();
-    for (size_t k = 0; k < sv->free_bufs.size(); ++k)
-        if (sv->free_bufs[k]->cap >= trk && (best == sv->free_bufs.size() || sv->free_bufs[k]->cap < sv->free_bufs[best]->cap))
-            best = k;
-    if (best < sv->free_bufs.size()) {
-        OutBuf *b = sv->free_bufs[best];
-        sv->free_bufs.erase(sv->free_bufs.begin() + best);
-        return b;
-    }
     const size_t bytes = outbuf_bytes(sv, cap);
-    while (sv->result_bytes + bytes > sv->opt.result_bytes && !sv->free_bufs.empty()) {
-        free_outbuf(sv, sv->free_bufs.back());
-        sv->free_bufs.pop_back();
-    }
     if (sv->result_bytes + bytes > sv->opt.result_bytes) return nullptr;
     OutBuf *b = new (std::nothrow) OutBuf();
     if (!b) return nullptr;
@@ -199,7 +183,38 @@ OutBuf *get_outbuf(tkf_server *sv, int trk)
         free_outbuf(sv, b);
         return nullptr;
     }
+    sv->stats.result_allocs += 1;
     return b;
+}
+
+OutBuf *get_outbuf(tkf_server *sv, int trk)
+{
+    int cap = 1024;
+    while (cap < trk) cap *= 2;
+    cap = std::min(cap, std::max(sv->opt.max_batch_tracks, trk));
+    // the smallest free buffer that holds the batch (of its size class or larger): the slots'
+    // buffers made at creation serve every batch while the client releases results promptly, so
+    // nothing is allocated (cudaMallocHost) or freed (cudaFreeHost) on the serving path
+    size_t best = sv->free_bufs.size();
+    for (size_t k = 0; k < sv->free_bufs.size(); ++k)
+        if (sv->free_bufs[k]->cap >= trk && (best == sv->free_bufs.size() || sv->free_bufs[k]->cap < sv->free_bufs[best]->cap))
+            best = k;
+    if (best < sv->free_bufs.size()) {
+        OutBuf *b = sv->free_bufs[best];
+        sv->free_bufs.erase(sv->free_bufs.begin() + best);
+        return b;
+    }
+    // a new buffer is made for the largest batch when the budget has room for it, so that it can
+    // serve any later batch: the pool then stops growing once it holds as many buffers as batches
+    // are held at once
+    const int cap_max = std::max(sv->opt.max_batch_tracks, trk);
+    if (sv->result_bytes + outbuf_bytes(sv, cap_max) <= sv->opt.result_bytes) cap = cap_max;
+    const size_t bytes = outbuf_bytes(sv, cap);
+    while (sv->result_bytes + bytes > sv->opt.result_bytes && !sv->free_bufs.empty()) {
+        free_outbuf(sv, sv->free_bufs.back());
+        sv->free_bufs.pop_back();
+    }
+    return new_outbuf(sv, cap);
 }
 
 void unref(tkf_server *sv, OutBuf *b)
@@ -530,9 +545,16 @@ int tkf_server_create(const tkf_config *cfg, const tkf_server_options *opt, tkf_
             return st;
         }
     }
+    // one full-size result buffer per slot (as many as the budget holds), made before any batch runs
+    for (int k = 0; k < opt->n_slots; ++k) {
+        OutBuf *b = new_outbuf(sv, opt->max_batch_tracks);
+        if (!b) break;
+        sv->free_bufs.push_back(b);
+    }
     if (cudaEventCreate(&sv->t_ref) != cudaSuccess || cudaEventRecord(sv->t_ref, sv->slots[0].stream) != cudaSuccess ||
         cudaEventSynchronize(sv->t_ref) != cudaSuccess) {
         for (Slot &t : sv->slots) free_slot(t);
+        for (OutBuf *b : sv->free_bufs) free_outbuf(sv, b);
         if (sv->t_ref) cudaEventDestroy(sv->t_ref);
         delete sv;
         return TKF_ERR_CUDA;

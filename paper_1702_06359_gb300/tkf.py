@@ -43,6 +43,7 @@ class Config(C.Structure):
         ("seeds_per_block", C.c_int32),
         ("seed_order", C.c_int32),
         ("hit_dr", C.c_double),
+        ("disk_z", C.c_double * MAX_LAYERS),
     ]
 
 
@@ -88,7 +89,7 @@ class Result(C.Structure):
 
 class ServerStats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("submitted", "rejected", "events_done", "tracks_done", "batches",
-                                         "max_batch_events")]
+                                         "max_batch_events", "result_allocs")]
 
 
 _lib = None
@@ -172,7 +173,7 @@ def default_config(**kw) -> Config:
     cfg = Config()
     lib().tkf_default_config(C.byref(cfg))
     for k, v in kw.items():
-        if k in ("radius", "x_over_x0", "prior_sigma"):
+        if k in ("radius", "x_over_x0", "prior_sigma", "disk_z"):
             arr = getattr(cfg, k)
             for i, x in enumerate(v):
                 arr[i] = x

@@ -160,8 +160,8 @@ def test_two_step_fit_reports_a_module_out_of_reach(prec):
         assert st == 0
         r2 = 8.5 if outer[t] else 7.5
         ph = math.atan2(p2[1], p2[0])
-        hits[2 * t] = (p1[0], p1[1], p1[2], det.sigma_rphi ** 2, det.sigma_z ** 2, 0)
-        hits[2 * t + 1] = (r2 * math.cos(ph), r2 * math.sin(ph), p2[2], det.sigma_rphi ** 2, det.sigma_z ** 2, 1)
+        hits[2 * t] = (p1[0], p1[1], p1[2], det.sigma_rphi ** 2, det.sigma_z ** 2, 0, 0)
+        hits[2 * t + 1] = (r2 * math.cos(ph), r2 * math.sin(ph), p2[2], det.sigma_rphi ** 2, det.sigma_z ** 2, 1, 0)
         ids[t, 0], ids[t, 1] = 2 * t, 2 * t + 1
     # the oracle on the float-rounded hits the GPU reads
     for k in ("x", "y", "z", "var_u", "var_v"):

