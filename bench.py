@@ -76,6 +76,9 @@ MODULE_DR = 1.0  # cm between the inner and outer module rows of a layer (hit_dr
 # each event's tracks; python oracle/opcount.py --events 64 --forward, 69674 seeds):
 FLOP_PROPAGATE_PLANE, FLOP_WINDOW_DISK, FLOP_CHI2_DISK, FLOP_UPDATE_DISK, FLOP_SCATTER_DISK = 296, 57, 57, 359, 23
 PER_SEED_DISK = dict(n_prop=25.7421, n_hits_examined=218.2409, n_updates=26.9508, n_kept=29.2005)
+# DRAM bytes (read + write) per seed of the FP32 endcap building kernel (one ncu capture of its
+# 640-event launch: 474.0 MB for 649 624 seeds; summary in profiles/); None when it changes
+BUILD3_DRAM_BYTES_PER_SEED = 729.7
 FLOP_PER_SEED_DISK = (PER_SEED_DISK["n_prop"] * (FLOP_PROPAGATE_PLANE + FLOP_WINDOW_DISK)
                       + PER_SEED_DISK["n_hits_examined"] * FLOP_CHI2_DISK
                       + PER_SEED_DISK["n_updates"] * FLOP_UPDATE_DISK
@@ -897,7 +900,10 @@ def main():
             "autotune_build_ms": [round(x, 4) for x in t3ms],
             "roofline": {"kernel": "k_build<6,float,float,disks>", "bound": "alu", "achieved": ach3,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach3 / FP32_PEAK_TFLOPS,
-                         "traffic": None, "launch_ms": d_build, "flop_per_seed": FLOP_PER_SEED_DISK,
+                         "traffic": BUILD3_DRAM_BYTES_PER_SEED * n3t if BUILD3_DRAM_BYTES_PER_SEED else None,
+                         "traffic_unit": "bytes per launch (ncu DRAM read + write of the 640-event endcap launch, "
+                                         "per seed)",
+                         "launch_ms": d_build, "flop_per_seed": FLOP_PER_SEED_DISK,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
             "form": "events 0..%d of the batched workload, each with a quarter of its tracks (the endcaps' "
                     "share) and its noise fraction, on the endcap tracker (ten pairs of disks at z = +-8..80 cm, "
