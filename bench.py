@@ -439,6 +439,21 @@ class LentEvents:
         self.d2h = b.n_tracks * (6 + 21 + 1 + 1 + n_layers) * 4
 
 
+def device_breakdown(res):
+    """Device side of one server pass, from the CUDA-event times each result carries (ms on the
+    server's clock, per batch): [span from the first batch's first copy to the last batch's last
+    copy, time with at least one batch in flight, input copies, kernels and result copies summed
+    over batches, batches]."""
+    batches = sorted({(r.gpu_start_ms, r.gpu_inputs_ms, r.gpu_results_ms, r.gpu_done_ms) for r in res})
+    busy, end = 0.0, -1e30
+    for b in batches:
+        busy += max(0.0, b[3] - max(b[0], end))
+        end = max(end, b[3])
+    span = max(b[3] for b in batches) - batches[0][0] if batches else 0.0
+    return [round(x, 3) for x in (span, busy, sum(b[1] - b[0] for b in batches), sum(b[2] - b[1] for b in batches),
+                                  sum(b[3] - b[2] for b in batches))] + [len(batches)]
+
+
 def server_pass(sv, lent):
     """Submits every event of the batch, waits for all results and releases them (one call
     each); returns (seconds, tracks)."""
@@ -450,7 +465,7 @@ def server_pass(sv, lent):
     if code != 0:
         raise RuntimeError("server pass: wait returned %d" % code)
     tracks = sum(r.n_tracks for r in res)
-    server_pass.gpu_span_ms = max(r.gpu_done_ms for r in res) - min(r.gpu_start_ms for r in res)
+    server_pass.device = device_breakdown(res)
     sv.release_many(tickets)
     return time.perf_counter() - t0, tracks
 
@@ -951,13 +966,13 @@ def main():
     allocs0 = sv.stats()["result_allocs"]
     gc.collect()
     gc.disable()  # a serving host does not collect garbage between a batch's submission and its results
-    gpu_spans = []
+    devices = []
     try:
         for _ in range(a.steps):
             dt, nt = server_pass(sv, lent)
             assert nt == n_tr
             e2e_s.append(dt)
-            gpu_spans.append(server_pass.gpu_span_ms)
+            devices.append(server_pass.device)
     finally:
         gc.enable()
     e2e_allocs = sv.stats()["result_allocs"] - allocs0
@@ -969,11 +984,13 @@ def main():
            "ms_per_step_p99": 1e3 * float(np.percentile(e2e_s, 99)),
            "passes_ms": [round(1e3 * x, 3) for x in e2e_s],
            "result_buffer_allocations_while_timed": e2e_allocs,
-           "gpu_span_ms": [round(x, 3) for x in gpu_spans],
+           "device_ms": devices,
            "form": "tkf_submit_events of all %d events (hit planes lent from pinned host memory), tkf_wait_all, "
                    "tkf_release_many; %d slots, batches of up to %d events; host wall clock, mean over the "
-                   "timed passes (Python garbage collection off during them); gpu_span_ms: per pass, the device "
-                   "time from the first batch's first copy to the last batch's last copy"
+                   "timed passes (Python garbage collection off during them); device_ms: per pass, the device "
+                   "span from the first batch's first copy to the last batch's last copy, the time with a batch "
+                   "in flight, the input copies, kernels and result copies summed over batches, and the "
+                   "batches"
                    % (b.n_events, a.e2e_slots, a.e2e_batch)}
 
     # ---------------- the same batched step in MIXED precision (FP64 inverse + Joseph update)

@@ -358,6 +358,7 @@ typedef struct {
     const int32_t *nhits, *hit_idx;
     int64_t t_submit_ns, t_start_ns, t_done_ns;
     float gpu_start_ms, gpu_done_ms;
+    float gpu_inputs_ms, gpu_results_ms; /* same clock: inputs copied in; kernels done (results start back) */
 } tkf_result;
 
 typedef struct {

@@ -342,6 +342,90 @@ template <class R> __device__ __forceinline__ void store_track(void *par, void *
     px[i] = chi2;
 }
 
+// Position of the k-th (0-based) set bit of m; m has more than k set bits.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int k)
+{
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const int c = __popc(m & ((1u << s) - 1u));
+        if (k >= c) {
+            k -= c;
+            m >>= s;
+            pos += s;
+        }
+    }
+    return pos;
+}
+
+// The Kalman updates of a block's candidates, packed into as few warps as they fill (mixed
+// precision).  The update is the kernel's only double-precision work, and the double-precision
+// pipe spends the same time on a warp instruction whatever its active lanes; a warp's own
+// candidates with a hit (about 13 of 32 lanes) would leave most of each instruction empty.
+// So every thread parks its state in shared memory, the block's update jobs are numbered in
+// (warp, lane) order, and job e runs on lane e % 32 of warp (e / 32 + rot) % W: 52 jobs take two
+// warps instead of four.  rot turns from step to step (and between blocks) so that the warps,
+// which sit on different sub-partitions of the SM, take turns.  Every job runs the same
+// arithmetic on the same inputs whichever thread runs it, so results do not depend on the
+// packing.  Called by every thread of the block (it holds two block barriers).
+template <class U, class R>
+__device__ __forceinline__ void pooled_update(R (&p)[6], R (&P)[21], bool job, const float4 &h, const float2 &hv,
+                                              bool disk, float *st, unsigned *bal_s, int rot)
+{
+    constexpr int T = kBuildThreads, W = kBuildThreads / 32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned bal = __ballot_sync(kFull, job);
+    if (lane == 0) bal_s[warp] = bal;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) st[k * T + tid] = p[k];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) st[(6 + k) * T + tid] = P[k];
+    if (job) {
+        st[27 * T + tid] = h.x;
+        st[28 * T + tid] = h.y;
+        st[29 * T + tid] = h.z;
+        st[30 * T + tid] = hv.x;
+        st[31 * T + tid] = hv.y;
+    }
+    __syncthreads();
+    const int e = ((warp - rot) & (W - 1)) * 32 + lane;  // the job this thread runs
+    int base = 0, o = -1;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const unsigned b = bal_s[w];
+        const int c = __popc(b);
+        if (o < 0 && e < base + c) o = w * 32 + nth_set_bit(b, e - base);
+        base += c;
+    }
+    if (o >= 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) p[k] = st[k * T + o];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) P[k] = st[(6 + k) * T + o];
+        const R hx = st[27 * T + o], hy = st[28 * T + o], hz = st[29 * T + o];
+        const R vu = st[30 * T + o], vv = st[31 * T + o];
+        U dc2 = U(0);
+        if (disk)
+            kalman_update<U, R, true>(p, P, hx, hy, hz, vu, vv, &dc2);
+        else
+            kalman_update<U, R, false>(p, P, hx, hy, hz, vu, vv, &dc2);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) st[k * T + o] = p[k];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) st[(6 + k) * T + o] = P[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[k] = st[k * T + tid];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) P[k] = st[(6 + k) * T + tid];
+}
+
+// Mixed precision packs the block's Kalman updates into full warps (pooled_update).
+#ifndef TKF_BUILD_POOL
+#define TKF_BUILD_POOL 1
+#endif
+
 // Resident blocks per SM requested from the register allocator: the all-float kernels with up
 // to 6 candidates are held to 72 registers per thread (7 blocks of 128 threads), their two-step
 // forms to 96 (5 blocks, no spills: 6 % faster than the natural 128 registers, the same results);
@@ -370,8 +454,13 @@ template <int NMAX, class R, class U, bool kTwo, bool kExactN, bool kDisk>
 __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTwo>::value)) k_build(const BuildArgs a)
 {
     constexpr int W = kBuildThreads / 32;
+    constexpr bool kPool = TKF_BUILD_POOL && sizeof(R) == 4 && sizeof(U) == 8;
     __shared__ int hist_hit[W][TKF_MAX_LAYERS][32];
     __shared__ signed char hist_par[W][TKF_MAX_LAYERS][32];
+    __shared__ float pool_st[kPool ? 32 * kBuildThreads : 1];
+    __shared__ unsigned pool_bal[W];
+    __shared__ int pool_tile;
+    int pool_step = blockIdx.x;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int N = kExactN ? NMAX : a.ncand;
@@ -383,15 +472,29 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTw
     const R kb = pick<R>(a.kb_f, a.kb), mass = pick<R>(a.mass_f, a.mass);
 
     // each warp pulls tiles of seeds_per_block seeds from the counter (no block barrier: a warp
-    // that finishes early takes the next tile at once)
+    // that finishes early takes the next tile at once).  With pooled updates the block pulls W
+    // tiles at once, one per warp, and its warps go through the layers together.
     for (;;) {
-        int tile = 0;
-        if (lane == 0) tile = atomicAdd(a.tile_counter, 1);
-        tile = __shfl_sync(kFull, tile, 0);
-        const long long t0 = (long long)tile * a.seeds_per_block;
-        if (t0 >= a.n_seeds) return;
-        const int t1 = (int)min((long long)a.n_seeds, t0 + a.seeds_per_block);
-        for (int sb = (int)t0; sb < t1; sb += spw) {
+        long long t0;
+        if (kPool) {
+            if (threadIdx.x == 0) pool_tile = atomicAdd(a.tile_counter, 1);
+            __syncthreads();
+            const long long b0 = (long long)pool_tile * W * a.seeds_per_block;
+            __syncthreads();  // every warp has read pool_tile before the next pull rewrites it
+            if (b0 >= a.n_seeds) return;
+            t0 = b0 + (long long)warp * a.seeds_per_block;
+        } else {
+            int tile = 0;
+            if (lane == 0) tile = atomicAdd(a.tile_counter, 1);
+            tile = __shfl_sync(kFull, tile, 0);
+            t0 = (long long)tile * a.seeds_per_block;
+            if (t0 >= a.n_seeds) return;
+        }
+        const int t1 = (int)min((long long)a.n_seeds, t0 + a.seeds_per_block);  // <= t0: no seed (pooled)
+        // the same number of seed groups in every warp of a pooled block
+        const int n_groups = kPool ? (a.seeds_per_block + spw - 1) / spw : (int)((t1 - t0 + spw - 1) / spw);
+        for (int it = 0; it < n_groups; ++it) {
+            const int sb = (int)t0 + it * spw;
             const int slot = sb + grp;
             bool has = lane_ok && slot < t1;
             const int seed = has ? (a.s_perm ? __ldg(&a.s_perm[slot]) : slot) : 0;
@@ -475,27 +578,35 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTw
                 for (int k = 0; k < 21; ++k) P[k] = __shfl_sync(kFull, P[k], src);
                 const R pchi2 = __shfl_sync(kFull, chi2, src);
                 alive = mine != kEmpty32;
+                int gh = -1;
+                float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+                float2 hv = make_float2(0.f, 0.f);
                 if (alive) {
                     nh = 31 - (int)(mine >> 27);
-                    const int hl = mine_h;
-                    int gh = -1;
                     // the total the ranking used (the scan's sum); FP64 keeps its own exact sum
                     chi2 = sizeof(R) == 8 ? pchi2 : R(key_chi2(mine));
-                    if (hl != kHoleId) {
-                        gh = __ldg(&a.ev_off[ev]) + hl;
+                    if (mine_h != kHoleId) {
+                        gh = __ldg(&a.ev_off[ev]) + mine_h;
                         const int pos = __ldg(&a.pos_of_hit[gh]);
-                        const float4 h = __ldg(&a.hxyzi[pos]);
-                        const float2 hv = __ldg(&a.hvar[pos]);
+                        h = __ldg(&a.hxyzi[pos]);
+                        hv = __ldg(&a.hvar[pos]);
                         // the second step, to the hit's own radius (the scan took the same step
                         // for this hit's chi2, so it succeeds here too)
                         if (kTwo) propagate<R, kPropStep>(p, P, sq(R(h.x) * R(h.x) + R(h.y) * R(h.y)), kb);
-                        U dc2 = U(0);
-                        if (disk)
-                            kalman_update<U, R, true>(p, P, R(h.x), R(h.y), R(h.z), R(hv.x), R(hv.y), &dc2);
-                        else
-                            kalman_update<U, R, false>(p, P, R(h.x), R(h.y), R(h.z), R(hv.x), R(hv.y), &dc2);
-                        if (sizeof(R) == 8) chi2 = pchi2 + R(dc2);
                     }
+                }
+                if (kPool) {
+                    pooled_update<U, R>(p, P, gh >= 0, h, hv, disk, pool_st, pool_bal, pool_step & (W - 1));
+                    ++pool_step;
+                } else if (gh >= 0) {
+                    U dc2 = U(0);
+                    if (disk)
+                        kalman_update<U, R, true>(p, P, R(h.x), R(h.y), R(h.z), R(hv.x), R(hv.y), &dc2);
+                    else
+                        kalman_update<U, R, false>(p, P, R(h.x), R(h.y), R(h.z), R(hv.x), R(hv.y), &dc2);
+                    if (sizeof(R) == 8) chi2 = pchi2 + R(dc2);
+                }
+                if (alive) {
                     if (l < a.L - 1) scatter<R>(p, P, pick<R>(a.xx0_f[l], a.xx0[l]), mass, disk);
                     hist_hit[warp][l][lane] = gh;
                     hist_par[warp][l][lane] = (signed char)parent;

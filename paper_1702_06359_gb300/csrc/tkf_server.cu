@@ -62,6 +62,7 @@ struct Done {
     int trk0 = 0;
     int64_t t_submit = 0, t_start = 0, t_done = 0;
     float gpu_start_ms = 0.f, gpu_done_ms = 0.f;  // the batch's device interval (server clock)
+    float gpu_inputs_ms = 0.f, gpu_results_ms = 0.f;  // inputs on the device; results start back
     int status = TKF_OK;
     int n = 0;
     bool done = false;
@@ -94,6 +95,7 @@ struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     cudaEvent_t t_begin = nullptr, t_end = nullptr;  // timed: the batch's first and last device work
+    cudaEvent_t t_in = nullptr, t_out = nullptr;     // timed: inputs copied; kernels done
     // host staging (pinned) for copied events, and the per-batch event offsets
     Pinned<float> hx, hy, hz, hvu, hvv;
     Pinned<int> hlayer, hraw, hoff, htoff;
@@ -143,6 +145,8 @@ void free_slot(Slot &s)
     if (s.done) cudaEventDestroy(s.done);
     if (s.t_begin) cudaEventDestroy(s.t_begin);
     if (s.t_end) cudaEventDestroy(s.t_end);
+    if (s.t_in) cudaEventDestroy(s.t_in);
+    if (s.t_out) cudaEventDestroy(s.t_out);
     for (void *p : {(void *)s.dx, (void *)s.dy, (void *)s.dz, (void *)s.dvu, (void *)s.dvv, (void *)s.dlayer,
                     (void *)s.draw, (void *)s.doff, (void *)s.dtoff, (void *)s.dseeds, (void *)s.dsev, (void *)s.dlocal})
         cudaFree(p);
@@ -160,10 +164,6 @@ void free_outbuf(tkf_server *sv, OutBuf *b)
     delete b;
 }
 
-// A result buffer for a batch of `trk` tracks (called with the lock held): a free one of the
-// batch's size class (the next power of two from 1024, at most max_batch_tracks), else a new
-// one within the pinned-memory budget opt.result_bytes, freeing idle buffers of other sizes
-// first.  nullptr when the budget is held by unreleased results (the batch waits).
 // A new pinned result buffer of `cap` tracks within the budget (nullptr if it does not fit or the
 // allocation fails).  cudaMallocHost can wait for the device, so the server makes n_slots of them
 // when it is created and allocates more only when results held by the client exceed them.
@@ -187,6 +187,12 @@ OutBuf *new_outbuf(tkf_server *sv, int cap)
     return b;
 }
 
+// A result buffer for a batch of `trk` tracks (called with the lock held): the smallest free one
+// that holds it, else a new one of the batch's size class (the next power of two from 1024, at
+// most max_batch_tracks) within the pinned-memory budget opt.result_bytes, freeing idle buffers
+// first.  A new buffer has the batch's own size, not the largest, so that a client holding the
+// results of many small batches does not exhaust the budget.  nullptr when the budget is held by
+// unreleased results (the batch waits).
 OutBuf *get_outbuf(tkf_server *sv, int trk)
 {
     int cap = 1024;
@@ -204,11 +210,6 @@ OutBuf *get_outbuf(tkf_server *sv, int trk)
         sv->free_bufs.erase(sv->free_bufs.begin() + best);
         return b;
     }
-    // a new buffer is made for the largest batch when the budget has room for it, so that it can
-    // serve any later batch: the pool then stops growing once it holds as many buffers as batches
-    // are held at once
-    const int cap_max = std::max(sv->opt.max_batch_tracks, trk);
-    if (sv->result_bytes + outbuf_bytes(sv, cap_max) <= sv->opt.result_bytes) cap = cap_max;
     const size_t bytes = outbuf_bytes(sv, cap);
     while (sv->result_bytes + bytes > sv->opt.result_bytes && !sv->free_bufs.empty()) {
         free_outbuf(sv, sv->free_bufs.back());
@@ -233,6 +234,8 @@ int init_slot(tkf_server *sv, Slot &s)
     if (!e) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     if (!e) e = cudaEventCreate(&s.t_begin);
     if (!e) e = cudaEventCreate(&s.t_end);
+    if (!e) e = cudaEventCreate(&s.t_in);
+    if (!e) e = cudaEventCreate(&s.t_out);
     if (!e) e = s.hx.alloc(H); if (!e) e = s.hy.alloc(H); if (!e) e = s.hz.alloc(H);
     if (!e) e = s.hvu.alloc(H); if (!e) e = s.hvv.alloc(H); if (!e) e = s.hlayer.alloc(H);
     if (!e) e = s.hraw.alloc(3 * T); if (!e) e = s.hoff.alloc(E + 1); if (!e) e = s.htoff.alloc(E + 1);
@@ -355,6 +358,7 @@ int launch_batch(tkf_server *sv, Slot &s, std::vector<Pending> &evs)
     s.n_tracks = trk;
     if (!e) e = cudaMemcpyAsync(s.doff, s.hoff.p, (E + 1) * 4, cudaMemcpyHostToDevice, st);
     if (!e) e = cudaMemcpyAsync(s.dtoff, s.htoff.p, (E + 1) * 4, cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaEventRecord(s.t_in, st);
     if (!e && trk) {
         k_prep_seeds<<<(trk + 255) / 256, 256, 0, st>>>(s.draw, s.dtoff, s.doff, E, trk, (int)T, s.dseeds, s.dsev);
         e = cudaGetLastError();
@@ -376,12 +380,14 @@ int launch_batch(tkf_server *sv, Slot &s, std::vector<Pending> &evs)
         k_local_hits<<<(trk + 255) / 256, 256, 0, st>>>(built.hit_idx, built.stride, s.dsev, s.doff, trk, L, (int)T,
                                                         s.dlocal);
         e = cudaGetLastError();
+        if (!e) e = cudaEventRecord(s.t_out, st);
         if (!e) e = cudaMemcpy2DAsync(o->par, hp, fitted.par, dp, trk * es, 6, cudaMemcpyDeviceToHost, st);
         if (!e) e = cudaMemcpy2DAsync(o->cov, hp, fitted.cov, dp, trk * es, 21, cudaMemcpyDeviceToHost, st);
         if (!e) e = cudaMemcpyAsync(o->chi2, fitted.chi2, trk * es, cudaMemcpyDeviceToHost, st);
         if (!e) e = cudaMemcpyAsync(o->nhits, fitted.nhits, trk * 4, cudaMemcpyDeviceToHost, st);
         if (!e) e = cudaMemcpy2DAsync(o->hit, hp, s.dlocal, T * 4, trk * 4, L, cudaMemcpyDeviceToHost, st);
     }
+    if (!e && !trk) e = cudaEventRecord(s.t_out, st);
     if (!e) e = cudaEventRecord(s.t_end, st);
     if (!e) e = cudaEventRecord(s.done, st);
     if (e) return TKF_ERR_CUDA;
@@ -394,10 +400,12 @@ int launch_batch(tkf_server *sv, Slot &s, std::vector<Pending> &evs)
 void harvest(tkf_server *sv, Slot &s)
 {
     const int64_t t_done = now_ns();
-    float g0 = 0.f, g1 = 0.f;  // the batch's device interval against the server's time zero
+    float g0 = 0.f, g1 = 0.f, gi = 0.f, go = 0.f;  // the batch's device times against the server's time zero
     if (cudaEventElapsedTime(&g0, sv->t_ref, s.t_begin) != cudaSuccess ||
-        cudaEventElapsedTime(&g1, sv->t_ref, s.t_end) != cudaSuccess)
-        g0 = g1 = -1.f;
+        cudaEventElapsedTime(&g1, sv->t_ref, s.t_end) != cudaSuccess ||
+        cudaEventElapsedTime(&gi, sv->t_ref, s.t_in) != cudaSuccess ||
+        cudaEventElapsedTime(&go, sv->t_ref, s.t_out) != cudaSuccess)
+        g0 = g1 = gi = go = -1.f;
     OutBuf *o = s.out;
     o->refs = 1;  // held by this function until the end
     for (const EvInfo &ev : s.evs) {
@@ -413,6 +421,8 @@ void harvest(tkf_server *sv, Slot &s)
         d.t_done = t_done;
         d.gpu_start_ms = g0;
         d.gpu_done_ms = g1;
+        d.gpu_inputs_ms = gi;
+        d.gpu_results_ms = go;
         d.status = TKF_OK;
         d.done = true;
         sv->stats.events_done += 1;
@@ -720,6 +730,8 @@ int tkf_poll(tkf_server *sv, uint64_t ticket, tkf_result *r, int64_t timeout_us)
     r->t_done_ns = d.t_done;
     r->gpu_start_ms = d.gpu_start_ms;
     r->gpu_done_ms = d.gpu_done_ms;
+    r->gpu_inputs_ms = d.gpu_inputs_ms;
+    r->gpu_results_ms = d.gpu_results_ms;
     return TKF_OK;
 }
 

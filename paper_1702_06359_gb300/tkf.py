@@ -84,7 +84,7 @@ class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_tracks", C.c_int32), ("stride", C.c_int32), ("par", C.c_void_p), ("cov", C.c_void_p),
                 ("chi2", C.c_void_p), ("nhits", C.c_void_p), ("hit_idx", C.c_void_p), ("t_submit_ns", C.c_int64),
                 ("t_start_ns", C.c_int64), ("t_done_ns", C.c_int64), ("gpu_start_ms", C.c_float),
-                ("gpu_done_ms", C.c_float)]
+                ("gpu_done_ms", C.c_float), ("gpu_inputs_ms", C.c_float), ("gpu_results_ms", C.c_float)]
 
 
 class ServerStats(C.Structure):
