@@ -84,10 +84,14 @@ template <> struct Lim<float> {
     // Newton steps from the straight-line start (error <= ~0.1 cm for 4 cm steps): two bring
     // it below 1e-9 cm, under the float rounding of the crossing itself
     static constexpr int newton = 2;
+    // a Newton step at most this fraction of the path: converged to the type's rounding (used by
+    // the inward propagation, which may need more steps than `newton`)
+    static constexpr float converged = 1e-6f;
 };
 template <> struct Lim<double> {
     static constexpr double series = 0.05;
     static constexpr int newton = 4;
+    static constexpr double converged = 1e-13;
 };
 
 template <class R> __host__ __device__ __forceinline__ R wrap_phi(R phi)
@@ -186,7 +190,9 @@ __host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R 
     }
     R S, C, Sd, Cd;
     // inward starts can be far from the crossing (a grazing entry, the circle intersection's
-    // rounding): more steps
+    // rounding): up to 3 newton + 2 steps, but a lane stops once a step (after the outward count
+    // and one more) moves s by less than Lim::converged of itself -- the usual start converges in
+    // those first steps
     constexpr int n_newton = kMode == kPropIn ? 3 * Lim<R>::newton + 2 : Lim<R>::newton;
 #pragma unroll
     for (int it = 0; it < n_newton; ++it) {
@@ -198,7 +204,9 @@ __host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R 
         const R c1 = cp * ca - sp * sa, s1 = sp * ca + cp * sa;
         const R g = xs * xs + ys * ys - radius * radius;
         const R dg = R(2) * (xs * c1 + ys * s1);
-        s -= g / dg;
+        const R ds = g / dg;
+        s -= ds;
+        if (kMode == kPropIn && it >= Lim<R>::newton && ab(ds) <= Lim<R>::converged * ab(s)) break;
     }
     const R a = kappa * s;
     helix_fn(a, S, C, Sd, Cd);
