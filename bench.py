@@ -1020,8 +1020,10 @@ def main():
                               "peak": None, "unit": "TFLOP/s", "frac": None,
                               "flop_per_seed_fp64": PER_SEED["n_updates"] * FLOP_UPDATE_FP64,
                               "note": "FP64 arithmetic of the updates against the measured FP64 multiply-add "
-                                      "rate (alu_peaks); ncu shows the FP64 pipe 87 % busy, most of it with the "
-                                      "float/double conversions and the division of each update"},
+                                      "rate (alu_peaks); each block's updates run packed into full warps; ncu "
+                                      "shows the FP64 pipe 77 % busy at 19 of 32 active lanes, the rest of its "
+                                      "work the update's other double operations (reciprocal, negations, "
+                                      "compares)"},
                  "precision": "mixed: FP32 propagation, window and chi2; FP64 innovation inverse and Joseph update",
                  "seeds_per_warp_tile": best_tile}
         mpipe.close()

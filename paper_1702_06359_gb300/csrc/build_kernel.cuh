@@ -368,11 +368,11 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int k)
 // which sit on different sub-partitions of the SM, take turns.  Every job runs the same
 // arithmetic on the same inputs whichever thread runs it, so results do not depend on the
 // packing.  Called by every thread of the block (it holds two block barriers).
-template <class U, class R>
+template <class U, class R, int T>
 __device__ __forceinline__ void pooled_update(R (&p)[6], R (&P)[21], bool job, const float4 &h, const float2 &hv,
                                               bool disk, float *st, unsigned *bal_s, int rot)
 {
-    constexpr int T = kBuildThreads, W = kBuildThreads / 32;
+    constexpr int W = T / 32;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned bal = __ballot_sync(kFull, job);
     if (lane == 0) bal_s[warp] = bal;
@@ -421,17 +421,26 @@ __device__ __forceinline__ void pooled_update(R (&p)[6], R (&P)[21], bool job, c
     for (int k = 0; k < 21; ++k) P[k] = st[(6 + k) * T + tid];
 }
 
-// Mixed precision packs the block's Kalman updates into full warps (pooled_update).
+// Mixed precision packs the block's Kalman updates into full warps (pooled_update), in blocks of
+// TKF_POOL_WARPS warps.
 #ifndef TKF_BUILD_POOL
 #define TKF_BUILD_POOL 1
 #endif
+#ifndef TKF_POOL_WARPS
+#define TKF_POOL_WARPS 4
+#endif
+template <class R, class U> struct BuildThreads {
+    static constexpr bool pool = TKF_BUILD_POOL && sizeof(R) == 4 && sizeof(U) == 8;
+    static constexpr int value = pool ? 32 * TKF_POOL_WARPS : kBuildThreads;
+};
 
 // Resident blocks per SM requested from the register allocator: the all-float kernels with up
 // to 6 candidates are held to 72 registers per thread (7 blocks of 128 threads), their two-step
 // forms to 96 (5 blocks, no spills: 6 % faster than the natural 128 registers, the same results);
-// the mixed-precision kernels with up to 6 candidates to 168 (3 blocks: 49.8 ms for the
-// 640-event build against 54.8 ms at their natural 230 registers and 2 blocks, the same hit
-// lists); the wider lists and the all-double kernels keep their natural register count.
+// the mixed-precision kernels with up to 6 candidates to 102 (5 blocks; a few spills): with the
+// pooled updates more resident blocks keep the double-precision pipes fed while other blocks scan
+// (640-event build 32.7 ms, against 36.0 ms at 4 blocks and 39.8 ms at 3, the same hit lists); the
+// wider lists and the all-double kernels keep their natural register count.
 #ifndef TKF_BUILD_MINBLOCKS_F32
 #define TKF_BUILD_MINBLOCKS_F32 7
 #endif
@@ -439,7 +448,7 @@ __device__ __forceinline__ void pooled_update(R (&p)[6], R (&P)[21], bool job, c
 #define TKF_BUILD2_MINBLOCKS_F32 5
 #endif
 #ifndef TKF_BUILD_MINBLOCKS_MIXED
-#define TKF_BUILD_MINBLOCKS_MIXED 3
+#define TKF_BUILD_MINBLOCKS_MIXED 5
 #endif
 template <int NMAX, class R, class U, bool kTwo> struct BuildMinBlocks {
     static constexpr int value = (sizeof(R) == 4 && sizeof(U) == 4 && NMAX <= 6)
@@ -451,13 +460,16 @@ template <int NMAX, class R, class U, bool kTwo> struct BuildMinBlocks {
 // are compile-time constants (unrolled); otherwise N = a.ncand <= NMAX at run time.
 // kDisk: the configuration has endcap disks; each layer then goes by its kind (cylinder or disk).
 template <int NMAX, class R, class U, bool kTwo, bool kExactN, bool kDisk>
-__global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTwo>::value)) k_build(const BuildArgs a)
+__global__ void __launch_bounds__((BuildThreads<R, U>::value), (BuildMinBlocks<NMAX, R, U, kTwo>::value))
+    k_build(const BuildArgs a)
 {
-    constexpr int W = kBuildThreads / 32;
-    constexpr bool kPool = TKF_BUILD_POOL && sizeof(R) == 4 && sizeof(U) == 8;
+    constexpr int kThreads = BuildThreads<R, U>::value;
+    constexpr int W = kThreads / 32;
+    constexpr bool kPool = BuildThreads<R, U>::pool;
+    static_assert((W & (W - 1)) == 0, "pooled updates rotate over a power-of-two number of warps");
     __shared__ int hist_hit[W][TKF_MAX_LAYERS][32];
     __shared__ signed char hist_par[W][TKF_MAX_LAYERS][32];
-    __shared__ float pool_st[kPool ? 32 * kBuildThreads : 1];
+    __shared__ float pool_st[kPool ? 32 * kThreads : 1];
     __shared__ unsigned pool_bal[W];
     __shared__ int pool_tile;
     int pool_step = blockIdx.x;
@@ -596,7 +608,7 @@ __global__ void __launch_bounds__(kBuildThreads, (BuildMinBlocks<NMAX, R, U, kTw
                     }
                 }
                 if (kPool) {
-                    pooled_update<U, R>(p, P, gh >= 0, h, hv, disk, pool_st, pool_bal, pool_step & (W - 1));
+                    pooled_update<U, R, kThreads>(p, P, gh >= 0, h, hv, disk, pool_st, pool_bal, pool_step & (W - 1));
                     ++pool_step;
                 } else if (gh >= 0) {
                     U dc2 = U(0);
@@ -672,9 +684,10 @@ cudaError_t launch_build_t(const BuildArgs &a, int nmax, int grid, cudaStream_t 
     default: return cudaErrorInvalidValue;
     }
 #undef TKF_K
-    if (occupancy) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, fn, kBuildThreads, 0);
+    constexpr int threads = BuildThreads<R, U>::value;
+    if (occupancy) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, fn, threads, 0);
     void *args[] = {(void *)&a};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(kBuildThreads), args, 0, s);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, 0, s);
 }
 
 }  // namespace tkf

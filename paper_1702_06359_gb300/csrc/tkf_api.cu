@@ -453,23 +453,15 @@ __device__ __forceinline__ void var_flush(int *s_var, int l, int mu, int mv)
 // with the event's bin counters in shared memory: (1) count the hits per (layer, eta bin, phi
 // bin) and reduce the largest variances per layer; (2) exclusive scan of the counts ->
 // bin_off (the event's hits keep their place [event_off[e], event_off[e+1]) in the index);
-// (3) place every hit into its bin.  k_bin_sort then orders the bins.  The same bins and
-// offsets as the multi-launch path.
-// One pass of bin arithmetic (TKF_INDEX_ONE_PASS): the counting pass keeps each hit's bin and
-// its arrival rank in the bin (the counter's old value) in key[i] = bin << 16 | rank, so the
-// placing pass reads that word instead of the hit's layer, computes no bin and takes no atomic:
-// its slot is the bin's offset plus the rank.  An event with a bin of more than 65 535 hits
-// places by shared-memory cursors instead (the bin still from key).
-#ifndef TKF_INDEX_ONE_PASS
-#define TKF_INDEX_ONE_PASS 1
-#endif
+// (3) place every hit into its bin (a shared-memory cursor per bin).  k_bin_sort then orders
+// the bins.  The same bins and offsets as the multi-launch path.
 constexpr int kEventThreads = 1024;
 constexpr int kEventWarps = kEventThreads / 32;
 constexpr int kEventUnroll = 4;
 
 __global__ void __launch_bounds__(kEventThreads)
 k_index_event(const IndexGeom g, const tkf_hits h, const int *perm, int n_bins_total, float4 *hxyzi, float2 *hvar,
-              int *bin_off, float2 *var_max, unsigned *key, int *err)
+              int *bin_off, float2 *var_max, int *err)
 {
     extern __shared__ int s_cnt[];  // [L * n_bins]: counts, then bin offsets / cursors
     __shared__ int s_var[2 * TKF_MAX_LAYERS];
@@ -503,9 +495,7 @@ k_index_event(const IndexGeom g, const tkf_hits h, const int *perm, int n_bins_t
             const bool in = i0 + tid + u * kEventThreads < h1;
             const bool ok = in && l[u] >= 0 && l[u] < g.L;
             if (ok) {
-                const int lb = l[u] * g.n_bins + hit_bin(g, l[u], x[u], y[u], z[u]);
-                const int rank = atomicAdd(&s_cnt[lb], 1);
-                if (TKF_INDEX_ONE_PASS) key[i0 + tid + u * kEventThreads] = (unsigned)lb << 16 | (unsigned)min(rank, 0xFFFF);
+                atomicAdd(&s_cnt[l[u] * g.n_bins + hit_bin(g, l[u], x[u], y[u], z[u])], 1);
                 if (l[u] != cur_l) {  // hits usually come grouped by layer: rare
                     var_flush(s_var, cur_l, mu, mv);
                     cur_l = l[u];
@@ -514,7 +504,6 @@ k_index_event(const IndexGeom g, const tkf_hits h, const int *perm, int n_bins_t
                 mu = max(mu, __float_as_int(fmaxf(vu[u], 0.f)));
                 mv = max(mv, __float_as_int(fmaxf(vv[u], 0.f)));
             } else if (in) {
-                if (TKF_INDEX_ONE_PASS) key[i0 + tid + u * kEventThreads] = 0xFFFFFFFFu;
                 atomicOr(err, kErrBadLayer);
             }
         }
@@ -529,11 +518,7 @@ k_index_event(const IndexGeom g, const tkf_hits h, const int *perm, int n_bins_t
     const int per = (nb_ev + kEventThreads - 1) / kEventThreads;
     const int c0 = min(tid * per, nb_ev), c1 = min(c0 + per, nb_ev);
     int sum = 0;
-    bool big = false;  // a bin of more than 65 535 hits: its ranks do not fit key's 16 bits
-    for (int k = c0; k < c1; ++k) {
-        sum += s_cnt[k];
-        big |= s_cnt[k] > 0xFFFF;
-    }
+    for (int k = c0; k < c1; ++k) sum += s_cnt[k];
     int incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -541,7 +526,7 @@ k_index_event(const IndexGeom g, const tkf_hits h, const int *perm, int n_bins_t
         if (lane >= o) incl += t;
     }
     if (lane == 31) s_part[w] = incl;
-    const bool any_big = __syncthreads_or(big);
+    __syncthreads();
     if (w == 0) {
         int x = lane < kEventWarps ? s_part[lane] : 0;
 #pragma unroll
@@ -565,33 +550,6 @@ k_index_event(const IndexGeom g, const tkf_hits h, const int *perm, int n_bins_t
         var_max[(size_t)e * g.L + tid] = make_float2(__int_as_float(s_var[2 * tid]), __int_as_float(s_var[2 * tid + 1]));
     __syncthreads();
     // (3) place the hits, kEventUnroll per thread and pass
-    if (TKF_INDEX_ONE_PASS) {
-        for (int i0 = h0; i0 < h1; i0 += kEventThreads * kEventUnroll) {
-            unsigned kk[kEventUnroll];
-            float x[kEventUnroll], y[kEventUnroll], z[kEventUnroll], vu[kEventUnroll], vv[kEventUnroll];
-#pragma unroll
-            for (int u = 0; u < kEventUnroll; ++u) {
-                const int i = i0 + tid + u * kEventThreads;
-                const int j = i < h1 ? i : h0;
-                kk[u] = key[j];
-                x[u] = h.x[j];
-                y[u] = h.y[j];
-                z[u] = h.z[j];
-                vu[u] = h.var_u[j];
-                vv[u] = h.var_v[j];
-            }
-#pragma unroll
-            for (int u = 0; u < kEventUnroll; ++u) {
-                const int i = i0 + tid + u * kEventThreads;
-                if (i >= h1 || kk[u] == 0xFFFFFFFFu) continue;  // past the event; a hit with a bad layer
-                const int lb = (int)(kk[u] >> 16);
-                const int pos = h0 + (any_big ? atomicAdd(&s_cnt[lb], 1) : s_cnt[lb] + (int)(kk[u] & 0xFFFFu));
-                hxyzi[pos] = make_float4(x[u], y[u], z[u], __int_as_float(i - h0));
-                hvar[pos] = make_float2(vu[u], vv[u]);
-            }
-        }
-        return;
-    }
     for (int i0 = h0; i0 < h1; i0 += kEventThreads * kEventUnroll) {
         int l[kEventUnroll];
         float x[kEventUnroll], y[kEventUnroll], z[kEventUnroll], vu[kEventUnroll], vv[kEventUnroll];
@@ -622,7 +580,6 @@ k_index_event(const IndexGeom g, const tkf_hits h, const int *perm, int n_bins_t
 // multi-launch path.
 constexpr size_t kEventStaticSmem = (size_t)kEventWarps * 4 + 2 * TKF_MAX_LAYERS * 4;
 constexpr size_t kEventMaxDynSmem = 227 * 1024 - kEventStaticSmem - 1024;
-static_assert(kEventMaxDynSmem / sizeof(int) <= 0xFFFF, "an event's bin index must fit the 16 bits k_index_event keeps");
 
 size_t index_event_smem(int n_layers, int n_bins)
 {
@@ -1286,8 +1243,7 @@ int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out,
             int *perm = idx->seg_base;  // >= n_events entries
             k_event_order<<<1, 1024, 0, s>>>(hits->event_off, hits->n_events, perm);
             k_index_event<<<(unsigned)hits->n_events, kEventThreads, ev_smem, s>>>(
-                g, *hits, perm, (int)n_bins, idx->hxyzi, idx->hvar, idx->bin_off, idx->var_max, (unsigned *)idx->keys,
-                ctx->d_err);
+                g, *hits, perm, (int)n_bins, idx->hxyzi, idx->hvar, idx->bin_off, idx->var_max, ctx->d_err);
             k_bin_sort<<<sort_blocks(n_bins), 32 * kSortWarps, 0, s>>>(g, idx->bin_off, idx->ev_off, (int)n_bins,
                                                                        idx->hxyzi, idx->hvar, idx->bin_sub,
                                                                        idx->pos_of_hit);
@@ -1709,7 +1665,7 @@ extern "C" int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits
     if (const size_t ev_smem = hits->n_events >= n_sm ? index_event_smem(L, NB) : 0) {  // one block per event
         k_event_order<<<1, 1024, 0, s>>>(hits->event_off, hits->n_events, seg_base);
         k_index_event<<<(unsigned)hits->n_events, kEventThreads, ev_smem, s>>>(
-            g, *hits, seg_base, (int)n_bins, hxyzi, hvar, out->bin_off, (float2 *)out->var_max, (unsigned *)keys, err);
+            g, *hits, seg_base, (int)n_bins, hxyzi, hvar, out->bin_off, (float2 *)out->var_max, err);
         k_bin_sort<<<sort_blocks(n_bins), 32 * kSortWarps, 0, s>>>(g, out->bin_off, out->event_off, (int)n_bins, hxyzi,
                                                                    hvar, (uint4 *)out->bin_sub, out->pos_of_hit);
         return cudaGetLastError() == cudaSuccess ? TKF_OK : TKF_ERR_CUDA;
