@@ -551,10 +551,18 @@ __global__ void __launch_bounds__((BuildThreads<R, U>::value), (BuildMinBlocks<N
                     lh[i] = 0;
                 }
                 if (ok) {
-                    if (disk)
+                    if (l == a.first && a.f_key) {
+                        // the first layer's window was scanned one lane per seed (k_first_scan)
+#pragma unroll
+                        for (int i = 0; i < NMAX; ++i) {
+                            lk[i] = __ldg(&a.f_key[(size_t)i * a.n_seeds + slot]);
+                            lh[i] = __ldg(&a.f_hit[(size_t)i * a.n_seeds + slot]);
+                        }
+                    } else if (disk) {
                         scan_window_disk<NMAX, R>(a, ev, l, p, P, chi2, nh, r, lk, lh);
-                    else
+                    } else {
                         scan_window<NMAX, R, kTwo>(a, ev, l, Rl, p, P, chi2, nh, r, lk, lh);
+                    }
                 }
 
                 // merge the segment's lists: N rounds of a segmented minimum
@@ -666,6 +674,54 @@ __global__ void __launch_bounds__((BuildThreads<R, U>::value), (BuildMinBlocks<N
     }
 }
 
+// The first building layer, one lane per seed: every seed enters it with one candidate (rank 0),
+// so in k_build five of a segment's six lanes would idle through its window scan.  Here each
+// lane propagates one seed (in k_build's processing order) to the layer and scans its window into
+// the same branch list k_build would build, stored as NMAX planes of keys and hit ids; k_build
+// then propagates again (the state is needed for the updates) and reads the list instead of
+// scanning.  The same functions on the same inputs give the same lists.
+template <int NMAX, class R, bool kTwo, bool kDisk>
+__global__ void __launch_bounds__(128) k_first_scan(const BuildArgs a)
+{
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= a.n_seeds) return;
+    const int seed = a.s_perm ? __ldg(&a.s_perm[slot]) : slot;
+    const int ev = a.s_event ? a.s_event[seed] : 0;
+    unsigned lk[NMAX];
+    int lh[NMAX];
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+        lk[i] = kEmpty32;
+        lh[i] = 0;
+    }
+    if (ev >= 0 && ev < a.n_events) {  // k_build reports a bad event id
+        R p[6], P[21];
+        const R *sp = (const R *)a.s_par, *sc_ = (const R *)a.s_cov;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) p[k] = sp[(size_t)k * a.s_stride + seed];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) P[k] = sc_[(size_t)k * a.s_stride + seed];
+        const R chi2 = ((const R *)a.s_chi2)[seed];
+        const int nh = a.s_nhits[seed];
+        const int l = a.first;
+        const R kb = pick<R>(a.kb_f, a.kb), Rl = pick<R>(a.radius_f[l], a.radius[l]);
+        const bool disk = kDisk && ((a.disk_mask >> l) & 1u);
+        const R zd = pick<R>(a.disk_z_f[l], a.disk_z[l]);
+        const bool ok = disk ? propagate_plane<R>(p, P, p[2] >= R(0) ? zd : -zd, kb) : propagate<R>(p, P, Rl, kb);
+        if (ok) {
+            if (disk)
+                scan_window_disk<NMAX, R>(a, ev, l, p, P, chi2, nh, 0, lk, lh);
+            else
+                scan_window<NMAX, R, kTwo>(a, ev, l, Rl, p, P, chi2, nh, 0, lk, lh);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NMAX; ++i) {
+        a.f_key[(size_t)i * a.n_seeds + slot] = lk[i];
+        a.f_hit[(size_t)i * a.n_seeds + slot] = lh[i];
+    }
+}
+
 #ifndef TKF_BUILD_EXACT_N
 #define TKF_BUILD_EXACT_N 1
 #endif
@@ -687,6 +743,20 @@ cudaError_t launch_build_t(const BuildArgs &a, int nmax, int grid, cudaStream_t 
     constexpr int threads = BuildThreads<R, U>::value;
     if (occupancy) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy, fn, threads, 0);
     void *args[] = {(void *)&a};
+    if (a.f_key && a.first < a.L && a.n_seeds > 0) {
+        const void *ff = nullptr;
+#define TKF_F(n) (const void *)k_first_scan<n, R, kTwo, kDisk>
+        switch (nmax) {
+        case 1: ff = TKF_F(1); break;
+        case 4: ff = TKF_F(4); break;
+        case 6: ff = TKF_F(6); break;
+        case 10: ff = TKF_F(10); break;
+        default: ff = TKF_F(16); break;
+        }
+#undef TKF_F
+        const cudaError_t e = cudaLaunchKernel(ff, dim3((a.n_seeds + 127) / 128), dim3(128), args, 0, s);
+        if (e != cudaSuccess) return e;
+    }
     return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, 0, s);
 }
 

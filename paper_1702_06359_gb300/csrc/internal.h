@@ -49,6 +49,10 @@ struct BuildArgs {
     int *a_nhits, *a_hit;
     int a_stride;
     int *n_cand_out;
+    // branch lists of the first building layer, [NMAX][n_seeds] by processing slot (written by
+    // k_first_scan before k_build; null: k_build scans that layer itself)
+    unsigned *f_key;
+    int *f_hit;
     int *tile_counter;
     int *err;
 };
@@ -90,6 +94,11 @@ int hit_index_reserve(tkf_ctx *ctx, tkf_hit_index **idx, size_t max_hits, size_t
 // events (grown on demand outside graph capture; reserved by the pipeline).
 int seed_order_reserve(tkf_ctx *ctx, size_t max_seeds, size_t max_events);
 
+// Branch lists of the first building layer (k_first_scan) for max_seeds seeds of the
+// configuration's candidate capacity (grown on demand outside graph capture; reserved by the
+// pipeline).
+int first_list_reserve(tkf_ctx *ctx, size_t max_seeds);
+
 inline int build_nmax(int n)
 {
     return n <= 1 ? 1 : n <= 4 ? 4 : n <= 6 ? 6 : n <= 10 ? 10 : 16;
@@ -108,6 +117,10 @@ struct tkf_ctx {
     int *ord_key = nullptr, *ord_perm = nullptr, *ord_counts = nullptr, *ord_off = nullptr;
     int *ord_seg_count = nullptr, *ord_seg_base = nullptr;
     size_t ord_cap_seeds = 0, ord_cap_bins = 0, ord_cap_events = 0;
+    // first-layer branch lists: key and hit id planes of first_cap entries each
+    unsigned *first_key = nullptr;
+    int *first_hit = nullptr;
+    size_t first_cap = 0;
 };
 
 struct tkf_hit_index {

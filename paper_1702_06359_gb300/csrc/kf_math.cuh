@@ -190,10 +190,11 @@ __host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R 
     }
     R S, C, Sd, Cd;
     // inward starts can be far from the crossing (a grazing entry, the circle intersection's
-    // rounding): up to 3 newton + 2 steps, but a lane stops once a step (after the outward count
-    // and one more) moves s by less than Lim::converged of itself -- the usual start converges in
-    // those first steps
+    // rounding): up to 3 newton + 2 steps.  The straight line's root of a crossing at more than
+    // about 6 degrees from the tangent is as close as the outward start, and takes the outward
+    // step count; any other start stops once a step moves s by less than Lim::converged of itself
     constexpr int n_newton = kMode == kPropIn ? 3 * Lim<R>::newton + 2 : Lim<R>::newton;
+    const bool clear = disc > R(0.01) * radius * radius;
 #pragma unroll
     for (int it = 0; it < n_newton; ++it) {
         const R a = kappa * s;
@@ -206,7 +207,7 @@ __host__ __device__ __forceinline__ bool propagate(R p[6], R P[21], R radius, R 
         const R dg = R(2) * (xs * c1 + ys * s1);
         const R ds = g / dg;
         s -= ds;
-        if (kMode == kPropIn && it >= Lim<R>::newton && ab(ds) <= Lim<R>::converged * ab(s)) break;
+        if (kMode == kPropIn && it + 1 >= Lim<R>::newton && (clear || ab(ds) <= Lim<R>::converged * ab(s))) break;
     }
     const R a = kappa * s;
     helix_fn(a, S, C, Sd, Cd);

@@ -1076,6 +1076,19 @@ int seed_order_reserve(tkf_ctx *ctx, size_t max_seeds, size_t max_events)
     return TKF_OK;
 }
 
+#ifndef TKF_BUILD_FIRST_PASS
+#define TKF_BUILD_FIRST_PASS 1
+#endif
+int first_list_reserve(tkf_ctx *ctx, size_t max_seeds)
+{
+    const size_t n = max_seeds * (size_t)build_nmax(ctx->cfg.n_cand);
+    if (n <= ctx->first_cap && ctx->first_key) return TKF_OK;
+    int st = grow(ctx, &ctx->first_key, n);
+    if (!st) st = grow(ctx, &ctx->first_hit, n);
+    ctx->first_cap = st ? 0 : n;
+    return st;
+}
+
 }  // namespace tkf
 
 // ====================================================================== C ABI
@@ -1173,7 +1186,8 @@ int tkf_destroy(tkf_ctx *ctx)
     if (!ctx) return TKF_ERR_INVALID;
     cudaFree(ctx->d_tile);
     cudaFree(ctx->d_err);
-    for (int *p : {ctx->ord_key, ctx->ord_perm, ctx->ord_counts, ctx->ord_off, ctx->ord_seg_count, ctx->ord_seg_base})
+    for (int *p : {ctx->ord_key, ctx->ord_perm, ctx->ord_counts, ctx->ord_off, ctx->ord_seg_count, ctx->ord_seg_base,
+                   (int *)ctx->first_key, ctx->first_hit})
         cudaFree(p);
     delete ctx;
     return TKF_OK;
@@ -1552,6 +1566,11 @@ int tkf_build_tracks(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_tracks *s
         a.s_perm = ctx->ord_perm;  // counts are back to zero after k_seed_place
     }
     const int nmax = build_nmax(c.n_cand);
+    if (TKF_BUILD_FIRST_PASS && c.first_build_layer < c.n_layers && seeds->n > 0) {
+        if ((st = tkf::first_list_reserve(ctx, (size_t)seeds->n))) return st;
+        a.f_key = ctx->first_key;
+        a.f_hit = ctx->first_hit;
+    }
     auto launch = a.disk_mask    ? (c.precision == TKF_FP32    ? launch_build3_fp32
                                     : c.precision == TKF_MIXED ? launch_build3_mixed
                                                                : launch_build3_fp64)

@@ -145,6 +145,7 @@ int tkf_pipeline_create(tkf_ctx *ctx, int32_t max_hits, int32_t max_events, int3
     int st = e == cudaSuccess ? TKF_OK : (e == cudaErrorMemoryAllocation ? TKF_ERR_NOMEM : TKF_ERR_CUDA);
     if (!st) st = tkf::hit_index_reserve(ctx, &p->idx, (size_t)max_hits, (size_t)max_events);  // no later allocation
     if (!st && ctx->cfg.seed_order) st = tkf::seed_order_reserve(ctx, (size_t)max_tracks, (size_t)max_events);
+    if (!st) st = tkf::first_list_reserve(ctx, (size_t)max_tracks);
     if (st) {
         tkf_pipeline_destroy(p);
         return st;
