@@ -76,32 +76,33 @@ MODULE_DR = 1.0  # cm between the inner and outer module rows of a layer (hit_dr
 # each event's tracks; python oracle/opcount.py --events 64 --forward, 69674 seeds):
 FLOP_PROPAGATE_PLANE, FLOP_WINDOW_DISK, FLOP_CHI2_DISK, FLOP_UPDATE_DISK, FLOP_SCATTER_DISK = 296, 57, 57, 359, 23
 PER_SEED_DISK = dict(n_prop=25.7421, n_hits_examined=218.2409, n_updates=26.9508, n_kept=29.2005)
-# DRAM bytes (read + write) per seed of the FP32 endcap building kernel (one ncu capture of its
-# 640-event launch: 474.0 MB for 649 624 seeds; summary in profiles/); None when it changes
-BUILD3_DRAM_BYTES_PER_SEED = 729.7
+# DRAM bytes (read + write) per seed of the FP32 endcap building (k_first_scan + k_build; one ncu
+# capture of its 640-event launches: 135.1 + 480.6 MB for 649 624 seeds; summary in profiles/);
+# None when a kernel changes
+BUILD3_DRAM_BYTES_PER_SEED = 947.7
 FLOP_PER_SEED_DISK = (PER_SEED_DISK["n_prop"] * (FLOP_PROPAGATE_PLANE + FLOP_WINDOW_DISK)
                       + PER_SEED_DISK["n_hits_examined"] * FLOP_CHI2_DISK
                       + PER_SEED_DISK["n_updates"] * FLOP_UPDATE_DISK
                       + PER_SEED_DISK["n_kept"] * 6.0 / 7.0 * FLOP_SCATTER_DISK)
-# DRAM bytes (read + write) per seed of the two-step FP32 building kernel, from one ncu capture
-# of the kernel as built now (160-event case: 404.6 MB for 701 095 seeds; summary in profiles/);
-# None whenever the kernel changes until it is captured again
-BUILD2_DRAM_BYTES_PER_SEED = 577.1
-# Warp instructions per seed of the two build kernels (ncu smsp__inst_executed.sum of the same
-# captures: 1.822 G and 4.066 G for 701 095 seeds), for the instruction-issue roofline beside the
-# FP32 one: an SM sub-partition issues at most one warp instruction per cycle, 4 per SM;
-# None whenever a kernel changes until it is captured again
-BUILD_WARP_INST_PER_SEED, BUILD2_WARP_INST_PER_SEED = 2599.2, 5798.8
+# DRAM bytes (read + write) per seed of the two-step FP32 building (k_first_scan + k_build), from
+# one ncu capture of the kernels as built now (160-event case: 130.3 + 431.0 MB for 701 095
+# seeds; summary in profiles/); None whenever a kernel changes until it is captured again
+BUILD2_DRAM_BYTES_PER_SEED = 800.5
+# Warp instructions per seed of the building kernels (ncu smsp__inst_executed.sum of the same
+# captures: 44.7 M + 1.675 G one-step, 159.9 M + 3.491 G two-step, for 701 095 seeds), for the
+# instruction-issue roofline beside the FP32 one: an SM sub-partition issues at most one warp
+# instruction per cycle, 4 per SM; None whenever a kernel changes until it is captured again
+BUILD_WARP_INST_PER_SEED, BUILD2_WARP_INST_PER_SEED = 2452.7, 5207.4
 # FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # libtkf.so kernels per step: hit index (event order, per-event count/scan/place, bin sort),
 # seed estimate with seed fit, seed ordering (key, segment totals, segment scan, bin scan,
-# place), build, final fit
-KERNELS_PER_STEP = 11
-# DRAM bytes (read + write) per seed of the FP32 building kernel, from one ncu capture of the
-# kernel as built now (160-event case: 406.3 MB for 701 095 seeds; summary in profiles/);
-# None whenever the kernel changes until it is captured again
-BUILD_DRAM_BYTES_PER_SEED = 579.6
+# place), first-layer scan, build, final fit
+KERNELS_PER_STEP = 12
+# DRAM bytes (read + write) per seed of the FP32 building (k_first_scan + k_build), from one ncu
+# capture of the kernels as built now (160-event case: 131.2 + 437.2 MB for 701 095 seeds;
+# summary in profiles/); None whenever a kernel changes until it is captured again
+BUILD_DRAM_BYTES_PER_SEED = 810.8
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 ISSUE_PEAK_WARP_INST_PER_S = SM_COUNT * 4 * SM_MAX_GHZ * 1e9
 
@@ -849,10 +850,10 @@ def main():
             "events": b2.n_events, "tracks": n2t, "hits": b2.n_hits, "efficiency": efficiency(b2, hid2),
             "own_hit_lists": float(np.mean(np.all(hid2.T == b2.trk_hits, axis=1))),
             "seeds_per_warp_tile": tile2, "autotune_build_ms": [round(x, 4) for x in t2ms],
-            "roofline": {"kernel": "k_build<6,float,float,two-step>", "bound": "alu", "achieved": ach2,
+            "roofline": {"kernel": "k_first_scan + k_build<6,float,float,two-step>", "bound": "alu", "achieved": ach2,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach2 / FP32_PEAK_TFLOPS,
                          "traffic": None if BUILD2_DRAM_BYTES_PER_SEED is None else BUILD2_DRAM_BYTES_PER_SEED * n2t,
-                         "traffic_unit": "bytes per launch (ncu DRAM read + write of the 160-event case, per seed)",
+                         "traffic_unit": "bytes per launch pair (ncu DRAM read + write of the 160-event case, per seed)",
                          "launch_ms": q_build, "flop_per_seed": FLOP_PER_SEED_TWO_STEP,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                          "issue": issue_roofline(BUILD2_WARP_INST_PER_SEED, n2t, q_build)},
@@ -913,10 +914,10 @@ def main():
             "events": b3.n_events, "tracks": n3t, "hits": b3.n_hits, "efficiency": efficiency(b3, hid3),
             "own_hit_lists": float(np.mean(own3 == L)), "seeds_per_warp_tile": tile3,
             "autotune_build_ms": [round(x, 4) for x in t3ms],
-            "roofline": {"kernel": "k_build<6,float,float,disks>", "bound": "alu", "achieved": ach3,
+            "roofline": {"kernel": "k_first_scan + k_build<6,float,float,disks>", "bound": "alu", "achieved": ach3,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach3 / FP32_PEAK_TFLOPS,
                          "traffic": BUILD3_DRAM_BYTES_PER_SEED * n3t if BUILD3_DRAM_BYTES_PER_SEED else None,
-                         "traffic_unit": "bytes per launch (ncu DRAM read + write of the 640-event endcap launch, "
+                         "traffic_unit": "bytes per launch pair (ncu DRAM read + write of the 640-event endcap launches, "
                                          "per seed)",
                          "launch_ms": d_build, "flop_per_seed": FLOP_PER_SEED_DISK,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
@@ -1016,7 +1017,7 @@ def main():
         mb_ms = statistics.mean(mb)
         m_fp64 = PER_SEED["n_updates"] * FLOP_UPDATE_FP64 * n_tr / (mb_ms / 1e3) / 1e12
         mixed = {"value": n_tr / (mms / 1e3), "unit": UNIT, "ms_per_step": mms, "build_ms": mb_ms,
-                 "roofline": {"kernel": "k_build<6,float,double>", "bound": "fp64", "achieved": m_fp64,
+                 "roofline": {"kernel": "k_first_scan + k_build<6,float,double>", "bound": "fp64", "achieved": m_fp64,
                               "peak": None, "unit": "TFLOP/s", "frac": None,
                               "flop_per_seed_fp64": PER_SEED["n_updates"] * FLOP_UPDATE_FP64,
                               "note": "FP64 arithmetic of the updates against the measured FP64 multiply-add "
@@ -1168,10 +1169,12 @@ def main():
                    "seeds_per_warp_tile": best_tile, "cuda_graph": True,
                    "l2": "inputs larger than L2 (%.0f MB of hit planes)" % (n_hits * 24 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"kernel": "k_build<6,float,float>", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": "k_first_scan + k_build<6,float,float>", "bound": "alu", "achieved": achieved,
                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                      "traffic": None if BUILD_DRAM_BYTES_PER_SEED is None else BUILD_DRAM_BYTES_PER_SEED * n_tr,
-                     "traffic_unit": "bytes per launch (ncu DRAM read + write, scaled by seeds from the 160-event case)",
+                     "traffic_unit": "bytes per launch pair (ncu DRAM read + write, scaled by seeds from the 160-event case)",
+                     "launch_note": "launch_ms: CUDA events around tkf_build_tracks inside the graph (seed ordering, "
+                                    "k_first_scan, k_build)",
                      "launch_ms": build_ms, "flop_per_seed": FLOP_PER_SEED,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                      "issue": issue_roofline(BUILD_WARP_INST_PER_SEED, n_tr, build_ms),
