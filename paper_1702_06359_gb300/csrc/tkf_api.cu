@@ -396,8 +396,13 @@ __device__ __forceinline__ void sort_bins_warp(const IndexGeom &g, int b, int b_
 }
 
 // Bin order of the whole index in one launch (used when an event's bins do not fit the
-// shared memory of the per-event kernel below): each warp takes kSortBinsPerWarp bins.
-__global__ void __launch_bounds__(32 * kSortWarps)
+// shared memory of the per-event kernel below): each warp takes kSortBinsPerWarp bins.  Held to
+// 5 blocks per SM (51 registers): 1.90 ms for the 640-event index against 2.08 ms at its natural
+// 64 registers and 4 blocks (6 blocks: 1.97 ms, with more spills), the same index.
+#ifndef TKF_SORT_MINBLOCKS
+#define TKF_SORT_MINBLOCKS 5
+#endif
+__global__ void __launch_bounds__(32 * kSortWarps, TKF_SORT_MINBLOCKS)
 k_bin_sort(const IndexGeom g, const int *bin_off, const int *ev_off, int n_bins_total, float4 *hxyzi, float2 *hvar,
            uint4 *bin_sub, int *pos_of_hit)
 {
