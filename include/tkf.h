@@ -227,7 +227,10 @@ int tkf_fit_backward(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init,
  * a branch, a candidate without any makes one hole branch, the branches of the seed are
  * ranked by (nHits desc, chi2 asc, parent rank asc, hit id asc) and the best n_cand are kept,
  * updated by the KF and given the layer's scattering noise.  One persistent launch over all
- * seeds of all events (tiles of seeds_per_block seeds pulled from an atomic counter).
+ * seeds of all events (tiles of seeds_per_block seeds pulled from an atomic counter), after a
+ * launch that scans the first building layer one lane per seed (every seed enters it with a
+ * single candidate) into branch lists held in the context (2 x 4 bytes per seed and candidate
+ * slot, allocated on first use and grown when a call has more seeds; a pipeline reserves them).
  *   out: best candidate per seed (out->stride >= seeds->n).
  *   out_all: NULL, or every final candidate: candidate r of seed s at s * n_cand + r
  *            (stride >= seeds->n * n_cand); n_cand_out (device int32 [seeds->n], may be NULL)
@@ -288,8 +291,9 @@ int tkf_pipeline_captures(const tkf_pipeline *p);
 /* The pipeline's hit index (valid after a run; owned by the pipeline). */
 const tkf_hit_index *tkf_pipeline_index(const tkf_pipeline *p);
 
-/* Milliseconds between CUDA events recorded just before and after the building kernel of the
- * last run (event-record nodes inside the graph); waits for the second event only.
+/* Milliseconds between CUDA events recorded just before and after tkf_build_tracks in the last
+ * run (the seed ordering, the first-layer scan and the building kernel; event-record nodes
+ * inside the graph); waits for the second event only.
  * Errors: TKF_ERR_INVALID (no run yet), TKF_ERR_CUDA. */
 int tkf_pipeline_build_ms(tkf_pipeline *p, float *ms);
 
@@ -424,7 +428,7 @@ typedef struct {
 /* Capacity of the fixed scratch of tkf_build_hit_index_noalloc. */
 #define TKF_NOALLOC_MAX_HITS (1 << 20)      /* hits per call */
 #define TKF_NOALLOC_MAX_BINS (1 << 18)      /* n_events * n_layers * n_eta_bins * n_phi_bins */
-#define TKF_NOALLOC_MAX_SEGMENTS 1024       /* n_events * n_layers */
+#define TKF_NOALLOC_MAX_SEGMENTS 4096       /* n_events * n_layers */
 
 /* The same hit index as tkf_build_hit_index, written into caller-owned arrays, for callers
  * that cannot allocate device memory: code running where cudaMalloc is not allowed or not

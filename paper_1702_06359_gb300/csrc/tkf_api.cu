@@ -460,7 +460,14 @@ __device__ __forceinline__ void var_flush(int *s_var, int l, int mu, int mv)
 // bin_off (the event's hits keep their place [event_off[e], event_off[e+1]) in the index);
 // (3) place every hit into its bin (a shared-memory cursor per bin).  k_bin_sort then orders
 // the bins.  The same bins and offsets as the multi-launch path.
-constexpr int kEventThreads = 1024;
+// The per-event kernels take a batch of at least TKF_INDEX_EVENTS_PER_SM events per SM; smaller
+// batches are spread over every SM by the multi-launch kernels.  Measured on the batched workload
+// (same indices): multi-launch 0.75 / 0.86 ms at 160 / 200 events against 0.91 / 0.98 ms per event,
+// per event 1.18 / 1.45 / 1.90 ms at 320 / 480 / 640 events against 1.23 / 1.85 / 2.62 ms.
+#ifndef TKF_INDEX_EVENTS_PER_SM
+#define TKF_INDEX_EVENTS_PER_SM 2
+#endif
+constexpr int kEventThreads = 1024;  // 512-thread blocks, two per SM: 2.46 ms against 1.88 ms (640 events)
 constexpr int kEventWarps = kEventThreads / 32;
 constexpr int kEventUnroll = 4;
 
@@ -1254,10 +1261,10 @@ int tkf_build_hit_index(tkf_ctx *ctx, const tkf_hits *hits, tkf_hit_index **out,
         const IndexGeom g = index_geom(c, hits->n_events);
         TKF_CUDA(ctx, cudaMemcpyAsync(idx->ev_off, hits->event_off, (hits->n_events + 1) * sizeof(int),
                                       cudaMemcpyDeviceToDevice, s));
-        // one block per event when the batch has enough events to fill the GPU and their bins fit
-        // a block's shared memory (set up by tkf_create); otherwise counts in global memory and
-        // every block on the hits of a few events
-        const size_t ev_smem = hits->n_events >= ctx->sm_count ? index_event_smem(L, NB) : 0;
+        // one block per event when the batch has enough events to fill the GPU twice and their
+        // bins fit a block's shared memory (set up by tkf_create); otherwise counts in global
+        // memory and every block on the hits of a few events
+        const size_t ev_smem = hits->n_events >= TKF_INDEX_EVENTS_PER_SM * ctx->sm_count ? index_event_smem(L, NB) : 0;
         if (ev_smem) {
             int *perm = idx->seg_base;  // >= n_events entries
             k_event_order<<<1, 1024, 0, s>>>(hits->event_off, hits->n_events, perm);
@@ -1686,7 +1693,8 @@ extern "C" int tkf_build_hit_index_noalloc(const tkf_config *cfg, const tkf_hits
     if (cudaMemcpyAsync(out->event_off, hits->event_off, (hits->n_events + 1) * sizeof(int), cudaMemcpyDeviceToDevice,
                         s) != cudaSuccess)
         return TKF_ERR_CUDA;
-    if (const size_t ev_smem = hits->n_events >= n_sm ? index_event_smem(L, NB) : 0) {  // one block per event
+    if (const size_t ev_smem = hits->n_events >= TKF_INDEX_EVENTS_PER_SM * n_sm ? index_event_smem(L, NB) : 0) {
+        // one block per event
         k_event_order<<<1, 1024, 0, s>>>(hits->event_off, hits->n_events, seg_base);
         k_index_event<<<(unsigned)hits->n_events, kEventThreads, ev_smem, s>>>(
             g, *hits, seg_base, (int)n_bins, hxyzi, hvar, out->bin_off, (float2 *)out->var_max, err);

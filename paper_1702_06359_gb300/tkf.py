@@ -19,7 +19,7 @@ MAX_LAYERS = 16
 MAX_CAND = 16
 FP32, MIXED, FP64 = 0, 1, 2
 OK, ERR_INVALID, ERR_CUDA, ERR_NOMEM, ERR_AGAIN, ERR_TIMEOUT, ERR_NOTREADY, ERR_KERNEL, ERR_TOO_LARGE = range(9)
-NOALLOC_MAX_HITS, NOALLOC_MAX_BINS, NOALLOC_MAX_SEGMENTS = 1 << 20, 1 << 18, 1024
+NOALLOC_MAX_HITS, NOALLOC_MAX_BINS, NOALLOC_MAX_SEGMENTS = 1 << 20, 1 << 18, 4096
 TRACK_NOREACH, TRACK_SINGULAR, TRACK_LOST = -1, -2, -3
 
 

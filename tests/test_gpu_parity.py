@@ -97,12 +97,12 @@ def test_hit_index_matches_oracle_bins(det):
 
 
 def test_hit_index_one_block_per_event_equals_multi_launch_index(det):
-    """A batch with more events than SMs takes the one-block-per-event kernel, a smaller one the
-    multi-launch path (global counts and scans); the index of the whole batch must equal the
-    two halves' indices laid end to end, bit for bit."""
+    """A batch with at least twice as many events as SMs takes the one-block-per-event kernel, a
+    smaller one the multi-launch path (global counts and scans); the index of the whole batch
+    must equal the two halves' indices laid end to end, bit for bit."""
     from synth import event_sizes
     sm = torch.cuda.get_device_properties(0).multi_processor_count
-    n_ev = sm + 40
+    n_ev = 2 * sm + 40
     sizes, noise = event_sizes(43, n_ev, median=120, lo=0, hi=900)
     b = generate(EventSpec(seed=43, n_events=n_ev, n_tracks=sizes, noise_frac=noise), det)
     ctx = _ctx()

@@ -34,10 +34,10 @@ def test_noalloc_rejects_inputs_beyond_its_capacity():
 @pytest.mark.parametrize("branch", ["multi_launch", "block_per_event"])
 def test_noalloc_index_equals_allocating_index_on_consecutive_calls(branch):
     """Two calls in a row against tkf_build_hit_index, bit for bit.  "multi_launch": a few
-    events on the ten-layer barrel (fewer events than SMs: the index is built by kernels that
-    spread one event over the GPU).  "block_per_event": 200 events (more than the SMs) on a
-    four-layer barrel with 8 x 8 bins (800 segments, 51 200 bins, inside the fixed capacity),
-    which takes the one-block-per-event kernels."""
+    events on the ten-layer barrel (fewer events than twice the SMs: the index is built by
+    kernels that spread one event over the GPU).  "block_per_event": 320 events (more than twice
+    the SMs) on a four-layer barrel with 8 x 8 bins (1 280 segments, 81 920 bins, inside the fixed
+    capacity), which takes the one-block-per-event kernels."""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
@@ -54,13 +54,13 @@ def test_noalloc_index_equals_allocating_index_on_consecutive_calls(branch):
         cfg = tkf.default_config(n_layers=4, radius=det.radii, x_over_x0=det.x_over_x0, n_eta_bins=8,
                                  n_phi_bins=8, eta_min=-1.6, eta_bin_w=0.4)
         rng = np.random.default_rng(53)
-        batches = [generate(EventSpec(seed=53, n_events=200, n_tracks=rng.integers(0, 400, 200).tolist(),
+        batches = [generate(EventSpec(seed=53, n_events=320, n_tracks=rng.integers(0, 400, 320).tolist(),
                                       noise_frac=0.3), det),
-                   generate(EventSpec(seed=54, n_events=200, n_tracks=rng.integers(0, 300, 200).tolist(),
+                   generate(EventSpec(seed=54, n_events=320, n_tracks=rng.integers(0, 300, 320).tolist(),
                                       noise_frac=0.5), det)]
         props = torch.cuda.get_device_properties(0)
-        assert all(b.n_events >= props.multi_processor_count for b in batches)
-        assert 200 * 4 <= tkf.NOALLOC_MAX_SEGMENTS and 200 * 4 * 64 <= tkf.NOALLOC_MAX_BINS
+        assert all(b.n_events >= 2 * props.multi_processor_count for b in batches)
+        assert 320 * 4 <= tkf.NOALLOC_MAX_SEGMENTS and 320 * 4 * 64 <= tkf.NOALLOC_MAX_BINS
     ctx = tkf.Context(cfg)
     L, NB = cfg.n_layers, cfg.n_eta_bins * cfg.n_phi_bins
 
