@@ -81,9 +81,13 @@ def test_graph_replay_equals_direct_calls():
     del n
 
 
-def test_results_do_not_depend_on_the_work_tile():
+@pytest.mark.parametrize("prec", [tkf.FP32, tkf.MIXED], ids=["fp32", "mixed"])
+def test_results_do_not_depend_on_the_work_tile(prec):
+    """The same hit lists and parameters bit for bit for every work tile.  In MIXED a block's
+    updates run packed into whichever of its warps the rotation picks, and the tile decides which
+    seeds share a block: the packing must not change any result."""
     b = _batch(63, n_events=12)
-    ctx = tkf.Context(tkf.default_config())
+    ctx = tkf.Context(tkf.default_config(precision=prec))
     L = ctx.cfg.n_layers
     dh = device_hits(b)
     sh = torch.as_tensor(np.ascontiguousarray(b.trk_hits[:, :3].T), dtype=torch.int32, device="cuda")
@@ -96,13 +100,13 @@ def test_results_do_not_depend_on_the_work_tile():
     class _T:
         def struct(self):
             return seeds
-    out = tkf.DeviceTracks.empty(b.n_tracks, L)
+    out = tkf.DeviceTracks.empty(b.n_tracks, L, prec)
     tiles = [1, 5, 10, 37, 128]
     best, ms = ctx.autotune_build(pipe.index(), _T(), out, tiles, repeats=2)
     assert best in tiles and len(ms) == len(tiles) and all(x > 0 for x in ms)
     assert ctx.config().seeds_per_block == best
     for tile in tiles:
-        c2 = tkf.Context(tkf.default_config(seeds_per_block=tile))
+        c2 = tkf.Context(tkf.default_config(seeds_per_block=tile, precision=prec))
         p2 = tkf.DevicePipeline(c2, b.n_hits, b.n_events, b.n_tracks, use_graph=True)
         p2.run(dh, sh, se, b.n_tracks)
         gb, gf = _pipe_out(p2, L, b.n_tracks)
