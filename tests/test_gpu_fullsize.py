@@ -3,8 +3,9 @@ lognormal batch (2.6 M seeds, 35 M hits) through the graph-replayed pipeline wit
 and the autotuned work tile, compared with the oracle on a seeded sample of seeds (the oracle
 builds and fits them one event at a time), plus properties checked on every seed; then the
 backward pass (tkf_fit_backward) over every fitted track, sampled against the oracle's.  The
-same for the bench's two-step case: the batch's first 160 events on modules 0.5 cm off the
-layers' cylinders (hit_dr = 0.5 cm)."""
+same for the bench's two-step case (the batch's first 160 events on modules 0.5 cm off the
+layers' cylinders, hit_dr = 0.5 cm) and its endcap case (all 640 events, each with a quarter of
+its tracks, on ten pairs of disks)."""
 import multiprocessing as mp
 import os
 
@@ -26,10 +27,10 @@ from paper_1702_06359_gb300 import tkf  # noqa: E402
 N_SAMPLE_EVENTS, SEEDS_PER_EVENT = 48, 40
 
 
-def _batch(n_events, module_dr=0.0):
+def _batch(n_events, module_dr=0.0, forward=False):
     import bench
     with mp.get_context("spawn").Pool(min(os.cpu_count() or 1, 16)) as pool:
-        return bench.workload(3, n_events, pool, module_dr=module_dr)
+        return bench.workload(3, n_events, pool, module_dr=module_dr, forward=forward)
 
 
 def test_full_batch_sampled_parity_and_properties():
@@ -40,6 +41,18 @@ def test_two_step_batch_sampled_parity_and_properties():
     _check_batch(_batch(160, module_dr=1.0), Detector(module_dr=1.0), {"hit_dr": 0.5}, 32)
 
 
+def test_endcap_batch_sampled_parity_and_properties():
+    """The bench's endcap leg: 650 k forward tracks on the disks, the oracle with the endcap
+    settings; the backward pass with covariance scale 1e2 (in FP32 a scale of 1e4 leaves too few
+    digits of the forward information on the first disks, as the endcap parity tests note)."""
+    import bench
+    from synth import FORWARD_PRIOR, forward_detector
+    det = forward_detector()
+    settings = O.Settings(eta_min=-3.0, n_eta_bins=60, prior_sigma=FORWARD_PRIOR)
+    _check_batch(_batch(640, forward=True), det, bench.forward_config(tkf, seed_order=1, seeds_per_block=5), 48,
+                 settings=settings, cov_scale=1e2, min_live=0.99)
+
+
 def test_largest_event_sampled_parity_and_properties():
     """One event at the workload's largest size: 20 000 tracks (the clip of the lognormal track
     count) with 50 % noise hits (the top of the noise range), 300 000 hits."""
@@ -48,7 +61,9 @@ def test_largest_event_sampled_parity_and_properties():
     _check_batch(b, Detector(), {}, 1, seeds_per_event=400)
 
 
-def _check_batch(b, det, cfg, n_sample_events, seeds_per_event=SEEDS_PER_EVENT):
+def _check_batch(b, det, cfg, n_sample_events, seeds_per_event=SEEDS_PER_EVENT, settings=None, cov_scale=1e4,
+                 min_live=0.999):
+    """cfg: keyword settings of the library configuration, or a whole tkf_config."""
     L = det.n_layers
     dev = torch.device("cuda", 0)
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(dev)
@@ -57,7 +72,7 @@ def _check_batch(b, det, cfg, n_sample_events, seeds_per_event=SEEDS_PER_EVENT):
                           t(b.hit_off, torch.int32))
     sh, se = t(b.trk_hits[:, :3].T, torch.int32), t(b.trk_event, torch.int32)
     n = b.n_tracks
-    ctx = tkf.Context(tkf.default_config(seed_order=1, seeds_per_block=5, **cfg))
+    ctx = tkf.Context(cfg if isinstance(cfg, tkf.Config) else tkf.default_config(seed_order=1, seeds_per_block=5, **cfg))
     pipe = tkf.DevicePipeline(ctx, b.n_hits, b.n_events, n, use_graph=True)
     for _ in range(2):  # capture, then a replay
         pipe.run(hits, sh, se, n)
@@ -79,14 +94,14 @@ def _check_batch(b, det, cfg, n_sample_events, seeds_per_event=SEEDS_PER_EVENT):
     assert ok.all(), "a hit id outside its seed's event"
     assert np.array_equal(hid[:, :3], b.trk_hits[:, :3]), "seed hits must stay on layers 0-2"
     live = bnh >= 0
-    assert live.mean() > 0.999
+    assert live.mean() > min_live
     assert np.array_equal((hid[live] >= 0).sum(1), bnh[live]), "nhits counts the built hits"
     assert np.all(chi2[live] >= 0) and np.all(cov_diag[:, live] > 0)
     layers = np.where(hid >= 0, b.layer[np.maximum(hid, 0)], -1)
     assert np.all((hid < 0) | (layers == np.arange(L)[None, :])), "hit of layer l in slot l"
 
     # sampled seeds against the oracle, one event at a time
-    g = O.make_geom(det)
+    g = O.make_geom(det, settings) if settings is not None else O.make_geom(det)
     rng = np.random.default_rng(1702)
     events = np.sort(rng.choice(b.n_events, n_sample_events, replace=False))
     n_cmp = n_div = 0
@@ -129,7 +144,7 @@ def _check_batch(b, det, cfg, n_sample_events, seeds_per_event=SEEDS_PER_EVENT):
         def struct(self):
             return self.t
     back = tkf.DeviceTracks.empty(n, L)
-    ctx.fit_backward(hits, _Raw(fitted), L - 1, 0, back, cov_scale=1e4, hit_idx=bt["hit_idx"])
+    ctx.fit_backward(hits, _Raw(fitted), L - 1, 0, back, cov_scale=cov_scale, hit_idx=bt["hit_idx"])
     ctx.sync_status()
     bk = dict(par=back.par, cov=back.cov, chi2=back.chi2, nhits=back.nhits)
     bnh2 = bk["nhits"][:n].cpu().numpy()
@@ -145,7 +160,7 @@ def _check_batch(b, det, cfg, n_sample_events, seeds_per_event=SEEDS_PER_EVENT):
         if not len(idx):
             continue
         init_cov = unpack_cov(fcov_all[:, idx].double().cpu().numpy())
-        rp, _, rc2, rn, rst = O.fit_backward(g, oh, par[idx], init_cov, rh, L - 1, 0, 1e4)
+        rp, _, rc2, rn, rst = O.fit_backward(g, oh, par[idx], init_cov, rh, L - 1, 0, cov_scale)
         assert np.all(rst == 0)
         assert np.array_equal(bnh2[idx], rn)
         assert not param_violations(bpar[idx], rp)[0].any()
