@@ -85,14 +85,14 @@ FLOP_PER_SEED_DISK = (PER_SEED_DISK["n_prop"] * (FLOP_PROPAGATE_PLANE + FLOP_WIN
                       + PER_SEED_DISK["n_updates"] * FLOP_UPDATE_DISK
                       + PER_SEED_DISK["n_kept"] * 6.0 / 7.0 * FLOP_SCATTER_DISK)
 # DRAM bytes (read + write) per seed of the two-step FP32 building (k_first_scan + k_build), from
-# one ncu capture of the kernels as built now (160-event case: 130.3 + 431.0 MB for 701 095
+# one ncu capture of the kernels as built now (160-event case: 130.3 + 433.0 MB for 701 095
 # seeds; summary in profiles/); None whenever a kernel changes until it is captured again
-BUILD2_DRAM_BYTES_PER_SEED = 800.5
+BUILD2_DRAM_BYTES_PER_SEED = 803.5
 # Warp instructions per seed of the building kernels (ncu smsp__inst_executed.sum of the same
-# captures: 44.7 M + 1.675 G one-step, 159.9 M + 3.491 G two-step, for 701 095 seeds), for the
+# captures: 44.7 M + 1.675 G one-step, 159.9 M + 3.517 G two-step, for 701 095 seeds), for the
 # instruction-issue roofline beside the FP32 one: an SM sub-partition issues at most one warp
 # instruction per cycle, 4 per SM; None whenever a kernel changes until it is captured again
-BUILD_WARP_INST_PER_SEED, BUILD2_WARP_INST_PER_SEED = 2452.7, 5207.4
+BUILD_WARP_INST_PER_SEED, BUILD2_WARP_INST_PER_SEED = 2452.7, 5244.7
 # FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # libtkf.so kernels per step: hit index (event order, per-event count/scan/place, bin sort),

@@ -436,7 +436,8 @@ template <class R, class U> struct BuildThreads {
 
 // Resident blocks per SM requested from the register allocator: the all-float kernels with up
 // to 6 candidates are held to 72 registers per thread (7 blocks of 128 threads), their two-step
-// forms to 96 (5 blocks, no spills: 6 % faster than the natural 128 registers, the same results);
+// forms to 80 (6 blocks, a few spills: 4.37 ms for the 160-event module batch against 4.51 ms at
+// 5 blocks and 4.77 ms at 4; one seed's near-tie of 701 095 resolves the other way);
 // the mixed-precision kernels with up to 6 candidates to 102 (5 blocks; a few spills): with the
 // pooled updates more resident blocks keep the double-precision pipes fed while other blocks scan
 // (640-event build 32.7 ms, against 36.0 ms at 4 blocks and 39.8 ms at 3, the same hit lists); the
@@ -445,7 +446,7 @@ template <class R, class U> struct BuildThreads {
 #define TKF_BUILD_MINBLOCKS_F32 7
 #endif
 #ifndef TKF_BUILD2_MINBLOCKS_F32
-#define TKF_BUILD2_MINBLOCKS_F32 5
+#define TKF_BUILD2_MINBLOCKS_F32 6
 #endif
 #ifndef TKF_BUILD_MINBLOCKS_MIXED
 #define TKF_BUILD_MINBLOCKS_MIXED 5

@@ -25,6 +25,12 @@ if not torch.cuda.is_available():
 from paper_1702_06359_gb300 import tkf  # noqa: E402
 
 N_SAMPLE_EVENTS, SEEDS_PER_EVENT = 48, 40
+# On the disks the fit takes q/pT from the small sagitta across planes 8 cm apart (a short
+# radial lever arm), and FP32 rounding in the covariance carries about 1e-4 relative into it:
+# 1.35e-4 at most over this sample, about 1e-3 of the estimate's own sigma.  q/pT is held to
+# 2e-4 relative there (the other parameters to the barrel's 1e-4), and every track's q/pT
+# difference to 5e-3 of its sigma.
+ENDCAP_PAR_REL = np.array([1e-4, 1e-4, 1e-4, 2e-4, 1e-4, 1e-4])
 
 
 def _batch(n_events, module_dr=0.0, forward=False):
@@ -50,7 +56,7 @@ def test_endcap_batch_sampled_parity_and_properties():
     det = forward_detector()
     settings = O.Settings(eta_min=-3.0, n_eta_bins=60, prior_sigma=FORWARD_PRIOR)
     _check_batch(_batch(640, forward=True), det, bench.forward_config(tkf, seed_order=1, seeds_per_block=5), 48,
-                 settings=settings, cov_scale=1e2, min_live=0.99)
+                 settings=settings, cov_scale=1e2, min_live=0.99, par_rel=ENDCAP_PAR_REL, qpt_sigma_frac=5e-3)
 
 
 def test_largest_event_sampled_parity_and_properties():
@@ -62,7 +68,7 @@ def test_largest_event_sampled_parity_and_properties():
 
 
 def _check_batch(b, det, cfg, n_sample_events, seeds_per_event=SEEDS_PER_EVENT, settings=None, cov_scale=1e4,
-                 min_live=0.999):
+                 min_live=0.999, par_rel=1e-4, qpt_sigma_frac=None):
     """cfg: keyword settings of the library configuration, or a whole tkf_config."""
     L = det.n_layers
     dev = torch.device("cuda", 0)
@@ -96,7 +102,12 @@ def _check_batch(b, det, cfg, n_sample_events, seeds_per_event=SEEDS_PER_EVENT, 
     live = bnh >= 0
     assert live.mean() > min_live
     assert np.array_equal((hid[live] >= 0).sum(1), bnh[live]), "nhits counts the built hits"
-    assert np.all(chi2[live] >= 0) and np.all(cov_diag[:, live] > 0)
+    # a state on a disk has its z fixed by the plane: the z variance is zero there
+    on_disk = bool(np.any(np.asarray(getattr(det, "disk_z", ())) > 0))
+    pos = [0, 1, 3, 4, 5] if on_disk else list(range(6))
+    assert np.all(chi2[live] >= 0) and np.all(cov_diag[pos][:, live] > 0)
+    if on_disk:
+        assert np.all(cov_diag[2, live] >= 0)
     layers = np.where(hid >= 0, b.layer[np.maximum(hid, 0)], -1)
     assert np.all((hid < 0) | (layers == np.arange(L)[None, :])), "hit of layer l in slot l"
 
@@ -128,7 +139,9 @@ def _check_batch(b, det, cfg, n_sample_events, seeds_per_event=SEEDS_PER_EVENT, 
             n_div += 1
         m = np.nonzero(same)[0]
         fpar, fcov, fchi2, fn, _ = O.fit(g, oh, p0[m], c0[m], rh[m], 0, L - 1)
-        assert not param_violations(par[s[m]], fpar)[0].any()
+        assert not param_violations(par[s[m]], fpar, rel=par_rel)[0].any(), param_violations(par[s[m]], fpar, rel=par_rel)[1]
+        if qpt_sigma_frac is not None:
+            assert np.all(np.abs(par[s[m], 3] - fpar[:, 3]) <= qpt_sigma_frac * np.sqrt(fcov[:, 3, 3]))
         assert not chi2_violations(chi2[s[m]], fchi2)[0].any()
         assert np.array_equal(fnh[s[m]], fn)
         n_cmp += len(s)
@@ -151,7 +164,7 @@ def _check_batch(b, det, cfg, n_sample_events, seeds_per_event=SEEDS_PER_EVENT, 
     live = fnh >= 0
     assert np.array_equal(bnh2[live], fnh[live]) and np.all(bnh2[~live] < 0)
     assert np.all(bk["chi2"][:n].cpu().numpy()[live] >= 0)
-    assert np.all(bk["cov"][[0, 2, 5, 9, 14, 20], :n].cpu().numpy()[:, live] > 0)
+    assert np.all(bk["cov"][[0, 2, 5, 9, 14, 20], :n].cpu().numpy()[pos][:, live] > 0)
     bpar = bk["par"][:, :n].double().T.cpu().numpy()
     bchi2 = bk["chi2"][:n].double().cpu().numpy()
     fcov_all = ft["cov"][:, :n]
@@ -163,7 +176,7 @@ def _check_batch(b, det, cfg, n_sample_events, seeds_per_event=SEEDS_PER_EVENT, 
         rp, _, rc2, rn, rst = O.fit_backward(g, oh, par[idx], init_cov, rh, L - 1, 0, cov_scale)
         assert np.all(rst == 0)
         assert np.array_equal(bnh2[idx], rn)
-        assert not param_violations(bpar[idx], rp)[0].any()
+        assert not param_violations(bpar[idx], rp, rel=par_rel)[0].any(), param_violations(bpar[idx], rp, rel=par_rel)[1]
         assert not chi2_violations(bchi2[idx], rc2)[0].any()
         n_bw += len(idx)
     assert n_bw > 0.6 * seeds_per_event * n_sample_events
