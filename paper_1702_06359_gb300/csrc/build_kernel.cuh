@@ -438,9 +438,10 @@ template <class R, class U> struct BuildThreads {
 // to 6 candidates are held to 72 registers per thread (7 blocks of 128 threads), their two-step
 // forms to 80 (6 blocks, a few spills: 4.37 ms for the 160-event module batch against 4.51 ms at
 // 5 blocks and 4.77 ms at 4; one seed's near-tie of 701 095 resolves the other way);
-// the mixed-precision kernels with up to 6 candidates to 102 (5 blocks; a few spills): with the
-// pooled updates more resident blocks keep the double-precision pipes fed while other blocks scan
-// (640-event build 32.7 ms, against 36.0 ms at 4 blocks and 39.8 ms at 3, the same hit lists); the
+// the mixed-precision kernels with up to 6 candidates to 85 (6 blocks, spilling; the barrel's
+// one-step kernel) or 102 (5 blocks; its two-step and endcap forms): with the pooled updates
+// more resident blocks keep the double-precision pipes fed while other blocks scan (640-event
+// build 32.0 ms at 6 blocks, 33.1 ms at 5, 36.0 ms at 4 and 39.8 ms at 3, the same hit lists); the
 // wider lists and the all-double kernels keep their natural register count.
 #ifndef TKF_BUILD_MINBLOCKS_F32
 #define TKF_BUILD_MINBLOCKS_F32 7
@@ -449,19 +450,25 @@ template <class R, class U> struct BuildThreads {
 #define TKF_BUILD2_MINBLOCKS_F32 6
 #endif
 #ifndef TKF_BUILD_MINBLOCKS_MIXED
-#define TKF_BUILD_MINBLOCKS_MIXED 5
+#define TKF_BUILD_MINBLOCKS_MIXED 6
 #endif
-template <int NMAX, class R, class U, bool kTwo> struct BuildMinBlocks {
-    static constexpr int value = (sizeof(R) == 4 && sizeof(U) == 4 && NMAX <= 6)
-                                     ? (kTwo ? TKF_BUILD2_MINBLOCKS_F32 : TKF_BUILD_MINBLOCKS_F32)
-                                     : ((sizeof(R) == 4 && sizeof(U) == 8 && NMAX <= 6) ? TKF_BUILD_MINBLOCKS_MIXED : 1);
+#ifndef TKF_BUILD2_MINBLOCKS_MIXED
+#define TKF_BUILD2_MINBLOCKS_MIXED 5
+#endif
+template <int NMAX, class R, class U, bool kTwo, bool kDisk> struct BuildMinBlocks {
+    static constexpr int value =
+        (sizeof(R) == 4 && sizeof(U) == 4 && NMAX <= 6)
+            ? (kTwo ? TKF_BUILD2_MINBLOCKS_F32 : TKF_BUILD_MINBLOCKS_F32)
+            : ((sizeof(R) == 4 && sizeof(U) == 8 && NMAX <= 6)
+                   ? (kTwo || kDisk ? TKF_BUILD2_MINBLOCKS_MIXED : TKF_BUILD_MINBLOCKS_MIXED)
+                   : 1);
 };
 
 // kExactN: the candidates kept per seed equal NMAX, so the segment width and the merge's loops
 // are compile-time constants (unrolled); otherwise N = a.ncand <= NMAX at run time.
 // kDisk: the configuration has endcap disks; each layer then goes by its kind (cylinder or disk).
 template <int NMAX, class R, class U, bool kTwo, bool kExactN, bool kDisk>
-__global__ void __launch_bounds__((BuildThreads<R, U>::value), (BuildMinBlocks<NMAX, R, U, kTwo>::value))
+__global__ void __launch_bounds__((BuildThreads<R, U>::value), (BuildMinBlocks<NMAX, R, U, kTwo, kDisk>::value))
     k_build(const BuildArgs a)
 {
     constexpr int kThreads = BuildThreads<R, U>::value;
