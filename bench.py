@@ -956,10 +956,11 @@ def main():
 
     # ---------------- end to end through the public serving API (host buffers lent to tkf_server)
     lent = LentEvents(tkf, b, host, L)
-    # pinned result memory for two passes' worth of batches: after the warm-up passes every batch
-    # finds a free result buffer and nothing is allocated or freed while timing
+    # pinned result memory for about 25 full-size batches (a pass holds the results of all its 10-16
+    # batches until it waits for them): after the warm-up passes every batch finds a free result
+    # buffer and nothing is allocated or freed while timing
     e2e_opts = dict(n_slots=a.e2e_slots, max_batch_events=a.e2e_batch, max_batch_hits=1 << 24,
-                    max_batch_tracks=1 << 20, result_bytes=2 << 30)
+                    max_batch_tracks=1 << 20, result_bytes=4 << 30)
     sv = tkf.Server(ctx.cfg, **e2e_opts)
     for _ in range(max(1, a.warmup)):
         server_pass(sv, lent)

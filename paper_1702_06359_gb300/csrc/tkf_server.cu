@@ -188,11 +188,12 @@ OutBuf *new_outbuf(tkf_server *sv, int cap)
 }
 
 // A result buffer for a batch of `trk` tracks (called with the lock held): the smallest free one
-// that holds it, else a new one of the batch's size class (the next power of two from 1024, at
-// most max_batch_tracks) within the pinned-memory budget opt.result_bytes, freeing idle buffers
-// first.  A new buffer has the batch's own size, not the largest, so that a client holding the
-// results of many small batches does not exhaust the budget.  nullptr when the budget is held by
-// unreleased results (the batch waits).
+// that holds it, else a new one within the pinned-memory budget opt.result_bytes: of the largest
+// batch (max_batch_tracks) while the budget has room for it, so that it can serve any later
+// batch and the pool stops growing (no cudaMallocHost on the serving path once it holds as many
+// buffers as batches are held at once), else of the batch's size class (the next power of two
+// from 1024), freeing idle buffers first -- a client holding the results of many small batches
+// then still fits.  nullptr when the budget is held by unreleased results (the batch waits).
 OutBuf *get_outbuf(tkf_server *sv, int trk)
 {
     int cap = 1024;
@@ -210,6 +211,8 @@ OutBuf *get_outbuf(tkf_server *sv, int trk)
         sv->free_bufs.erase(sv->free_bufs.begin() + best);
         return b;
     }
+    const int cap_max = std::max(sv->opt.max_batch_tracks, trk);
+    if (sv->result_bytes + outbuf_bytes(sv, cap_max) <= sv->opt.result_bytes) cap = cap_max;
     const size_t bytes = outbuf_bytes(sv, cap);
     while (sv->result_bytes + bytes > sv->opt.result_bytes && !sv->free_bufs.empty()) {
         free_outbuf(sv, sv->free_bufs.back());
