@@ -3,9 +3,9 @@ lognormal batch (2.6 M seeds, 35 M hits) through the graph-replayed pipeline wit
 and the autotuned work tile, compared with the oracle on a seeded sample of seeds (the oracle
 builds and fits them one event at a time), plus properties checked on every seed; then the
 backward pass (tkf_fit_backward) over every fitted track, sampled against the oracle's.  The
-same for the bench's two-step case (the batch's first 160 events on modules 0.5 cm off the
-layers' cylinders, hit_dr = 0.5 cm) and its endcap case (all 640 events, each with a quarter of
-its tracks, on ten pairs of disks)."""
+same in MIXED precision, and for the bench's two-step case (the batch's first 160 events on
+modules 0.5 cm off the layers' cylinders, hit_dr = 0.5 cm) and its endcap case (all 640 events,
+each with a quarter of its tracks, on ten pairs of disks)."""
 import multiprocessing as mp
 import os
 
@@ -41,6 +41,12 @@ def _batch(n_events, module_dr=0.0, forward=False):
 
 def test_full_batch_sampled_parity_and_properties():
     _check_batch(_batch(640), Detector(), {}, N_SAMPLE_EVENTS)
+
+
+def test_full_batch_mixed_precision_sampled_parity_and_properties():
+    """The bench's MIXED leg: the same batch and launch configuration with the FP64 innovation
+    inverse and Joseph update (the block's updates packed into full warps)."""
+    _check_batch(_batch(640), Detector(), {"precision": tkf.MIXED}, 24)
 
 
 def test_two_step_batch_sampled_parity_and_properties():
