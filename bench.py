@@ -77,22 +77,22 @@ MODULE_DR = 1.0  # cm between the inner and outer module rows of a layer (hit_dr
 FLOP_PROPAGATE_PLANE, FLOP_WINDOW_DISK, FLOP_CHI2_DISK, FLOP_UPDATE_DISK, FLOP_SCATTER_DISK = 296, 57, 57, 359, 23
 PER_SEED_DISK = dict(n_prop=25.7421, n_hits_examined=218.2409, n_updates=26.9508, n_kept=29.2005)
 # DRAM bytes (read + write) per seed of the FP32 endcap building (k_first_scan + k_build; one ncu
-# capture of its 640-event launches: 135.1 + 480.6 MB for 649 624 seeds; summary in profiles/);
+# capture of its 640-event launches: 130.8 + 480.2 MB for 649 624 seeds; summary in profiles/);
 # None when a kernel changes
-BUILD3_DRAM_BYTES_PER_SEED = 947.7
+BUILD3_DRAM_BYTES_PER_SEED = 940.6
 FLOP_PER_SEED_DISK = (PER_SEED_DISK["n_prop"] * (FLOP_PROPAGATE_PLANE + FLOP_WINDOW_DISK)
                       + PER_SEED_DISK["n_hits_examined"] * FLOP_CHI2_DISK
                       + PER_SEED_DISK["n_updates"] * FLOP_UPDATE_DISK
                       + PER_SEED_DISK["n_kept"] * 6.0 / 7.0 * FLOP_SCATTER_DISK)
 # DRAM bytes (read + write) per seed of the two-step FP32 building (k_first_scan + k_build), from
-# one ncu capture of the kernels as built now (160-event case: 130.3 + 433.0 MB for 701 095
+# one ncu capture of the kernels as built now (160-event case: 124.2 + 434.8 MB for 701 095
 # seeds; summary in profiles/); None whenever a kernel changes until it is captured again
-BUILD2_DRAM_BYTES_PER_SEED = 803.5
+BUILD2_DRAM_BYTES_PER_SEED = 797.3
 # Warp instructions per seed of the building kernels (ncu smsp__inst_executed.sum of the same
-# captures: 44.7 M + 1.675 G one-step, 159.9 M + 3.517 G two-step, for 701 095 seeds), for the
+# captures: 47.3 M + 1.675 G one-step, 170.9 M + 3.516 G two-step, for 701 095 seeds), for the
 # instruction-issue roofline beside the FP32 one: an SM sub-partition issues at most one warp
 # instruction per cycle, 4 per SM; None whenever a kernel changes until it is captured again
-BUILD_WARP_INST_PER_SEED, BUILD2_WARP_INST_PER_SEED = 2452.7, 5244.7
+BUILD_WARP_INST_PER_SEED, BUILD2_WARP_INST_PER_SEED = 2455.9, 5259.1
 # FP32 FMA peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # libtkf.so kernels per step: hit index (event order, per-event count/scan/place, bin sort),
@@ -100,9 +100,9 @@ SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 # place), first-layer scan, build, final fit
 KERNELS_PER_STEP = 12
 # DRAM bytes (read + write) per seed of the FP32 building (k_first_scan + k_build), from one ncu
-# capture of the kernels as built now (160-event case: 131.2 + 437.2 MB for 701 095 seeds;
+# capture of the kernels as built now (160-event case: 124.1 + 433.3 MB for 701 095 seeds;
 # summary in profiles/); None whenever a kernel changes until it is captured again
-BUILD_DRAM_BYTES_PER_SEED = 810.8
+BUILD_DRAM_BYTES_PER_SEED = 795.1
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 ISSUE_PEAK_WARP_INST_PER_S = SM_COUNT * 4 * SM_MAX_GHZ * 1e9
 

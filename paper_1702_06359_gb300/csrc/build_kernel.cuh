@@ -563,8 +563,8 @@ __global__ void __launch_bounds__((BuildThreads<R, U>::value), (BuildMinBlocks<N
                         // the first layer's window was scanned one lane per seed (k_first_scan)
 #pragma unroll
                         for (int i = 0; i < NMAX; ++i) {
-                            lk[i] = __ldg(&a.f_key[(size_t)i * a.n_seeds + slot]);
-                            lh[i] = __ldg(&a.f_hit[(size_t)i * a.n_seeds + slot]);
+                            lk[i] = __ldg(&a.f_key[(size_t)i * a.n_seeds + seed]);
+                            lh[i] = __ldg(&a.f_hit[(size_t)i * a.n_seeds + seed]);
                         }
                     } else if (disk) {
                         scan_window_disk<NMAX, R>(a, ev, l, p, P, chi2, nh, r, lk, lh);
@@ -684,16 +684,18 @@ __global__ void __launch_bounds__((BuildThreads<R, U>::value), (BuildMinBlocks<N
 
 // The first building layer, one lane per seed: every seed enters it with one candidate (rank 0),
 // so in k_build five of a segment's six lanes would idle through its window scan.  Here each
-// lane propagates one seed (in k_build's processing order) to the layer and scans its window into
-// the same branch list k_build would build, stored as NMAX planes of keys and hit ids; k_build
-// then propagates again (the state is needed for the updates) and reads the list instead of
-// scanning.  The same functions on the same inputs give the same lists.
+// lane propagates one seed to the layer and scans its window into the same branch list k_build
+// would build, stored as NMAX planes of keys and hit ids indexed by seed; k_build then propagates
+// again (the state is needed for the updates) and reads the list instead of scanning.  The same
+// functions on the same inputs give the same lists.  Seeds are taken in their input order, not
+// k_build's processing order: their states are then read coalesced (in the processing order,
+// 29 scattered words per seed left this kernel waiting on memory), and an event's seeds still
+// come together, so its hits stay in L2.
 template <int NMAX, class R, bool kTwo, bool kDisk>
 __global__ void __launch_bounds__(128) k_first_scan(const BuildArgs a)
 {
-    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= a.n_seeds) return;
-    const int seed = a.s_perm ? __ldg(&a.s_perm[slot]) : slot;
+    const int seed = blockIdx.x * blockDim.x + threadIdx.x;
+    if (seed >= a.n_seeds) return;
     const int ev = a.s_event ? a.s_event[seed] : 0;
     unsigned lk[NMAX];
     int lh[NMAX];
@@ -725,8 +727,8 @@ __global__ void __launch_bounds__(128) k_first_scan(const BuildArgs a)
     }
 #pragma unroll
     for (int i = 0; i < NMAX; ++i) {
-        a.f_key[(size_t)i * a.n_seeds + slot] = lk[i];
-        a.f_hit[(size_t)i * a.n_seeds + slot] = lh[i];
+        a.f_key[(size_t)i * a.n_seeds + seed] = lk[i];
+        a.f_hit[(size_t)i * a.n_seeds + seed] = lh[i];
     }
 }
 

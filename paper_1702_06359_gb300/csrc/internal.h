@@ -49,8 +49,8 @@ struct BuildArgs {
     int *a_nhits, *a_hit;
     int a_stride;
     int *n_cand_out;
-    // branch lists of the first building layer, [NMAX][n_seeds] by processing slot (written by
-    // k_first_scan before k_build; null: k_build scans that layer itself)
+    // branch lists of the first building layer, [NMAX][n_seeds] by seed (written by k_first_scan
+    // before k_build; null: k_build scans that layer itself)
     unsigned *f_key;
     int *f_hit;
     int *tile_counter;
