@@ -119,6 +119,12 @@ def lib():
         L.orc_hit_index.argtypes = [C.POINTER(Geom), C.c_int, vp, ip, ip, ip]
         L.orc_build_batch.argtypes = [C.POINTER(Geom), C.POINTER(Event), C.c_int, dp, dp, dp, ip, ip, C.c_int,
                                       ip, dp, dp, dp, ip, ip, ip, C.POINTER(Stats)]
+        L.orc_seed_kappa_max.argtypes = [C.POINTER(Geom), C.POINTER(SeedCuts)]
+        L.orc_seed_kappa_max.restype = C.c_double
+        L.orc_seed_eval.argtypes = [C.POINTER(Geom), C.POINTER(SeedCuts), C.POINTER(Hit), C.POINTER(Hit),
+                                    C.POINTER(Hit), C.POINTER(Hit), C.POINTER(SeedQuant)]
+        L.orc_find_seeds.argtypes = [C.POINTER(Geom), C.POINTER(SeedCuts), C.c_int, vp, vp]
+        L.orc_find_seeds_of.argtypes = [C.POINTER(Geom), C.POINTER(SeedCuts), C.c_int, vp, C.c_int, ip, vp]
         _lib = L
     return _lib
 
@@ -252,6 +258,58 @@ def fit_backward(g: Geom, hits: np.ndarray, par, cov, hit_ids, last, first, cov_
     lib().orc_fit_backward_batch(C.byref(g), hits.ctypes.data, n, _d(par), _d(cov), float(cov_scale), _i(hit_ids),
                                  int(last), int(first), _d(po), _d(co), _d(c2), _i(nh), _i(status))
     return po, co.reshape(n, 6, 6), c2, nh, status
+
+
+class SeedCuts(C.Structure):
+    """Cuts of the seeding from hit triplets (orc_seed_cuts); defaults: pT >= 0.5 GeV with 15 %
+    curvature slack, |z_vertex| <= 4 cm, |d0| <= 0.8 mm, |dz| <= 0.8 mm, confirmation within 1 mm."""
+
+    _fields_ = [("pt_min", C.c_double), ("kappa_slack", C.c_double), ("z_vertex", C.c_double),
+                ("d0_max", C.c_double), ("dz_max", C.c_double), ("conf_rphi", C.c_double), ("conf_z", C.c_double),
+                ("confirm", C.c_int)]
+
+    def __init__(self, pt_min=0.5, kappa_slack=0.15, z_vertex=4.0, d0_max=0.08, dz_max=0.08, conf_rphi=0.1,
+                 conf_z=0.1, confirm=1):
+        super().__init__(pt_min, kappa_slack, z_vertex, d0_max, dz_max, conf_rphi, conf_z, confirm)
+
+
+class SeedQuant(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("chord01", "kappa01", "zv", "chord12", "kappa", "d0", "dz", "chord23",
+                                          "f3", "dz3")] + [("collinear", C.c_int)]
+
+
+SEED_PICK_DTYPE = np.dtype([("h1", "i4"), ("h2", "i4"), ("h3", "i4"), ("n_pass", "i4"), ("score", "f8"),
+                            ("margin", "f8"), ("gap", "f8")], align=True)
+
+
+def seed_kappa_max(g: Geom, cuts: SeedCuts) -> float:
+    return lib().orc_seed_kappa_max(C.byref(g), C.byref(cuts))
+
+
+def seed_eval(g: Geom, cuts: SeedCuts, a: Hit, b: Hit, c: Hit | None = None, e: Hit | None = None):
+    """Quantities of one pair / triplet / confirmed triplet: (passes, SeedQuant)."""
+    q = SeedQuant()
+    ref = lambda h: C.byref(h) if h is not None else None
+    ok = lib().orc_seed_eval(C.byref(g), C.byref(cuts), C.byref(a), C.byref(b), ref(c), ref(e), C.byref(q))
+    return bool(ok), q
+
+
+def find_seeds(g: Geom, cuts: SeedCuts, hits: np.ndarray, first=None) -> np.ndarray:
+    """Best triplet of every first-layer hit of one event (brute force over all hits): a
+    SEED_PICK_DTYPE record per hit (h1 = -1: none, or not a first-layer hit), or per entry of
+    `first` (event-local ids of first-layer hits) when given."""
+    hits = np.ascontiguousarray(hits)
+    n = len(hits)
+    if first is None:
+        out = np.zeros(n, dtype=SEED_PICK_DTYPE)
+        st = lib().orc_find_seeds(C.byref(g), C.byref(cuts), n, hits.ctypes.data, out.ctypes.data)
+    else:
+        first = np.ascontiguousarray(first, dtype=np.int32)
+        out = np.zeros(len(first), dtype=SEED_PICK_DTYPE)
+        st = lib().orc_find_seeds_of(C.byref(g), C.byref(cuts), n, hits.ctypes.data, len(first), _i(first),
+                                     out.ctypes.data)
+    assert st == 0, st
+    return out
 
 
 @dataclass

@@ -925,3 +925,225 @@ int orc_build_batch(const orc_geom *g, const orc_event *ev, int n, const double 
     }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------ seeding from hit triplets */
+/*
+ * Sec. 2 names seeding as the first stage (the initial estimate from a few hits of the innermost
+ * layers) and leaves it unspecified.  Reading used here, written out as a definition and
+ * evaluated by brute force over every hit of layers 1, 2 and 3 of the event:
+ *   - a seed is a triplet (a, b, c) of hits on layers 0, 1, 2, compatible with a helix that
+ *     leaves the beam line (x = y = 0) with transverse momentum >= pt_min, confirmed by a hit e
+ *     on layer 3; r below is a hit's transverse radius, R_l the layer radius;
+ *   - pair (a, b): transverse chord |b - a| <= 2 (R_1 - R_0) (a track moving outwards, not the
+ *     far crossing of a looping circle); the circle through the beam line point, a and b has
+ *     |curvature| <= kappa_max; the r-z line through a and b meets r = 0 within |z| <= z_vertex;
+ *   - triplet: chord |c - b| <= 2 (R_2 - R_1); the circle through a, b, c (not collinear) has
+ *     curvature <= kappa_max and passes the beam line point at d0 = (|U|^2 - rho^2) / (2 rho)
+ *     (U its centre, rho its radius: the point's power divided by the diameter, its signed
+ *     distance from the circle to first order), |d0| <= d0_max; the third hit's z lies within
+ *     dz_max of the r-z line through a and b, taken at r_c;
+ *   - confirmation: a hit e on layer 3 with chord |e - c| <= 2 (R_3 - R_2), signed distance
+ *     f = (|e - U|^2 - rho^2) / (2 rho) from the triplet circle with |f| <= conf_rphi, and z
+ *     within conf_z of the r-z line through b and c, taken at r_e;
+ *   - score s = (d0 / d0_max)^2 + (dz / dz_max)^2 + min over confirming e of
+ *     (f / conf_rphi)^2 + (dz3 / conf_z)^2; each first-layer hit keeps its passing triplet of
+ *     smallest score (equal scores: smallest layer-1 id, then layer-2 id), so a hit starts at
+ *     most one seed.
+ */
+double orc_seed_kappa_max(const orc_geom *g, const orc_seed_cuts *c)
+{
+    return ORC_KB * g->bz / c->pt_min * (1.0 + c->kappa_slack);
+}
+
+static double seed_rt(const orc_hit *h) { return sqrt(h->x * h->x + h->y * h->y); }
+
+static double seed_chord(const orc_hit *a, const orc_hit *b)
+{
+    return sqrt((b->x - a->x) * (b->x - a->x) + (b->y - a->y) * (b->y - a->y));
+}
+
+/* circumscribed circle of three points (centre where the perpendicular bisectors meet); 0 when
+ * the points are collinear */
+static int circumcircle(double ax, double ay, double bx, double by, double cx, double cy, double *ux, double *uy,
+                        double *rho)
+{
+    const double d = 2.0 * (ax * (by - cy) + bx * (cy - ay) + cx * (ay - by));
+    if (d == 0.0) return 0;
+    const double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by, c2 = cx * cx + cy * cy;
+    *ux = (a2 * (by - cy) + b2 * (cy - ay) + c2 * (ay - by)) / d;
+    *uy = (a2 * (cx - bx) + b2 * (ax - cx) + c2 * (bx - ax)) / d;
+    *rho = sqrt((ax - *ux) * (ax - *ux) + (ay - *uy) * (ay - *uy));
+    return 1;
+}
+
+/* pair stage; returns 1 if it passes */
+static int seed_pair(const orc_geom *g, const orc_seed_cuts *c, const orc_hit *a, const orc_hit *b, orc_seed_quant *q)
+{
+    const double ra = seed_rt(a), rb = seed_rt(b);
+    double ux, uy, rho;
+    q->chord01 = seed_chord(a, b);
+    q->kappa01 = 0.0;  /* a, b and the beam line point on one straight line */
+    if (circumcircle(0.0, 0.0, a->x, a->y, b->x, b->y, &ux, &uy, &rho))
+        q->kappa01 = (a->x * b->y - a->y * b->x > 0.0 ? 1.0 : -1.0) / rho;
+    if (rb == ra) return 0;
+    q->zv = a->z - ra * (b->z - a->z) / (rb - ra);
+    return q->chord01 <= 2.0 * (g->radius[1] - g->radius[0]) && fabs(q->kappa01) <= orc_seed_kappa_max(g, c) &&
+           fabs(q->zv) <= c->z_vertex;
+}
+
+/* triplet stage (the pair passed); circle centre and radius returned for the confirmation */
+static int seed_triplet(const orc_geom *g, const orc_seed_cuts *c, const orc_hit *a, const orc_hit *b,
+                        const orc_hit *cc, orc_seed_quant *q, double *ux, double *uy, double *rho)
+{
+    const double ra = seed_rt(a), rb = seed_rt(b), rc = seed_rt(cc);
+    q->chord12 = seed_chord(b, cc);
+    if (!circumcircle(a->x, a->y, b->x, b->y, cc->x, cc->y, ux, uy, rho)) {
+        q->collinear = 1;
+        return 0;
+    }
+    q->kappa = 1.0 / *rho;
+    q->d0 = (*ux * *ux + *uy * *uy - *rho * *rho) / (2.0 * *rho);
+    q->dz = cc->z - (a->z + (b->z - a->z) * (rc - ra) / (rb - ra));
+    return q->chord12 <= 2.0 * (g->radius[2] - g->radius[1]) && q->kappa <= orc_seed_kappa_max(g, c) &&
+           fabs(q->d0) <= c->d0_max && fabs(q->dz) <= c->dz_max;
+}
+
+/* confirmation stage */
+static int seed_confirm(const orc_geom *g, const orc_seed_cuts *c, const orc_hit *b, const orc_hit *cc,
+                        const orc_hit *e, double ux, double uy, double rho, orc_seed_quant *q)
+{
+    const double rb = seed_rt(b), rc = seed_rt(cc), re = seed_rt(e);
+    q->chord23 = seed_chord(cc, e);
+    q->f3 = ((e->x - ux) * (e->x - ux) + (e->y - uy) * (e->y - uy) - rho * rho) / (2.0 * rho);
+    if (rc == rb) {
+        q->dz3 = 1e30;
+        return 0;
+    }
+    q->dz3 = e->z - (b->z + (cc->z - b->z) * (re - rb) / (rc - rb));
+    return q->chord23 <= 2.0 * (g->radius[3] - g->radius[2]) && fabs(q->f3) <= c->conf_rphi &&
+           fabs(q->dz3) <= c->conf_z;
+}
+
+int orc_seed_eval(const orc_geom *g, const orc_seed_cuts *c, const orc_hit *a, const orc_hit *b, const orc_hit *cc,
+                  const orc_hit *e, orc_seed_quant *q)
+{
+    memset(q, 0, sizeof *q);
+    int ok = seed_pair(g, c, a, b, q);
+    if (!cc) return ok;
+    double ux = 0.0, uy = 0.0, rho = 0.0;
+    ok = seed_triplet(g, c, a, b, cc, q, &ux, &uy, &rho) && ok;
+    if (!e || q->collinear) return ok;
+    return seed_confirm(g, c, b, cc, e, ux, uy, rho, q) && ok;
+}
+
+/* |x| / cut for each quantity of one stage; folds the stage's decision into *margin: every
+ * quantity of a passing stage, the single failing quantity of a stage that fails on one */
+static void fold_margin(const double *ratio, int n, double *margin)
+{
+    int fails = 0, k_fail = -1;
+    double m = 1e30;
+    for (int k = 0; k < n; ++k) {
+        if (ratio[k] > 1.0) {
+            ++fails;
+            k_fail = k;
+        }
+        const double d = fabs(ratio[k] - 1.0);
+        if (d < m) m = d;
+    }
+    if (fails == 0 && m < *margin) *margin = m;
+    if (fails == 1 && fabs(ratio[k_fail] - 1.0) < *margin) *margin = fabs(ratio[k_fail] - 1.0);
+}
+
+static void seed_of(const orc_geom *g, const orc_seed_cuts *c, int n, const orc_hit *hits, int ia, orc_seed_pick *p)
+{
+    const double kmax = orc_seed_kappa_max(g, c);
+    const double lim01 = 2.0 * (g->radius[1] - g->radius[0]), lim12 = 2.0 * (g->radius[2] - g->radius[1]);
+    const double lim23 = 2.0 * (g->radius[3] - g->radius[2]);
+    double best = 1e300, second = 1e300;
+    p->h1 = p->h2 = p->h3 = -1;
+    p->n_pass = 0;
+    p->score = 0.0;
+    p->margin = 1e30;
+    const orc_hit *a = &hits[ia];
+    for (int ib = 0; ib < n; ++ib) {
+        if (hits[ib].layer != 1) continue;
+        orc_seed_quant q;
+        memset(&q, 0, sizeof q);
+        const int pair_ok = seed_pair(g, c, a, &hits[ib], &q);
+        if (seed_rt(&hits[ib]) == seed_rt(a)) continue;
+        const double r01[3] = {q.chord01 / lim01, fabs(q.kappa01) / kmax, fabs(q.zv) / c->z_vertex};
+        fold_margin(r01, 3, &p->margin);
+        if (!pair_ok) continue;
+        for (int ic = 0; ic < n; ++ic) {
+            if (hits[ic].layer != 2) continue;
+            double ux, uy, rho;
+            const int trip_ok = seed_triplet(g, c, a, &hits[ib], &hits[ic], &q, &ux, &uy, &rho);
+            if (q.collinear) {
+                q.collinear = 0;
+                continue;
+            }
+            const double r12[4] = {q.chord12 / lim12, q.kappa / kmax, fabs(q.d0) / c->d0_max, fabs(q.dz) / c->dz_max};
+            fold_margin(r12, 4, &p->margin);
+            if (!trip_ok) continue;
+            double c3 = 0.0;
+            int h3 = -1;
+            if (c->confirm) {
+                c3 = 1e300;
+                for (int ie = 0; ie < n; ++ie) {
+                    if (hits[ie].layer != 3) continue;
+                    const int conf_ok = seed_confirm(g, c, &hits[ib], &hits[ic], &hits[ie], ux, uy, rho, &q);
+                    const double r23[3] = {q.chord23 / lim23, fabs(q.f3) / c->conf_rphi, fabs(q.dz3) / c->conf_z};
+                    fold_margin(r23, 3, &p->margin);
+                    if (!conf_ok) continue;
+                    const double v = (q.f3 / c->conf_rphi) * (q.f3 / c->conf_rphi) + (q.dz3 / c->conf_z) * (q.dz3 / c->conf_z);
+                    if (v < c3) {
+                        c3 = v;
+                        h3 = ie;
+                    }
+                }
+                if (h3 < 0) continue;
+            }
+            const double s = (q.d0 / c->d0_max) * (q.d0 / c->d0_max) + (q.dz / c->dz_max) * (q.dz / c->dz_max) + c3;
+            ++p->n_pass;
+            /* hits are visited in increasing id order, so a strict comparison keeps the smallest
+               ids among equal scores */
+            if (s < best) {
+                second = best;
+                best = s;
+                p->h1 = ib;
+                p->h2 = ic;
+                p->h3 = h3;
+            } else if (s < second) {
+                second = s;
+            }
+        }
+    }
+    if (p->h1 >= 0) p->score = best;
+    p->gap = second < 1e299 ? second - best : 1e30;
+}
+
+int orc_find_seeds_of(const orc_geom *g, const orc_seed_cuts *c, int n, const orc_hit *hits, int n_first,
+                      const int *first, orc_seed_pick *pick)
+{
+    if (g->n_layers < 4 || c->pt_min <= 0.0 || c->z_vertex <= 0.0 || c->d0_max <= 0.0 || c->dz_max <= 0.0 ||
+        c->conf_rphi <= 0.0 || c->conf_z <= 0.0)
+        return ORC_ERR_INVALID;
+    for (int k = 0; k < n_first; ++k) {
+        if (first[k] < 0 || first[k] >= n || hits[first[k]].layer != 0) return ORC_ERR_INVALID;
+        seed_of(g, c, n, hits, first[k], &pick[k]);
+    }
+    return ORC_OK;
+}
+
+int orc_find_seeds(const orc_geom *g, const orc_seed_cuts *c, int n, const orc_hit *hits, orc_seed_pick *pick)
+{
+    for (int i = 0; i < n; ++i) {
+        memset(&pick[i], 0, sizeof pick[i]);
+        pick[i].h1 = pick[i].h2 = pick[i].h3 = -1;
+        pick[i].margin = pick[i].gap = 1e30;
+        if (hits[i].layer != 0) continue;
+        const int st = orc_find_seeds_of(g, c, n, hits, 1, &i, &pick[i]);
+        if (st != ORC_OK) return st;
+    }
+    return ORC_OK;
+}

@@ -87,6 +87,51 @@ int orc_hit_index(const orc_geom *g, int n, const orc_hit *hits, int *bin_of_hit
 int orc_build_seed(const orc_geom *g, const orc_event *ev, const double sp[6], const double sP[36],
                    double schi2, int snhits, const int *shits, orc_seed_result *res, orc_stats *stats);
 
+/* Seeding from hit triplets on layers 0, 1, 2 with a confirmation hit on layer 3 (the seeding
+ * stage of Sec. 2, which the paper names but does not specify; the reading is in tkf_oracle.c).
+ * Lengths in cm, pt_min in GeV. */
+typedef struct {
+    double pt_min;      /* curvature limit kappa_max = ORC_KB * bz / pt_min * (1 + kappa_slack) */
+    double kappa_slack;
+    double z_vertex;    /* |z at r = 0| of the r-z line through the first two hits */
+    double d0_max;      /* |power of the beam line point / circle diameter| of the triplet circle */
+    double dz_max;      /* |z of the third hit - the r-z line through the first two| */
+    double conf_rphi;   /* |signed distance of the layer-3 hit from the triplet circle| */
+    double conf_z;      /* |z of the layer-3 hit - the r-z line through the second and third hits| */
+    int confirm;        /* 1: a confirmation hit on layer 3 is required */
+} orc_seed_cuts;
+
+/* The quantities of one candidate; a stage not reached keeps zeros. */
+typedef struct {
+    double chord01, kappa01, zv;          /* pair (first, second hit) */
+    double chord12, kappa, d0, dz;        /* triplet */
+    double chord23, f3, dz3;              /* confirmation hit (when one is given) */
+    int collinear;                        /* the triplet's three points are collinear: rejected */
+} orc_seed_quant;
+
+/* Best triplet for one first-layer hit. */
+typedef struct {
+    int h1, h2, h3;   /* event-local ids of the chosen hits on layers 1, 2 and the confirmation hit
+                         on layer 3 (h1 = -1: no seed) */
+    int n_pass;       /* triplets that pass every cut (with a confirmation hit when required) */
+    double score;     /* score of the chosen triplet */
+    double margin;    /* smallest relative distance |q - cut| / cut over the decisions that could
+                         change the result: every quantity of a passing candidate, the one failing
+                         quantity of a candidate that fails on exactly one (1e30: none) */
+    double gap;       /* second best minus best passing score (1e30: fewer than two) */
+} orc_seed_pick;
+
+double orc_seed_kappa_max(const orc_geom *g, const orc_seed_cuts *c);
+/* quantities of (a, b, cc[, e]) (e may be NULL); returns 1 if every cut passes */
+int orc_seed_eval(const orc_geom *g, const orc_seed_cuts *c, const orc_hit *a, const orc_hit *b, const orc_hit *cc,
+                  const orc_hit *e, orc_seed_quant *q);
+/* every hit of layer 0 among hits[0..n) (one event): its best triplet in pick[hit id]; entries of
+ * hits on other layers get h1 = -1 */
+int orc_find_seeds(const orc_geom *g, const orc_seed_cuts *c, int n, const orc_hit *hits, orc_seed_pick *pick);
+/* the same for the listed first-layer hits only (pick[k] for first[k]) */
+int orc_find_seeds_of(const orc_geom *g, const orc_seed_cuts *c, int n, const orc_hit *hits, int n_first,
+                      const int *first, orc_seed_pick *pick);
+
 /* batch helpers (plain loops over the single-object functions above) */
 int orc_seed_batch(const orc_geom *g, const orc_hit *hits, int n, const int *seed_hits /*[n][3]*/,
                    double *par /*[n][6]*/, double *cov /*[n][36]*/);

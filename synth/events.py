@@ -51,10 +51,19 @@ class Detector:
     # radius; () or 0 keeps the layer a cylinder of radius radii[l].
     disk_z: tuple = ()
     disk_rmin: float = 1.0
+    # Pixel seeding layers: layers 0 .. pixel_layers - 1 measure (r-phi, z) with pixel_sigma
+    # instead of (sigma_rphi, sigma_z), the fine inner layers a seeding from hit triplets needs
+    # (with 1 mm in z three hits 4 cm apart do not single out a track in a dense event).
+    pixel_layers: int = 0
+    pixel_sigma: tuple = (0.002, 0.005)
 
     @property
     def n_layers(self) -> int:
         return len(self.radii)
+
+    def sigma(self, l: int):
+        """(r-phi, second coordinate) resolution of layer l in cm."""
+        return tuple(self.pixel_sigma) if l < self.pixel_layers else (self.sigma_rphi, self.sigma_z)
 
     def is_disk(self, l: int) -> bool:
         return bool(self.disk_z) and self.disk_z[l] > 0.0
@@ -258,8 +267,9 @@ def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
             phi_pos = np.arctan2(y, x)
             r_pos = np.hypot(x, y)
             if spec.smear:
-                phi_h = phi_pos + det.sigma_rphi * g_rphi / r_pos
-                r_h = r_pos + det.sigma_z * g_r
+                sr, sz = det.sigma(l)
+                phi_h = phi_pos + sr * g_rphi / r_pos
+                r_h = r_pos + sz * g_r
             else:
                 phi_h, r_h = phi_pos, r_pos
             sig_hit[:, l] = np.stack([r_h * np.cos(phi_h), r_h * np.sin(phi_h), z], axis=1)
@@ -277,8 +287,9 @@ def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
         g_rphi, g_z = normals(key, (tl, _LAYER0 + l, 0, 0))
         phi_pos = np.arctan2(y, x)
         if spec.smear:
-            phi_h = phi_pos + det.sigma_rphi * g_rphi / R
-            z_h = z + det.sigma_z * g_z
+            sr, sz = det.sigma(l)
+            phi_h = phi_pos + sr * g_rphi / R
+            z_h = z + sz * g_z
         else:
             phi_h, z_h = phi_pos, z.copy()
         sig_hit[:, l] = np.stack([R * np.cos(phi_h), R * np.sin(phi_h), z_h], axis=1)
@@ -339,12 +350,14 @@ def generate(spec: EventSpec, det: Detector = Detector()) -> EventBatch:
     if spec.keep_f64:
         extras["xyz64"] = np.stack([np.concatenate(xs), np.concatenate(ys), np.concatenate(zs)], axis=1)
     cat = lambda parts, dt: np.concatenate(parts).astype(dt) if parts else np.zeros(0, dt)
+    layer = cat(lays, np.int32)
+    var_l = np.array([[det.sigma(l)[0] ** 2, det.sigma(l)[1] ** 2] for l in range(L)], dtype=np.float64)
     batch = EventBatch(
         detector=det, spec=spec, hit_off=hit_off, trk_off=trk_off,
         x=cat(xs, np.float32), y=cat(ys, np.float32), z=cat(zs, np.float32),
-        var_u=np.full(n_hits, det.sigma_rphi ** 2, dtype=np.float32),
-        var_v=np.full(n_hits, det.sigma_z ** 2, dtype=np.float32),
-        layer=cat(lays, np.int32), mc=cat(mcs, np.int64),
+        var_u=var_l[layer, 0].astype(np.float32) if n_hits else np.zeros(0, np.float32),
+        var_v=var_l[layer, 1].astype(np.float32) if n_hits else np.zeros(0, np.float32),
+        layer=layer, mc=cat(mcs, np.int64),
         trk_event=trk_event, trk_hits=trk_hits, truth=truth, truth_after=truth_after,
         vertex_state=vertex_state, extras=extras,
     )
