@@ -109,25 +109,28 @@ ISSUE_PEAK_WARP_INST_PER_S = SM_COUNT * 4 * SM_MAX_GHZ * 1e9
 
 def _gen_chunk(args):
     from synth import FORWARD_ETA, Detector, EventSpec, event_sizes, forward_detector, generate
-    seed, e0, e1, module_dr, forward = args
+    seed, e0, e1, module_dr, forward = args[:5]
+    pixel = args[5] if len(args) > 5 else 0
     n, f = event_sizes(seed, 640)
     eta = dict(eta_min=FORWARD_ETA[0], eta_max=FORWARD_ETA[1]) if forward else {}
     if forward:  # the endcaps' share: a quarter of each event's tracks
         n = np.maximum(1, np.rint(0.25 * n)).astype(np.int64)
     return generate(EventSpec(seed=seed, n_events=e1 - e0, n_tracks=n[e0:e1], noise_frac=f[e0:e1], first_event=e0,
-                              **eta), forward_detector() if forward else Detector(module_dr=module_dr))
+                              **eta), forward_detector() if forward else Detector(module_dr=module_dr, pixel_layers=pixel))
 
 
-def workload(seed: int, n_events: int, pool=None, module_dr=0.0, forward=False):
+def workload(seed: int, n_events: int, pool=None, module_dr=0.0, forward=False, pixel_layers=0):
     """The first n_events events of the 640-event batched workload (generated in parallel
     chunks when a process pool is given; the result does not depend on the chunking);
     module_dr > 0: the same events on modules off the layers' cylinders; forward: a quarter of each
-    event's tracks on the endcap tracker (ten pairs of disks), with 1.7 <= |eta| <= 2.5."""
+    event's tracks on the endcap tracker (ten pairs of disks), with 1.7 <= |eta| <= 2.5;
+    pixel_layers: the same events with that many inner layers of pixel resolution (the seeding
+    workload)."""
     from synth import concat
     if pool is None or n_events < 32:
-        return _gen_chunk((seed, 0, n_events, module_dr, forward))
+        return _gen_chunk((seed, 0, n_events, module_dr, forward, pixel_layers))
     step = max(1, n_events // 64)
-    chunks = [(seed, e, min(e + step, n_events), module_dr, forward) for e in range(0, n_events, step)]
+    chunks = [(seed, e, min(e + step, n_events), module_dr, forward, pixel_layers) for e in range(0, n_events, step)]
     return concat(pool.map(_gen_chunk, chunks, chunksize=1))
 
 
@@ -235,6 +238,21 @@ def efficiency(b, hit_idx):
     own = (h >= 0) & (b.mc[np.maximum(h, 0)] == np.arange(h.shape[1])[None, :])
     nh = (h >= 0).sum(0)
     return float(np.mean(own.sum(0) >= 0.75 * np.maximum(nh, 1)))
+
+
+def seeded_efficiency(b, first_hits, hit_idx):
+    """Tracking with found seeds: a built track matches simulated track t when >= 75 % of its hits
+    are t's; returns the fraction of simulated tracks matched by some seed, the fraction of seeds
+    that match none (fakes) and matched seeds per matched track minus one (duplicates).
+    first_hits: [n] layer-0 hit of each seed; hit_idx: [L, n] built hit ids (-1 = hole)."""
+    h = np.asarray(hit_idx)
+    t = b.mc[np.asarray(first_hits)]
+    own = (h >= 0) & (b.mc[np.maximum(h, 0)] == t[None, :])
+    nh = (h >= 0).sum(0)
+    match = (t >= 0) & (own.sum(0) >= 0.75 * np.maximum(nh, 1))
+    found = np.unique(t[match])
+    return {"track_efficiency": float(len(found) / b.n_tracks), "fake_rate": float(1.0 - match.mean()),
+            "duplicate_rate": float(match.sum() / max(len(found), 1) - 1.0)}
 
 
 # ----------------------------------------------------------------------------- replicas
@@ -561,6 +579,8 @@ def main():
     ap.add_argument("--disks", type=int, default=640,
                     help="events of the batch also timed on the endcap tracker, each with a quarter of its tracks "
                          "(forward tracks on disks); 0: skip")
+    ap.add_argument("--seeding", type=int, default=640,
+                    help="events of the seeding leg (hit triplets on pixel inner layers; 0: off)")
     ap.add_argument("--tile", type=int, default=0, help="seeds per warp work tile (0: autotuned)")
     ap.add_argument("--e2e-batch", type=int, default=160, help="events per server batch in the e2e measurement")
     ap.add_argument("--e2e-slots", type=int, default=4, help="server slots in the e2e measurement")
@@ -929,6 +949,79 @@ def main():
         c3.close()
         del d3, hits3
 
+    # ---------------- seeding from hit triplets, then the whole chain with the found seeds
+    seeding = None
+    if a.seeding > 0:
+        n4 = min(a.seeding, 640)
+        b4 = workload(a.seed + 1000 * rank, n4, pool, pixel_layers=4)
+        t4 = lambda arr, dt: torch.as_tensor(np.ascontiguousarray(arr), dtype=dt).to(dev)
+        hits4 = tkf.DeviceHits(t4(b4.x, torch.float32), t4(b4.y, torch.float32), t4(b4.z, torch.float32),
+                               t4(b4.var_u, torch.float32), t4(b4.var_v, torch.float32), t4(b4.layer, torch.int32),
+                               t4(b4.hit_off, torch.int32))
+        c4 = tkf.Context(tkf.default_config(seed_order=a.seed_order, seeds_per_block=best_tile))
+        idx4 = c4.build_hit_index(hits4, stream=stream)
+        cuts4 = tkf.default_seed_cuts()
+        n_first = int((b4.layer == 0).sum())
+        sh4 = torch.empty((3, n_first), dtype=torch.int32, device=dev)
+        se4 = torch.empty(n_first, dtype=torch.int32, device=dev)
+        nf4 = torch.zeros(1, dtype=torch.int32, device=dev)
+        find4 = lambda: c4.find_seeds(idx4, cuts4, n_first, sh4, se4, nf4, stream=stream)
+        for _ in range(max(3, a.warmup)):
+            find4()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(a.steps):
+            find4()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        c4.sync_status(stream)
+        seed_ms = s0.elapsed_time(s1) / a.steps
+        n_found = int(nf4.item())
+        seeds_np = sh4[:, :n_found].cpu().numpy()
+        th4 = b4.trk_hits
+        pick1 = np.full(b4.n_hits, -1, dtype=np.int64)
+        pick2 = np.full(b4.n_hits, -1, dtype=np.int64)
+        pick1[seeds_np[0]], pick2[seeds_np[0]] = seeds_np[1], seeds_np[2]
+        own_trip = float(np.mean((pick1[th4[:, 0]] == th4[:, 1]) & (pick2[th4[:, 0]] == th4[:, 2])))
+        # the chain: index, seeding into the pipeline's seed rows, seed fit, building, final fit
+        shc = torch.empty((3, n_found), dtype=torch.int32, device=dev)
+        sec = torch.empty(n_found, dtype=torch.int32, device=dev)
+        p4 = tkf.DevicePipeline(c4, b4.n_hits, b4.n_events, n_found, use_graph=True)
+
+        def chain():
+            c4.build_hit_index(hits4, reuse=idx4, stream=stream)
+            c4.find_seeds(idx4, cuts4, n_found, shc, sec, nf4, stream=stream)
+            p4.run(hits4, shc, sec, n_found, stream=stream)
+
+        for _ in range(max(3, a.warmup)):
+            chain()
+        torch.cuda.synchronize()
+        s0.record(stream)
+        for _ in range(a.steps):
+            chain()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        c4.sync_status(stream)
+        chain_ms = s0.elapsed_time(s1) / a.steps
+        hid4 = tkf.tracks_tensors(p4.outputs()[2], L)["hit_idx"][:, :n_found].cpu().numpy()
+        seeding = {
+            "value": b4.n_tracks / (chain_ms / 1e3), "unit": UNIT, "ms_per_step": chain_ms,
+            "seeding_ms": seed_ms, "first_hits_per_s": n_first / (seed_ms / 1e3), "events": b4.n_events,
+            "tracks": b4.n_tracks, "hits": b4.n_hits, "first_layer_hits": n_first, "seeds": n_found,
+            "seeds_per_track": n_found / b4.n_tracks, "own_triplet": own_trip,
+            **seeded_efficiency(b4, seeds_np[0], hid4),
+            "cuts": {k: getattr(cuts4, k) for k in ("pt_min", "kappa_slack", "z_vertex", "d0_max", "dz_max",
+                                                    "conf_rphi", "conf_z", "confirm")},
+            "form": "the batched workload's events 0..%d with pixel resolution (20 um r-phi, 50 um z) on layers "
+                    "0-3: tkf_find_seeds over the hit index (k_seed_find, one thread per layer-0 hit, then "
+                    "count, scan and scatter) timed alone (seeding_ms); value = simulated tracks per second "
+                    "of the chain hit index + seeding + pipeline (its own index, seed fit, building, final "
+                    "fit) with the found seeds; FP32, N = 6" % (b4.n_events - 1)}
+        p4.close()
+        c4.close()
+        del hits4, sh4, se4, shc, sec
+
     # ---------------- end to end through host buffers
     _, built_t, fitted_t = pipe.outputs()
     fv = tkf.tracks_tensors(fitted_t, L)
@@ -1188,6 +1281,7 @@ def main():
         "backward_pass": backward,
         "two_step": two_step,
         "disks": disks,
+        "seeding": seeding,
         "batch_scan": batch_scan,
         "physics": phys,
         "fit": fit_leg,

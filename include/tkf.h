@@ -204,6 +204,50 @@ int tkf_fit_continue(tkf_ctx *ctx, const tkf_hits *hits, const tkf_tracks *init,
 int tkf_seed_fit(tkf_ctx *ctx, const tkf_hits *hits, const int32_t *seed_hits, int32_t last_layer, tkf_tracks *out,
                  tkf_stream stream);
 
+/* Cuts of the seeding from hit triplets (tkf_find_seeds); lengths in cm.  Defaults
+ * (tkf_default_seed_cuts): pt_min 0.5 GeV, kappa_slack 0.15, z_vertex 4, d0_max 0.08,
+ * dz_max 0.08, conf_rphi 0.1, conf_z 0.1, confirm 1. */
+typedef struct {
+    double pt_min;      /* curvature limit kappa_max = 0.00299792458 * bz / pt_min * (1 + kappa_slack) */
+    double kappa_slack;
+    double z_vertex;    /* |z at r = 0| of the r-z line through the layer-0 and layer-1 hits */
+    double d0_max;      /* |power of the beam line point (x = y = 0) / diameter| of the triplet circle */
+    double dz_max;      /* |z of the layer-2 hit - the r-z line through the first two, at its r| */
+    double conf_rphi;   /* |signed distance of the layer-3 hit from the triplet circle| */
+    double conf_z;      /* |z of the layer-3 hit - the r-z line through the layer-1 and layer-2 hits| */
+    int32_t confirm;    /* 1: a seed needs a confirmation hit on layer 3 */
+    int32_t reserved;
+} tkf_seed_cuts;
+
+void tkf_default_seed_cuts(tkf_seed_cuts *cuts);
+
+/* Seeding from hit triplets (the seeding stage of Sec. 2, which the paper names without
+ * specifying it): for every hit a of layer 0, the triplet (a, b, c) of hits on layers 0, 1, 2 of
+ * smallest score that passes every cut -- transverse chords |b - a| <= 2 (R1 - R0) and
+ * |c - b| <= 2 (R2 - R1) (outward, not a looping circle's far crossing); |curvature| <= kappa_max
+ * for the circle through the beam line point, a and b, and for the circle through a, b, c; the
+ * z-vertex, d0 and dz cuts of tkf_seed_cuts -- and, with confirm, a layer-3 hit e with
+ * |e - c| <= 2 (R3 - R2) inside the conf_rphi / conf_z cuts.  Score = (d0 / d0_max)^2 +
+ * (dz / dz_max)^2 + the smallest (f / conf_rphi)^2 + (dz3 / conf_z)^2 of its confirming hits;
+ * equal scores keep the smallest event-local hit ids (b first).  r of a hit is its transverse
+ * radius.  Layers 0..3 must be cylinders of increasing radius.  The search walks the index's
+ * eta-phi bins around each pair's and triplet's extrapolation and applies the exact cuts to
+ * every hit there, so the result equals a scan over all hits of the layers (up to the FP32
+ * evaluation of quantities within about 1e-4 of a cut).
+ *   idx: a hit index of this context (tkf_build_hit_index).
+ *   seed_hits: device int32 [3][max_seeds]: global hit ids (into the indexed tkf_hits) of a, b, c,
+ *              the layout tkf_seed_fit and tkf_pipeline_run take.
+ *   seed_event: device int32 [max_seeds], the event of each seed.
+ *   seed_score: device float [max_seeds] or NULL.
+ *   n_found: device int32 [1]: the number of seeds found, which may exceed max_seeds (then only
+ *            the first max_seeds are written).
+ * Seeds are ordered by event, then by the index position of their layer-0 hit (eta bin, phi
+ * bin, phi sixteenth, hit id).  Scratch (12 bytes per indexed hit) is held by the context.
+ * Errors: TKF_ERR_INVALID (null pointers, cuts not positive, fewer than 4 layers, a disk among
+ * layers 0..3), TKF_ERR_NOMEM, TKF_ERR_CUDA. */
+int tkf_find_seeds(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_seed_cuts *cuts, int32_t max_seeds,
+                   int32_t *seed_hits, int32_t *seed_event, float *seed_score, int32_t *n_found, tkf_stream stream);
+
 /* Backward pass of the final fit (Sec. 2: the final fit gives the best estimate of the track's
  * parameters; this pass carries that estimate to the production point): an inward Kalman
  * filter over each track's hits from layer last_layer down to first_layer.  `init` holds the

@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FAST_MATH = ["-use_fast_math"]
 SOURCES = ["tkf_api.cu", "tkf_build_fp32.cu", "tkf_build_mixed.cu", "tkf_build_fp64.cu", "tkf_build2_fp32.cu",
            "tkf_build2_mixed.cu", "tkf_build2_fp64.cu", "tkf_build3_fp32.cu", "tkf_build3_mixed.cu",
-           "tkf_build3_fp64.cu", "tkf_pipeline.cu", "tkf_server.cu", "tkf_probe.cu"]
+           "tkf_build3_fp64.cu", "tkf_pipeline.cu", "tkf_server.cu", "tkf_probe.cu", "tkf_seeding.cu"]
 
 
 def nvcc() -> str:

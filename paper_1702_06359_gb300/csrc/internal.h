@@ -121,6 +121,10 @@ struct tkf_ctx {
     unsigned *first_key = nullptr;
     int *first_hit = nullptr;
     size_t first_cap = 0;
+    // seeding scratch: best layer-1 / layer-2 hit and score per sorted hit position, seeds per block
+    int *seed_b = nullptr, *seed_c = nullptr, *seed_cnt = nullptr;
+    float *seed_s = nullptr;
+    size_t seed_cap = 0, seed_cnt_cap = 0;
 };
 
 struct tkf_hit_index {

@@ -1199,7 +1199,7 @@ int tkf_destroy(tkf_ctx *ctx)
     cudaFree(ctx->d_tile);
     cudaFree(ctx->d_err);
     for (int *p : {ctx->ord_key, ctx->ord_perm, ctx->ord_counts, ctx->ord_off, ctx->ord_seg_count, ctx->ord_seg_base,
-                   (int *)ctx->first_key, ctx->first_hit})
+                   (int *)ctx->first_key, ctx->first_hit, ctx->seed_b, ctx->seed_c, ctx->seed_cnt, (int *)ctx->seed_s})
         cudaFree(p);
     delete ctx;
     return TKF_OK;

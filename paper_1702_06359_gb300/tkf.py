@@ -58,6 +58,24 @@ class Tracks(C.Structure):
                 ("hit_idx", C.c_void_p), ("event", C.c_void_p), ("n", C.c_int32), ("stride", C.c_int32)]
 
 
+class SeedCuts(C.Structure):
+    """tkf_seed_cuts: cuts of the seeding from hit triplets (lengths in cm, pt_min in GeV)."""
+
+    _fields_ = [("pt_min", C.c_double), ("kappa_slack", C.c_double), ("z_vertex", C.c_double),
+                ("d0_max", C.c_double), ("dz_max", C.c_double), ("conf_rphi", C.c_double), ("conf_z", C.c_double),
+                ("confirm", C.c_int32), ("reserved", C.c_int32)]
+
+
+def default_seed_cuts(**kw) -> SeedCuts:
+    c = SeedCuts()
+    lib().tkf_default_seed_cuts(C.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise AttributeError(k)
+        setattr(c, k, v)
+    return c
+
+
 class HitIndexOut(C.Structure):
     _fields_ = [("hit_xyzi", C.c_void_p), ("hit_var", C.c_void_p), ("bin_sub", C.c_void_p), ("pos_of_hit", C.c_void_p),
                 ("bin_off", C.c_void_p), ("var_max", C.c_void_p), ("event_off", C.c_void_p)]
@@ -152,10 +170,13 @@ def lib():
         L.tkf_submit_events.argtypes = [vp, C.POINTER(Event), i32, C.POINTER(C.c_uint64), C.POINTER(i32)]
         L.tkf_wait_all.argtypes = [vp, C.POINTER(C.c_uint64), i32, C.POINTER(Result), C.c_int64]
         L.tkf_release_many.argtypes = [vp, C.POINTER(C.c_uint64), i32]
+        L.tkf_default_seed_cuts.argtypes = [C.POINTER(SeedCuts)]
+        L.tkf_default_seed_cuts.restype = None
+        L.tkf_find_seeds.argtypes = [vp, vp, C.POINTER(SeedCuts), i32, vp, vp, vp, vp, vp]
         L.tkf_build_hit_index_noalloc.argtypes = [C.POINTER(Config), C.POINTER(Hits), C.POINTER(HitIndexOut), vp]
         for name in declared_functions():
             if name not in ("tkf_last_error", "tkf_status_string", "tkf_default_config", "tkf_pipeline_index",
-                            "tkf_server_default_options"):
+                            "tkf_server_default_options", "tkf_default_seed_cuts"):
                 getattr(L, name).restype = C.c_int
         L.tkf_pipeline_index.restype = vp
         L.tkf_server_default_options.restype = None
@@ -332,6 +353,13 @@ class Context:
         hs, to = hits.struct(), out.struct()
         self._check(lib().tkf_seed_fit(self.handle, C.byref(hs), _ptr(seed_hits), int(last), C.byref(to),
                                        _stream(stream)))
+
+    def find_seeds(self, index: HitIndex, cuts: SeedCuts, max_seeds, seed_hits, seed_event, n_found, seed_score=None,
+                   stream=None):
+        """tkf_find_seeds into caller-owned device tensors: seed_hits int32 [3][max_seeds],
+        seed_event int32 [max_seeds], n_found int32 [1], seed_score float [max_seeds] or None."""
+        self._check(lib().tkf_find_seeds(self.handle, index.handle, C.byref(cuts), int(max_seeds), _ptr(seed_hits),
+                                         _ptr(seed_event), _ptr(seed_score), _ptr(n_found), _stream(stream)))
 
     def build_tracks(self, index: HitIndex, seeds: DeviceTracks, out: DeviceTracks, out_all: DeviceTracks = None,
                      n_cand_out=None, stream=None):
