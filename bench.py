@@ -103,6 +103,10 @@ KERNELS_PER_STEP = 12
 # capture of the kernels as built now (160-event case: 124.1 + 433.3 MB for 701 095 seeds;
 # summary in profiles/); None whenever a kernel changes until it is captured again
 BUILD_DRAM_BYTES_PER_SEED = 795.1
+# warp instructions of k_seed_find per layer-0 hit and active lanes per instruction, from one ncu
+# capture of the 160-event seeding case (3.522 G instructions for 932 025 first hits; summary in
+# profiles/); None whenever the kernel changes until it is captured again
+SEED_WARP_INST_PER_FIRST_HIT, SEED_LANES_ACTIVE = 3778.6, 18.32
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 ISSUE_PEAK_WARP_INST_PER_S = SM_COUNT * 4 * SM_MAX_GHZ * 1e9
 
@@ -1010,6 +1014,14 @@ def main():
             "seeding_ms": seed_ms, "first_hits_per_s": n_first / (seed_ms / 1e3), "events": b4.n_events,
             "tracks": b4.n_tracks, "hits": b4.n_hits, "first_layer_hits": n_first, "seeds": n_found,
             "seeds_per_track": n_found / b4.n_tracks, "own_triplet": own_trip,
+            "roofline": None if SEED_WARP_INST_PER_FIRST_HIT is None else {
+                "kernel": "k_seed_find (+ k_seed_count, k_seed_scan, k_seed_scatter in seeding_ms)", "bound": "issue",
+                "achieved": SEED_WARP_INST_PER_FIRST_HIT * n_first / (seed_ms / 1e3),
+                "peak": ISSUE_PEAK_WARP_INST_PER_S, "unit": "warp instructions/s",
+                "frac": SEED_WARP_INST_PER_FIRST_HIT * n_first / (seed_ms / 1e3) / ISSUE_PEAK_WARP_INST_PER_S,
+                "inst_per_first_hit": SEED_WARP_INST_PER_FIRST_HIT, "lanes_active": SEED_LANES_ACTIVE,
+                "source": "ncu smsp__inst_executed.sum per layer-0 hit and thread instructions per warp instruction "
+                          "of the 160-event capture; 152 SMs x 4 x 2.07 GHz"},
             **seeded_efficiency(b4, seeds_np[0], hid4),
             "cuts": {k: getattr(cuts4, k) for k in ("pt_min", "kappa_slack", "z_vertex", "d0_max", "dz_max",
                                                     "conf_rphi", "conf_z", "confirm")},

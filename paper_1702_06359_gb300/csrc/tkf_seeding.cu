@@ -68,175 +68,431 @@ __device__ __forceinline__ void eta_bins(const SeedGeom &g, float R, float z_lo,
     b1 = max(0, min(b1, g.n_eta - 1));
 }
 
-// phi bins of [phi - half, phi + half]: first bin p0 (0 .. n_phi - 1) and count np (wrapping)
-__device__ __forceinline__ void phi_bins(const SeedGeom &g, float phi, float half, int &p0, int &np)
+// The phi window [phi - half, phi + half] as at most two runs of consecutive (phi bin, phi
+// sixteenth) cells of an eta row (two when it wraps around phi = +-pi): run r covers cells
+// lo[r] .. hi[r], a cell numbered bin * kSubBins + sixteenth (hi < lo: empty).
+struct PhiWin {
+    int lo[2], hi[2];
+};
+
+__device__ __forceinline__ PhiWin phi_window(const SeedGeom &g, float phi, float half)
 {
-    if (half >= 3.1f) {
-        p0 = 0;
-        np = g.n_phi;
-        return;
-    }
+    PhiWin w;
+    w.lo[1] = 0;
+    w.hi[1] = -1;
+    const float tp = 2.f * (float)kPi;
+    phi -= tp * floorf((phi + (float)kPi) / tp);  // into [-pi, pi)
     const float c_lo = (phi - half + (float)kPi) * g.phi_scale, c_hi = (phi + half + (float)kPi) * g.phi_scale;
+    const int nphi = g.n_phi, last = nphi * kSubBins - 1;
+    if (!(c_hi - c_lo < (float)(nphi - 1)) || !(c_lo > (float)-nphi) || !(c_hi < (float)(2 * nphi))) {
+        w.lo[0] = 0;  // the whole row
+        w.hi[0] = last;
+        return w;
+    }
     const int k0 = (int)floorf(c_lo), k1 = (int)floorf(c_hi);
-    np = min(k1 - k0 + 1, g.n_phi);
-    p0 = ((k0 % g.n_phi) + g.n_phi) % g.n_phi;
+    const int s0 = min(max((int)floorf((c_lo - (float)k0) * (float)kSubBins), 0), kSubBins - 1);
+    const int s1 = min(max((int)floorf((c_hi - (float)k1) * (float)kSubBins), 0), kSubBins - 1);
+    if (k0 < 0) {
+        w.lo[0] = (k0 + nphi) * kSubBins + s0;
+        w.hi[0] = last;
+        w.hi[1] = k1 * kSubBins + s1;
+    } else if (k1 >= nphi) {
+        w.lo[0] = k0 * kSubBins + s0;
+        w.hi[0] = last;
+        w.hi[1] = (k1 - nphi) * kSubBins + s1;
+    } else {
+        w.lo[0] = k0 * kSubBins + s0;
+        w.hi[0] = k1 * kSubBins + s1;
+    }
+    return w;
 }
 
-// Calls visit(j) for every sorted position j of the hits in the window's bins of one
-// (event, layer) segment.
-template <class Visit>
-__device__ __forceinline__ void for_window(const SeedGeom &g, const int *bin_off, int seg, int e0, int e1, int p0,
-                                           int np, Visit visit)
+// start of phi sixteenth t (1 <= t < kSubBins) of a bin from its packed bin_sub word (byte t - 1)
+__device__ __forceinline__ int sixteenth_start(const uint4 w, int t)
 {
-    for (int eb = e0; eb <= e1; ++eb) {
-        const int row = seg * g.n_bins + eb * g.n_phi;
-        for (int k = 0; k < np; ++k) {
-            int pb = p0 + k;
-            pb -= pb >= g.n_phi ? g.n_phi : 0;
-            const int j0 = __ldg(&bin_off[row + pb]), j1 = __ldg(&bin_off[row + pb + 1]);
-            for (int j = j0; j < j1; ++j) visit(j);
+    const unsigned word = t <= 4 ? w.x : (t <= 8 ? w.y : (t <= 12 ? w.z : w.w));
+    return (int)((word >> (8 * ((t - 1) & 3))) & 0xFFu);
+}
+
+// A walk over the hits of a window: eta rows eb .. e1 of one (event, layer) segment, runs 0 and 1
+// of the phi window in each row; [j, jend) is the current run's range of sorted positions.
+struct Cursor {
+    int eb, e1, r, j, jend;
+};
+
+// Moves the cursor to its next non-empty run; false when the window is exhausted.
+__device__ __forceinline__ bool cursor_next(const SeedGeom &g, const int *bin_off, const uint4 *bin_sub, int seg,
+                                            const PhiWin &w, Cursor &c)
+{
+    while (c.eb <= c.e1) {
+        if (c.r >= 2) {
+            c.r = 0;
+            ++c.eb;
+            continue;
+        }
+        const int lo = c.r == 0 ? w.lo[0] : w.lo[1], hi = c.r == 0 ? w.hi[0] : w.hi[1];
+        ++c.r;
+        if (hi < lo) continue;
+        const int row = seg * g.n_bins + c.eb * g.n_phi;
+        const int ps0 = lo & (kSubBins - 1), ps1 = hi & (kSubBins - 1);
+        const int ba = row + lo / kSubBins, bb = row + hi / kSubBins;
+        const int oa = __ldg(&bin_off[ba]), ob = __ldg(&bin_off[bb]), ob1 = __ldg(&bin_off[bb + 1]);
+        const uint4 wa = __ldg(&bin_sub[ba]), wb = __ldg(&bin_sub[bb]);
+        c.j = oa + ((ps0 <= 0 || wa.w == 0xFFFFFFFFu) ? 0 : sixteenth_start(wa, ps0));
+        c.jend = ob + ((ps1 >= kSubBins - 1 || wb.w == 0xFFFFFFFFu) ? ob1 - ob : sixteenth_start(wb, ps1 + 1));
+        if (c.j < c.jend) return true;
+    }
+    return false;
+}
+
+// Queues of one warp: its 32 first hits (slot = lane), passing pairs waiting for their layer-2
+// scan, layer-2 hits within the pair's chord and z cuts waiting for the circle through the
+// three, passing triplets waiting for their confirmation scan.  Entries are appended in (step,
+// lane) order, so the queues' contents do not depend on timing.
+constexpr int kQueue = 64;
+struct WarpQueues {
+    float4 a[32];  // x, y, z, r of the slot's first hit
+    float pha[32];
+    int seg0[32];  // event * L
+    int p_slot[kQueue], p_b[kQueue];
+    float p_k01[kQueue], p_slope[kQueue];
+    int f_slot[kQueue], f_b[kQueue], f_c[kQueue];
+    float f_dz[kQueue];
+    int t_slot[kQueue], t_b[kQueue], t_c[kQueue];
+    float t_s2[kQueue], t_kap[kQueue], t_nx[kQueue], t_ny[kQueue], t_d0[kQueue];
+};
+
+// Every lane reaches the warp-wide operations below: the loops are warp-uniform, and the lanes
+// without work carry their flags through them.
+// Held to 3 blocks of 256 threads per SM.
+#ifndef TKF_SEED_MINBLOCKS
+#define TKF_SEED_MINBLOCKS 3
+#endif
+__global__ void __launch_bounds__(kSeedThreads, TKF_SEED_MINBLOCKS)
+k_seed_find(const SeedGeom g, const float4 *__restrict__ hxyzi, const int *__restrict__ bin_off,
+            const uint4 *__restrict__ bin_sub, const int *__restrict__ ev_off, int n, int *__restrict__ res_b,
+            int *__restrict__ res_c, float *__restrict__ res_s)
+{
+    __shared__ WarpQueues s_q[kSeedThreads / 32];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    WarpQueues &q = s_q[threadIdx.x >> 5];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+
+    // this lane's first hit
+    bool valid = false;
+    int e = 0, seg0 = 0;
+    float ax = 0.f, ay = 0.f, az = 0.f, ra = 1.f, pha = 0.f;
+    if (t < n) {
+        e = seed_find_event(ev_off, g.n_events, t);
+        seg0 = e * g.L;
+        if (t < __ldg(&bin_off[(seg0 + 1) * g.n_bins])) {
+            const float4 A = hxyzi[t];
+            ax = A.x; ay = A.y; az = A.z;
+            ra = sqrtf(ax * ax + ay * ay);
+            valid = ra > 1e-6f;  // a hit on the beam line starts no seed
+            if (!valid) ra = 1.f;
+            pha = atan2f(ay, ax);
         }
     }
-}
-
-__global__ void __launch_bounds__(kSeedThreads)
-k_seed_find(const SeedGeom g, const float4 *__restrict__ hxyzi, const int *__restrict__ bin_off,
-            const int *__restrict__ ev_off, int n, int *__restrict__ res_b, int *__restrict__ res_c,
-            float *__restrict__ res_s)
-{
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const int e = seed_find_event(ev_off, g.n_events, t);
-    const int seg0 = e * g.L;
-    if (t >= __ldg(&bin_off[(seg0 + 1) * g.n_bins])) {  // not on layer 0
-        res_b[t] = -1;
-        return;
-    }
-    const float4 A = hxyzi[t];
-    const float ax = A.x, ay = A.y, az = A.z;
-    const float ra2 = ax * ax + ay * ay, ra = sqrtf(ra2);
-    if (!(ra > 1e-6f)) {  // a hit on the beam line starts no seed
-        res_b[t] = -1;
-        return;
-    }
-    const float pha = atan2f(ay, ax);
+    q.a[lane] = make_float4(ax, ay, az, ra);
+    q.pha[lane] = pha;
+    q.seg0[lane] = seg0;
     float best_s = kInf;
     int best_b = 0x7fffffff, best_c = 0x7fffffff;
-    const float zpad = 1e-3f + 1e-5f * fabsf(az);
 
     // layer-1 window: circles from the beam line through a with |kappa| <= kmax, z-vertex cut
-    int e0, e1, p0, np;
-    {
+    Cursor cb{0, -1, 0, 0, 0};
+    PhiWin w1;
+    w1.lo[0] = w1.lo[1] = 0;
+    w1.hi[0] = w1.hi[1] = -1;
+    if (valid) {
         const float R1 = g.R[1];
         const float rlo = R1 - g.hit_dr, rhi = R1 + g.hit_dr;
+        const float zpad = 1e-3f + 1e-5f * fabsf(az);
         const float zc_lo = fminf(az * rlo / ra - g.zv * (rlo / ra - 1.f), az * rhi / ra - g.zv * (rhi / ra - 1.f));
         const float zc_hi = fmaxf(az * rlo / ra + g.zv * (rlo / ra - 1.f), az * rhi / ra + g.zv * (rhi / ra - 1.f));
-        eta_bins(g, R1, zc_lo - zpad, zc_hi + zpad, e0, e1);
+        eta_bins(g, R1, zc_lo - zpad, zc_hi + zpad, cb.eb, cb.e1);
         const float s1 = g.kmax * rhi * 0.5f;
         const float half = s1 >= 1.f ? 4.f : asinf(s1) - asinf(g.kmax * ra * 0.5f) + 2e-3f;
-        phi_bins(g, pha, half, p0, np);
+        w1 = phi_window(g, pha, half);
     }
-    for_window(g, bin_off, seg0 + 1, e0, e1, p0, np, [&](int jb) {
-        const float4 B = hxyzi[jb];
-        const float bx = B.x - ax, by = B.y - ay;
-        const float chord01 = sqrtf(bx * bx + by * by);
-        if (!(chord01 <= g.lim01) || chord01 == 0.f) return;
-        const float rb = sqrtf(B.x * B.x + B.y * B.y);
-        const float k01 = 2.f * (ax * B.y - ay * B.x) / (ra * rb * chord01);
-        if (!(fabsf(k01) <= g.kmax) || rb == ra) return;
-        const float slope = (B.z - az) / (rb - ra);
-        const float zv = az - ra * slope;
-        if (!(fabsf(zv) <= g.zv)) return;
-        const int b_id = __float_as_int(B.w);
-        // layer-2 window: z along the r-z line of a and b, phi around the crossing of the circle
-        // through the beam line, a and b, widened by the d0 cut's lever arm
-        int f0, f1, q0, nq;
+    bool more = valid;
+    __syncwarp();
+
+    int n_p = 0, n_f = 0, n_t = 0;  // queued pairs, layer-2 candidates and triplets (warp-uniform)
+
+    // the confirmation scan of the first cnt queued triplets, one per lane, folded into the
+    // best triplet of each slot (held by the slot's lane); then the queue's rest moves up
+    auto confirm = [&](int cnt) {
+        const bool has = lane < cnt;
+        int ts = 0, tb = 0, tc = 0, b_id = 0, c_id = 0;
+        float s = kInf;
+        if (has) {
+            ts = q.t_slot[lane];
+            tb = q.t_b[lane];
+            tc = q.t_c[lane];
+            const float s2 = q.t_s2[lane];
+            const float4 B = hxyzi[tb], Cc = hxyzi[tc];
+            b_id = __float_as_int(B.w);
+            c_id = __float_as_int(Cc.w);
+            if (!g.confirm) {
+                s = s2;
+            } else {
+                const float4 A = q.a[ts];
+                const float kap = q.t_kap[lane], nx = q.t_nx[lane], ny = q.t_ny[lane], d0 = q.t_d0[lane];
+                const float rb = sqrtf(B.x * B.x + B.y * B.y), rc = sqrtf(Cc.x * Cc.x + Cc.y * Cc.y);
+                if (rc != rb) {
+                    const float slope23 = (Cc.z - B.z) / (rc - rb);
+                    // where the circle crosses r = R3 nearest to c: its centre is U = a + rho n, and
+                    // the crossing lies along U at (R3^2 + 2 rho d0) / (2 |U|) (|U|^2 - rho^2 = 2 rho d0)
+                    const float rho = 1.f / kap;
+                    const float ux = A.x + rho * nx, uy = A.y + rho * ny;
+                    const float D = sqrtf(ux * ux + uy * uy);
+                    const float R3 = g.R[3];
+                    const float along = (R3 * R3 + 2.f * rho * d0) / (2.f * D);
+                    const float h2 = R3 * R3 - along * along;
+                    if (h2 >= 0.f) {
+                        const float h = sqrtf(h2), ex = ux / D, ey = uy / D;
+                        const float px1 = along * ex - h * ey, py1 = along * ey + h * ex;
+                        const float px2 = along * ex + h * ey, py2 = along * ey - h * ex;
+                        const bool first = (px1 - Cc.x) * (px1 - Cc.x) + (py1 - Cc.y) * (py1 - Cc.y) <=
+                                           (px2 - Cc.x) * (px2 - Cc.x) + (py2 - Cc.y) * (py2 - Cc.y);
+                        const float ph3 = atan2f(first ? py1 : py2, first ? px1 : px2);
+                        const float zc3 = B.z + slope23 * (R3 - rb);
+                        Cursor ce{0, -1, 0, 0, 0};
+                        const float wz = g.z3 + 1e-3f + 1e-5f * fabsf(zc3) + g.hit_dr * fabsf(slope23);
+                        eta_bins(g, R3, zc3 - wz, zc3 + wz, ce.eb, ce.e1);
+                        const PhiWin w3 =
+                            phi_window(g, ph3, (3.f * g.w3 + 0.02f + 2.f * g.hit_dr * kap) / (R3 - g.hit_dr) + 2e-3f);
+                        const int seg3 = q.seg0[ts] + 3;
+                        float c3 = kInf;
+                        while (cursor_next(g, bin_off, bin_sub, seg3, w3, ce)) {
+                            for (; ce.j < ce.jend; ++ce.j) {
+                                const float4 E = hxyzi[ce.j];
+                                const float d23x = E.x - Cc.x, d23y = E.y - Cc.y;
+                                if (!(sqrtf(d23x * d23x + d23y * d23y) <= g.lim23)) continue;
+                                const float qx = E.x - A.x, qy = E.y - A.y;
+                                const float f3 = kap * (qx * qx + qy * qy) * 0.5f - (qx * nx + qy * ny);
+                                const float re = sqrtf(E.x * E.x + E.y * E.y);
+                                const float dz3 = E.z - (B.z + slope23 * (re - rb));
+                                if (!(fabsf(f3) <= g.w3) || !(fabsf(dz3) <= g.z3)) continue;
+                                const float pu = f3 / g.w3, pv = dz3 / g.z3;
+                                c3 = fminf(c3, pu * pu + pv * pv);
+                            }
+                        }
+                        if (c3 < kInf) s = s2 + c3;
+                    }
+                }
+            }
+        }
+        unsigned m = __ballot_sync(full, s < kInf);
+        while (m) {
+            const int k = __ffs(m) - 1;
+            m &= m - 1u;
+            const int ks = __shfl_sync(full, ts, k), kb = __shfl_sync(full, b_id, k), kc = __shfl_sync(full, c_id, k);
+            const float kv = __shfl_sync(full, s, k);
+            if (lane == ks && (kv < best_s || (kv == best_s && (kb < best_b || (kb == best_b && kc < best_c))))) {
+                best_s = kv;
+                best_b = kb;
+                best_c = kc;
+            }
+        }
+        // the queue's rest (fewer than 32 entries) to its front
+        const bool mv = lane + cnt < n_t;
+        int r_slot = 0, r_b = 0, r_c = 0;
+        float r_s2 = 0.f, r_kap = 0.f, r_nx = 0.f, r_ny = 0.f, r_d0 = 0.f;
+        if (mv) {
+            const int k = lane + cnt;
+            r_slot = q.t_slot[k]; r_b = q.t_b[k]; r_c = q.t_c[k]; r_s2 = q.t_s2[k];
+            r_kap = q.t_kap[k]; r_nx = q.t_nx[k]; r_ny = q.t_ny[k]; r_d0 = q.t_d0[k];
+        }
+        __syncwarp();
+        if (mv) {
+            q.t_slot[lane] = r_slot; q.t_b[lane] = r_b; q.t_c[lane] = r_c; q.t_s2[lane] = r_s2;
+            q.t_kap[lane] = r_kap; q.t_nx[lane] = r_nx; q.t_ny[lane] = r_ny; q.t_d0[lane] = r_d0;
+        }
+        n_t -= cnt;
+        __syncwarp();
+    };
+
+    // the circle through the first cnt queued candidates (a, b, c), one per lane: curvature and
+    // d0 cuts and the score without confirmation; passing triplets join the triplet queue
+    auto circle = [&](int cnt) {
+        const bool has = lane < cnt;
+        int fs = 0, fb = 0, fc = 0;
+        float dz = 0.f;
+        if (has) {
+            fs = q.f_slot[lane]; fb = q.f_b[lane]; fc = q.f_c[lane]; dz = q.f_dz[lane];
+        }
+        const float best_fs = __shfl_sync(full, best_s, fs);
+        bool pass = false;
+        float s2 = 0.f, kap = 0.f, nx = 0.f, ny = 0.f, d0 = 0.f;
+        if (has) {
+            const float4 A = q.a[fs], B = hxyzi[fb], Cc = hxyzi[fc];
+            const float bx = B.x - A.x, by = B.y - A.y, cx = Cc.x - A.x, cy = Cc.y - A.y;
+            const float det = bx * cy - by * cx;
+            if (det != 0.f) {
+                const float bb2 = bx * bx + by * by, cc2 = cx * cx + cy * cy;
+                const float wx = cy * bb2 - by * cc2, wy = bx * cc2 - cx * bb2;
+                const float wn = sqrtf(wx * wx + wy * wy);
+                kap = 2.f * fabsf(det) / wn;
+                const float sg = det > 0.f ? 1.f : -1.f;
+                nx = sg * wx / wn;
+                ny = sg * wy / wn;
+                d0 = kap * (A.x * A.x + A.y * A.y) * 0.5f + (A.x * nx + A.y * ny);
+                if (kap <= g.kmax && fabsf(d0) <= g.d0) {
+                    const float u = d0 / g.d0, v = dz / g.dz;
+                    s2 = u * u + v * v;
+                    pass = !(s2 > best_fs);  // the confirmation term only adds
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(full, pass);
+        if (pass) {
+            const int k = n_t + __popc(m & below);
+            q.t_slot[k] = fs; q.t_b[k] = fb; q.t_c[k] = fc; q.t_s2[k] = s2;
+            q.t_kap[k] = kap; q.t_nx[k] = nx; q.t_ny[k] = ny; q.t_d0[k] = d0;
+        }
+        n_t += __popc(m);
+        const bool mv = lane + cnt < n_f;
+        int r_slot = 0, r_b = 0, r_c = 0;
+        float r_dz = 0.f;
+        if (mv) {
+            r_slot = q.f_slot[lane + cnt]; r_b = q.f_b[lane + cnt]; r_c = q.f_c[lane + cnt]; r_dz = q.f_dz[lane + cnt];
+        }
+        __syncwarp();
+        if (mv) {
+            q.f_slot[lane] = r_slot; q.f_b[lane] = r_b; q.f_c[lane] = r_c; q.f_dz[lane] = r_dz;
+        }
+        n_f -= cnt;
+        __syncwarp();
+        if (n_t >= 32) confirm(32);
+    };
+
+    while (true) {
+        // (1) pairs: each lane tests the next hit of its first hit's layer-1 window
+        while (n_p < 32 && __any_sync(full, more)) {
+            bool pass = false;
+            int jb = 0;
+            float k01 = 0.f, slope = 0.f;
+            if (more) {
+                if (cb.j < cb.jend) {
+                    jb = cb.j++;
+                    const float4 B = hxyzi[jb];
+                    const float bx = B.x - ax, by = B.y - ay;
+                    const float chord01 = sqrtf(bx * bx + by * by);
+                    if (chord01 <= g.lim01 && chord01 != 0.f) {
+                        const float rb = sqrtf(B.x * B.x + B.y * B.y);
+                        k01 = 2.f * (ax * B.y - ay * B.x) / (ra * rb * chord01);
+                        if (fabsf(k01) <= g.kmax && rb != ra) {
+                            slope = (B.z - az) / (rb - ra);
+                            pass = fabsf(az - ra * slope) <= g.zv;
+                        }
+                    }
+                } else {
+                    more = cursor_next(g, bin_off, bin_sub, seg0 + 1, w1, cb);
+                }
+            }
+            const unsigned m = __ballot_sync(full, pass);
+            if (pass) {
+                const int k = n_p + __popc(m & below);
+                q.p_slot[k] = lane;
+                q.p_b[k] = jb;
+                q.p_k01[k] = k01;
+                q.p_slope[k] = slope;
+            }
+            n_p += __popc(m);
+        }
+        __syncwarp();
+        if (n_p == 0) break;
+        // (2) up to 32 queued pairs, one per lane: the layer-2 window of each
+        const int take = min(n_p, 32);
+        bool cmore = lane < take;
+        int ps = 0, pb = 0;
+        float k01 = 0.f, slope = 0.f;
+        if (cmore) {
+            ps = q.p_slot[lane]; pb = q.p_b[lane]; k01 = q.p_k01[lane]; slope = q.p_slope[lane];
+        }
         {
-            const float R2 = g.R[2];
-            const float zc = az + slope * (R2 - ra);
-            const float w = g.dz + 1e-3f + 1e-5f * fabsf(zc) + g.hit_dr * fabsf(slope);
-            eta_bins(g, R2, zc - w, zc + w, f0, f1);
+            const bool mv = lane + take < n_p;
+            int r_slot = 0, r_b = 0;
+            float r_k = 0.f, r_sl = 0.f;
+            if (mv) {
+                r_slot = q.p_slot[lane + take]; r_b = q.p_b[lane + take];
+                r_k = q.p_k01[lane + take]; r_sl = q.p_slope[lane + take];
+            }
+            __syncwarp();
+            if (mv) {
+                q.p_slot[lane] = r_slot; q.p_b[lane] = r_b; q.p_k01[lane] = r_k; q.p_slope[lane] = r_sl;
+            }
+            n_p -= take;
+        }
+        float4 A = make_float4(0.f, 0.f, 0.f, 1.f);
+        float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
+        float rb = 0.f;
+        int pseg = 0;
+        Cursor cc{0, -1, 0, 0, 0};
+        PhiWin w2;
+        w2.lo[0] = w2.lo[1] = 0;
+        w2.hi[0] = w2.hi[1] = -1;
+        if (cmore) {
+            A = q.a[ps];
+            pseg = q.seg0[ps];
+            B = hxyzi[pb];
+            rb = sqrtf(B.x * B.x + B.y * B.y);
+            // layer-2 window: z along the r-z line of a and b, phi around the crossing of the circle
+            // through the beam line, a and b, widened by the d0 cut's lever arm
+            const float R2 = g.R[2], ra_ = A.w;
+            const float zc = A.z + slope * (R2 - ra_);
+            const float wz = g.dz + 1e-3f + 1e-5f * fabsf(zc) + g.hit_dr * fabsf(slope);
+            eta_bins(g, R2, zc - wz, zc + wz, cc.eb, cc.e1);
             // the circles through a and b that pass within d0 of the beam line differ from the one
             // through it by about d0 (R2 - ra) (R2 - rb) / (ra rb) at R2: twice that, plus slack
-            const float s2 = k01 * R2 * 0.5f;
-            float half = 4.f, mid = pha;
+            float half = 4.f, mid = q.pha[ps];
             if (fabsf(k01) * (R2 + g.hit_dr) * 0.5f < 1.f) {
-                const float lever = (R2 - ra) * (R2 - rb) / (ra * rb);
+                const float lever = (R2 - ra_) * (R2 - rb) / (ra_ * rb);
                 half = (2.f * g.d0 * fabsf(lever) + 0.01f + 2.f * g.hit_dr * fabsf(k01)) / (R2 - g.hit_dr) + 2e-3f;
-                mid = pha + asinf(s2) - asinf(k01 * ra * 0.5f);
+                mid = q.pha[ps] + asinf(k01 * R2 * 0.5f) - asinf(k01 * ra_ * 0.5f);
             }
-            phi_bins(g, mid, half, q0, nq);
+            w2 = phi_window(g, mid, half);
         }
-        const float bb2 = bx * bx + by * by;
-        for_window(g, bin_off, seg0 + 2, f0, f1, q0, nq, [&](int jc) {
-            const float4 Cc = hxyzi[jc];
-            const float d12x = Cc.x - B.x, d12y = Cc.y - B.y;
-            if (!(sqrtf(d12x * d12x + d12y * d12y) <= g.lim12)) return;
-            const float cx = Cc.x - ax, cy = Cc.y - ay;
-            const float det = bx * cy - by * cx;
-            if (det == 0.f) return;
-            const float cc2 = cx * cx + cy * cy;
-            const float wx = cy * bb2 - by * cc2, wy = bx * cc2 - cx * bb2;
-            const float wn = sqrtf(wx * wx + wy * wy);
-            const float kap = 2.f * fabsf(det) / wn;
-            if (!(kap <= g.kmax)) return;
-            const float sg = det > 0.f ? 1.f : -1.f;
-            const float nx = sg * wx / wn, ny = sg * wy / wn;
-            const float d0 = kap * ra2 * 0.5f + (ax * nx + ay * ny);
-            const float rc = sqrtf(Cc.x * Cc.x + Cc.y * Cc.y);
-            const float dz = Cc.z - (az + slope * (rc - ra));
-            if (!(fabsf(d0) <= g.d0) || !(fabsf(dz) <= g.dz)) return;
-            const float u = d0 / g.d0, v = dz / g.dz;
-            const float s2 = u * u + v * v;
-            if (s2 > best_s) return;  // the confirmation term only adds
-            const int c_id = __float_as_int(Cc.w);
-            float c3 = 0.f;
-            if (g.confirm) {
-                if (rc == rb) return;
-                const float slope23 = (Cc.z - B.z) / (rc - rb);
-                // where the circle crosses r = R3 nearest to c: centre U = a + w / (2 det); the
-                // crossing lies along U at a = (R3^2 + 2 rho d0) / (2 |U|) (|U|^2 - rho^2 = 2 rho d0)
-                const float rho = 1.f / kap;
-                const float ux = ax + wx / (2.f * det), uy = ay + wy / (2.f * det);
-                const float D = sqrtf(ux * ux + uy * uy);
-                const float R3 = g.R[3];
-                const float along = (R3 * R3 + 2.f * rho * d0) / (2.f * D);
-                const float h2 = R3 * R3 - along * along;
-                if (!(h2 >= 0.f)) return;
-                const float h = sqrtf(h2), ex = ux / D, ey = uy / D;
-                const float px1 = along * ex - h * ey, py1 = along * ey + h * ex;
-                const float px2 = along * ex + h * ey, py2 = along * ey - h * ex;
-                const bool first = (px1 - Cc.x) * (px1 - Cc.x) + (py1 - Cc.y) * (py1 - Cc.y) <=
-                                   (px2 - Cc.x) * (px2 - Cc.x) + (py2 - Cc.y) * (py2 - Cc.y);
-                const float ph3 = atan2f(first ? py1 : py2, first ? px1 : px2);
-                const float zc3 = B.z + slope23 * (R3 - rb);
-                int h0b, h1b, r0, nr;
-                const float wz = g.z3 + 1e-3f + 1e-5f * fabsf(zc3) + g.hit_dr * fabsf(slope23);
-                eta_bins(g, R3, zc3 - wz, zc3 + wz, h0b, h1b);
-                phi_bins(g, ph3, (3.f * g.w3 + 0.02f + 2.f * g.hit_dr * kap) / (R3 - g.hit_dr) + 2e-3f, r0, nr);
-                c3 = kInf;
-                for_window(g, bin_off, seg0 + 3, h0b, h1b, r0, nr, [&](int je) {
-                    const float4 E = hxyzi[je];
-                    const float d23x = E.x - Cc.x, d23y = E.y - Cc.y;
-                    if (!(sqrtf(d23x * d23x + d23y * d23y) <= g.lim23)) return;
-                    const float qx = E.x - ax, qy = E.y - ay;
-                    const float f3 = kap * (qx * qx + qy * qy) * 0.5f - (qx * nx + qy * ny);
-                    const float re = sqrtf(E.x * E.x + E.y * E.y);
-                    const float dz3 = E.z - (B.z + slope23 * (re - rb));
-                    if (!(fabsf(f3) <= g.w3) || !(fabsf(dz3) <= g.z3)) return;
-                    const float p = f3 / g.w3, q = dz3 / g.z3;
-                    c3 = fminf(c3, p * p + q * q);
-                });
-                if (c3 == kInf) return;
+        __syncwarp();
+        // (3) each lane tests the next hit of its pair's layer-2 window against the chord and z
+        // cuts; the queue of those that pass goes through the circle cuts whenever it holds 32
+        while (__any_sync(full, cmore)) {
+            bool pass = false;
+            int jc = 0;
+            float dz = 0.f;
+            if (cmore) {
+                if (cc.j < cc.jend) {
+                    jc = cc.j++;
+                    const float4 Cc = hxyzi[jc];
+                    const float d12x = Cc.x - B.x, d12y = Cc.y - B.y;
+                    const float rc = sqrtf(Cc.x * Cc.x + Cc.y * Cc.y);
+                    dz = Cc.z - (A.z + slope * (rc - A.w));
+                    pass = sqrtf(d12x * d12x + d12y * d12y) <= g.lim12 && fabsf(dz) <= g.dz;
+                } else {
+                    cmore = cursor_next(g, bin_off, bin_sub, pseg + 2, w2, cc);
+                }
             }
-            const float s = s2 + c3;
-            if (s < best_s || (s == best_s && (b_id < best_b || (b_id == best_b && c_id < best_c)))) {
-                best_s = s;
-                best_b = b_id;
-                best_c = c_id;
+            const unsigned m = __ballot_sync(full, pass);
+            if (pass) {
+                const int k = n_f + __popc(m & below);
+                q.f_slot[k] = ps; q.f_b[k] = pb; q.f_c[k] = jc; q.f_dz[k] = dz;
             }
-        });
-    });
+            n_f += __popc(m);
+            __syncwarp();
+            if (n_f >= 32) circle(32);
+        }
+    }
+    if (n_f > 0) circle(n_f);
+    if (n_t > 0) confirm(n_t);
+    if (!valid || t >= n) {
+        if (t < n) res_b[t] = -1;
+        return;
+    }
     if (best_s < kInf) {
         const int base = __ldg(&ev_off[e]);
         res_b[t] = base + best_b;
@@ -418,7 +674,7 @@ extern "C" int tkf_find_seeds(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_
     g.lim23 = (float)(2.0 * (c.radius[3] - c.radius[2]));
     g.hit_dr = (float)c.hit_dr;
     g.confirm = cuts->confirm != 0;
-    k_seed_find<<<blocks, kSeedThreads, 0, s>>>(g, idx->hxyzi, idx->bin_off, idx->ev_off, n, ctx->seed_b,
+    k_seed_find<<<blocks, kSeedThreads, 0, s>>>(g, idx->hxyzi, idx->bin_off, idx->bin_sub, idx->ev_off, n, ctx->seed_b,
                                                 ctx->seed_c, ctx->seed_s);
     k_seed_count<<<blocks, kSeedThreads, 0, s>>>(ctx->seed_b, n, ctx->seed_cnt);
     k_seed_scan<<<1, 1024, 0, s>>>(ctx->seed_cnt, blocks, n_found);
