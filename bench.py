@@ -104,9 +104,9 @@ KERNELS_PER_STEP = 12
 # summary in profiles/); None whenever a kernel changes until it is captured again
 BUILD_DRAM_BYTES_PER_SEED = 795.1
 # warp instructions of k_seed_find per layer-0 hit and active lanes per instruction, from one ncu
-# capture of the 160-event seeding case (3.522 G instructions for 932 025 first hits; summary in
+# capture of the 160-event seeding case (3.185 G instructions for 932 025 first hits; summary in
 # profiles/); None whenever the kernel changes until it is captured again
-SEED_WARP_INST_PER_FIRST_HIT, SEED_LANES_ACTIVE = 3778.6, 18.32
+SEED_WARP_INST_PER_FIRST_HIT, SEED_LANES_ACTIVE = 3417.5, 19.01
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
 ISSUE_PEAK_WARP_INST_PER_S = SM_COUNT * 4 * SM_MAX_GHZ * 1e9
 

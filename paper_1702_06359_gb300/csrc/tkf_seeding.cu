@@ -115,34 +115,69 @@ __device__ __forceinline__ int sixteenth_start(const uint4 w, int t)
 }
 
 // A walk over the hits of a window: eta rows eb .. e1 of one (event, layer) segment, runs 0 and 1
-// of the phi window in each row; [j, jend) is the current run's range of sorted positions.
-struct Cursor {
-    int eb, e1, r, j, jend;
+// of the phi window in each row.  [j, jend) is the range being read; [jn, jen) the next one,
+// fetched ahead (its index loads are issued when the walk moves to the current range, so they
+// arrive while the current range is read); (eb, r) is the row and run the fetch after that takes.
+struct Walk {
+    int eb, e1, r, j, jend, jn, jen;
 };
 
-// Moves the cursor to its next non-empty run; false when the window is exhausted.
-__device__ __forceinline__ bool cursor_next(const SeedGeom &g, const int *bin_off, const uint4 *bin_sub, int seg,
-                                            const PhiWin &w, Cursor &c)
+// the positions of run r of the phi window in eta row eb of segment seg
+__device__ __forceinline__ void run_range(const SeedGeom &g, const int *bin_off, const uint4 *bin_sub, int seg,
+                                          int eb, int lo, int hi, int &j, int &jend)
 {
-    while (c.eb <= c.e1) {
-        if (c.r >= 2) {
-            c.r = 0;
-            ++c.eb;
+    const int row = seg * g.n_bins + eb * g.n_phi;
+    const int ps0 = lo & (kSubBins - 1), ps1 = hi & (kSubBins - 1);
+    const int ba = row + lo / kSubBins, bb = row + hi / kSubBins;
+    const int oa = __ldg(&bin_off[ba]), ob = __ldg(&bin_off[bb]), ob1 = __ldg(&bin_off[bb + 1]);
+    const uint4 wa = __ldg(&bin_sub[ba]), wb = __ldg(&bin_sub[bb]);
+    j = oa + ((ps0 <= 0 || wa.w == 0xFFFFFFFFu) ? 0 : sixteenth_start(wa, ps0));
+    jend = ob + ((ps1 >= kSubBins - 1 || wb.w == 0xFFFFFFFFu) ? ob1 - ob : sixteenth_start(wb, ps1 + 1));
+}
+
+// fetches the next run of the window into [jn, jen) (empty once the window is exhausted)
+__device__ __forceinline__ void walk_fetch(const SeedGeom &g, const int *bin_off, const uint4 *bin_sub, int seg,
+                                           const PhiWin &w, Walk &k)
+{
+    k.jn = k.jen = 0;
+    while (k.eb <= k.e1) {
+        if (k.r >= 2) {
+            k.r = 0;
+            ++k.eb;
             continue;
         }
-        const int lo = c.r == 0 ? w.lo[0] : w.lo[1], hi = c.r == 0 ? w.hi[0] : w.hi[1];
-        ++c.r;
+        const int lo = k.r == 0 ? w.lo[0] : w.lo[1], hi = k.r == 0 ? w.hi[0] : w.hi[1];
+        ++k.r;
         if (hi < lo) continue;
-        const int row = seg * g.n_bins + c.eb * g.n_phi;
-        const int ps0 = lo & (kSubBins - 1), ps1 = hi & (kSubBins - 1);
-        const int ba = row + lo / kSubBins, bb = row + hi / kSubBins;
-        const int oa = __ldg(&bin_off[ba]), ob = __ldg(&bin_off[bb]), ob1 = __ldg(&bin_off[bb + 1]);
-        const uint4 wa = __ldg(&bin_sub[ba]), wb = __ldg(&bin_sub[bb]);
-        c.j = oa + ((ps0 <= 0 || wa.w == 0xFFFFFFFFu) ? 0 : sixteenth_start(wa, ps0));
-        c.jend = ob + ((ps1 >= kSubBins - 1 || wb.w == 0xFFFFFFFFu) ? ob1 - ob : sixteenth_start(wb, ps1 + 1));
-        if (c.j < c.jend) return true;
+        run_range(g, bin_off, bin_sub, seg, k.eb, lo, hi, k.jn, k.jen);
+        return;
     }
-    return false;
+}
+
+// a walk over eta rows e0 .. e1: the first run current, the second fetched
+__device__ __forceinline__ Walk walk_start(const SeedGeom &g, const int *bin_off, const uint4 *bin_sub, int seg,
+                                           const PhiWin &w, int e0, int e1)
+{
+    Walk k{e0, e1, 0, 0, 0, 0, 0};
+    walk_fetch(g, bin_off, bin_sub, seg, w, k);
+    k.j = k.jn;
+    k.jend = k.jen;
+    walk_fetch(g, bin_off, bin_sub, seg, w, k);
+    return k;
+}
+
+// the next hit position of the walk: false when exhausted; moves over empty runs
+__device__ __forceinline__ bool walk_next(const SeedGeom &g, const int *bin_off, const uint4 *bin_sub, int seg,
+                                          const PhiWin &w, Walk &k, int &pos)
+{
+    while (k.j >= k.jend) {
+        if (k.jn >= k.jen && k.eb > k.e1) return false;
+        k.j = k.jn;
+        k.jend = k.jen;
+        walk_fetch(g, bin_off, bin_sub, seg, w, k);
+    }
+    pos = k.j++;
+    return true;
 }
 
 // Queues of one warp: its 32 first hits (slot = lane), passing pairs waiting for their layer-2
@@ -150,21 +185,23 @@ __device__ __forceinline__ bool cursor_next(const SeedGeom &g, const int *bin_of
 // three, passing triplets waiting for their confirmation scan.  Entries are appended in (step,
 // lane) order, so the queues' contents do not depend on timing.
 constexpr int kQueue = 64;
+constexpr int kQueueF = 96;  // a step appends up to 64 to fewer than 32 queued
 struct WarpQueues {
     float4 a[32];  // x, y, z, r of the slot's first hit
     float pha[32];
     int seg0[32];  // event * L
     int p_slot[kQueue], p_b[kQueue];
     float p_k01[kQueue], p_slope[kQueue];
-    int f_slot[kQueue], f_b[kQueue], f_c[kQueue];
-    float f_dz[kQueue];
+    int f_slot[kQueueF], f_b[kQueueF], f_c[kQueueF];
+    float f_dz[kQueueF];
     int t_slot[kQueue], t_b[kQueue], t_c[kQueue];
     float t_s2[kQueue], t_kap[kQueue], t_nx[kQueue], t_ny[kQueue], t_d0[kQueue];
 };
 
 // Every lane reaches the warp-wide operations below: the loops are warp-uniform, and the lanes
 // without work carry their flags through them.
-// Held to 3 blocks of 256 threads per SM.
+// Held to 3 blocks of 256 threads per SM (80 registers, a few bytes spilled; the queues take
+// 42 KB of shared memory per block).
 #ifndef TKF_SEED_MINBLOCKS
 #define TKF_SEED_MINBLOCKS 3
 #endif
@@ -203,7 +240,8 @@ k_seed_find(const SeedGeom g, const float4 *__restrict__ hxyzi, const int *__res
     int best_b = 0x7fffffff, best_c = 0x7fffffff;
 
     // layer-1 window: circles from the beam line through a with |kappa| <= kmax, z-vertex cut
-    Cursor cb{0, -1, 0, 0, 0};
+    Walk cb{0, -1, 0, 0, 0, 0, 0};
+    int e0 = 0, e1 = -1;
     PhiWin w1;
     w1.lo[0] = w1.lo[1] = 0;
     w1.hi[0] = w1.hi[1] = -1;
@@ -213,10 +251,11 @@ k_seed_find(const SeedGeom g, const float4 *__restrict__ hxyzi, const int *__res
         const float zpad = 1e-3f + 1e-5f * fabsf(az);
         const float zc_lo = fminf(az * rlo / ra - g.zv * (rlo / ra - 1.f), az * rhi / ra - g.zv * (rhi / ra - 1.f));
         const float zc_hi = fmaxf(az * rlo / ra + g.zv * (rlo / ra - 1.f), az * rhi / ra + g.zv * (rhi / ra - 1.f));
-        eta_bins(g, R1, zc_lo - zpad, zc_hi + zpad, cb.eb, cb.e1);
+        eta_bins(g, R1, zc_lo - zpad, zc_hi + zpad, e0, e1);
         const float s1 = g.kmax * rhi * 0.5f;
         const float half = s1 >= 1.f ? 4.f : asinf(s1) - asinf(g.kmax * ra * 0.5f) + 2e-3f;
         w1 = phi_window(g, pha, half);
+        cb = walk_start(g, bin_off, bin_sub, seg0 + 1, w1, e0, e1);
     }
     bool more = valid;
     __syncwarp();
@@ -261,16 +300,18 @@ k_seed_find(const SeedGeom g, const float4 *__restrict__ hxyzi, const int *__res
                                            (px2 - Cc.x) * (px2 - Cc.x) + (py2 - Cc.y) * (py2 - Cc.y);
                         const float ph3 = atan2f(first ? py1 : py2, first ? px1 : px2);
                         const float zc3 = B.z + slope23 * (R3 - rb);
-                        Cursor ce{0, -1, 0, 0, 0};
+                        int h0b, h1b;
                         const float wz = g.z3 + 1e-3f + 1e-5f * fabsf(zc3) + g.hit_dr * fabsf(slope23);
-                        eta_bins(g, R3, zc3 - wz, zc3 + wz, ce.eb, ce.e1);
+                        eta_bins(g, R3, zc3 - wz, zc3 + wz, h0b, h1b);
                         const PhiWin w3 =
                             phi_window(g, ph3, (3.f * g.w3 + 0.02f + 2.f * g.hit_dr * kap) / (R3 - g.hit_dr) + 2e-3f);
                         const int seg3 = q.seg0[ts] + 3;
+                        Walk ce = walk_start(g, bin_off, bin_sub, seg3, w3, h0b, h1b);
                         float c3 = kInf;
-                        while (cursor_next(g, bin_off, bin_sub, seg3, w3, ce)) {
-                            for (; ce.j < ce.jend; ++ce.j) {
-                                const float4 E = hxyzi[ce.j];
+                        int je;
+                        while (walk_next(g, bin_off, bin_sub, seg3, w3, ce, je)) {
+                            {
+                                const float4 E = hxyzi[je];
                                 const float d23x = E.x - Cc.x, d23y = E.y - Cc.y;
                                 if (!(sqrtf(d23x * d23x + d23y * d23y) <= g.lim23)) continue;
                                 const float qx = E.x - A.x, qy = E.y - A.y;
@@ -356,15 +397,21 @@ k_seed_find(const SeedGeom g, const float4 *__restrict__ hxyzi, const int *__res
             q.t_kap[k] = kap; q.t_nx[k] = nx; q.t_ny[k] = ny; q.t_d0[k] = d0;
         }
         n_t += __popc(m);
-        const bool mv = lane + cnt < n_f;
-        int r_slot = 0, r_b = 0, r_c = 0;
-        float r_dz = 0.f;
-        if (mv) {
-            r_slot = q.f_slot[lane + cnt]; r_b = q.f_b[lane + cnt]; r_c = q.f_c[lane + cnt]; r_dz = q.f_dz[lane + cnt];
-        }
-        __syncwarp();
-        if (mv) {
-            q.f_slot[lane] = r_slot; q.f_b[lane] = r_b; q.f_c[lane] = r_c; q.f_dz[lane] = r_dz;
+        // the queue's rest (up to 63 entries) to its front, 32 at a time
+        for (int base = 0; base < n_f - cnt; base += 32) {
+            const bool mv = base + lane + cnt < n_f;
+            int r_slot = 0, r_b = 0, r_c = 0;
+            float r_dz = 0.f;
+            if (mv) {
+                const int k = base + lane + cnt;
+                r_slot = q.f_slot[k]; r_b = q.f_b[k]; r_c = q.f_c[k]; r_dz = q.f_dz[k];
+            }
+            __syncwarp();
+            if (mv) {
+                const int k = base + lane;
+                q.f_slot[k] = r_slot; q.f_b[k] = r_b; q.f_c[k] = r_c; q.f_dz[k] = r_dz;
+            }
+            __syncwarp();
         }
         n_f -= cnt;
         __syncwarp();
@@ -378,8 +425,8 @@ k_seed_find(const SeedGeom g, const float4 *__restrict__ hxyzi, const int *__res
             int jb = 0;
             float k01 = 0.f, slope = 0.f;
             if (more) {
-                if (cb.j < cb.jend) {
-                    jb = cb.j++;
+                more = walk_next(g, bin_off, bin_sub, seg0 + 1, w1, cb, jb);
+                if (more) {
                     const float4 B = hxyzi[jb];
                     const float bx = B.x - ax, by = B.y - ay;
                     const float chord01 = sqrtf(bx * bx + by * by);
@@ -391,8 +438,6 @@ k_seed_find(const SeedGeom g, const float4 *__restrict__ hxyzi, const int *__res
                             pass = fabsf(az - ra * slope) <= g.zv;
                         }
                     }
-                } else {
-                    more = cursor_next(g, bin_off, bin_sub, seg0 + 1, w1, cb);
                 }
             }
             const unsigned m = __ballot_sync(full, pass);
@@ -433,7 +478,7 @@ k_seed_find(const SeedGeom g, const float4 *__restrict__ hxyzi, const int *__res
         float4 B = make_float4(0.f, 0.f, 0.f, 0.f);
         float rb = 0.f;
         int pseg = 0;
-        Cursor cc{0, -1, 0, 0, 0};
+        Walk cc{0, -1, 0, 0, 0, 0, 0};
         PhiWin w2;
         w2.lo[0] = w2.lo[1] = 0;
         w2.hi[0] = w2.hi[1] = -1;
@@ -447,7 +492,8 @@ k_seed_find(const SeedGeom g, const float4 *__restrict__ hxyzi, const int *__res
             const float R2 = g.R[2], ra_ = A.w;
             const float zc = A.z + slope * (R2 - ra_);
             const float wz = g.dz + 1e-3f + 1e-5f * fabsf(zc) + g.hit_dr * fabsf(slope);
-            eta_bins(g, R2, zc - wz, zc + wz, cc.eb, cc.e1);
+            int f0, f1;
+            eta_bins(g, R2, zc - wz, zc + wz, f0, f1);
             // the circles through a and b that pass within d0 of the beam line differ from the one
             // through it by about d0 (R2 - ra) (R2 - rb) / (ra rb) at R2: twice that, plus slack
             float half = 4.f, mid = q.pha[ps];
@@ -457,34 +503,46 @@ k_seed_find(const SeedGeom g, const float4 *__restrict__ hxyzi, const int *__res
                 mid = q.pha[ps] + asinf(k01 * R2 * 0.5f) - asinf(k01 * ra_ * 0.5f);
             }
             w2 = phi_window(g, mid, half);
+            cc = walk_start(g, bin_off, bin_sub, pseg + 2, w2, f0, f1);
         }
         __syncwarp();
-        // (3) each lane tests the next hit of its pair's layer-2 window against the chord and z
-        // cuts; the queue of those that pass goes through the circle cuts whenever it holds 32
+        // (3) each lane tests the next two hits of its pair's layer-2 window against the chord and
+        // z cuts; the queue of those that pass goes through the circle cuts 32 at a time.  (One hit
+        // per step: 17.3 ms on the 640-event seeding batch, two: 15.8 ms, four: 16.7 ms; two
+        // layer-1 hits per pair step were slower too.)
+        const float lim12sq = g.lim12 * g.lim12;
+        auto near_z = [&](int jc, float &dz) {
+            const float4 Cc = hxyzi[jc];
+            const float d12x = Cc.x - B.x, d12y = Cc.y - B.y;
+            const float rc = sqrtf(Cc.x * Cc.x + Cc.y * Cc.y);
+            dz = Cc.z - (A.z + slope * (rc - A.w));
+            return d12x * d12x + d12y * d12y <= lim12sq && fabsf(dz) <= g.dz;
+        };
         while (__any_sync(full, cmore)) {
-            bool pass = false;
-            int jc = 0;
-            float dz = 0.f;
+            bool p0 = false, p1 = false;
+            int jc0 = 0, jc1 = 0;
+            float dz0 = 0.f, dz1 = 0.f;
             if (cmore) {
-                if (cc.j < cc.jend) {
-                    jc = cc.j++;
-                    const float4 Cc = hxyzi[jc];
-                    const float d12x = Cc.x - B.x, d12y = Cc.y - B.y;
-                    const float rc = sqrtf(Cc.x * Cc.x + Cc.y * Cc.y);
-                    dz = Cc.z - (A.z + slope * (rc - A.w));
-                    pass = sqrtf(d12x * d12x + d12y * d12y) <= g.lim12 && fabsf(dz) <= g.dz;
-                } else {
-                    cmore = cursor_next(g, bin_off, bin_sub, pseg + 2, w2, cc);
+                cmore = walk_next(g, bin_off, bin_sub, pseg + 2, w2, cc, jc0);
+                if (cmore) {
+                    p0 = near_z(jc0, dz0);
+                    cmore = walk_next(g, bin_off, bin_sub, pseg + 2, w2, cc, jc1);
+                    if (cmore) p1 = near_z(jc1, dz1);
                 }
             }
-            const unsigned m = __ballot_sync(full, pass);
-            if (pass) {
-                const int k = n_f + __popc(m & below);
-                q.f_slot[k] = ps; q.f_b[k] = pb; q.f_c[k] = jc; q.f_dz[k] = dz;
+            const unsigned m0 = __ballot_sync(full, p0), m1 = __ballot_sync(full, p1);
+            if (p0) {
+                const int k = n_f + __popc(m0 & below);
+                q.f_slot[k] = ps; q.f_b[k] = pb; q.f_c[k] = jc0; q.f_dz[k] = dz0;
             }
-            n_f += __popc(m);
+            n_f += __popc(m0);
+            if (p1) {
+                const int k = n_f + __popc(m1 & below);
+                q.f_slot[k] = ps; q.f_b[k] = pb; q.f_c[k] = jc1; q.f_dz[k] = dz1;
+            }
+            n_f += __popc(m1);
             __syncwarp();
-            if (n_f >= 32) circle(32);
+            while (n_f >= 32) circle(32);
         }
     }
     if (n_f > 0) circle(n_f);
