@@ -1,6 +1,6 @@
-"""Host-side logic of bench.py (no GPU): the building-efficiency measure, the layout of events
-lent to the server, the balanced dealing of oracle events to host cores, and the sample
-selection."""
+"""Host-side logic of bench.py (no GPU): the building-efficiency measure and the seeding leg's
+tracking measure, the layout of events lent to the server, the balanced dealing of oracle events
+to host cores, and the sample selection."""
 import ctypes as C
 
 import numpy as np
@@ -122,3 +122,26 @@ def test_issue_roofline_arithmetic():
     assert r["peak"] == pytest.approx(152 * 4 * 2.07e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert bench.issue_roofline(None, 1, 1.0) is None
+
+
+def test_seeded_efficiency_counts_found_fake_and_duplicate(small_batch):
+    """The seeding leg's tracking measure: with one seed per track on its own hits every track is
+    found; a second seed of a track is a duplicate; a seed that starts on a noise hit, or whose
+    built track has fewer than 75 % of one track's hits, is a fake."""
+    b = small_batch
+    truth = b.trk_hits.T.copy()  # [L, n]
+    first = truth[0].copy()
+    r = bench.seeded_efficiency(b, first, truth)
+    assert r == {"track_efficiency": 1.0, "fake_rate": 0.0, "duplicate_rate": 0.0}
+    # track 0 seeded twice, track 1's built track mostly noise, one seed on a noise hit
+    noise = np.nonzero(b.mc < 0)[0]
+    hits = np.concatenate([truth, truth[:, :1], truth[:, :1]], axis=1)
+    firsts = np.concatenate([first, first[:1], [noise[0]]])
+    hits[:, -1] = -1
+    hits[0, -1] = noise[0]
+    hits[3:6, 1] = noise[1:4]  # 7 of 10 own: below 75 %
+    r = bench.seeded_efficiency(b, firsts, hits)
+    n = b.n_tracks
+    assert r["track_efficiency"] == pytest.approx((n - 1) / n)
+    assert r["fake_rate"] == pytest.approx(2 / (n + 2))
+    assert r["duplicate_rate"] == pytest.approx(1 / (n - 1))
