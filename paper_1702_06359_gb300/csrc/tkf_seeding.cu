@@ -1,15 +1,17 @@
 // Seeding from hit triplets on layers 0, 1, 2 with a confirmation hit on layer 3 (the seeding
 // stage of Sec. 2, which the paper names without specifying): tkf_find_seeds.
 //
-// Each hit of layer 0 takes one thread, which walks the hit index: the layer-1 bins that a
-// circle from the beam line through the hit can reach with |curvature| <= kappa_max and a
-// z-vertex within z_vertex, then for every pair that passes the layer-2 bins around the
-// pair's extrapolation, then for every triplet that passes the layer-3 bins around the
-// triplet circle's crossing.  The windows only choose bins; every hit in them is tested
-// against the exact cuts, so the seeds are those of a scan over all hits of the layers.  The
-// thread keeps its triplet of smallest score; seeds are then compacted in the index order of
-// their first hits (event by event, eta-phi bin by bin), which keeps a warp's seeds near one
-// another for the building that follows.
+// The search walks the hit index: for each layer-0 hit, the layer-1 cells (eta row, phi
+// sixteenths) that a circle from the beam line through the hit can reach with |curvature| <=
+// kappa_max and a z-vertex within z_vertex; for every pair that passes, the layer-2 cells around
+// the pair's extrapolation; for every triplet that passes, the layer-3 cells around the triplet
+// circle's crossing.  The windows only choose index ranges; every hit in them is tested against
+// the exact cuts, so the seeds are those of a scan over all hits of the layers.  A warp owns 32
+// consecutive index positions and shares their work out over its lanes through queues in shared
+// memory (k_seed_find below); the lane of each layer-0 hit keeps that hit's triplet of smallest
+// score.  Seeds are then compacted in the index order of their first hits (event by event,
+// eta-phi cell by cell), which keeps a warp's seeds near one another for the building that
+// follows.
 //
 // Circle quantities are evaluated in the frame of the first hit a: with b' = b - a and
 // c' = c - a, the circle through a, b, c has centre a + w / (2 det) (det = b' x c',
