@@ -163,6 +163,20 @@ def test_truncation_single_track_events_and_errors():
         ctx.find_seeds(idx, _cuts(), -1, buf, ev, nf)
 
 
+def test_empty_events_and_empty_batch():
+    """An event without hits between others starts no seed and leaves the others unchanged; a
+    batch without any hit finds none."""
+    b = generate(EventSpec(seed=86, n_events=3, n_tracks=np.array([150, 0, 90]), noise_frac=0.2), PIX)
+    assert b.hit_off[1] == b.hit_off[2]
+    gpu = _gpu_seeds(b, _cuts())
+    assert gpu["n"] > 200 and not np.any(gpu["event"] == 1)
+    _compare(b, gpu, _oracle_picks(b, _cuts(True), events=[0, 2]), min_seeds=250)
+    _check_order(b, gpu)
+    empty = generate(EventSpec(seed=87, n_events=2, n_tracks=np.array([0, 0]), noise_frac=0.0), PIX)
+    assert empty.n_hits == 0
+    assert _gpu_seeds(empty, _cuts(), max_seeds=4)["n"] == 0
+
+
 def test_seeds_feed_the_pipeline():
     """Seeds found on the device go straight into tkf_pipeline_run (the seed rows and event
     ids it takes), and the built tracks of true seeds carry their tracks' hits."""
