@@ -244,7 +244,7 @@ void tkf_default_seed_cuts(tkf_seed_cuts *cuts);
  * Seeds are ordered by event, then by the index position of their layer-0 hit (eta bin, phi
  * bin, phi sixteenth, hit id).  Scratch (12 bytes per indexed hit) is held by the context.
  * Errors: TKF_ERR_INVALID (null pointers, cuts not positive, fewer than 4 layers, a disk among
- * layers 0..3), TKF_ERR_NOMEM, TKF_ERR_CUDA. */
+ * layers 0..3, an index binned by another configuration), TKF_ERR_NOMEM, TKF_ERR_CUDA. */
 int tkf_find_seeds(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_seed_cuts *cuts, int32_t max_seeds,
                    int32_t *seed_hits, int32_t *seed_event, float *seed_score, int32_t *n_found, tkf_stream stream);
 

@@ -678,8 +678,9 @@ extern "C" int tkf_find_seeds(tkf_ctx *ctx, const tkf_hit_index *idx, const tkf_
     if (!idx || !cuts || !n_found || max_seeds < 0 || (max_seeds > 0 && (!seed_hits || !seed_event)))
         return seed_fail(ctx, TKF_ERR_INVALID, "find_seeds: null argument or negative max_seeds");
     const tkf_config &c = ctx->cfg;
-    if (c.n_layers < 4 || idx->n_layers != c.n_layers)
-        return seed_fail(ctx, TKF_ERR_INVALID, "find_seeds: needs an index of at least 4 layers of this context");
+    if (c.n_layers < 4 || idx->n_layers != c.n_layers || idx->n_bins != c.n_eta_bins * c.n_phi_bins)
+        return seed_fail(ctx, TKF_ERR_INVALID,
+                         "find_seeds: needs an index of at least 4 layers built with this context's bins");
     for (int l = 0; l < 4; ++l)
         if (c.disk_z[l] > 0.0) return seed_fail(ctx, TKF_ERR_INVALID, "find_seeds: layers 0..3 must be cylinders");
     if (!(cuts->pt_min > 0) || !(cuts->kappa_slack >= 0) || !(cuts->z_vertex > 0) || !(cuts->d0_max > 0) ||

@@ -161,6 +161,10 @@ def test_truncation_single_track_events_and_errors():
             ctx.find_seeds(idx, _cuts(**bad), 8, buf, ev, nf)
     with pytest.raises(tkf.TkfError):
         ctx.find_seeds(idx, _cuts(), -1, buf, ev, nf)
+    # an index binned by another configuration
+    other = tkf.Context(tkf.default_config(n_eta_bins=20, eta_bin_w=0.2))
+    with pytest.raises(tkf.TkfError):
+        other.find_seeds(idx, _cuts(), 8, buf, ev, nf)
 
 
 def test_empty_events_and_empty_batch():
