@@ -100,33 +100,39 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(compile_library())
-        dp, ip, vp = C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p
-        L.orc_propagate.argtypes = [C.POINTER(Geom), dp, C.c_double, dp, dp]
-        L.orc_propagate_plane.argtypes = [C.POINTER(Geom), dp, C.c_double, dp, dp]
-        L.orc_hit_eta_bin.argtypes = [C.POINTER(Geom), C.POINTER(Hit)]
-        L.orc_scatter.argtypes = [C.POINTER(Geom), C.c_int, dp, dp]
-        L.orc_scatter.restype = None
-        L.orc_chi2.argtypes = [dp, dp, C.POINTER(Hit)]
-        L.orc_chi2.restype = C.c_double
-        L.orc_update.argtypes = [dp, dp, C.POINTER(Hit), dp]
-        L.orc_seed_batch.argtypes = [C.POINTER(Geom), vp, C.c_int, ip, dp, dp]
-        L.orc_fit_batch.argtypes = [C.POINTER(Geom), vp, C.c_int, dp, dp, ip, C.c_int, C.c_int, dp, dp, dp, ip, ip]
-        L.orc_fit_backward_batch.argtypes = [C.POINTER(Geom), vp, C.c_int, dp, dp, C.c_double, ip, C.c_int, C.c_int,
-                                             dp, dp, dp, ip, ip]
-        L.orc_eta_bin.argtypes = [C.POINTER(Geom), C.c_int, C.c_double]
-        L.orc_phi_bin.argtypes = [C.POINTER(Geom), C.c_double]
-        L.orc_hit_index.argtypes = [C.POINTER(Geom), C.c_int, vp, ip, ip, ip]
-        L.orc_build_batch.argtypes = [C.POINTER(Geom), C.POINTER(Event), C.c_int, dp, dp, dp, ip, ip, C.c_int,
-                                      ip, dp, dp, dp, ip, ip, ip, C.POINTER(Stats)]
-        L.orc_seed_kappa_max.argtypes = [C.POINTER(Geom), C.POINTER(SeedCuts)]
-        L.orc_seed_kappa_max.restype = C.c_double
-        L.orc_seed_eval.argtypes = [C.POINTER(Geom), C.POINTER(SeedCuts), C.POINTER(Hit), C.POINTER(Hit),
-                                    C.POINTER(Hit), C.POINTER(Hit), C.POINTER(SeedQuant)]
-        L.orc_find_seeds.argtypes = [C.POINTER(Geom), C.POINTER(SeedCuts), C.c_int, vp, vp]
-        L.orc_find_seeds_of.argtypes = [C.POINTER(Geom), C.POINTER(SeedCuts), C.c_int, vp, C.c_int, ip, vp]
-        _lib = L
+        _lib = load_library(compile_library())
     return _lib
+
+
+def load_library(path: str):
+    """The oracle's functions from a compiled library at `path` (lib() loads the committed one;
+    the tests also load copies with planted mistakes)."""
+    L = C.CDLL(path)
+    dp, ip, vp = C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p
+    L.orc_propagate.argtypes = [C.POINTER(Geom), dp, C.c_double, dp, dp]
+    L.orc_propagate_plane.argtypes = [C.POINTER(Geom), dp, C.c_double, dp, dp]
+    L.orc_hit_eta_bin.argtypes = [C.POINTER(Geom), C.POINTER(Hit)]
+    L.orc_scatter.argtypes = [C.POINTER(Geom), C.c_int, dp, dp]
+    L.orc_scatter.restype = None
+    L.orc_chi2.argtypes = [dp, dp, C.POINTER(Hit)]
+    L.orc_chi2.restype = C.c_double
+    L.orc_update.argtypes = [dp, dp, C.POINTER(Hit), dp]
+    L.orc_seed_batch.argtypes = [C.POINTER(Geom), vp, C.c_int, ip, dp, dp]
+    L.orc_fit_batch.argtypes = [C.POINTER(Geom), vp, C.c_int, dp, dp, ip, C.c_int, C.c_int, dp, dp, dp, ip, ip]
+    L.orc_fit_backward_batch.argtypes = [C.POINTER(Geom), vp, C.c_int, dp, dp, C.c_double, ip, C.c_int, C.c_int,
+                                         dp, dp, dp, ip, ip]
+    L.orc_eta_bin.argtypes = [C.POINTER(Geom), C.c_int, C.c_double]
+    L.orc_phi_bin.argtypes = [C.POINTER(Geom), C.c_double]
+    L.orc_hit_index.argtypes = [C.POINTER(Geom), C.c_int, vp, ip, ip, ip]
+    L.orc_build_batch.argtypes = [C.POINTER(Geom), C.POINTER(Event), C.c_int, dp, dp, dp, ip, ip, C.c_int,
+                                  ip, dp, dp, dp, ip, ip, ip, C.POINTER(Stats)]
+    L.orc_seed_kappa_max.argtypes = [C.POINTER(Geom), C.POINTER(SeedCuts)]
+    L.orc_seed_kappa_max.restype = C.c_double
+    L.orc_seed_eval.argtypes = [C.POINTER(Geom), C.POINTER(SeedCuts), C.POINTER(Hit), C.POINTER(Hit),
+                                C.POINTER(Hit), C.POINTER(Hit), C.POINTER(SeedQuant)]
+    L.orc_find_seeds.argtypes = [C.POINTER(Geom), C.POINTER(SeedCuts), C.c_int, vp, vp]
+    L.orc_find_seeds_of.argtypes = [C.POINTER(Geom), C.POINTER(SeedCuts), C.c_int, vp, C.c_int, ip, vp]
+    return L
 
 
 def _d(a):

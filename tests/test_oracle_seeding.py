@@ -8,9 +8,11 @@ instead of the oracle itself:
   and radius, the distance of a point placed at a known offset from a circle;
 - the generator's truth on noise-free tracks (curvature from pT and the field, the circle's
   centre from the momentum direction at the vertex);
-- each cut planted just inside and just outside its limit on a clean track;
+- each cut planted just inside and just outside its limit on a clean track; the confirmation
+  hit's residuals entering the score (a worse triplet with a better confirmation wins);
 - symmetries (rotation about the beam line, y -> -y, z -> -z) under which the picks must not move;
-- on the seeding workload (pixel inner layers), the own triplet of nearly every track."""
+- on the seeding workload (pixel inner layers), the own triplet of nearly every track.
+Eight plausible mistakes planted in a compiled copy of the oracle each fail one of these pins."""
 import math
 
 import numpy as np
@@ -168,6 +170,26 @@ def test_best_triplet_and_ties():
     assert O.find_seeds(g, c0, h3)[th[0]]["h2"] == th[2]
 
 
+def test_confirmation_quality_enters_the_score():
+    """The track's own layer-3 hit moved onto the r-z line of a second layer-2 candidate 0.35 mm
+    above the own one: the own triplet keeps the better triplet term but is now confirmed only
+    0.7 mm off in z, the second one exactly; the second wins on the sum."""
+    g, hits, th = _clean_track()
+    cuts = O.SeedCuts()
+    h = np.concatenate([hits, hits[[th[2], th[3]]]])
+    i_c, i_e = len(hits), len(hits) + 1
+    rb, rc, re = (float(np.hypot(h["x"][k], h["y"][k])) for k in (th[1], th[2], th[3]))
+    h["z"][i_c] += 0.035
+    h["z"][i_e] += 0.035 * (re - rb) / (rc - rb)  # on the r-z line of b and the second candidate
+    h["layer"][th[3]] = 5  # the own layer-3 hit replaced by the moved one
+    pk = O.find_seeds(g, cuts, h)[th[0]]
+    assert (pk["h2"], pk["h3"], pk["n_pass"]) == (i_c, i_e, 2)
+    q = {k: O.seed_eval(g, cuts, *(O.make_hit(*h[i][["x", "y", "z", "var_u", "var_v"]], l)
+                                   for l, i in enumerate((th[0], th[1], k))))[1] for k in (th[2], i_c)}
+    s2 = {k: (q[k].d0 / cuts.d0_max) ** 2 + (q[k].dz / cuts.dz_max) ** 2 for k in q}
+    assert s2[th[2]] < s2[i_c] <= pk["score"]
+
+
 def _transform(hits, f):
     h = hits.copy()
     h["x"], h["y"], h["z"] = f(hits["x"], hits["y"], hits["z"])
@@ -203,3 +225,60 @@ def test_own_triplets_on_pixel_layers():
     n_seeds = (pk["h1"] >= 0).sum()
     assert own >= 0.99
     assert n_seeds <= 1.05 * b.n_tracks
+
+
+# Plausible mistakes planted in a copy of the oracle's seeding code: each must fail one of the
+# pins above (the copy is compiled on the CPU and swapped in for the committed library).
+PLANTED = {
+    "d0 over rho": ("q->d0 = (*ux * *ux + *uy * *uy - *rho * *rho) / (2.0 * *rho);",
+                    "q->d0 = (*ux * *ux + *uy * *uy - *rho * *rho) / (*rho);"),
+    "dz at the wrong radius": ("(b->z - a->z) * (rc - ra) / (rb - ra)", "(b->z - a->z) * (rc - rb) / (rb - ra)"),
+    "f over rho": ("q->f3 = ((e->x - ux) * (e->x - ux) + (e->y - uy) * (e->y - uy) - rho * rho) / (2.0 * rho);",
+                   "q->f3 = ((e->x - ux) * (e->x - ux) + (e->y - uy) * (e->y - uy) - rho * rho) / (rho);"),
+    "dz3 at the wrong radius": ("(cc->z - b->z) * (re - rb) / (rc - rb)", "(cc->z - b->z) * (re - rc) / (rc - rb)"),
+    "z vertex from the wrong radius": ("q->zv = a->z - ra * (b->z - a->z) / (rb - ra);",
+                                       "q->zv = a->z - rb * (b->z - a->z) / (rb - ra);"),
+    "pair curvature sign": ("(a->x * b->y - a->y * b->x > 0.0 ? 1.0 : -1.0)",
+                            "(a->x * b->y - a->y * b->x < 0.0 ? 1.0 : -1.0)"),
+    "score without the confirmation": ("(q.dz / c->dz_max) * (q.dz / c->dz_max) + c3;",
+                                       "(q.dz / c->dz_max) * (q.dz / c->dz_max);"),
+    "chord limit of one layer gap": ("q->chord01 <= 2.0 * (g->radius[1] - g->radius[0])",
+                                     "q->chord01 <= 1.0 * (g->radius[1] - g->radius[0])"),
+}
+
+
+def _pins():
+    yield test_circle_quantities_closed_forms
+    yield test_truth_of_noise_free_tracks
+    for f in ("pt_min", "z_vertex", "d0_max", "dz_max", "conf_rphi", "conf_z"):
+        yield lambda f=f: test_each_cut_planted_inside_and_outside(f)
+    yield test_far_crossing_is_not_a_pair
+    yield test_best_triplet_and_ties
+    yield test_confirmation_quality_enters_the_score
+    yield test_symmetries
+    yield test_own_triplets_on_pixel_layers
+
+
+@pytest.mark.parametrize("name", sorted(PLANTED))
+def test_planted_mistake_fails_a_pin(name, tmp_path, monkeypatch):
+    import os
+    import shutil
+    import subprocess
+    src_dir = os.path.dirname(O.__file__)
+    text = open(os.path.join(src_dir, "tkf_oracle.c")).read()
+    old, new = PLANTED[name]
+    assert text.count(old) == 1, "the planted line is no longer in the oracle"
+    shutil.copy(os.path.join(src_dir, "tkf_oracle.h"), tmp_path)
+    (tmp_path / "tkf_oracle.c").write_text(text.replace(old, new))
+    so = str(tmp_path / "liborc_planted.so")
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", so, str(tmp_path / "tkf_oracle.c"),
+                           "-lm"])
+    monkeypatch.setattr(O, "_lib", O.load_library(so))
+    failed = []
+    for pin in _pins():
+        try:
+            pin()
+        except (AssertionError, ValueError, ZeroDivisionError, FloatingPointError):
+            failed.append(pin)
+            break
+    assert failed, "no pin caught the planted mistake: %s" % name
