@@ -98,9 +98,11 @@ _lib = None
 
 
 def lib():
+    """The committed oracle, compiled on first use; ORC_LIBRARY names another compiled copy
+    instead (the planted-mistake tests run the pins against copies with a mistake)."""
     global _lib
     if _lib is None:
-        _lib = load_library(compile_library())
+        _lib = load_library(os.environ.get("ORC_LIBRARY") or compile_library())
     return _lib
 
 
