@@ -227,6 +227,27 @@ def test_own_triplets_on_pixel_layers():
     assert n_seeds <= 1.05 * b.n_tracks
 
 
+def test_cuts_keep_true_triplets():
+    """The default cuts sit above the true triplets' distributions on the seeding detector (with
+    smearing and scattering): at least 99.5 % of 3 000 tracks pass every cut with their own
+    hits, and each quantity's 99th percentile stays inside its cut."""
+    b = generate(EventSpec(seed=75, n_tracks=3000, noise_frac=0.0), PIX)
+    g = O.make_geom(PIX)
+    cuts = O.SeedCuts()
+    hits = O.hits_of(b)
+    th = b.trk_hits
+    kmax = O.seed_kappa_max(g, cuts)
+    ok, ratios = [], []
+    for t in range(b.n_tracks):
+        passed, q = O.seed_eval(g, cuts, *(O.make_hit(*hits[th[t, l]][["x", "y", "z", "var_u", "var_v"]], l)
+                                           for l in range(4)))
+        ok.append(passed)
+        ratios.append([abs(q.kappa01) / kmax, abs(q.zv) / cuts.z_vertex, q.kappa / kmax, abs(q.d0) / cuts.d0_max,
+                       abs(q.dz) / cuts.dz_max, abs(q.f3) / cuts.conf_rphi, abs(q.dz3) / cuts.conf_z])
+    assert np.mean(ok) >= 0.995
+    assert np.all(np.percentile(np.array(ratios), 99, axis=0) < 1.0)
+
+
 # Plausible mistakes planted in a copy of the oracle's seeding code: each must fail one of the
 # pins above (the copy is compiled on the CPU and swapped in for the committed library).
 PLANTED = {
